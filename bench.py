@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the E-join tensor-join hot path on one GB300 (or N replicas).
+
+One step = one full pass of the path over one batch of synthetic input:
+selection + normalisation of R and S, the blocked similarity contraction
+fused with the threshold and compaction, the exact re-score, and the pair
+count read-back (one ejoin_threshold call through the C ABI).
+
+Default workload (the metric's configuration): R = 1,000,000 and S = 100,000
+rows, d = 300, clustered unit vectors (1000 centres, ~0.3 rad spread), the
+relational predicate attr < 100 on R (10 % selectivity) pushed into the path,
+eps = 0.85, BF16 contraction with FP32/FP64 re-score of the guard band.
+
+Prints ONE JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E-join pair comparisons/sec at exact-set match vs FP64; % of tensor peak"
+UNIT = "pairs/s"
+CONTRACT_SOURCES = ["sim_tc.cu", "sim_simt.cu", "ejoin_internal.cuh"]
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            m = json.load(f)
+        return {"hbm_gbs": m["hbm_gbs"], "bf16_tflops": m["bf16_tflops"],
+                "bf16_tflops_sustained": m.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def contract_source_sha():
+    h = hashlib.sha256()
+    for f in CONTRACT_SOURCES:
+        with open(os.path.join(ROOT, "paper_2312_01476_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if its source hash still matches."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        t = json.load(f)
+    e = t.get(kernel_key)
+    if not e or e.get("source_sha") != contract_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ejoin_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx = max(mx, float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_workload(args, seed_offset=0):
+    import ejoin_inputs as inputs
+    if args.workload == "c2":
+        w = inputs.c2_clustered_selection(threads=os.cpu_count() or 8)
+    elif args.workload == "c2-small":
+        w = inputs.c2_clustered_selection(nR=100_000, nS=20_000, threads=os.cpu_count() or 8)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    return w
+
+
+def cpu_oracle_sample(w, target_s: float, threads: int):
+    """Time the FP64 oracle on selected R rows x all S rows, about target_s seconds of work."""
+    import oracle
+    sel = np.nonzero(w.attrR < w.cR)[0] if w.attrR is not None else np.arange(w.R.shape[0])
+    selR = oracle.Selection(w.attrR, w.opR, w.cR) if w.attrR is not None else None
+    n_s = w.S.shape[0]
+    probe = sel[:8]
+    t = time.perf_counter()
+    oracle.join(w.R, w.S, w.eps, selR, rows=probe, threads=threads)
+    dt = max(time.perf_counter() - t, 1e-3)
+    k = int(min(len(sel), max(8, target_s / dt * len(probe))))
+    rows = sel[:k]
+    t = time.perf_counter()
+    oracle.join(w.R, w.S, w.eps, selR, rows=rows, threads=threads)
+    dt = time.perf_counter() - t
+    return {"value": k * n_s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{k} selected R rows x all {n_s} S rows (FP64, extrapolated pairs/s)",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = make_workload(args)
+    threads = os.cpu_count() or 1
+    n_sel_r = int((w.attrR < w.cR).sum()) if w.attrR is not None else w.R.shape[0]
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_oracle_sample(w, args.ref_step_s, threads)
+        if s >= args.warmup:
+            vals.append(r)
+    v = statistics.median([r["value"] for r in vals])
+    ms = n_sel_r * w.S.shape[0] / v * 1e3
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": w.name, "pairs_per_step": n_sel_r * w.S.shape[0], "d": int(w.R.shape[1])},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def sample_parity(w, res_i, res_j, res_s, n_rows=48):
+    """Compare the GPU pairs of a few selected R rows with the FP64 oracle (untimed)."""
+    import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity_util import compare
+    sel = np.nonzero(w.attrR < w.cR)[0] if w.attrR is not None else np.arange(w.R.shape[0])
+    rng = np.random.default_rng(7)
+    rows = np.sort(rng.choice(sel, size=min(n_rows, len(sel)), replace=False))
+    selR = oracle.Selection(w.attrR, w.opR, w.cR) if w.attrR is not None else None
+    oi, oj, os_ = oracle.join(w.R, w.S, w.eps, selR, rows=rows)
+    st = compare(w.R, w.S, w.eps, res_i, res_j, res_s, oi, oj, os_, rows=rows)
+    st["rows"] = int(len(rows))
+    st["oracle_pairs"] = int(len(oi))
+    return st
+
+
+def run_ejoin(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2312_01476_gb300 as pkg
+
+    w = make_workload(args)
+    d = int(w.R.shape[1])
+    R = torch.from_numpy(w.R).cuda()
+    S = torch.from_numpy(w.S).cuda()
+    attr = torch.from_numpy(w.attrR).cuda() if w.attrR is not None else None
+    selR = pkg.Sel(attr, w.opR, w.cR) if attr is not None else None
+    ctx = pkg.Ctx(device=local, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    for _ in range(args.warmup):
+        res = pkg.ejoin_threshold(ctx, R, S, w.eps, selR)
+    torch.cuda.synchronize()
+    st0 = pkg.ejoin_last_stats(ctx)
+    pairs_per_step = int(st0["n_sel_r"]) * int(st0["n_sel_s"])
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    contract_ms, launches, stage = [], 0, {"normalize": [], "rescore": []}
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # L2 flush between steps (not timed)
+        ev[k][0].record()
+        res = pkg.ejoin_threshold(ctx, R, S, w.eps, selR)
+        ev[k][1].record()
+        st = pkg.ejoin_last_stats(ctx)
+        contract_ms.append(st["ms_contract"])
+        stage["normalize"].append(st["ms_normalize"])
+        stage["rescore"].append(st["ms_rescore"])
+        launches += int(st["launches"])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    n_pairs = int(res.count)
+    value = world * pairs_per_step / (ms * 1e-3)
+
+    pk = peaks()
+    c_ms = statistics.mean(contract_ms)
+    flop = 2.0 * d * pairs_per_step
+    if args.prec == "bf16":
+        peak, peak_note = pk["bf16_tflops"], f"bf16 dense burst, {pk['source']}"
+    elif args.prec == "fp8":
+        peak, peak_note = 2 * pk["bf16_tflops"], f"2 x bf16 burst ({pk['source']}, nominal fp8/bf16 ratio)"
+    elif args.prec == "tf32":
+        peak, peak_note = 0.5 * pk["bf16_tflops"], f"0.5 x bf16 burst ({pk['source']}, nominal tf32/bf16 ratio)"
+    else:
+        peak, peak_note = None, "fp32 SIMT"
+    kernel_key = f"sim_tc_{args.prec}_{args.workload}" if args.prec != "f32" else f"sim_simt_{args.workload}"
+    achieved = flop / (c_ms * 1e-3) / 1e12
+    roofline = {"kernel": kernel_key, "bound": "tensor", "achieved": round(achieved, 2),
+                "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4) if peak else None,
+                "peak_note": peak_note, "traffic": recorded_traffic(kernel_key),
+                "flop_per_launch": flop, "ms_per_launch": round(c_ms, 4)}
+
+    # parity on sampled rows (untimed)
+    parity = None
+    if not args.no_parity and rank == 0:
+        try:
+            parity = sample_parity(w, res.i.cpu().numpy().view(np.uint32), res.j.cpu().numpy().view(np.uint32),
+                                   res.sim.cpu().numpy())
+            parity["match"] = True
+        except AssertionError as e:
+            parity = {"match": False, "error": str(e)[:300]}
+
+    # end to end through the host-memory entry point (pinned buffers, copies timed)
+    e2e = None
+    if not args.no_e2e:
+        Rp = torch.from_numpy(w.R).pin_memory()
+        Sp = torch.from_numpy(w.S).pin_memory()
+        Ap = torch.from_numpy(w.attrR).pin_memory() if w.attrR is not None else None
+        cap = n_pairs + (1 << 20)
+        out = torch.empty(cap * 12, dtype=torch.uint8).pin_memory().numpy().view(pkg.PAIR_DTYPE)
+        hsel = pkg.Sel(Ap.numpy(), w.opR, w.cR) if Ap is not None else None
+        for _ in range(2):
+            pkg.ejoin_threshold_host(ctx, Rp.numpy(), Sp.numpy(), w.eps, hsel, out=out)
+        e_ms, h2d_ms = [], []
+        for k in range(max(3, args.steps // 2)):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            pr, cnt = pkg.ejoin_threshold_host(ctx, Rp.numpy(), Sp.numpy(), w.eps, hsel, out=out)
+            b.record()
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+            h2d_ms.append(pkg.ejoin_last_stats(ctx)["ms_h2d"])
+        em = statistics.mean(e_ms)
+        h2d = w.R.nbytes + w.S.nbytes + (w.attrR.nbytes if w.attrR is not None else 0)
+        e2e = {"value": world * pairs_per_step / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(cnt * 12 + 8), "ms_per_step": round(em, 3),
+               "ms_h2d": round(statistics.mean(h2d_ms), 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample(w, args.cpu_s, os.cpu_count() or 1)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+               "config": {"workload": w.name, "pairs_per_step": pairs_per_step, "d": d,
+                          "n_sel_r": int(st0["n_sel_r"]), "n_sel_s": int(st0["n_sel_s"]),
+                          "result_pairs": n_pairs, "candidates": int(st0["candidates"]),
+                          "fp64_rescored": int(st0["fp64_rescored"]), "band": st0["band"],
+                          "l2": "256 MB buffer written between timed steps (untimed)",
+                          "parallelism": f"{world} independent replica(s)"},
+               "stages_ms": {"normalize": round(statistics.mean(stage["normalize"]), 4),
+                             "contract": round(c_ms, 4), "rescore": round(statistics.mean(stage["rescore"]), 4)},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clocks, "parity": parity}
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ejoin", choices=["ejoin", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp8", "tf32", "f32"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
+    ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ejoin":
+        log("warning: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ejoin(args)
+
+
+if __name__ == "__main__":
+    main()

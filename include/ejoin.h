@@ -1,0 +1,198 @@
+/*
+ * ejoin.h -- C ABI of the GB300 (sm_103a) tensor-join hot path of the
+ * context-enhanced E-join ("Optimizing Context-Enhanced Relational Joins",
+ * arXiv 2312.01476).
+ *
+ * The operator (Sec. III-C, Eq. (E-theta-Join)):
+ *
+ *     R join_{E,mu,theta} S  =  sigma_theta( E_mu(R) x E_mu(S) )
+ *
+ * with theta = selR(r) and selS(s) and cos(r, s) >= eps, where cos is
+ * Sec. III-A, Eq. (Cosine Similarity).  The embeddings E_mu(R), E_mu(S) are
+ * given as FP32 row-major matrices (the embedding model itself is out of
+ * scope).  Evaluation follows the tensor formulation of Sec. IV-C: the rows
+ * are normalised once (cosine equals the dot product of normalised rows),
+ * the similarity matrix D = R S^T is formed block by block (Eq. Block Matrix
+ * Dot Product Decomposition; Sec. V-B: D is never materialised, only one
+ * tile at a time lives on chip), and the pairs passing the threshold are
+ * mapped back to tuple ids through the tile offsets (Sec. IV-C, late
+ * materialisation).  Relational predicates are pushed below the vector work
+ * (Eq. (E-Selection); Sec. VI-E pre-filter).
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an ejoin_status; nothing aborts and no C++
+ *     exception crosses the ABI.  ejoin_strerror() gives the text.
+ *   - Unless stated otherwise, pointers named d_* or documented as "device"
+ *     are CUDA device pointers owned by the caller; all work is enqueued on
+ *     the context's stream in order.
+ *   - Pair ids are 0-based row numbers of the ORIGINAL relations (before any
+ *     selection).  A self-join (R and S describe the same matrix and the same
+ *     selection) yields every ordered pair, including (i, i).
+ *   - Result: every pair whose FP64 similarity differs from eps by at least
+ *     1e-5 is in the result iff sim >= eps; each emitted similarity is within
+ *     1e-5 of the FP64 value (it is re-scored in FP32 from the input rows,
+ *     in FP64 when it lies within fp64_band of eps).  Order is unspecified.
+ */
+#ifndef EJOIN_H
+#define EJOIN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ejoin_status {
+    EJOIN_OK = 0,
+    EJOIN_EINVAL = 1,       /* bad argument (null pointer, d mismatch, d out of range, ...) */
+    EJOIN_ENOMEM = 2,       /* device allocation failed */
+    EJOIN_EOVERFLOW = 3,    /* more pairs than the caller's capacity; count holds the total */
+    EJOIN_ENONFINITE = 4,   /* an input row holds NaN or Inf */
+    EJOIN_ECUDA = 5,        /* a CUDA runtime/driver call failed (no device, launch error, ...) */
+    EJOIN_ETIMEOUT = 6,     /* a bounded device-side wait gave up; results are invalid */
+    EJOIN_EUNSUPPORTED = 7  /* precision or shape not supported on this device */
+} ejoin_status;
+
+/* Arithmetic of the bulk similarity contraction.  Every precision is followed
+ * by an exact re-score of the candidates within a guard band of eps, so all
+ * of them return the same result set (see the conventions above). */
+typedef enum ejoin_prec {
+    EJOIN_F32 = 0,      /* FP32 CUDA-core contraction (the plain FP32 path) */
+    EJOIN_BF16 = 1,     /* tcgen05 kind::f16 on BF16 rows, FP32 accumulation in TMEM */
+    EJOIN_FP8_E4M3 = 2, /* tcgen05 kind::f8f6f4 on e4m3 rows with per-row FP32 scales */
+    EJOIN_TF32 = 3      /* tcgen05 kind::tf32 on FP32 rows, FP32 accumulation in TMEM */
+} ejoin_prec;
+
+/* ejoin_config.flags */
+#define EJOIN_FLAG_COUNT_ONLY 0x1u /* count the pairs, store none (a "count pass") */
+#define EJOIN_FLAG_TIMING     0x2u /* record CUDA events around each stage (ejoin_last_stats) */
+
+typedef struct ejoin_config {
+    int32_t device;          /* CUDA device ordinal */
+    void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
+    int32_t prec;            /* ejoin_prec */
+    float band;              /* guard band around eps for re-scoring; < 0: the rigorous default
+                                for prec and d (see DESIGN notes of each precision) */
+    float fp64_band;         /* candidates with |sim32 - eps| < fp64_band are re-scored in FP64;
+                                < 0: default 2e-5 */
+    uint64_t capacity_hint;  /* initial candidate-buffer size in pairs (0: 1 << 20); grows on demand */
+    uint32_t flags;          /* EJOIN_FLAG_* */
+    uint64_t timeout_cycles; /* bound on every device-side spin-wait, in SM clock cycles
+                                (0: 2^31, about one second) */
+} ejoin_config;
+
+/* A relation: n rows of d FP32 values, row r at x + r * ld (ld >= d).
+ * Device memory for ejoin_threshold/ejoin_normalize; host memory for
+ * ejoin_threshold_host.  1 <= d <= 4096 and n < 2^31 - 256. */
+typedef struct ejoin_rel {
+    const float *x;
+    int64_t n;
+    int32_t d;
+    int64_t ld;
+} ejoin_rel;
+
+/* Relational selection pushed below the join (Sec. III-C, Eq. (Selection) and
+ * Eq. (E-Selection)): keep row r iff attr[r] <op> c, and, when bits is not
+ * NULL, bit (r % 32) of bits[r / 32] is set.  attr may be NULL (bits only).
+ * A NULL ejoin_sel* keeps every row.  Arrays have n entries (bits: ceil(n/32)). */
+typedef enum ejoin_op { EJOIN_LT = 0, EJOIN_LE = 1, EJOIN_GT = 2, EJOIN_GE = 3, EJOIN_EQ = 4, EJOIN_NE = 5 } ejoin_op;
+typedef struct ejoin_sel {
+    const int32_t *attr;
+    int32_t op;
+    int32_t c;
+    const uint32_t *bits;
+} ejoin_sel;
+
+/* One result tuple: the pair of original row ids and its similarity (Sec. IV-C:
+ * "tuples of offsets"). */
+typedef struct ejoin_pair {
+    uint32_t i;
+    uint32_t j;
+    float sim;
+} ejoin_pair;
+
+/* Result buffer.  If d_pairs == NULL on entry the library allocates it (sized to
+ * the candidate count) and ejoin_pairs_free releases it; otherwise the caller's
+ * buffer of `capacity` records is used.  d_count (device, optional) receives the
+ * exact total; count (host) receives it too when the call returns. */
+typedef struct ejoin_pairs {
+    ejoin_pair *d_pairs;
+    uint64_t capacity;
+    uint64_t *d_count;
+    uint64_t count;
+} ejoin_pairs;
+
+typedef struct ejoin_ctx ejoin_ctx;
+
+/* Per-call statistics of the last ejoin_threshold / ejoin_threshold_host call. */
+typedef struct ejoin_stats {
+    uint64_t n_sel_r, n_sel_s;  /* rows kept by the selections */
+    uint64_t candidates;        /* pairs at or above eps - band in the bulk precision */
+    uint64_t fp64_rescored;     /* candidates re-scored in FP64 */
+    uint64_t pairs;             /* result pairs */
+    uint64_t launches;          /* kernels launched by the call */
+    float band;                 /* guard band used */
+    float ms_select, ms_normalize, ms_contract, ms_rescore, ms_total; /* FLAG_TIMING only */
+    float ms_h2d, ms_d2h;       /* ejoin_threshold_host only, FLAG_TIMING only */
+    int32_t contract_retries;   /* candidate-buffer regrowths */
+} ejoin_stats;
+
+/* Create a context on cfg->device (made current for the call).  cfg may be
+ * NULL (device 0, default stream, BF16).  *out receives the context. */
+ejoin_status ejoin_create(ejoin_ctx **out, const ejoin_config *cfg);
+
+/* Release the context, its workspace and events.  NULL is ignored. */
+void ejoin_destroy(ejoin_ctx *ctx);
+
+/* Row normalisation with selection pushdown (Sec. IV-C: cosine is the dot
+ * product of normalised rows; Eq. (E-Selection)).  For each kept row r, in
+ * ascending order c = 0, 1, ..., writes y = x_r / ||x_r|| (0 for a zero row)
+ * in `prec`'s storage format to d_out + c * ld_out (elements; ld_out >= the
+ * padded dimension ejoin_padded_dim(prec, d), padding zero-filled),
+ * 1/||x_r|| to d_inv_norm[c] (optional), the e4m3 scale to d_scale[c]
+ * (required for EJOIN_FP8_E4M3, else ignored), r to d_ids[c] (optional), and
+ * the number of kept rows to *d_n_sel (device int64).  Non-finite input sets
+ * the context's error word; the next synchronising call reports ENONFINITE.
+ * Storage: F32 and TF32 float, BF16 __nv_bfloat16, FP8 __nv_fp8_e4m3. */
+ejoin_status ejoin_normalize(ejoin_ctx *ctx, ejoin_rel in, const ejoin_sel *sel, int32_t prec,
+                             void *d_out, int64_t ld_out, float *d_inv_norm, float *d_scale,
+                             uint32_t *d_ids, int64_t *d_n_sel);
+
+/* Padded row length (elements) used for `prec` at dimension d. */
+int64_t ejoin_padded_dim(int32_t prec, int32_t d);
+
+/* The threshold E-join of R and S on the device (Sec. III-C, Eq. (E-theta-Join);
+ * tensor formulation Sec. IV-C; tiled, memory-bounded evaluation Sec. V-B).
+ * R.x, S.x, the selections' arrays and out->d_pairs / out->d_count are device
+ * pointers.  Synchronises the context stream before returning (the pair count
+ * is read back).  EJOIN_EOVERFLOW: out->count holds the exact total and the
+ * first out->capacity records are valid; retry with a larger buffer. */
+ejoin_status ejoin_threshold(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, float eps,
+                             const ejoin_sel *selR, const ejoin_sel *selS, ejoin_pairs *out);
+
+/* Same operator with HOST inputs and a HOST result buffer: R.x, S.x, the
+ * selections' arrays and h_pairs are host pointers (pinned memory gives full
+ * copy bandwidth).  The inputs are copied to the device, joined, and the
+ * pairs copied back; *count receives the total (EOVERFLOW as above). */
+ejoin_status ejoin_threshold_host(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, float eps,
+                                  const ejoin_sel *selR, const ejoin_sel *selS,
+                                  ejoin_pair *h_pairs, uint64_t capacity, uint64_t *count);
+
+/* Release a result buffer that the library allocated. */
+ejoin_status ejoin_pairs_free(ejoin_ctx *ctx, ejoin_pairs *pairs);
+
+/* Statistics of the last call on ctx. */
+ejoin_status ejoin_last_stats(const ejoin_ctx *ctx, ejoin_stats *out);
+
+/* Static text for a status code. */
+const char *ejoin_strerror(ejoin_status s);
+
+/* Library version string. */
+const char *ejoin_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EJOIN_H */

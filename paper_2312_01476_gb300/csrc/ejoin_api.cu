@@ -1,0 +1,652 @@
+// C ABI of libejoin: context, workspace, argument validation, dispatch of the
+// select -> normalise -> contract -> re-score pipeline, tensor-map encoding,
+// and error reporting.  All device work goes through the kernels of this
+// library; there is no host fallback.
+//
+// The pipeline evaluates the E-theta-join of Sec. III-C (Eq. (E-theta-Join))
+// with the relational predicates pushed below the vector work (Eq.
+// (E-Selection), Sec. VI-E pre-filter), in the tensor formulation of Sec.
+// IV-C, tile by tile (Sec. V-B), mapping passing entries back to tuple ids
+// through the partition offsets (Sec. IV-C).
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ejoin_internal.cuh"
+
+using namespace ej;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+cudaError_t ensure(Buf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (b.bytes >= bytes) return cudaSuccess;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e == cudaSuccess) {
+        b.bytes = bytes;
+        // padding rows of the operand buffers are read by the contraction
+        // (and masked); give them defined contents once
+        e = cudaMemset(b.p, 0, bytes);
+    }
+    return e;
+}
+
+void release(Buf &b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+struct Side {
+    Buf norm, inv, scale, ids, blk_counts, blk_offsets;
+};
+
+ejoin_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return EJOIN_OK;
+    if (e == cudaErrorMemoryAllocation) return EJOIN_ENOMEM;
+    return EJOIN_ECUDA;
+}
+
+int fmt_of(int prec)
+{
+    switch (prec) {
+    case EJOIN_BF16: return FMT_BF16;
+    case EJOIN_FP8_E4M3: return FMT_FP8;
+    default: return FMT_F32;
+    }
+}
+
+size_t fmt_bytes(int fmt) { return fmt == FMT_BF16 ? 2 : (fmt == FMT_FP8 ? 1 : 4); }
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D K-major operand [rows x kp] with a (128-byte x box_rows) box and 128-byte swizzle.
+bool make_tmap(CUtensorMap *m, const void *base, int fmt, int64_t kp, int64_t rows, uint32_t box_rows)
+{
+    auto enc = encode_fn();
+    if (!enc) return false;
+    CUtensorMapDataType dt = fmt == FMT_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                             : fmt == FMT_FP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const size_t eb = fmt_bytes(fmt);
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(kp * eb)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / eb), box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+constexpr int N_EV = 8;
+
+}  // namespace
+
+struct ejoin_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int prec = EJOIN_BF16;
+    float band_cfg = -1.f;
+    float fp64_band = 2e-5f;
+    uint64_t cap_hint = 1u << 20;
+    uint32_t flags = 0;
+    uint64_t timeout = 1ull << 31;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    Side side[2];
+    Buf misc;
+    Buf cand;
+    uint64_t cand_cap = 0;
+    Buf host_in[6];
+    Buf host_pairs;
+    cudaEvent_t ev[N_EV] = {};
+    bool events = false;
+    ejoin_stats stats{};
+};
+
+extern "C" {
+
+const char *ejoin_version(void) { return "ejoin-gb300 0.1 (sm_103a)"; }
+
+const char *ejoin_strerror(ejoin_status s)
+{
+    switch (s) {
+    case EJOIN_OK: return "ok";
+    case EJOIN_EINVAL: return "invalid argument";
+    case EJOIN_ENOMEM: return "device allocation failed";
+    case EJOIN_EOVERFLOW: return "result exceeds the pair buffer capacity";
+    case EJOIN_ENONFINITE: return "input holds NaN or Inf";
+    case EJOIN_ECUDA: return "CUDA error";
+    case EJOIN_ETIMEOUT: return "device-side wait timed out";
+    case EJOIN_EUNSUPPORTED: return "unsupported precision or shape on this device";
+    }
+    return "unknown status";
+}
+
+int64_t ejoin_padded_dim(int32_t prec, int32_t d)
+{
+    if (d <= 0) return 0;
+    switch (prec) {
+    case EJOIN_BF16: return round_up(d, 64);
+    case EJOIN_FP8_E4M3: return round_up(d, 128);
+    case EJOIN_TF32: return round_up(d, 32);
+    default: return round_up(d, 32);
+    }
+}
+
+ejoin_status ejoin_create(ejoin_ctx **out, const ejoin_config *cfg)
+{
+    if (!out) return EJOIN_EINVAL;
+    *out = nullptr;
+    ejoin_ctx *c = new (std::nothrow) ejoin_ctx();
+    if (!c) return EJOIN_ENOMEM;
+    if (cfg) {
+        c->device = cfg->device;
+        c->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
+        c->prec = cfg->prec;
+        c->band_cfg = cfg->band;
+        c->fp64_band = cfg->fp64_band < 0.f ? 2e-5f : cfg->fp64_band;
+        c->cap_hint = cfg->capacity_hint ? cfg->capacity_hint : (1u << 20);
+        c->flags = cfg->flags;
+        c->timeout = cfg->timeout_cycles ? cfg->timeout_cycles : (1ull << 31);
+    }
+    if (c->prec < EJOIN_F32 || c->prec > EJOIN_TF32) {
+        delete c;
+        return EJOIN_EINVAL;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || c->device < 0 || c->device >= ndev) {
+        delete c;
+        return e != cudaSuccess ? EJOIN_ECUDA : EJOIN_EINVAL;
+    }
+    DeviceGuard g(c->device);
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return EJOIN_ECUDA;
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    if (c->prec != EJOIN_F32 && !(prop.major == 10 && prop.minor == 3)) {
+        // the tensor-core kernels are built for sm_103a only
+        delete c;
+        return EJOIN_EUNSUPPORTED;
+    }
+    for (int i = 0; i < N_EV; ++i) {
+        if (cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(c->ev[k]);
+            delete c;
+            return EJOIN_ECUDA;
+        }
+    }
+    c->events = true;
+    e = ensure(c->misc, sizeof(DevMisc));
+    if (e != cudaSuccess) {
+        ejoin_destroy(c);
+        return from_cuda(e);
+    }
+    *out = c;
+    return EJOIN_OK;
+}
+
+void ejoin_destroy(ejoin_ctx *c)
+{
+    if (!c) return;
+    {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        for (auto &s : c->side) {
+            release(s.norm);
+            release(s.inv);
+            release(s.scale);
+            release(s.ids);
+            release(s.blk_counts);
+            release(s.blk_offsets);
+        }
+        release(c->misc);
+        release(c->cand);
+        for (auto &b : c->host_in) release(b);
+        release(c->host_pairs);
+        if (c->events)
+            for (auto &ev : c->ev) cudaEventDestroy(ev);
+    }
+    delete c;
+}
+
+ejoin_status ejoin_last_stats(const ejoin_ctx *c, ejoin_stats *out)
+{
+    if (!c || !out) return EJOIN_EINVAL;
+    *out = c->stats;
+    return EJOIN_OK;
+}
+
+ejoin_status ejoin_pairs_free(ejoin_ctx *c, ejoin_pairs *p)
+{
+    if (!c || !p) return EJOIN_EINVAL;
+    if (p->d_pairs) {
+        DeviceGuard g(c->device);
+        cudaStreamSynchronize(c->stream);
+        cudaFree(p->d_pairs);
+    }
+    p->d_pairs = nullptr;
+    p->capacity = 0;
+    return EJOIN_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+bool rel_ok(const ejoin_rel &r)
+{
+    if (r.n < 0 || r.n > (int64_t)0x7FFFFEFF) return false;
+    if (r.d < 1 || r.d > 4096) return false;
+    if (r.ld < r.d) return false;
+    if (r.n > 0 && !r.x) return false;
+    return true;
+}
+
+bool sel_ok(const ejoin_sel *s)
+{
+    if (!s) return true;
+    if (!s->attr && !s->bits) return false;
+    if (s->attr && (s->op < EJOIN_LT || s->op > EJOIN_NE)) return false;
+    return true;
+}
+
+bool same_sel(const ejoin_sel *a, const ejoin_sel *b)
+{
+    if (!a || !b) return a == b;
+    return a->attr == b->attr && a->bits == b->bits && (a->attr == nullptr || (a->op == b->op && a->c == b->c));
+}
+
+float default_band(int prec, int64_t kp)
+{
+    const double g = (double)kp * std::ldexp(1.0, -24);  // FP32 accumulation over kp terms
+    const double small = 8.0 * std::ldexp(1.0, -24);     // FP32 normalisation of both rows
+    double b;
+    switch (prec) {
+    case EJOIN_BF16: {
+        const double u = std::ldexp(1.0, -8);
+        b = 2 * u + u * u + 2 * g + small;
+        break;
+    }
+    case EJOIN_TF32: {
+        const double u = std::ldexp(1.0, -10);  // conservative: truncation to 10 stored bits
+        b = 2 * u + u * u + 2 * g + small;
+        break;
+    }
+    case EJOIN_FP8_E4M3: {
+        const double u = std::ldexp(1.0, -4);
+        const double er = u + std::ldexp(1.0, -10) / 448.0 * std::sqrt((double)kp);
+        b = 2 * er + er * er + 2 * g + small;
+        break;
+    }
+    default: b = 2 * g + small; break;
+    }
+    return (float)(1.25 * b);
+}
+
+// Selection + normalisation of one relation into side buffers (or caller buffers).
+ejoin_status prepare_side(ejoin_ctx *c, int which, const ejoin_rel &r, const ejoin_sel *sel, int fmt, int64_t kp,
+                          void *out, int64_t ld_out, float *inv, float *scale, uint32_t *ids, long long *n_sel,
+                          unsigned *status, bool timing_split)
+{
+    Side &sd = c->side[which];
+    cudaError_t e;
+    if (sel) {
+        const int64_t nb = std::max<int64_t>(1, (r.n + SEL_ROWS_PER_BLOCK - 1) / SEL_ROWS_PER_BLOCK);
+        if ((e = ensure(sd.blk_counts, nb * 4)) != cudaSuccess) return from_cuda(e);
+        if ((e = ensure(sd.blk_offsets, nb * 4)) != cudaSuccess) return from_cuda(e);
+        SelArgs s{sel->attr, sel->op, sel->c, sel->bits};
+        uint32_t *bc = (uint32_t *)sd.blk_counts.p, *bo = (uint32_t *)sd.blk_offsets.p;
+        if ((e = launch_sel_count(s, r.n, bc, c->stream)) != cudaSuccess) return from_cuda(e);
+        if ((e = launch_sel_scan(bc, (r.n + SEL_ROWS_PER_BLOCK - 1) / SEL_ROWS_PER_BLOCK, bo, n_sel, c->stream)) !=
+            cudaSuccess)
+            return from_cuda(e);
+        if ((e = launch_sel_scatter(s, r.n, bo, ids, c->stream)) != cudaSuccess) return from_cuda(e);
+        c->stats.launches += r.n > 0 ? 3 : 1;
+    } else {
+        if ((e = launch_set_count(n_sel, (long long)r.n, c->stream)) != cudaSuccess) return from_cuda(e);
+        c->stats.launches += 1;
+    }
+    if (timing_split && (c->flags & EJOIN_FLAG_TIMING)) cudaEventRecord(c->ev[1 + which], c->stream);
+    if (r.n > 0) {
+        e = launch_normalize(fmt, r.x, r.ld, r.d, sel ? ids : nullptr, n_sel, r.n, out, ld_out, (int)kp, inv, scale,
+                             status, c->num_sms, c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        c->stats.launches += 1;
+    }
+    return EJOIN_OK;
+}
+
+float elapsed(cudaEvent_t a, cudaEvent_t b)
+{
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) return 0.f;
+    return ms;
+}
+
+// Device pipeline shared by ejoin_threshold and ejoin_threshold_host.
+ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, float eps, const ejoin_sel *selR,
+                           const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
+                           uint64_t *d_count_user, uint64_t *count_out)
+{
+    c->stats = ejoin_stats{};
+    if (!rel_ok(R) || !rel_ok(S) || R.d != S.d || !sel_ok(selR) || !sel_ok(selS)) return EJOIN_EINVAL;
+    if (std::isnan(eps)) return EJOIN_EINVAL;
+    const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
+    const bool count_only = (c->flags & EJOIN_FLAG_COUNT_ONLY) != 0;
+    const int prec = c->prec;
+    const int fmt = fmt_of(prec);
+    const int64_t kp = ejoin_padded_dim(prec, R.d);
+    const size_t eb = fmt_bytes(fmt);
+    const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld && same_sel(selR, selS);
+    const float band = c->band_cfg >= 0.f ? c->band_cfg : default_band(prec, kp);
+    c->stats.band = band;
+    cudaError_t e;
+
+    // workspace
+    const ejoin_rel *rels[2] = {&R, &S};
+    const ejoin_sel *sels[2] = {selR, selS};
+    for (int w = 0; w < (self ? 1 : 2); ++w) {
+        const int64_t rows = round_up(std::max<int64_t>(rels[w]->n, 1), 256);
+        Side &sd = c->side[w];
+        if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) != cudaSuccess) return from_cuda(e);
+        if ((e = ensure(sd.inv, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+        if (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+        if (sels[w] && (e = ensure(sd.ids, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+    }
+    if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
+    if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), c->stream)) != cudaSuccess) return from_cuda(e);
+
+    if (timing) cudaEventRecord(c->ev[0], c->stream);
+    Side &sa = c->side[0];
+    Side &sb = self ? c->side[0] : c->side[1];
+    ejoin_status st = prepare_side(c, 0, R, selR, fmt, kp, sa.norm.p, kp, (float *)sa.inv.p, (float *)sa.scale.p,
+                                   (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false);
+    if (st != EJOIN_OK) return st;
+    if (!self) {
+        st = prepare_side(c, 1, S, selS, fmt, kp, sb.norm.p, kp, (float *)sb.inv.p, (float *)sb.scale.p,
+                          (uint32_t *)sb.ids.p, &dm->n_sel[1], &dm->status, false);
+        if (st != EJOIN_OK) return st;
+    }
+    const long long *nA = &dm->n_sel[0];
+    const long long *nB = self ? &dm->n_sel[0] : &dm->n_sel[1];
+    if (timing) cudaEventRecord(c->ev[1], c->stream);
+
+    // bulk contraction -> candidates
+    const float thr = eps - band;
+    CUtensorMap tmA, tmB;
+    if (prec != EJOIN_F32) {
+        const int64_t rowsA = round_up(std::max<int64_t>(R.n, 1), 256);
+        const int64_t rowsB = round_up(std::max<int64_t>(S.n, 1), 256);
+        if (!make_tmap(&tmA, sa.norm.p, fmt, kp, rowsA, 128) || !make_tmap(&tmB, sb.norm.p, fmt, kp, rowsB, 256))
+            return EJOIN_ECUDA;
+    }
+    auto contract = [&]() -> ejoin_status {
+        cudaError_t ee;
+        if (prec == EJOIN_F32) {
+            ee = launch_sim_simt((const float *)sa.norm.p, (const float *)sb.norm.p, (int)kp, nA, nB, thr,
+                                 (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, 0, c->num_sms, c->stream);
+        } else {
+            const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
+            ee = launch_sim_tc(kind, &tmA, &tmB, (int)kp, nA, nB, thr, (const float *)sa.scale.p,
+                               (const float *)sb.scale.p, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count,
+                               &dm->status, c->timeout, 0, c->num_sms, c->stream);
+        }
+        c->stats.launches += 1;
+        return from_cuda(ee);
+    };
+    if ((st = contract()) != EJOIN_OK) return st;
+    if (timing) cudaEventRecord(c->ev[2], c->stream);
+
+    DevMisc hm;
+    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return from_cuda(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+    c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
+    c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
+    if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+    if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+    if (hm.status) return EJOIN_ECUDA;
+    while (hm.cand_count > c->cand_cap) {
+        // candidate buffer too small: grow and run the contraction again
+        c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+        if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+        if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+            return from_cuda(e);
+        if ((st = contract()) != EJOIN_OK) return st;
+        if (timing) cudaEventRecord(c->ev[2], c->stream);
+        if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return from_cuda(e);
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        c->stats.contract_retries++;
+    }
+    c->stats.candidates = hm.cand_count;
+
+    // result buffer
+    if (*pairs_io == nullptr && may_alloc && !count_only) {
+        const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
+        void *p = nullptr;
+        if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
+        *pairs_io = (ejoin_pair *)p;
+        *cap_io = cap;
+    }
+    if (*pairs_io == nullptr && !count_only) *cap_io = 0;
+
+    // exact re-score of the candidates
+    e = hm.cand_count == 0 ? cudaSuccess : launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
+                       selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
+                       (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
+                       count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0, c->num_sms,
+                       c->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    c->stats.launches += hm.cand_count ? 1 : 0;
+    if (timing) cudaEventRecord(c->ev[3], c->stream);
+    if (d_count_user) {
+        if ((e = cudaMemcpyAsync(d_count_user, &dm->pair_count, sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                 c->stream)) != cudaSuccess)
+            return from_cuda(e);
+    }
+    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+        return from_cuda(e);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+    c->stats.pairs = hm.pair_count;
+    c->stats.fp64_rescored = hm.band_count;
+    if (timing) {
+        c->stats.ms_normalize = elapsed(c->ev[0], c->ev[1]);
+        c->stats.ms_contract = elapsed(c->ev[1], c->ev[2]);
+        c->stats.ms_rescore = elapsed(c->ev[2], c->ev[3]);
+        c->stats.ms_total = elapsed(c->ev[0], c->ev[3]);
+    }
+    *count_out = hm.pair_count;
+    if (!count_only && hm.pair_count > *cap_io) return EJOIN_EOVERFLOW;
+    return EJOIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ejoin_status ejoin_threshold(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float eps, const ejoin_sel *selR,
+                             const ejoin_sel *selS, ejoin_pairs *out)
+{
+    if (!c || !out) return EJOIN_EINVAL;
+    DeviceGuard g(c->device);
+    uint64_t count = 0;
+    ejoin_pair *p = out->d_pairs;
+    uint64_t cap = out->capacity;
+    const bool alloc = p == nullptr;
+    ejoin_status st = run_threshold(c, R, S, eps, selR, selS, &p, &cap, alloc, out->d_count, &count);
+    if (alloc && p) {
+        out->d_pairs = p;
+        out->capacity = cap;
+    }
+    out->count = count;
+    return st;
+}
+
+ejoin_status ejoin_threshold_host(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float eps, const ejoin_sel *selR,
+                                  const ejoin_sel *selS, ejoin_pair *h_pairs, uint64_t capacity, uint64_t *count)
+{
+    if (!c || !count || (capacity && !h_pairs)) return EJOIN_EINVAL;
+    if (!rel_ok(R) || !rel_ok(S) || R.d != S.d || !sel_ok(selR) || !sel_ok(selS)) return EJOIN_EINVAL;
+    DeviceGuard g(c->device);
+    const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
+    cudaError_t e;
+    const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld && same_sel(selR, selS);
+    if (timing) cudaEventRecord(c->ev[4], c->stream);
+    // host -> device copies of the inputs (rows are copied densely: ld = d)
+    auto up_rel = [&](int slot, const ejoin_rel &r, ejoin_rel &dr) -> cudaError_t {
+        dr = r;
+        dr.ld = r.d;
+        if (r.n == 0) {
+            dr.x = nullptr;
+            return cudaSuccess;
+        }
+        cudaError_t ee = ensure(c->host_in[slot], (size_t)r.n * r.d * 4);
+        if (ee != cudaSuccess) return ee;
+        dr.x = (const float *)c->host_in[slot].p;
+        if (r.ld == r.d)
+            return cudaMemcpyAsync(c->host_in[slot].p, r.x, (size_t)r.n * r.d * 4, cudaMemcpyHostToDevice, c->stream);
+        return cudaMemcpy2DAsync(c->host_in[slot].p, (size_t)r.d * 4, r.x, (size_t)r.ld * 4, (size_t)r.d * 4,
+                                 (size_t)r.n, cudaMemcpyHostToDevice, c->stream);
+    };
+    auto up_sel = [&](int slot, const ejoin_sel *s, int64_t n, ejoin_sel &ds) -> cudaError_t {
+        ds = *s;
+        const size_t abytes = s->attr ? (size_t)n * 4 : 0;
+        const size_t bbytes = s->bits ? (size_t)((n + 31) / 32) * 4 : 0;
+        cudaError_t ee = ensure(c->host_in[slot], abytes + bbytes + 16);
+        if (ee != cudaSuccess) return ee;
+        char *base = (char *)c->host_in[slot].p;
+        if (s->attr && n) {
+            if ((ee = cudaMemcpyAsync(base, s->attr, abytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+                return ee;
+            ds.attr = (const int32_t *)base;
+        }
+        if (s->bits && n) {
+            char *bb = base + ((abytes + 15) & ~size_t(15));
+            if ((ee = cudaMemcpyAsync(bb, s->bits, bbytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+                return ee;
+            ds.bits = (const uint32_t *)bb;
+        }
+        return cudaSuccess;
+    };
+    ejoin_rel dR, dS;
+    ejoin_sel dsR, dsS;
+    if ((e = up_rel(0, R, dR)) != cudaSuccess) return from_cuda(e);
+    if (self) {
+        dS = dR;
+    } else if ((e = up_rel(1, S, dS)) != cudaSuccess) {
+        return from_cuda(e);
+    }
+    if (selR && (e = up_sel(2, selR, R.n, dsR)) != cudaSuccess) return from_cuda(e);
+    if (selS) {
+        if (self) {
+            dsS = dsR;
+        } else if ((e = up_sel(3, selS, S.n, dsS)) != cudaSuccess) {
+            return from_cuda(e);
+        }
+    }
+    if (timing) cudaEventRecord(c->ev[5], c->stream);
+    if ((e = ensure(c->host_pairs, std::max<uint64_t>(capacity, 1) * sizeof(ejoin_pair))) != cudaSuccess)
+        return from_cuda(e);
+    ejoin_pair *dp = (ejoin_pair *)c->host_pairs.p;
+    uint64_t cap = capacity;
+    uint64_t cnt = 0;
+    ejoin_status st =
+        run_threshold(c, dR, dS, eps, selR ? &dsR : nullptr, selS ? &dsS : nullptr, &dp, &cap, false, nullptr, &cnt);
+    *count = cnt;
+    if (st != EJOIN_OK && st != EJOIN_EOVERFLOW) return st;
+    const uint64_t ncopy = std::min<uint64_t>(cnt, capacity);
+    if (timing) cudaEventRecord(c->ev[6], c->stream);
+    if (ncopy && (c->flags & EJOIN_FLAG_COUNT_ONLY) == 0) {
+        if ((e = cudaMemcpyAsync(h_pairs, dp, ncopy * sizeof(ejoin_pair), cudaMemcpyDeviceToHost, c->stream)) !=
+            cudaSuccess)
+            return from_cuda(e);
+    }
+    if (timing) cudaEventRecord(c->ev[7], c->stream);
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+    if (timing) {
+        c->stats.ms_h2d = elapsed(c->ev[4], c->ev[5]);
+        c->stats.ms_d2h = elapsed(c->ev[6], c->ev[7]);
+    }
+    return st;
+}
+
+ejoin_status ejoin_normalize(ejoin_ctx *c, ejoin_rel in, const ejoin_sel *sel, int32_t prec, void *d_out,
+                             int64_t ld_out, float *d_inv_norm, float *d_scale, uint32_t *d_ids, int64_t *d_n_sel)
+{
+    if (!c || !rel_ok(in) || !sel_ok(sel) || !d_out || !d_n_sel) return EJOIN_EINVAL;
+    if (prec < EJOIN_F32 || prec > EJOIN_TF32) return EJOIN_EINVAL;
+    const int64_t kp = ejoin_padded_dim(prec, in.d);
+    if (ld_out < kp) return EJOIN_EINVAL;
+    const int fmt = fmt_of(prec);
+    if (fmt == FMT_FP8 && !d_scale) return EJOIN_EINVAL;
+    // vector stores of 4 elements per lane: 16-byte (F32), 8-byte (BF16), 4-byte (e4m3) alignment
+    if ((ld_out & 3) || (reinterpret_cast<uintptr_t>(d_out) & (4 * fmt_bytes(fmt) - 1))) return EJOIN_EINVAL;
+    DeviceGuard g(c->device);
+    cudaError_t e;
+    Side &sd = c->side[0];
+    uint32_t *ids = d_ids;
+    if (sel && !ids) {
+        if ((e = ensure(sd.ids, (size_t)std::max<int64_t>(in.n, 1) * 4)) != cudaSuccess) return from_cuda(e);
+        ids = (uint32_t *)sd.ids.p;
+    }
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    return prepare_side(c, 0, in, sel, fmt, kp, d_out, ld_out, d_inv_norm, d_scale, ids, (long long *)d_n_sel,
+                        &dm->status, false);
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Internal declarations shared by the CUDA translation units of libejoin.
+// Device-side PTX wrappers for mbarrier / TMA / tcgen05 (sm_103a), the
+// device error word, and the kernel launchers called by the C ABI layer.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ejoin.h"
+
+namespace ej {
+
+// Bits of the device error word (DevMisc::status).
+enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+
+// Storage format of normalised rows.
+enum Fmt : int { FMT_F32 = 0, FMT_BF16 = 1, FMT_FP8 = 2 };
+
+// Device-resident counters of one call (one 64-byte block of the workspace).
+struct DevMisc {
+    unsigned long long cand_count;  // candidates found by the contraction (may exceed capacity)
+    unsigned long long pair_count;  // result pairs written by the re-score (may exceed capacity)
+    unsigned long long band_count;  // candidates re-scored in FP64
+    long long n_sel[2];             // rows kept by the selection of R (0) and S (1)
+    unsigned status;                // ERR_* bits
+    unsigned pad;
+    unsigned long long pad2[2];
+};
+
+struct SelArgs {
+    const int32_t *attr;
+    int op;
+    int c;
+    const uint32_t *bits;
+};
+
+// Rows per selection block (count / scatter kernels).
+constexpr int SEL_THREADS = 512;
+constexpr int SEL_ITEMS = 16;
+constexpr int64_t SEL_ROWS_PER_BLOCK = (int64_t)SEL_THREADS * SEL_ITEMS;
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_sel_count(const SelArgs &s, int64_t n, uint32_t *block_counts, cudaStream_t st);
+cudaError_t launch_sel_scan(const uint32_t *block_counts, int64_t n_blocks, uint32_t *block_offsets,
+                            long long *n_sel, cudaStream_t st);
+cudaError_t launch_sel_scatter(const SelArgs &s, int64_t n, const uint32_t *block_offsets, uint32_t *ids,
+                               cudaStream_t st);
+cudaError_t launch_set_count(long long *n_sel, long long value, cudaStream_t st);
+cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const uint32_t *ids,
+                             const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
+                             int kp, float *inv_norm, float *scale, unsigned *status, int num_sms,
+                             cudaStream_t st);
+cudaError_t launch_sim_simt(const float *A, const float *B, int kp, const long long *nA, const long long *nB,
+                            float thr, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
+                            int count_only, int num_sms, cudaStream_t st);
+// kind: 0 = BF16 (kind::f16), 1 = e4m3 (kind::f8f6f4), 2 = TF32 (kind::tf32)
+cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                          const long long *nA, const long long *nB, float thr, const float *scaleA,
+                          const float *scaleB, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
+                          unsigned *status, uint64_t timeout, int count_only, int grid, cudaStream_t st);
+size_t sim_tc_smem_bytes();
+cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                           const float *R, int64_t ldR, const float *S, int64_t ldS, int d,
+                           const uint32_t *idsR, const uint32_t *idsS, const float *invR, const float *invS,
+                           float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
+                           unsigned long long *out_count, unsigned long long *band_count, int count_only,
+                           int num_sms, cudaStream_t st);
+
+// ------------------------------------------------------- device PTX helpers
+#if defined(__CUDACC__)
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase.  Gives up (returns false) after
+// `timeout` SM cycles or when another role has raised the CTA's abort flag;
+// the first role to time out raises the flag and the device error word.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t timeout,
+                                                  volatile int *abort_flag, unsigned *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if ((uint64_t)(clock64() - t0) > timeout) {
+            *abort_flag = 1;
+            atomicOr(status, ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_prefetch_desc(const CUtensorMap *map)
+{
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// 2-D tiled TMA load of one box into shared memory; completion is signalled
+// on `bar` as transaction bytes.  x = innermost (element) coordinate.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t holder_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(holder_smem), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Arrive on `bar` once every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void tc_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA
+// with 128-byte swizzling: rows of 128 bytes, 8-row core groups 1024 bytes
+// apart (stride byte offset), leading byte offset unused for this layout,
+// descriptor version 1, layout type 2 = SWIZZLE_128B.  The tile base must be
+// 1024-byte aligned; advancing along K inside the 128-byte row is done by
+// adding the byte offset to the start address.
+__device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&v)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+#endif  // __CUDACC__
+
+}  // namespace ej

@@ -1,0 +1,304 @@
+// Selection pushdown and row normalisation (HBM-bound passes).
+//
+// Selection (Sec. III-C, Eq. (Selection); pushed below the embedding work as
+// in Eq. (E-Selection), and applied as a relational pre-filter in Sec. VI-E):
+// an order-preserving stream compaction of the kept row ids in three passes
+// (per-block count, one-block scan of the block counts, per-block scatter).
+//
+// Normalisation (Sec. IV-C: cosine similarity equals the dot product of
+// normalised vectors; each row is normalised exactly once, the "prefetch"
+// formulation of Sec. IV-A, Eq. nlj-prefetch): one warp per kept row, FP32
+// sum of squares accumulated per lane then by a butterfly tree, y = x / ||x||
+// (0 for a zero row), stored as FP32 / BF16 / e4m3 with zero padding to the
+// contraction's K granularity.
+#include "ejoin_internal.cuh"
+
+namespace ej {
+
+__device__ __forceinline__ bool sel_keep(const SelArgs &s, int64_t r)
+{
+    bool k = true;
+    if (s.attr) {
+        const int a = s.attr[r];
+        switch (s.op) {
+        case EJOIN_LT: k = a < s.c; break;
+        case EJOIN_LE: k = a <= s.c; break;
+        case EJOIN_GT: k = a > s.c; break;
+        case EJOIN_GE: k = a >= s.c; break;
+        case EJOIN_EQ: k = a == s.c; break;
+        case EJOIN_NE: k = a != s.c; break;
+        default: k = false;
+        }
+    }
+    if (k && s.bits) k = (s.bits[r >> 5] >> (r & 31)) & 1u;
+    return k;
+}
+
+__device__ __forceinline__ int block_sum(int v, int *red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    int t = 0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    return t;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) sel_count_kernel(SelArgs s, int64_t n, uint32_t *block_counts)
+{
+    __shared__ int red[SEL_THREADS / 32];
+    const int64_t base = (int64_t)blockIdx.x * SEL_ROWS_PER_BLOCK;
+    int cnt = 0;
+#pragma unroll 4
+    for (int it = 0; it < SEL_ITEMS; ++it) {
+        const int64_t r = base + (int64_t)it * SEL_THREADS + threadIdx.x;
+        if (r < n && sel_keep(s, r)) ++cnt;
+    }
+    cnt = block_sum(cnt, red);
+    if (threadIdx.x == 0) block_counts[blockIdx.x] = (uint32_t)cnt;
+}
+
+// Exclusive scan of the per-block counts by one block; writes the total.
+__global__ void __launch_bounds__(1024) sel_scan_kernel(const uint32_t *counts, int64_t nb, uint32_t *offsets,
+                                                        long long *n_sel)
+{
+    __shared__ unsigned long long warp_tot[32];
+    __shared__ unsigned long long carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += 1024) {
+        const int64_t i = base + threadIdx.x;
+        unsigned long long v = i < nb ? counts[i] : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;  // inclusive over warps
+        }
+        __syncthreads();
+        const unsigned long long warp_excl = warp ? warp_tot[warp - 1] : 0ull;
+        if (i < nb) offsets[i] = (uint32_t)(carry + warp_excl + x - v);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *n_sel = (long long)carry;
+}
+
+__global__ void __launch_bounds__(SEL_THREADS) sel_scatter_kernel(SelArgs s, int64_t n, const uint32_t *offsets,
+                                                                  uint32_t *ids)
+{
+    __shared__ int wcount[SEL_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = (int64_t)blockIdx.x * SEL_ROWS_PER_BLOCK;
+    uint32_t running = offsets[blockIdx.x];
+    for (int it = 0; it < SEL_ITEMS; ++it) {
+        const int64_t r = base + (int64_t)it * SEL_THREADS + threadIdx.x;
+        const bool k = r < n && sel_keep(s, r);
+        const unsigned m = __ballot_sync(0xffffffffu, k);
+        if (lane == 0) wcount[warp] = __popc(m);
+        __syncthreads();
+        uint32_t before = 0, strip = 0;
+        for (int w = 0; w < SEL_THREADS / 32; ++w) {
+            const int c = wcount[w];
+            before += (w < warp) ? c : 0;
+            strip += c;
+        }
+        if (k) ids[running + before + __popc(m & ((1u << lane) - 1u))] = (uint32_t)r;
+        running += strip;
+        __syncthreads();
+    }
+}
+
+__global__ void set_count_kernel(long long *p, long long v) { *p = v; }
+
+// One warp per kept row c: source row ids[c] (or c), output row c.
+template <int FMT>
+__global__ void __launch_bounds__(256) normalize_kernel(const float *__restrict__ x, int64_t ld, int d,
+                                                        const uint32_t *__restrict__ ids,
+                                                        const long long *__restrict__ n_rows_dev,
+                                                        int64_t n_rows_max, void *__restrict__ out, int64_t ld_out,
+                                                        int kp, float *__restrict__ inv_norm,
+                                                        float *__restrict__ scale, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n_rows = n_rows_dev ? (int64_t)*n_rows_dev : n_rows_max;
+    if (n_rows > n_rows_max) n_rows = n_rows_max;
+    const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    const int groups = kp >> 2;  // kp is a multiple of 32
+
+    for (int64_t c = warp_global; c < n_rows; c += n_warps) {
+        const int64_t r = ids ? (int64_t)ids[c] : c;
+        const float *src = x + r * ld;
+
+        auto load4 = [&](int k) -> float4 {
+            float4 v;
+            if (vec && k + 3 < d) {
+                v = __ldg(reinterpret_cast<const float4 *>(src + k));
+            } else {
+                v.x = k + 0 < d ? __ldg(src + k + 0) : 0.f;
+                v.y = k + 1 < d ? __ldg(src + k + 1) : 0.f;
+                v.z = k + 2 < d ? __ldg(src + k + 2) : 0.f;
+                v.w = k + 3 < d ? __ldg(src + k + 3) : 0.f;
+            }
+            return v;
+        };
+
+        // pass 1: sum of squares and max |x|
+        float ss = 0.f, mx = 0.f;
+        for (int g = lane; 4 * g < d; g += 32) {
+            const float4 v = load4(4 * g);
+            ss = fmaf(v.x, v.x, ss);
+            ss = fmaf(v.y, v.y, ss);
+            ss = fmaf(v.z, v.z, ss);
+            ss = fmaf(v.w, v.w, ss);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ss += __shfl_xor_sync(0xffffffffu, ss, o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        float inv;
+        bool bad = false;
+        if (isnan(ss) || !isfinite(mx)) {
+            // NaN or Inf in the row (fmaxf drops NaN, the sum of squares keeps it)
+            bad = true;
+            inv = 0.f;
+        } else if (isfinite(ss) && (ss >= 0x1p-100f || mx == 0.f)) {
+            inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+        } else {
+            // overflow or underflow of the plain sum: rescale by max |x|
+            const float rm = 1.0f / mx;
+            float s2 = 0.f;
+            for (int g = lane; 4 * g < d; g += 32) {
+                const float4 v = load4(4 * g);
+                s2 = fmaf(v.x * rm, v.x * rm, s2);
+                s2 = fmaf(v.y * rm, v.y * rm, s2);
+                s2 = fmaf(v.z * rm, v.z * rm, s2);
+                s2 = fmaf(v.w * rm, v.w * rm, s2);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            inv = (1.0f / sqrtf(s2)) / mx;
+        }
+        if (bad && lane == 0) atomicOr(status, ERR_NONFINITE);
+
+        float sc = 1.f, rsc = 1.f;
+        if (FMT == FMT_FP8) {
+            const float ymax = mx * inv;  // max |y|
+            sc = ymax > 0.f ? ymax / 448.f : 1.f;
+            rsc = 1.0f / sc;
+            if (lane == 0) scale[c] = sc;
+        }
+        if (lane == 0 && inv_norm) inv_norm[c] = inv;
+
+        // pass 2: write the normalised row, zero padded to kp
+        for (int g = lane; g < groups; g += 32) {
+            const int k = 4 * g;
+            float4 v = k < d ? load4(k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v.x *= inv;
+            v.y *= inv;
+            v.z *= inv;
+            v.w *= inv;
+            if (FMT == FMT_F32) {
+                float *o = reinterpret_cast<float *>(out) + c * ld_out + k;
+                *reinterpret_cast<float4 *>(o) = v;
+            } else if (FMT == FMT_BF16) {
+                __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out) + c * ld_out + k;
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+                __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+                uint2 u;
+                u.x = *reinterpret_cast<uint32_t *>(&lo);
+                u.y = *reinterpret_cast<uint32_t *>(&hi);
+                *reinterpret_cast<uint2 *>(o) = u;
+            } else {
+                __nv_fp8_storage_t *o = reinterpret_cast<__nv_fp8_storage_t *>(out) + c * ld_out + k;
+                const __nv_fp8x2_storage_t lo =
+                    __nv_cvt_float2_to_fp8x2(make_float2(v.x * rsc, v.y * rsc), __NV_SATFINITE, __NV_E4M3);
+                const __nv_fp8x2_storage_t hi =
+                    __nv_cvt_float2_to_fp8x2(make_float2(v.z * rsc, v.w * rsc), __NV_SATFINITE, __NV_E4M3);
+                *reinterpret_cast<uint32_t *>(o) = (uint32_t)lo | ((uint32_t)hi << 16);
+            }
+        }
+    }
+}
+
+cudaError_t launch_sel_count(const SelArgs &s, int64_t n, uint32_t *block_counts, cudaStream_t st)
+{
+    const int64_t nb = (n + SEL_ROWS_PER_BLOCK - 1) / SEL_ROWS_PER_BLOCK;
+    if (nb == 0) return cudaSuccess;
+    sel_count_kernel<<<(unsigned)nb, SEL_THREADS, 0, st>>>(s, n, block_counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sel_scan(const uint32_t *block_counts, int64_t n_blocks, uint32_t *block_offsets,
+                            long long *n_sel, cudaStream_t st)
+{
+    sel_scan_kernel<<<1, 1024, 0, st>>>(block_counts, n_blocks, block_offsets, n_sel);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sel_scatter(const SelArgs &s, int64_t n, const uint32_t *block_offsets, uint32_t *ids,
+                               cudaStream_t st)
+{
+    const int64_t nb = (n + SEL_ROWS_PER_BLOCK - 1) / SEL_ROWS_PER_BLOCK;
+    if (nb == 0) return cudaSuccess;
+    sel_scatter_kernel<<<(unsigned)nb, SEL_THREADS, 0, st>>>(s, n, block_offsets, ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_count(long long *n_sel, long long value, cudaStream_t st)
+{
+    set_count_kernel<<<1, 1, 0, st>>>(n_sel, value);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const uint32_t *ids,
+                             const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out, int kp,
+                             float *inv_norm, float *scale, unsigned *status, int num_sms, cudaStream_t st)
+{
+    if (n_rows_max <= 0) return cudaSuccess;
+    // 8 warps per block, up to 16 blocks per SM, grid-stride over rows
+    int64_t blocks = (n_rows_max + 7) / 8;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    switch (fmt) {
+    case FMT_F32:
+        normalize_kernel<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
+                                                                    ld_out, kp, inv_norm, scale, status);
+        break;
+    case FMT_BF16:
+        normalize_kernel<FMT_BF16><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
+                                                                     ld_out, kp, inv_norm, scale, status);
+        break;
+    case FMT_FP8:
+        normalize_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
+                                                                    ld_out, kp, inv_norm, scale, status);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ej

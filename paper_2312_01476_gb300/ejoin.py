@@ -1,0 +1,317 @@
+"""ctypes binding of libejoin (the C ABI declared in include/ejoin.h).
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  Names mirror the C entry points.  Device arrays are torch CUDA
+tensors; host arrays are numpy arrays (or CPU tensors).  If the compiled
+library is missing, loading raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libejoin.so")
+
+EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
+EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
+EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
+EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING = 0x1, 0x2
+OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
+PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
+
+
+class ejoin_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("prec", ctypes.c_int32),
+                ("band", ctypes.c_float), ("fp64_band", ctypes.c_float), ("capacity_hint", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32), ("timeout_cycles", ctypes.c_uint64)]
+
+
+class ejoin_rel(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int32), ("ld", ctypes.c_int64)]
+
+
+class ejoin_sel(ctypes.Structure):
+    _fields_ = [("attr", ctypes.c_void_p), ("op", ctypes.c_int32), ("c", ctypes.c_int32),
+                ("bits", ctypes.c_void_p)]
+
+
+class ejoin_pair(ctypes.Structure):
+    _fields_ = [("i", ctypes.c_uint32), ("j", ctypes.c_uint32), ("sim", ctypes.c_float)]
+
+
+class ejoin_pairs(ctypes.Structure):
+    _fields_ = [("d_pairs", ctypes.c_void_p), ("capacity", ctypes.c_uint64), ("d_count", ctypes.c_void_p),
+                ("count", ctypes.c_uint64)]
+
+
+class ejoin_stats(ctypes.Structure):
+    _fields_ = [("n_sel_r", ctypes.c_uint64), ("n_sel_s", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("fp64_rescored", ctypes.c_uint64), ("pairs", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("band", ctypes.c_float), ("ms_select", ctypes.c_float), ("ms_normalize", ctypes.c_float),
+                ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("ms_h2d", ctypes.c_float), ("ms_d2h", ctypes.c_float), ("contract_retries", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def _open(path: str):
+    if not os.path.exists(path):
+        raise RuntimeError(f"libejoin.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    return ctypes.CDLL(path)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libejoin.so (built by paper_2312_01476_gb300.build); raises if it is missing."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    lib = _open(path)
+    P = ctypes.POINTER
+    lib.ejoin_create.restype = ctypes.c_int
+    lib.ejoin_create.argtypes = [P(ctypes.c_void_p), P(ejoin_config)]
+    lib.ejoin_destroy.restype = None
+    lib.ejoin_destroy.argtypes = [ctypes.c_void_p]
+    lib.ejoin_normalize.restype = ctypes.c_int
+    lib.ejoin_normalize.argtypes = [ctypes.c_void_p, ejoin_rel, P(ejoin_sel), ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+    lib.ejoin_padded_dim.restype = ctypes.c_int64
+    lib.ejoin_padded_dim.argtypes = [ctypes.c_int32, ctypes.c_int32]
+    lib.ejoin_threshold.restype = ctypes.c_int
+    lib.ejoin_threshold.argtypes = [ctypes.c_void_p, ejoin_rel, ejoin_rel, ctypes.c_float, P(ejoin_sel),
+                                    P(ejoin_sel), P(ejoin_pairs)]
+    lib.ejoin_threshold_host.restype = ctypes.c_int
+    lib.ejoin_threshold_host.argtypes = [ctypes.c_void_p, ejoin_rel, ejoin_rel, ctypes.c_float, P(ejoin_sel),
+                                         P(ejoin_sel), ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_uint64)]
+    lib.ejoin_pairs_free.restype = ctypes.c_int
+    lib.ejoin_pairs_free.argtypes = [ctypes.c_void_p, P(ejoin_pairs)]
+    lib.ejoin_last_stats.restype = ctypes.c_int
+    lib.ejoin_last_stats.argtypes = [ctypes.c_void_p, P(ejoin_stats)]
+    lib.ejoin_strerror.restype = ctypes.c_char_p
+    lib.ejoin_strerror.argtypes = [ctypes.c_int]
+    lib.ejoin_version.restype = ctypes.c_char_p
+    lib.ejoin_version.argtypes = []
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+class EJoinError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {ejoin_strerror(status)} (status {status})")
+
+
+def ejoin_strerror(status: int) -> str:
+    return load_library().ejoin_strerror(int(status)).decode()
+
+
+def ejoin_version() -> str:
+    return load_library().ejoin_version().decode()
+
+
+def ejoin_padded_dim(prec: int, d: int) -> int:
+    return int(load_library().ejoin_padded_dim(int(prec), int(d)))
+
+
+def _check(status: int, where: str):
+    if status != EJOIN_OK:
+        raise EJoinError(status, where)
+
+
+@dataclass
+class Sel:
+    """Selection ``attr op c`` (and/or a bitmask) on one relation (Sec. III-C, Eq. Selection)."""
+    attr: object = None  # int32 array (torch CUDA tensor for device calls, numpy for host calls)
+    op: str = "<"
+    c: int = 0
+    bits: object = None  # uint32 words, bit r % 32 of word r // 32
+
+
+class Ctx:
+    """An ejoin context: device, stream, precision, bands, flags."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None, prec="bf16", band: float = -1.0,
+                 fp64_band: float = -1.0, capacity_hint: int = 0, flags: int = 0, timeout_cycles: int = 0):
+        lib = load_library()
+        self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+        cfg = ejoin_config(int(device), ctypes.c_void_p(stream or 0), self.prec, float(band), float(fp64_band),
+                           int(capacity_hint), int(flags), int(timeout_cycles))
+        h = ctypes.c_void_p()
+        _check(lib.ejoin_create(ctypes.byref(h), ctypes.byref(cfg)), "ejoin_create")
+        self.handle = h
+        self.device = device
+        self._out = None  # cached device result buffer (torch int32 [cap, 3])
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().ejoin_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def ejoin_create(**kw) -> Ctx:
+    return Ctx(**kw)
+
+
+def ejoin_destroy(ctx: Ctx):
+    ctx.close()
+
+
+def _dev_rel(x) -> ejoin_rel:
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
+        raise TypeError("relation must be a 2-D float32 CUDA tensor")
+    if x.stride(1) != 1:
+        raise TypeError("relation rows must be contiguous")
+    return ejoin_rel(ctypes.c_void_p(x.data_ptr()), x.shape[0], x.shape[1], x.stride(0))
+
+
+def _dev_sel(s: Optional[Sel]):
+    if s is None:
+        return None
+    import torch
+    for a, dt in ((s.attr, torch.int32), (s.bits, torch.int32)):
+        if a is not None and (not isinstance(a, torch.Tensor) or not a.is_cuda or not a.is_contiguous()
+                              or a.dtype not in (torch.int32, torch.uint32)):
+            raise TypeError("selection arrays must be contiguous int32 CUDA tensors")
+    return ejoin_sel(ctypes.c_void_p(s.attr.data_ptr() if s.attr is not None else 0), OPS[s.op], int(s.c),
+                     ctypes.c_void_p(s.bits.data_ptr() if s.bits is not None else 0))
+
+
+def _sel_ptr(s):
+    return ctypes.byref(s) if s is not None else None
+
+
+@dataclass
+class Result:
+    i: object    # uint32-valued int32 tensor (original R row ids)
+    j: object    # original S row ids
+    sim: object  # float32 similarities
+    count: int
+
+
+def ejoin_threshold(ctx: Ctx, R, S, eps: float, selR: Optional[Sel] = None, selS: Optional[Sel] = None,
+                    capacity: Optional[int] = None) -> Result:
+    """Device E-join (Sec. III-C, Eq. (E-theta-Join)) of CUDA tensors R, S; returns views of a
+    cached device result buffer (valid until the next call on ctx)."""
+    import torch
+    lib = load_library()
+    rR, rS = _dev_rel(R), _dev_rel(S)
+    sR, sS = _dev_sel(selR), _dev_sel(selS)
+    cap = capacity or (ctx._out.shape[0] if ctx._out is not None else 1 << 16)
+    for _ in range(3):
+        if ctx._out is None or ctx._out.shape[0] < cap:
+            ctx._out = torch.empty((cap, 3), dtype=torch.int32, device=R.device)
+        out = ejoin_pairs(ctypes.c_void_p(ctx._out.data_ptr()), ctx._out.shape[0], None, 0)
+        st = lib.ejoin_threshold(ctx.handle, rR, rS, ctypes.c_float(eps), _sel_ptr(sR), _sel_ptr(sS),
+                                 ctypes.byref(out))
+        if st == EJOIN_EOVERFLOW:
+            cap = int(out.count) + 1024
+            continue
+        _check(st, "ejoin_threshold")
+        n = int(out.count)
+        v = ctx._out[:n]
+        return Result(v[:, 0], v[:, 1], v[:, 2].view(torch.float32), n)
+    raise EJoinError(EJOIN_EOVERFLOW, "ejoin_threshold")
+
+
+def _host_arr(a, dtype):
+    if a is None:
+        return None
+    if hasattr(a, "numpy"):
+        a = a.numpy()
+    a = np.asarray(a)
+    if a.dtype != dtype:
+        raise TypeError(f"expected {dtype} host array, got {a.dtype}")
+    return a
+
+
+def ejoin_threshold_host(ctx: Ctx, R, S, eps: float, selR: Optional[Sel] = None, selS: Optional[Sel] = None,
+                         out=None):
+    """Host-memory E-join: inputs are copied to the device, joined, and the pairs copied back.
+
+    ``out``: optional numpy structured buffer (pinned memory recommended) of dtype PAIR_DTYPE.
+    Returns (pairs numpy structured array view, count)."""
+    lib = load_library()
+    Rh = _host_arr(R, np.float32)
+    Sh = _host_arr(S, np.float32)
+    if Rh.ndim != 2 or Sh.ndim != 2 or Rh.strides[1] != 4 or Sh.strides[1] != 4:
+        raise TypeError("host relations must be 2-D float32 with contiguous rows")
+    rR = ejoin_rel(ctypes.c_void_p(Rh.ctypes.data), Rh.shape[0], Rh.shape[1], Rh.strides[0] // 4)
+    rS = ejoin_rel(ctypes.c_void_p(Sh.ctypes.data), Sh.shape[0], Sh.shape[1], Sh.strides[0] // 4)
+    keep = []
+
+    def hsel(s):
+        if s is None:
+            return None
+        a = _host_arr(s.attr, np.int32)
+        b = None if s.bits is None else np.asarray(s.bits).view(np.uint32)
+        keep.extend([a, b])
+        return ejoin_sel(ctypes.c_void_p(a.ctypes.data if a is not None else 0), OPS[s.op], int(s.c),
+                         ctypes.c_void_p(b.ctypes.data if b is not None else 0))
+
+    sR, sS = hsel(selR), hsel(selS)
+    if out is None:
+        out = np.empty(1 << 16, dtype=PAIR_DTYPE)
+    for _ in range(3):
+        cnt = ctypes.c_uint64(0)
+        st = lib.ejoin_threshold_host(ctx.handle, rR, rS, ctypes.c_float(eps), _sel_ptr(sR), _sel_ptr(sS),
+                                      ctypes.c_void_p(out.ctypes.data), len(out), ctypes.byref(cnt))
+        if st == EJOIN_EOVERFLOW:
+            out = np.empty(int(cnt.value) + 1024, dtype=PAIR_DTYPE)
+            continue
+        _check(st, "ejoin_threshold_host")
+        return out[: int(cnt.value)], int(cnt.value)
+    raise EJoinError(EJOIN_EOVERFLOW, "ejoin_threshold_host")
+
+
+PAIR_DTYPE = np.dtype([("i", np.uint32), ("j", np.uint32), ("sim", np.float32)])
+
+
+def ejoin_normalize(ctx: Ctx, X, prec="bf16", sel: Optional[Sel] = None):
+    """Selection + normalisation of one device relation.  Returns (rows, inv_norm, scale, ids, n_sel)
+    where rows is the padded normalised matrix in the precision's storage type."""
+    import torch
+    lib = load_library()
+    p = PRECS[prec] if isinstance(prec, str) else int(prec)
+    r = _dev_rel(X)
+    n, d = X.shape
+    kp = ejoin_padded_dim(p, d)
+    dt = {EJOIN_F32: torch.float32, EJOIN_TF32: torch.float32, EJOIN_BF16: torch.bfloat16,
+          EJOIN_FP8_E4M3: torch.uint8}[p]
+    out = torch.zeros((max(n, 1), kp), dtype=dt, device=X.device)
+    inv = torch.zeros(max(n, 1), dtype=torch.float32, device=X.device)
+    scale = torch.zeros(max(n, 1), dtype=torch.float32, device=X.device)
+    ids = torch.zeros(max(n, 1), dtype=torch.int32, device=X.device)
+    n_sel = torch.zeros(1, dtype=torch.int64, device=X.device)
+    s = _dev_sel(sel)
+    _check(lib.ejoin_normalize(ctx.handle, r, _sel_ptr(s), p, ctypes.c_void_p(out.data_ptr()), kp,
+                               ctypes.c_void_p(inv.data_ptr()), ctypes.c_void_p(scale.data_ptr()),
+                               ctypes.c_void_p(ids.data_ptr()), ctypes.c_void_p(n_sel.data_ptr())),
+           "ejoin_normalize")
+    return out, inv, scale, ids, n_sel
+
+
+def ejoin_last_stats(ctx: Ctx) -> dict:
+    st = ejoin_stats()
+    _check(load_library().ejoin_last_stats(ctx.handle, ctypes.byref(st)), "ejoin_last_stats")
+    return {name: getattr(st, name) for name, _ in ejoin_stats._fields_}
