@@ -191,6 +191,43 @@ const char *ejoin_strerror(ejoin_status s);
 /* Library version string. */
 const char *ejoin_version(void);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free variant of ejoin_threshold.  The paper has no counterpart.
+ *
+ * For callers that cannot call cudaMalloc: a database executor or serving
+ * process whose device memory belongs to its own pool allocator, a process
+ * held to a fixed memory budget, or a latency-critical loop in which
+ * cudaMalloc / cudaFree would synchronise the device or fail under
+ * fragmentation.  It runs the BF16 path (normalise, tcgen05 contraction with
+ * the fused threshold, exact re-score) with every piece of scratch in one
+ * fixed-size array that lives in the library's device image, and calls no
+ * allocating routine.  No selection predicate; no context.
+ *
+ * R.x, S.x and d_pairs are device pointers on the CURRENT device; the work is
+ * enqueued on `stream` (cudaStream_t; NULL = legacy default stream) and the
+ * call synchronises that stream before returning.  *count receives the number
+ * of result pairs; EJOIN_EOVERFLOW with *count > capacity means the first
+ * `capacity` records are valid (as for ejoin_threshold); EJOIN_EOVERFLOW with
+ * *count == 0 means the candidates exceeded EJOIN_STATIC_MAX_CANDIDATES and
+ * the result is incomplete (use ejoin_threshold for such joins).
+ *
+ * Limits (EJOIN_EINVAL beyond them): R.n, S.n <= EJOIN_STATIC_MAX_ROWS and
+ * (ceil(R.n/256) + ceil(S.n/256)) * 256 * ceil(d/64) * 64 <=
+ * EJOIN_STATIC_MAX_OPERAND_ELEMS.  Every GPU that loads the library holds the
+ * EJOIN_STATIC_SCRATCH_BYTES array until the process exits.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents; counters are cleared at the start of
+ * each call, and calls that overlap on the GPU race on the array.
+ * ------------------------------------------------------------------------- */
+#define EJOIN_STATIC_MAX_ROWS 65536
+#define EJOIN_STATIC_MAX_OPERAND_ELEMS (1u << 24)
+#define EJOIN_STATIC_MAX_CANDIDATES (1u << 20)
+#define EJOIN_STATIC_SCRATCH_BYTES \
+    (1024u + 2u * 4u * EJOIN_STATIC_MAX_ROWS + 8u * EJOIN_STATIC_MAX_CANDIDATES + 2u * EJOIN_STATIC_MAX_OPERAND_ELEMS)
+ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float eps, ejoin_pair *d_pairs, uint64_t capacity,
+                                    uint64_t *count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

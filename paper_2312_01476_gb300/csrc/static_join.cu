@@ -1,0 +1,176 @@
+// Allocation-free entry point: ejoin_threshold_static.
+//
+// Some callers cannot call cudaMalloc at all: a database executor or serving
+// process whose device memory is owned by its own pool allocator, a process
+// held to a fixed memory budget, or a latency-critical loop in which
+// cudaMalloc / cudaFree would synchronise the device or fail under
+// fragmentation.  For them this entry point runs the BF16 join (normalise,
+// tcgen05 contraction with fused threshold, exact re-score) with all of its
+// scratch in one file-scope device array of fixed size, so the call itself
+// allocates nothing.  The caller passes the inputs and the output buffer.
+//
+// The array lives in this library's device image: every GPU that loads the
+// library holds it (EJOIN_STATIC_SCRATCH_BYTES) until the process exits.  All
+// calls share it and it keeps the contents of the last call, so the counters
+// are cleared at the start of every call, and calls that overlap on the GPU
+// (different streams, or different host threads on one device) race on it.
+//
+// The paper has no counterpart of this entry point.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "ejoin_internal.cuh"
+
+using namespace ej;
+
+namespace {
+
+constexpr size_t MISC_BYTES = 1024;
+constexpr size_t INV_BYTES = (size_t)EJOIN_STATIC_MAX_ROWS * 4;
+constexpr size_t CAND_BYTES = (size_t)EJOIN_STATIC_MAX_CANDIDATES * 8;
+constexpr size_t OPER_BYTES = (size_t)EJOIN_STATIC_MAX_OPERAND_ELEMS * 2;  // BF16
+constexpr size_t OFF_MISC = 0;
+constexpr size_t OFF_INV_A = OFF_MISC + MISC_BYTES;
+constexpr size_t OFF_INV_B = OFF_INV_A + INV_BYTES;
+constexpr size_t OFF_CAND = OFF_INV_B + INV_BYTES;
+constexpr size_t OFF_OPER = OFF_CAND + CAND_BYTES;
+constexpr size_t SCRATCH_BYTES = OFF_OPER + OPER_BYTES;
+static_assert(SCRATCH_BYTES == EJOIN_STATIC_SCRATCH_BYTES, "scratch size stated in ejoin.h");
+static_assert(OFF_OPER % 1024 == 0, "operand area alignment for TMA");
+static_assert(sizeof(DevMisc) <= MISC_BYTES, "counter block");
+
+// The scratch array.  Host code must not use its name as a device address:
+// the address comes from cudaGetSymbolAddress in device_setup().
+static __device__ __align__(256) unsigned char g_static_scratch[SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+struct DeviceState {
+    bool ready = false;
+    unsigned char *scratch = nullptr;
+    int num_sms = 0;
+    bool sm103 = false;
+};
+DeviceState g_dev[MAX_DEVICES];
+std::mutex g_mu;
+
+ejoin_status device_setup(int dev, DeviceState **out)
+{
+    if (dev < 0 || dev >= MAX_DEVICES) return EJOIN_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_mu);
+    DeviceState &s = g_dev[dev];
+    if (!s.ready) {
+        void *p = nullptr;
+        // `dev` is the current device here (the caller's)
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return EJOIN_ECUDA;
+        int sms = 0, major = 0, minor = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+            return EJOIN_ECUDA;
+        s.scratch = static_cast<unsigned char *>(p);
+        s.num_sms = sms;
+        s.sm103 = major == 10 && minor == 3;
+        s.ready = true;
+    }
+    *out = &s;
+    return EJOIN_OK;
+}
+
+bool encode_bf16_tmap(CUtensorMap *m, const void *base, int64_t kp, int64_t rows, uint32_t box_rows)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return false;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(kp * 2)};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+ejoin_status st_of(cudaError_t e)
+{
+    if (e == cudaSuccess) return EJOIN_OK;
+    return e == cudaErrorMemoryAllocation ? EJOIN_ENOMEM : EJOIN_ECUDA;
+}
+
+}  // namespace
+
+extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float eps, ejoin_pair *d_pairs,
+                                               uint64_t capacity, uint64_t *count, void *stream)
+{
+    if (!count) return EJOIN_EINVAL;
+    *count = 0;
+    if (R.d != S.d || R.d < 1 || R.d > 4096 || R.n < 0 || S.n < 0 || R.ld < R.d || S.ld < S.d) return EJOIN_EINVAL;
+    if ((R.n && !R.x) || (S.n && !S.x) || (capacity && !d_pairs) || eps != eps) return EJOIN_EINVAL;
+    // size limits of the fixed scratch array
+    const int64_t kp = rup(R.d, 64);
+    const int64_t rowsA = rup(R.n > 0 ? R.n : 1, 256), rowsB = rup(S.n > 0 ? S.n : 1, 256);
+    if (R.n > EJOIN_STATIC_MAX_ROWS || S.n > EJOIN_STATIC_MAX_ROWS ||
+        (rowsA + rowsB) * kp > (int64_t)EJOIN_STATIC_MAX_OPERAND_ELEMS)
+        return EJOIN_EINVAL;
+    if (R.n == 0 || S.n == 0) return EJOIN_OK;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return EJOIN_ECUDA;
+    DeviceState *ds = nullptr;
+    ejoin_status st = device_setup(dev, &ds);
+    if (st != EJOIN_OK) return st;
+    if (!ds->sm103) return EJOIN_EUNSUPPORTED;
+
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *base = ds->scratch;
+    DevMisc *dm = reinterpret_cast<DevMisc *>(base + OFF_MISC);
+    float *invA = reinterpret_cast<float *>(base + OFF_INV_A);
+    float *invB = reinterpret_cast<float *>(base + OFF_INV_B);
+    uint2 *cand = reinterpret_cast<uint2 *>(base + OFF_CAND);
+    void *A = base + OFF_OPER;
+    void *B = base + OFF_OPER + (size_t)rowsA * kp * 2;
+    const float band = [&] {
+        // rigorous BF16 band (same expression as the context path's default)
+        const double u = 1.0 / 256.0, g = (double)kp / 16777216.0, small = 8.0 / 16777216.0;
+        return (float)(1.25 * (2 * u + u * u + 2 * g + small));
+    }();
+
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), s)) != cudaSuccess) return st_of(e);
+    if ((e = launch_set_count(&dm->n_sel[0], R.n, s)) != cudaSuccess) return st_of(e);
+    if ((e = launch_set_count(&dm->n_sel[1], S.n, s)) != cudaSuccess) return st_of(e);
+    if ((e = launch_normalize(FMT_BF16, R.x, R.ld, R.d, nullptr, &dm->n_sel[0], R.n, A, kp, (int)kp, invA, nullptr,
+                              &dm->status, ds->num_sms, s)) != cudaSuccess)
+        return st_of(e);
+    if ((e = launch_normalize(FMT_BF16, S.x, S.ld, S.d, nullptr, &dm->n_sel[1], S.n, B, kp, (int)kp, invB, nullptr,
+                              &dm->status, ds->num_sms, s)) != cudaSuccess)
+        return st_of(e);
+    CUtensorMap tmA, tmB;
+    if (!encode_bf16_tmap(&tmA, A, kp, rowsA, 128) || !encode_bf16_tmap(&tmB, B, kp, rowsB, 256)) return EJOIN_ECUDA;
+    if ((e = launch_sim_tc(0, &tmA, &tmB, (int)kp, &dm->n_sel[0], &dm->n_sel[1], eps - band, nullptr, nullptr, cand,
+                           EJOIN_STATIC_MAX_CANDIDATES, &dm->cand_count, &dm->status, 1ull << 31, 0, ds->num_sms,
+                           s)) != cudaSuccess)
+        return st_of(e);
+    if ((e = launch_rescore(cand, &dm->cand_count, EJOIN_STATIC_MAX_CANDIDATES, R.x, R.ld, S.x, S.ld, R.d, nullptr,
+                            nullptr, invA, invB, eps, 2e-5f, d_pairs, capacity, &dm->pair_count, &dm->band_count, 0,
+                            ds->num_sms, s)) != cudaSuccess)
+        return st_of(e);
+    DevMisc hm;
+    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return st_of(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return st_of(e);
+    if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+    if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+    if (hm.status) return EJOIN_ECUDA;
+    if (hm.cand_count > EJOIN_STATIC_MAX_CANDIDATES) return EJOIN_EOVERFLOW;  // *count stays 0: set incomplete
+    *count = hm.pair_count;
+    return hm.pair_count > capacity ? EJOIN_EOVERFLOW : EJOIN_OK;
+}
