@@ -93,7 +93,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -133,8 +133,9 @@ def make_workload(args, seed_offset=0):
     import ejoin_inputs as inputs
     if args.workload == "c2":
         w = inputs.c2_clustered_selection(threads=os.cpu_count() or 8)
-    elif args.workload == "c2-small":
-        w = inputs.c2_clustered_selection(nR=100_000, nS=20_000, threads=os.cpu_count() or 8)
+    elif args.workload == "c2-capture":
+        # same structure at 30 % of R: the size used for full ncu captures
+        w = inputs.c2_clustered_selection(nR=300_000, nS=100_000, threads=os.cpu_count() or 8)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     return w
@@ -215,7 +216,7 @@ def run_ejoin(args):
     S = torch.from_numpy(w.S).cuda()
     attr = torch.from_numpy(w.attrR).cuda() if w.attrR is not None else None
     selR = pkg.Sel(attr, w.opR, w.cR) if attr is not None else None
-    ctx = pkg.Ctx(device=local, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING)
+    ctx = pkg.Ctx(device=local, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING, group_m=args.group_m)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     for _ in range(args.warmup):
@@ -336,13 +337,14 @@ def run_ejoin(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ejoin", choices=["ejoin", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp8", "tf32", "f32"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2-small"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2-capture"])
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds of oracle work per reference step")
+    ap.add_argument("--group-m", type=int, default=0, help="contraction raster group width (0: auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")

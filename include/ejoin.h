@@ -80,6 +80,8 @@ typedef struct ejoin_config {
     uint32_t flags;          /* EJOIN_FLAG_* */
     uint64_t timeout_cycles; /* bound on every device-side spin-wait, in SM clock cycles
                                 (0: 2^31, about one second) */
+    int32_t group_m;         /* tensor-core contraction raster: row tiles per group (0: sized so
+                                that one group's FP32 rows take about 16 MB) */
 } ejoin_config;
 
 /* A relation: n rows of d FP32 values, row r at x + r * ld (ld >= d).
@@ -181,6 +183,69 @@ ejoin_status ejoin_threshold_host(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, floa
 
 /* Release a result buffer that the library allocated. */
 ejoin_status ejoin_pairs_free(ejoin_ctx *ctx, ejoin_pairs *pairs);
+
+/* ---------------------------------------------------------------------------
+ * Batched joins: many independent E-joins (each the operator above, with its
+ * own eps and its own, possibly very different, sizes) in one persistent
+ * tensor-core launch.  The rows of all jobs' R and S are normalised into two
+ * concatenated operands; a device job table maps the global tile space onto
+ * (job, row tile, column tile), so tiles of every job share one persistent
+ * grid (the tiles of different jobs are independent blocks of the
+ * decomposition of Sec. IV-C, Eq. (Block Matrix Dot Product Decomposition)).
+ * No selection predicates (apply ejoin_normalize-style compaction upstream).
+ * ------------------------------------------------------------------------- */
+typedef struct ejoin_job {
+    ejoin_rel R;  /* device rows of this job's R (all jobs of a batch share d) */
+    ejoin_rel S;  /* device rows of this job's S */
+    float eps;    /* this job's similarity threshold */
+} ejoin_job;
+
+/* One result record of a batched join: job index, original row ids, similarity. */
+typedef struct ejoin_batch_pair {
+    uint32_t job;
+    uint32_t i;
+    uint32_t j;
+    float sim;
+} ejoin_batch_pair;
+
+typedef struct ejoin_batch ejoin_batch;
+
+/* ejoin_batch_create flags */
+#define EJOIN_BATCH_GRAPH    0x1u /* capture the whole run in a CUDA graph (runs replay it) */
+#define EJOIN_BATCH_AUTOTUNE 0x2u /* time candidate raster widths once per size class and keep the fastest
+                                     (cached per process, and in the file named by EJOIN_TUNE_FILE) */
+
+typedef struct ejoin_batch_stats {
+    int32_t n_jobs;
+    int64_t total_tiles;
+    int64_t rows_r, rows_s;
+    int32_t group_m;      /* raster width in use */
+    int32_t graph;        /* 1 if runs replay a CUDA graph */
+    uint64_t candidate_capacity, pair_capacity;
+    float band;
+} ejoin_batch_stats;
+
+/* Plan a batch over the jobs' device inputs (the pointers are captured: the
+ * plan reads whatever those rows hold when it runs).  Runs the pipeline once
+ * to size the candidate and result buffers (synchronises), optionally
+ * autotunes, optionally captures a CUDA graph.  ctx must use BF16, e4m3 or
+ * TF32.  A later run whose counts exceed the sized buffers reports
+ * EJOIN_EOVERFLOW from ejoin_batch_wait (re-create the plan). */
+ejoin_status ejoin_batch_create(ejoin_ctx *ctx, const ejoin_job *jobs, int32_t n_jobs, uint32_t flags,
+                                ejoin_batch **out);
+
+/* Enqueue one run on the context's stream (a graph launch when captured); no host synchronisation. */
+ejoin_status ejoin_batch_run(ejoin_batch *batch);
+
+/* Wait for the enqueued runs; *count = result pairs of the last run. */
+ejoin_status ejoin_batch_wait(ejoin_batch *batch, uint64_t *count);
+
+/* Device buffer holding the last run's records (valid after ejoin_batch_wait). */
+ejoin_status ejoin_batch_result(const ejoin_batch *batch, const ejoin_batch_pair **d_pairs, uint64_t *capacity);
+
+ejoin_status ejoin_batch_info(const ejoin_batch *batch, ejoin_batch_stats *out);
+
+void ejoin_batch_destroy(ejoin_batch *batch);
 
 /* Statistics of the last call on ctx. */
 ejoin_status ejoin_last_stats(const ejoin_ctx *ctx, ejoin_stats *out);

@@ -90,6 +90,10 @@ def _ptr(a: Optional[np.ndarray], ctype):
 
 def _rows_f32(x: np.ndarray) -> np.ndarray:
     x = np.asarray(x)
+    if x.ndim == 2 and x.dtype == np.float32 and x.size == 0:
+        return x  # no rows: callers return before touching the data
+    if x.ndim == 2 and x.dtype == np.float32 and x.shape[0] == 1:
+        x = np.ascontiguousarray(x)  # the row stride of a one-row array is arbitrary
     if x.dtype != np.float32 or x.ndim != 2 or x.strides[1] != 4:
         raise TypeError("relation must be a 2-D float32 array with contiguous rows")
     return x
@@ -117,6 +121,8 @@ def join(R: np.ndarray, S: np.ndarray, eps: float, selR: Optional[Selection] = N
     S = _rows_f32(S)
     if R.shape[1] != S.shape[1]:
         raise ValueError("R and S must have the same dimension")
+    if R.shape[0] == 0 or S.shape[0] == 0:
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.float64)
     d = R.shape[1]
     ldR = R.strides[0] // 4
     ldS = S.strides[0] // 4
@@ -157,6 +163,8 @@ def sim_pairs(R: np.ndarray, S: np.ndarray, i: np.ndarray, j: np.ndarray, thread
     i = np.ascontiguousarray(i, dtype=np.uint32)
     j = np.ascontiguousarray(j, dtype=np.uint32)
     out = np.empty(len(i), dtype=np.float64)
+    if len(i) == 0:
+        return out
     lib.oracle_sim_pairs(_ptr(R, ctypes.c_float), R.strides[0] // 4, _ptr(S, ctypes.c_float),
                          S.strides[0] // 4, R.shape[1], _ptr(i, ctypes.c_uint32),
                          _ptr(j, ctypes.c_uint32), len(i), _ptr(out, ctypes.c_double), int(threads))

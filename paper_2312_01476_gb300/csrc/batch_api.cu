@@ -1,0 +1,394 @@
+// Batched E-joins: many independent joins (uneven, post-selection sizes) in
+// one persistent contraction launch, captured once in a CUDA graph.
+//
+// Every job is the operator of Sec. III-C (Eq. (E-theta-Join)) with its own
+// threshold.  The rows of all jobs' R (and S) are normalised into one
+// concatenated operand each, so one pair of TMA tensor maps covers the whole
+// batch; a device job table maps the global tile space onto (job, row tile,
+// column tile) (tiles of different jobs are independent blocks of the
+// decomposition of Eq. (Block Matrix Dot Product Decomposition)).  A sizing
+// run fixes the candidate and pair buffers, an optional autotuner picks the
+// raster width of the contraction, and the whole sequence (counter reset,
+// two normalisations, contraction, re-score) is captured into a CUDA graph
+// that later runs replay without any host synchronisation.
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "host_internal.h"
+
+using namespace ej;
+using namespace ej::host;
+
+struct ejoin_batch {
+    ejoin_ctx *ctx = nullptr;
+    int n_jobs = 0;
+    int d = 0;
+    int64_t kp = 0;
+    int fmt = FMT_BF16;
+    int kind = 0;
+    float band = 0.f;
+    int group_m = 16;
+    uint32_t flags = 0;
+    // device tables
+    Buf tile_off, a_off, b_off, nA, nB, thr, eps, xR, ldR, xS, ldS, rowoffA, rowoffB;
+    // operands and results
+    Buf A, B, invA, invB, scaleA, scaleB, misc, cand, pairs;
+    uint64_t cand_cap = 0, pair_cap = 0;
+    int64_t rowsA = 0, rowsB = 0, total_tiles = 0;
+    bool aligned = false;
+    CUtensorMap tmA{}, tmB{};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches_per_run = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t upload(Buf &b, const std::vector<T> &v)
+{
+    cudaError_t e = ensure(b, std::max<size_t>(v.size() * sizeof(T), 16));
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+// Enqueue one run of the batch pipeline on stream st (eager or under capture).
+cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_only = false)
+{
+    ejoin_ctx *c = b->ctx;
+    DevMisc *dm = (DevMisc *)b->misc.p;
+    cudaError_t e;
+    if (!contract_only) {
+        if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), st)) != cudaSuccess) return e;
+        if ((e = launch_normalize_batch(b->fmt, (const float *const *)b->xR.p, (const long long *)b->ldR.p,
+                                        (const long long *)b->rowoffA.p, b->n_jobs, b->rowsA, b->d, b->A.p,
+                                        (int)b->kp, (float *)b->invA.p, (float *)b->scaleA.p, &dm->status,
+                                        c->num_sms, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_normalize_batch(b->fmt, (const float *const *)b->xS.p, (const long long *)b->ldS.p,
+                                        (const long long *)b->rowoffB.p, b->n_jobs, b->rowsB, b->d, b->B.p,
+                                        (int)b->kp, (float *)b->invB.p, (float *)b->scaleB.p, &dm->status,
+                                        c->num_sms, st)) != cudaSuccess)
+            return e;
+    } else {
+        if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    }
+    BatchTables bt{(const long long *)b->tile_off.p, (const long long *)b->a_off.p, (const long long *)b->b_off.p,
+                   (const int *)b->nA.p, (const int *)b->nB.p, (const float *)b->thr.p, b->n_jobs};
+    if ((e = launch_sim_tc_batch(b->kind, &b->tmA, &b->tmB, (int)b->kp, bt, (const float *)b->scaleA.p,
+                                 (const float *)b->scaleB.p, (uint2 *)b->cand.p, b->cand_cap, &dm->cand_count,
+                                 &dm->status, c->timeout, c->num_sms, group_m, st)) != cudaSuccess)
+        return e;
+    if (contract_only) return cudaSuccess;
+    BatchRows br{(const float *const *)b->xR.p, (const long long *)b->ldR.p, (const float *const *)b->xS.p,
+                 (const long long *)b->ldS.p, (const long long *)b->a_off.p, (const long long *)b->b_off.p,
+                 (const float *)b->eps.p, b->n_jobs};
+    return launch_rescore_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, br, b->d,
+                                (const float *)b->invA.p, (const float *)b->invB.p, c->fp64_band,
+                                (BatchPair *)b->pairs.p, b->pair_cap, &dm->pair_count, &dm->band_count, b->aligned,
+                                c->num_sms, st);
+}
+
+ejoin_status read_misc(ejoin_batch *b, DevMisc &hm, cudaStream_t st)
+{
+    cudaError_t e = cudaMemcpyAsync(&hm, b->misc.p, sizeof(DevMisc), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+    if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+    if (hm.status) return EJOIN_ECUDA;
+    return EJOIN_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Cache of the fastest raster width per size class, in memory and (when the
+// environment variable EJOIN_TUNE_FILE names a file) on disk, one
+// "key value" line per entry.
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = std::getenv("EJOIN_TUNE_FILE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int v;
+    while (std::fscanf(f, "%255s %d", key, &v) == 2) g_tune[key] = v;
+    std::fclose(f);
+}
+
+void tune_store()
+{
+    const char *path = std::getenv("EJOIN_TUNE_FILE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : g_tune) std::fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+    std::fclose(f);
+}
+
+std::string size_class(const ejoin_batch *b)
+{
+    // kind, padded dim, log2 of jobs and of mean tiles per job
+    auto lg = [](double x) { return x < 1 ? 0 : (int)std::floor(std::log2(x)); };
+    char k[128];
+    std::snprintf(k, sizeof k, "batch:k%d:d%lld:j%d:t%d", b->kind, (long long)b->kp, lg(b->n_jobs),
+                  lg((double)b->total_tiles / std::max(1, b->n_jobs)));
+    return k;
+}
+
+ejoin_status autotune(ejoin_batch *b)
+{
+    const std::string key = size_class(b);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            b->group_m = it->second;
+            return EJOIN_OK;
+        }
+    }
+    ejoin_ctx *c = b->ctx;
+    const int cands[] = {4, 8, 16, 32, 64, 128};
+    float best = 1e30f;
+    int best_g = b->group_m;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return EJOIN_ECUDA;
+    for (int g : cands) {
+        float ms_sum = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            if (enqueue(b, c->stream, g, true) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return EJOIN_ECUDA;
+            }
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) ms_sum += ms;  // first repetition warms caches
+        }
+        if (ms_sum < best) {
+            best = ms_sum;
+            best_g = g;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->group_m = best_g;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_g;
+    tune_store();
+    return EJOIN_OK;
+}
+
+void destroy_batch(ejoin_batch *b)
+{
+    if (!b) return;
+    DeviceGuard g(b->ctx->device);
+    if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
+    cudaStreamSynchronize(b->ctx->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (Buf *x : {&b->tile_off, &b->a_off, &b->b_off, &b->nA, &b->nB, &b->thr, &b->eps, &b->xR, &b->ldR, &b->xS,
+                   &b->ldS, &b->rowoffA, &b->rowoffB, &b->A, &b->B, &b->invA, &b->invB, &b->scaleA, &b->scaleB,
+                   &b->misc, &b->cand, &b->pairs})
+        release(*x);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+ejoin_status ejoin_batch_create(ejoin_ctx *c, const ejoin_job *jobs, int32_t n_jobs, uint32_t flags,
+                                ejoin_batch **out)
+{
+    if (!c || !out || n_jobs < 1 || !jobs) return EJOIN_EINVAL;
+    *out = nullptr;
+    if (c->prec == EJOIN_F32) return EJOIN_EUNSUPPORTED;  // the batched contraction runs on tensor cores
+    const int d = jobs[0].R.d;
+    int64_t sumA = 0, sumB = 0;
+    bool aligned = d % 4 == 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ejoin_job &jb = jobs[j];
+        for (const ejoin_rel *r : {&jb.R, &jb.S}) {
+            if (r->d != d || r->d < 1 || r->d > 4096 || r->n < 0 || r->n > 0x7FFFFEFF || r->ld < r->d ||
+                (r->n > 0 && !r->x))
+                return EJOIN_EINVAL;
+            if ((reinterpret_cast<uintptr_t>(r->x) & 15) || (r->ld & 3)) aligned = false;
+        }
+        if (std::isnan(jb.eps)) return EJOIN_EINVAL;
+        sumA += jb.R.n;
+        sumB += jb.S.n;
+    }
+    if (sumA > 0xFFFFFEFFll || sumB > 0xFFFFFEFFll) return EJOIN_EINVAL;  // concatenated rows index with u32
+    DeviceGuard g(c->device);
+    ejoin_batch *b = new (std::nothrow) ejoin_batch();
+    if (!b) return EJOIN_ENOMEM;
+    b->ctx = c;
+    b->n_jobs = n_jobs;
+    b->d = d;
+    b->flags = flags;
+    b->fmt = fmt_of(c->prec);
+    b->kind = c->prec == EJOIN_BF16 ? 0 : (c->prec == EJOIN_FP8_E4M3 ? 1 : 2);
+    b->kp = ejoin_padded_dim(c->prec, d);
+    b->band = c->band_cfg >= 0.f ? c->band_cfg : default_band(c->prec, b->kp);
+    b->group_m = c->group_m > 0 ? c->group_m : 16;
+    b->aligned = aligned;
+    b->rowsA = sumA;
+    b->rowsB = sumB;
+
+    // host tables
+    std::vector<long long> tile_off(n_jobs + 1), a_off(n_jobs + 1), b_off(n_jobs + 1), ldR(n_jobs), ldS(n_jobs);
+    std::vector<int> nA(n_jobs), nB(n_jobs);
+    std::vector<float> thr(n_jobs), eps(n_jobs);
+    std::vector<const float *> xR(n_jobs), xS(n_jobs);
+    long long t = 0, ra = 0, rb = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const ejoin_job &jb = jobs[j];
+        tile_off[j] = t;
+        a_off[j] = ra;
+        b_off[j] = rb;
+        t += ((jb.R.n + 127) / 128) * ((jb.S.n + 255) / 256);
+        ra += jb.R.n;
+        rb += jb.S.n;
+        nA[j] = (int)jb.R.n;
+        nB[j] = (int)jb.S.n;
+        eps[j] = jb.eps;
+        thr[j] = jb.eps - b->band;
+        xR[j] = jb.R.x;
+        xS[j] = jb.S.x;
+        ldR[j] = jb.R.ld;
+        ldS[j] = jb.S.ld;
+    }
+    tile_off[n_jobs] = t;
+    a_off[n_jobs] = ra;
+    b_off[n_jobs] = rb;
+    b->total_tiles = t;
+    cudaError_t e = cudaSuccess;
+    ejoin_status st = EJOIN_OK;
+    auto fail = [&](ejoin_status s) {
+        destroy_batch(b);
+        return s;
+    };
+    if ((e = upload(b->tile_off, tile_off)) || (e = upload(b->a_off, a_off)) || (e = upload(b->b_off, b_off)) ||
+        (e = upload(b->nA, nA)) || (e = upload(b->nB, nB)) || (e = upload(b->thr, thr)) ||
+        (e = upload(b->eps, eps)) || (e = upload(b->xR, xR)) || (e = upload(b->xS, xS)) ||
+        (e = upload(b->ldR, ldR)) || (e = upload(b->ldS, ldS)) || (e = upload(b->rowoffA, a_off)) ||
+        (e = upload(b->rowoffB, b_off)))
+        return fail(from_cuda(e));
+    const size_t eb = fmt_bytes(b->fmt);
+    const int64_t pa = round_up(std::max<int64_t>(sumA, 1), 256), pb = round_up(std::max<int64_t>(sumB, 1), 256);
+    if ((e = ensure(b->A, (size_t)pa * b->kp * eb)) || (e = ensure(b->B, (size_t)pb * b->kp * eb)) ||
+        (e = ensure(b->invA, (size_t)pa * 4)) || (e = ensure(b->invB, (size_t)pb * 4)) ||
+        (e = ensure(b->misc, sizeof(DevMisc))))
+        return fail(from_cuda(e));
+    if (b->fmt == FMT_FP8 && ((e = ensure(b->scaleA, (size_t)pa * 4)) || (e = ensure(b->scaleB, (size_t)pb * 4))))
+        return fail(from_cuda(e));
+    if (!make_tmap(&b->tmA, b->A.p, b->fmt, b->kp, pa, 128) || !make_tmap(&b->tmB, b->B.p, b->fmt, b->kp, pb, 256))
+        return fail(EJOIN_ECUDA);
+
+    // sizing run: candidates, then pairs
+    b->cand_cap = std::max<uint64_t>(c->cap_hint, 1u << 20);
+    b->pair_cap = 0;
+    if ((e = ensure(b->cand, b->cand_cap * sizeof(uint2))) != cudaSuccess) return fail(from_cuda(e));
+    if ((e = ensure(b->pairs, 16)) != cudaSuccess) return fail(from_cuda(e));
+    DevMisc hm;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if ((e = enqueue(b, c->stream, b->group_m)) != cudaSuccess) return fail(from_cuda(e));
+        if ((st = read_misc(b, hm, c->stream)) != EJOIN_OK) return fail(st);
+        if (hm.cand_count <= b->cand_cap) break;
+        b->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+        if ((e = ensure(b->cand, b->cand_cap * sizeof(uint2))) != cudaSuccess) return fail(from_cuda(e));
+    }
+    if (hm.cand_count > b->cand_cap) return fail(EJOIN_EOVERFLOW);
+    b->pair_cap = std::max<uint64_t>(hm.cand_count, 1);
+    if ((e = ensure(b->pairs, b->pair_cap * sizeof(BatchPair))) != cudaSuccess) return fail(from_cuda(e));
+
+    if (flags & EJOIN_BATCH_AUTOTUNE) {
+        if ((st = autotune(b)) != EJOIN_OK) return fail(st);
+    }
+    if (flags & EJOIN_BATCH_GRAPH) {
+        if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return fail(from_cuda(e));
+        if ((e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+            return fail(from_cuda(e));
+        cudaError_t e2 = enqueue(b, b->cap_stream, b->group_m);
+        cudaError_t e3 = cudaStreamEndCapture(b->cap_stream, &b->graph);
+        if (e2 != cudaSuccess || e3 != cudaSuccess) return fail(from_cuda(e2 != cudaSuccess ? e2 : e3));
+        if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return fail(from_cuda(e));
+    }
+    b->launches_per_run = 4;  // two normalisations, contraction, re-score
+    *out = b;
+    return EJOIN_OK;
+}
+
+ejoin_status ejoin_batch_run(ejoin_batch *b)
+{
+    if (!b) return EJOIN_EINVAL;
+    DeviceGuard g(b->ctx->device);
+    cudaError_t e = b->exec ? cudaGraphLaunch(b->exec, b->ctx->stream) : enqueue(b, b->ctx->stream, b->group_m);
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_batch_wait(ejoin_batch *b, uint64_t *count)
+{
+    if (!b || !count) return EJOIN_EINVAL;
+    DeviceGuard g(b->ctx->device);
+    DevMisc hm;
+    ejoin_status st = read_misc(b, hm, b->ctx->stream);
+    *count = hm.pair_count;
+    if (st != EJOIN_OK) return st;
+    if (hm.cand_count > b->cand_cap || hm.pair_count > b->pair_cap) return EJOIN_EOVERFLOW;
+    b->ctx->stats = ejoin_stats{};
+    b->ctx->stats.candidates = hm.cand_count;
+    b->ctx->stats.pairs = hm.pair_count;
+    b->ctx->stats.fp64_rescored = hm.band_count;
+    b->ctx->stats.launches = b->launches_per_run;
+    b->ctx->stats.band = b->band;
+    return EJOIN_OK;
+}
+
+ejoin_status ejoin_batch_result(const ejoin_batch *b, const ejoin_batch_pair **d_pairs, uint64_t *capacity)
+{
+    if (!b || !d_pairs) return EJOIN_EINVAL;
+    *d_pairs = (const ejoin_batch_pair *)b->pairs.p;
+    if (capacity) *capacity = b->pair_cap;
+    return EJOIN_OK;
+}
+
+ejoin_status ejoin_batch_info(const ejoin_batch *b, ejoin_batch_stats *out)
+{
+    if (!b || !out) return EJOIN_EINVAL;
+    out->n_jobs = b->n_jobs;
+    out->total_tiles = b->total_tiles;
+    out->rows_r = b->rowsA;
+    out->rows_s = b->rowsB;
+    out->group_m = b->group_m;
+    out->graph = b->exec != nullptr;
+    out->candidate_capacity = b->cand_cap;
+    out->pair_capacity = b->pair_cap;
+    out->band = b->band;
+    return EJOIN_OK;
+}
+
+void ejoin_batch_destroy(ejoin_batch *b) { destroy_batch(b); }
+
+}  // extern "C"

@@ -16,16 +16,12 @@
 #include <cstring>
 #include <new>
 
-#include "ejoin_internal.cuh"
+#include "host_internal.h"
 
 using namespace ej;
 
-namespace {
-
-struct Buf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
+namespace ej {
+namespace host {
 
 cudaError_t ensure(Buf &b, size_t bytes)
 {
@@ -51,9 +47,6 @@ void release(Buf &b)
     b.bytes = 0;
 }
 
-struct Side {
-    Buf norm, inv, scale, ids, blk_counts, blk_offsets;
-};
 
 ejoin_status from_cuda(cudaError_t e)
 {
@@ -73,7 +66,6 @@ int fmt_of(int prec)
 
 size_t fmt_bytes(int fmt) { return fmt == FMT_BF16 ? 2 : (fmt == FMT_FP8 ? 1 : 4); }
 
-int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -108,45 +100,39 @@ bool make_tmap(CUtensorMap *m, const void *base, int fmt, int64_t kp, int64_t ro
     return r == CUDA_SUCCESS;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
+
+
+float default_band(int prec, int64_t kp)
+{
+    const double g = (double)kp * std::ldexp(1.0, -24);  // FP32 accumulation over kp terms
+    const double small = 8.0 * std::ldexp(1.0, -24);     // FP32 normalisation of both rows
+    double b;
+    switch (prec) {
+    case EJOIN_BF16: {
+        const double u = std::ldexp(1.0, -8);
+        b = 2 * u + u * u + 2 * g + small;
+        break;
     }
-    ~DeviceGuard()
-    {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    case EJOIN_TF32: {
+        const double u = std::ldexp(1.0, -10);  // conservative: truncation to 10 stored bits
+        b = 2 * u + u * u + 2 * g + small;
+        break;
     }
-};
+    case EJOIN_FP8_E4M3: {
+        const double u = std::ldexp(1.0, -4);
+        const double er = u + std::ldexp(1.0, -10) / 448.0 * std::sqrt((double)kp);
+        b = 2 * er + er * er + 2 * g + small;
+        break;
+    }
+    default: b = 2 * g + small; break;
+    }
+    return (float)(1.25 * b);
+}
 
-constexpr int N_EV = 8;
+}  // namespace host
+}  // namespace ej
 
-}  // namespace
-
-struct ejoin_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int prec = EJOIN_BF16;
-    float band_cfg = -1.f;
-    float fp64_band = 2e-5f;
-    uint64_t cap_hint = 1u << 20;
-    uint32_t flags = 0;
-    uint64_t timeout = 1ull << 31;
-    int num_sms = 0;
-    int cc_major = 0, cc_minor = 0;
-    Side side[2];
-    Buf misc;
-    Buf cand;
-    uint64_t cand_cap = 0;
-    Buf host_in[6];
-    Buf host_pairs;
-    cudaEvent_t ev[N_EV] = {};
-    bool events = false;
-    ejoin_stats stats{};
-};
+using namespace ej::host;
 
 extern "C" {
 
@@ -193,6 +179,7 @@ ejoin_status ejoin_create(ejoin_ctx **out, const ejoin_config *cfg)
         c->cap_hint = cfg->capacity_hint ? cfg->capacity_hint : (1u << 20);
         c->flags = cfg->flags;
         c->timeout = cfg->timeout_cycles ? cfg->timeout_cycles : (1ull << 31);
+        c->group_m = cfg->group_m;
     }
     if (c->prec < EJOIN_F32 || c->prec > EJOIN_TF32) {
         delete c;
@@ -307,32 +294,6 @@ bool same_sel(const ejoin_sel *a, const ejoin_sel *b)
     return a->attr == b->attr && a->bits == b->bits && (a->attr == nullptr || (a->op == b->op && a->c == b->c));
 }
 
-float default_band(int prec, int64_t kp)
-{
-    const double g = (double)kp * std::ldexp(1.0, -24);  // FP32 accumulation over kp terms
-    const double small = 8.0 * std::ldexp(1.0, -24);     // FP32 normalisation of both rows
-    double b;
-    switch (prec) {
-    case EJOIN_BF16: {
-        const double u = std::ldexp(1.0, -8);
-        b = 2 * u + u * u + 2 * g + small;
-        break;
-    }
-    case EJOIN_TF32: {
-        const double u = std::ldexp(1.0, -10);  // conservative: truncation to 10 stored bits
-        b = 2 * u + u * u + 2 * g + small;
-        break;
-    }
-    case EJOIN_FP8_E4M3: {
-        const double u = std::ldexp(1.0, -4);
-        const double er = u + std::ldexp(1.0, -10) / 448.0 * std::sqrt((double)kp);
-        b = 2 * er + er * er + 2 * g + small;
-        break;
-    }
-    default: b = 2 * g + small; break;
-    }
-    return (float)(1.25 * b);
-}
 
 // Selection + normalisation of one relation into side buffers (or caller buffers).
 ejoin_status prepare_side(ejoin_ctx *c, int which, const ejoin_rel &r, const ejoin_sel *sel, int fmt, int64_t kp,
@@ -442,7 +403,8 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
             const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
             ee = launch_sim_tc(kind, &tmA, &tmB, (int)kp, nA, nB, thr, (const float *)sa.scale.p,
                                (const float *)sb.scale.p, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count,
-                               &dm->status, c->timeout, 0, c->num_sms, c->stream);
+                               &dm->status, c->timeout, 0, c->num_sms,
+                               c->group_m > 0 ? c->group_m : default_group_m(kp), c->stream);
         }
         c->stats.launches += 1;
         return from_cuda(ee);

@@ -37,6 +37,39 @@ struct SelArgs {
     const uint32_t *bits;
 };
 
+// Job table of a batched contraction (device arrays).  Job j owns the tiles
+// [tile_off[j], tile_off[j+1]) of the global tile space, the operand rows
+// [a_off[j], a_off[j] + nA[j]) of the concatenated R operand and
+// [b_off[j], b_off[j] + nB[j]) of the concatenated S operand, and compares
+// against thr[j].
+struct BatchTables {
+    const long long *tile_off;
+    const long long *a_off;
+    const long long *b_off;
+    const int *nA;
+    const int *nB;
+    const float *thr;
+    int n_jobs;
+};
+
+// Per-job row sources of a batched re-score (device arrays).
+struct BatchRows {
+    const float *const *R;
+    const long long *ldR;
+    const float *const *S;
+    const long long *ldS;
+    const long long *a_off;
+    const long long *b_off;
+    const float *eps;
+    int n_jobs;
+};
+
+// One result record of a batched join.
+struct BatchPair {
+    uint32_t job, i, j;
+    float sim;
+};
+
 // Rows per selection block (count / scatter kernels).
 constexpr int SEL_THREADS = 512;
 constexpr int SEL_ITEMS = 16;
@@ -53,6 +86,9 @@ cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const u
                              const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
                              int kp, float *inv_norm, float *scale, unsigned *status, int num_sms,
                              cudaStream_t st);
+cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
+                                   int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
+                                   float *scale, unsigned *status, int num_sms, cudaStream_t st);
 cudaError_t launch_sim_simt(const float *A, const float *B, int kp, const long long *nA, const long long *nB,
                             float thr, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
                             int count_only, int num_sms, cudaStream_t st);
@@ -60,7 +96,26 @@ cudaError_t launch_sim_simt(const float *A, const float *B, int kp, const long l
 cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                           const long long *nA, const long long *nB, float thr, const float *scaleA,
                           const float *scaleB, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
-                          unsigned *status, uint64_t timeout, int count_only, int grid, cudaStream_t st);
+                          unsigned *status, uint64_t timeout, int count_only, int grid, int group_m,
+                          cudaStream_t st);
+// Batched contraction over a job table (BF16 / e4m3 / TF32 kinds as above).
+cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                                const BatchTables &bt, const float *scaleA, const float *scaleB, uint2 *cand,
+                                uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                                int grid, int group_m, cudaStream_t st);
+cudaError_t launch_rescore_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                 const BatchRows &br, int d, const float *invA, const float *invB, float fp64_band,
+                                 BatchPair *out, uint64_t out_cap, unsigned long long *out_count,
+                                 unsigned long long *band_count, bool aligned, int num_sms, cudaStream_t st);
+// Default row-tile group width of the contraction's raster for operands of
+// padded dimension kp: about 16 MB of FP32 input rows per group.
+inline int default_group_m(int64_t kp)
+{
+    int64_t g = (16ll << 20) / (128 * 4 * (kp > 0 ? kp : 1));
+    if (g < 8) g = 8;
+    if (g > 256) g = 256;
+    return (int)g;
+}
 size_t sim_tc_smem_bytes();
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                            const float *R, int64_t ldR, const float *S, int64_t ldS, int d,
@@ -200,6 +255,20 @@ __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&v)[32]
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Wait for outstanding tcgen05.ld and tie the wait to the destination
+// registers, so that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&v)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]),
+                   "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]),
+                   "+r"(v[22]), "+r"(v[23]), "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]),
+                   "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :
+                 : "memory");
+}
 
 #endif  // __CUDACC__
 

@@ -1,0 +1,76 @@
+// Host-side internals shared by the C ABI translation units: the context,
+// device buffers, tensor-map encoding, guard bands.
+#pragma once
+
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "ejoin_internal.cuh"
+
+namespace ej {
+namespace host {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Grow-only device buffer (contents zeroed on growth).
+cudaError_t ensure(Buf &b, size_t bytes);
+void release(Buf &b);
+ejoin_status from_cuda(cudaError_t e);
+int fmt_of(int prec);
+size_t fmt_bytes(int fmt);
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+// 2-D K-major operand [rows x kp] with a (128-byte x box_rows) box and 128-byte swizzle.
+bool make_tmap(CUtensorMap *m, const void *base, int fmt, int64_t kp, int64_t rows, uint32_t box_rows);
+// Rigorous default guard band of a precision at padded dimension kp.
+float default_band(int prec, int64_t kp);
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Side {
+    Buf norm, inv, scale, ids, blk_counts, blk_offsets;
+};
+
+constexpr int N_EV = 8;
+
+}  // namespace host
+}  // namespace ej
+
+struct ejoin_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int prec = EJOIN_BF16;
+    float band_cfg = -1.f;
+    float fp64_band = 2e-5f;
+    uint64_t cap_hint = 1u << 20;
+    uint32_t flags = 0;
+    uint64_t timeout = 1ull << 31;
+    int group_m = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    ej::host::Side side[2];
+    ej::host::Buf misc;
+    ej::host::Buf cand;
+    uint64_t cand_cap = 0;
+    ej::host::Buf host_in[6];
+    ej::host::Buf host_pairs;
+    cudaEvent_t ev[ej::host::N_EV] = {};
+    bool events = false;
+    ejoin_stats stats{};
+};

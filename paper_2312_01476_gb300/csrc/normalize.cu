@@ -130,6 +130,106 @@ __global__ void __launch_bounds__(SEL_THREADS) sel_scatter_kernel(SelArgs s, int
 
 __global__ void set_count_kernel(long long *p, long long v) { *p = v; }
 
+// Normalise one row (one warp): y = x / ||x|| (0 for a zero row), written as
+// FMT with zero padding to kp; 1/||x|| and the e4m3 scale are written by lane 0.
+template <int FMT>
+__device__ __forceinline__ void normalize_row(const float *__restrict__ src, int d, bool vec, void *__restrict__ out,
+                                              int64_t c, int64_t ld_out, int kp, float *__restrict__ inv_norm,
+                                              float *__restrict__ scale, unsigned *status, int lane)
+{
+    const int groups = kp >> 2;  // kp is a multiple of 32
+    auto load4 = [&](int k) -> float4 {
+        float4 v;
+        if (vec && k + 3 < d) {
+            v = __ldg(reinterpret_cast<const float4 *>(src + k));
+        } else {
+            v.x = k + 0 < d ? __ldg(src + k + 0) : 0.f;
+            v.y = k + 1 < d ? __ldg(src + k + 1) : 0.f;
+            v.z = k + 2 < d ? __ldg(src + k + 2) : 0.f;
+            v.w = k + 3 < d ? __ldg(src + k + 3) : 0.f;
+        }
+        return v;
+    };
+
+    // pass 1: sum of squares and max |x|
+    float ss = 0.f, mx = 0.f;
+    for (int g = lane; 4 * g < d; g += 32) {
+        const float4 v = load4(4 * g);
+        ss = fmaf(v.x, v.x, ss);
+        ss = fmaf(v.y, v.y, ss);
+        ss = fmaf(v.z, v.z, ss);
+        ss = fmaf(v.w, v.w, ss);
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    float inv;
+    bool bad = false;
+    if (isnan(ss) || !isfinite(mx)) {
+        // NaN or Inf in the row (fmaxf drops NaN, the sum of squares keeps it)
+        bad = true;
+        inv = 0.f;
+    } else if (isfinite(ss) && (ss >= 0x1p-100f || mx == 0.f)) {
+        inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
+    } else {
+        // overflow or underflow of the plain sum: rescale by max |x|
+        const float rm = 1.0f / mx;
+        float s2 = 0.f;
+        for (int g = lane; 4 * g < d; g += 32) {
+            const float4 v = load4(4 * g);
+            s2 = fmaf(v.x * rm, v.x * rm, s2);
+            s2 = fmaf(v.y * rm, v.y * rm, s2);
+            s2 = fmaf(v.z * rm, v.z * rm, s2);
+            s2 = fmaf(v.w * rm, v.w * rm, s2);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        inv = (1.0f / sqrtf(s2)) / mx;
+    }
+    if (bad && lane == 0) atomicOr(status, ERR_NONFINITE);
+
+    float sc = 1.f, rsc = 1.f;
+    if (FMT == FMT_FP8) {
+        const float ymax = mx * inv;  // max |y|
+        sc = ymax > 0.f ? ymax / 448.f : 1.f;
+        rsc = 1.0f / sc;
+        if (lane == 0) scale[c] = sc;
+    }
+    if (lane == 0 && inv_norm) inv_norm[c] = inv;
+
+    // pass 2: write the normalised row, zero padded to kp
+    for (int g = lane; g < groups; g += 32) {
+        const int k = 4 * g;
+        float4 v = k < d ? load4(k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v.x *= inv;
+        v.y *= inv;
+        v.z *= inv;
+        v.w *= inv;
+        if (FMT == FMT_F32) {
+            float *o = reinterpret_cast<float *>(out) + c * ld_out + k;
+            *reinterpret_cast<float4 *>(o) = v;
+        } else if (FMT == FMT_BF16) {
+            __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out) + c * ld_out + k;
+            __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+            uint2 u;
+            u.x = *reinterpret_cast<uint32_t *>(&lo);
+            u.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(o) = u;
+        } else {
+            __nv_fp8_storage_t *o = reinterpret_cast<__nv_fp8_storage_t *>(out) + c * ld_out + k;
+            const __nv_fp8x2_storage_t lo =
+                __nv_cvt_float2_to_fp8x2(make_float2(v.x * rsc, v.y * rsc), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi =
+                __nv_cvt_float2_to_fp8x2(make_float2(v.z * rsc, v.w * rsc), __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<uint32_t *>(o) = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+    }
+}
+
 // One warp per kept row c: source row ids[c] (or c), output row c.
 template <int FMT>
 __global__ void __launch_bounds__(256) normalize_kernel(const float *__restrict__ x, int64_t ld, int d,
@@ -145,102 +245,37 @@ __global__ void __launch_bounds__(256) normalize_kernel(const float *__restrict_
     int64_t n_rows = n_rows_dev ? (int64_t)*n_rows_dev : n_rows_max;
     if (n_rows > n_rows_max) n_rows = n_rows_max;
     const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-    const int groups = kp >> 2;  // kp is a multiple of 32
-
     for (int64_t c = warp_global; c < n_rows; c += n_warps) {
         const int64_t r = ids ? (int64_t)ids[c] : c;
-        const float *src = x + r * ld;
+        normalize_row<FMT>(x + r * ld, d, vec, out, c, ld_out, kp, inv_norm, scale, status, lane);
+    }
+}
 
-        auto load4 = [&](int k) -> float4 {
-            float4 v;
-            if (vec && k + 3 < d) {
-                v = __ldg(reinterpret_cast<const float4 *>(src + k));
-            } else {
-                v.x = k + 0 < d ? __ldg(src + k + 0) : 0.f;
-                v.y = k + 1 < d ? __ldg(src + k + 1) : 0.f;
-                v.z = k + 2 < d ? __ldg(src + k + 2) : 0.f;
-                v.w = k + 3 < d ? __ldg(src + k + 3) : 0.f;
-            }
-            return v;
-        };
-
-        // pass 1: sum of squares and max |x|
-        float ss = 0.f, mx = 0.f;
-        for (int g = lane; 4 * g < d; g += 32) {
-            const float4 v = load4(4 * g);
-            ss = fmaf(v.x, v.x, ss);
-            ss = fmaf(v.y, v.y, ss);
-            ss = fmaf(v.z, v.z, ss);
-            ss = fmaf(v.w, v.w, ss);
-            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+// Batched form: the rows of many relations go to one concatenated operand.
+// Global row g belongs to relation j with row_off[j] <= g < row_off[j + 1].
+template <int FMT>
+__global__ void __launch_bounds__(256) normalize_batch_kernel(const float *const *__restrict__ xs,
+                                                              const long long *__restrict__ lds,
+                                                              const long long *__restrict__ row_off, int n_rel,
+                                                              int d, void *__restrict__ out, int kp,
+                                                              float *__restrict__ inv_norm,
+                                                              float *__restrict__ scale, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = row_off[n_rel];
+    for (int64_t g = warp_global; g < total; g += n_warps) {
+        int lo = 0, hi = n_rel;  // row_off[lo] <= g < row_off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(row_off + mid) <= g) lo = mid;
+            else hi = mid;
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ss += __shfl_xor_sync(0xffffffffu, ss, o);
-            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        float inv;
-        bool bad = false;
-        if (isnan(ss) || !isfinite(mx)) {
-            // NaN or Inf in the row (fmaxf drops NaN, the sum of squares keeps it)
-            bad = true;
-            inv = 0.f;
-        } else if (isfinite(ss) && (ss >= 0x1p-100f || mx == 0.f)) {
-            inv = ss > 0.f ? 1.0f / sqrtf(ss) : 0.f;
-        } else {
-            // overflow or underflow of the plain sum: rescale by max |x|
-            const float rm = 1.0f / mx;
-            float s2 = 0.f;
-            for (int g = lane; 4 * g < d; g += 32) {
-                const float4 v = load4(4 * g);
-                s2 = fmaf(v.x * rm, v.x * rm, s2);
-                s2 = fmaf(v.y * rm, v.y * rm, s2);
-                s2 = fmaf(v.z * rm, v.z * rm, s2);
-                s2 = fmaf(v.w * rm, v.w * rm, s2);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            inv = (1.0f / sqrtf(s2)) / mx;
-        }
-        if (bad && lane == 0) atomicOr(status, ERR_NONFINITE);
-
-        float sc = 1.f, rsc = 1.f;
-        if (FMT == FMT_FP8) {
-            const float ymax = mx * inv;  // max |y|
-            sc = ymax > 0.f ? ymax / 448.f : 1.f;
-            rsc = 1.0f / sc;
-            if (lane == 0) scale[c] = sc;
-        }
-        if (lane == 0 && inv_norm) inv_norm[c] = inv;
-
-        // pass 2: write the normalised row, zero padded to kp
-        for (int g = lane; g < groups; g += 32) {
-            const int k = 4 * g;
-            float4 v = k < d ? load4(k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            v.x *= inv;
-            v.y *= inv;
-            v.z *= inv;
-            v.w *= inv;
-            if (FMT == FMT_F32) {
-                float *o = reinterpret_cast<float *>(out) + c * ld_out + k;
-                *reinterpret_cast<float4 *>(o) = v;
-            } else if (FMT == FMT_BF16) {
-                __nv_bfloat16 *o = reinterpret_cast<__nv_bfloat16 *>(out) + c * ld_out + k;
-                __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
-                __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
-                uint2 u;
-                u.x = *reinterpret_cast<uint32_t *>(&lo);
-                u.y = *reinterpret_cast<uint32_t *>(&hi);
-                *reinterpret_cast<uint2 *>(o) = u;
-            } else {
-                __nv_fp8_storage_t *o = reinterpret_cast<__nv_fp8_storage_t *>(out) + c * ld_out + k;
-                const __nv_fp8x2_storage_t lo =
-                    __nv_cvt_float2_to_fp8x2(make_float2(v.x * rsc, v.y * rsc), __NV_SATFINITE, __NV_E4M3);
-                const __nv_fp8x2_storage_t hi =
-                    __nv_cvt_float2_to_fp8x2(make_float2(v.z * rsc, v.w * rsc), __NV_SATFINITE, __NV_E4M3);
-                *reinterpret_cast<uint32_t *>(o) = (uint32_t)lo | ((uint32_t)hi << 16);
-            }
-        }
+        const float *x = xs[lo];
+        const int64_t ld = lds[lo];
+        const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+        normalize_row<FMT>(x + (g - row_off[lo]) * ld, d, vec, out, g, kp, kp, inv_norm, scale, status, lane);
     }
 }
 
@@ -295,6 +330,32 @@ cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const u
     case FMT_FP8:
         normalize_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
                                                                     ld_out, kp, inv_norm, scale, status);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
+                                   int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
+                                   float *scale, unsigned *status, int num_sms, cudaStream_t st)
+{
+    if (total_rows <= 0) return cudaSuccess;
+    int64_t blocks = (total_rows + 7) / 8;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    switch (fmt) {
+    case FMT_F32:
+        normalize_batch_kernel<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
+                                                                          inv_norm, scale, status);
+        break;
+    case FMT_BF16:
+        normalize_batch_kernel<FMT_BF16><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
+                                                                           inv_norm, scale, status);
+        break;
+    case FMT_FP8:
+        normalize_batch_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
+                                                                          inv_norm, scale, status);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -138,6 +138,301 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
     }
 }
 
+// Variant for d <= 128 * V with 16-byte aligned rows: each warp gathers the
+// rows of C candidates at once (V float4 per lane per row, all loads issued
+// before the first FMA), so that 2*C*V independent loads are in flight per
+// lane instead of a dependent chain per candidate.
+template <int V, int C>
+__global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
+    const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
+    const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
+    const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
+    const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
+    unsigned long long *out_count, unsigned long long *band_count, int count_only)
+{
+    static_assert(RS_PER_WARP % C == 0, "candidates per warp step");
+    __shared__ int wcnt[RS_WARPS];
+    __shared__ unsigned long long base_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t n = *cand_count;
+    if (n > cand_cap) n = cand_cap;
+    const int d4 = d >> 2;  // d is a multiple of 4 here
+    const double eps_d = (double)eps;
+
+    for (uint64_t blk = (uint64_t)blockIdx.x * RS_PER_BLOCK; blk < n; blk += (uint64_t)gridDim.x * RS_PER_BLOCK) {
+        bool my_emit = false;
+        uint32_t my_i = 0, my_j = 0;
+        float my_sim = 0.f;
+        int my_band = 0;
+        const uint64_t wbase = blk + (uint64_t)warp * RS_PER_WARP;
+        // lanes 0..RS_PER_WARP-1 fetch the warp's candidates and their ids / inverse norms
+        uint32_t ci = 0, cj = 0, gi = 0, gj = 0;
+        float sc = 0.f;
+        bool valid = false;
+        if (lane < RS_PER_WARP && wbase + lane < n) {
+            const uint2 c = cand[wbase + lane];
+            ci = c.x;
+            cj = c.y;
+            gi = idsR ? idsR[ci] : ci;
+            gj = idsS ? idsS[cj] : cj;
+            sc = invR[ci] * invS[cj];
+            valid = true;
+        }
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+#pragma unroll 1
+        for (int q0 = 0; q0 < RS_PER_WARP; q0 += C) {
+            if (!((vmask >> q0) & 1u)) break;  // warp-uniform
+            float4 a[C][V], b[C][V];
+            uint32_t ii[C], jj[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                ii[c] = __shfl_sync(0xffffffffu, gi, q0 + c);
+                jj[c] = __shfl_sync(0xffffffffu, gj, q0 + c);
+                const bool ok = (vmask >> (q0 + c)) & 1u;
+                const float4 *r = reinterpret_cast<const float4 *>(R + (int64_t)ii[c] * ldR);
+                const float4 *s = reinterpret_cast<const float4 *>(S + (int64_t)jj[c] * ldS);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int g = lane + 32 * v;
+                    const bool in = ok && g < d4;
+                    a[c][v] = in ? __ldg(r + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    b[c][v] = in ? __ldg(s + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+            float acc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                acc[c] = 0.f;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    acc[c] = fmaf(a[c][v].x, b[c][v].x, acc[c]);
+                    acc[c] = fmaf(a[c][v].y, b[c][v].y, acc[c]);
+                    acc[c] = fmaf(a[c][v].z, b[c][v].z, acc[c]);
+                    acc[c] = fmaf(a[c][v].w, b[c][v].w, acc[c]);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int q = q0 + c;
+                if (!((vmask >> q) & 1u)) break;
+                float sim = acc[c] * __shfl_sync(0xffffffffu, sc, q);
+                sim = fminf(1.f, fmaxf(-1.f, sim));
+                bool emit = sim >= eps;
+                int band = 0;
+                if (fabsf(sim - eps) < fp64_band) {
+                    const float *r = R + (int64_t)ii[c] * ldR;
+                    const float *s = S + (int64_t)jj[c] * ldS;
+                    double dd = 0.0, nr = 0.0, ns = 0.0;
+                    for (int kk = lane; kk < d; kk += 32) {
+                        const double x = (double)__ldg(r + kk), y = (double)__ldg(s + kk);
+                        dd = fma(x, y, dd);
+                        nr = fma(x, x, nr);
+                        ns = fma(y, y, ns);
+                    }
+                    dd = warp_sum_d(dd);
+                    nr = warp_sum_d(nr);
+                    ns = warp_sum_d(ns);
+                    double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
+                    s64 = fmin(1.0, fmax(-1.0, s64));
+                    emit = s64 >= eps_d;
+                    sim = (float)s64;
+                    band = 1;
+                }
+                if (lane == q) {
+                    my_emit = emit;
+                    my_i = ii[c];
+                    my_j = jj[c];
+                    my_sim = sim;
+                    my_band = band;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, my_emit);
+        const int nb = __popc(__ballot_sync(0xffffffffu, my_band != 0));
+        if (lane == 0) {
+            wcnt[warp] = __popc(m);
+            if (nb) atomicAdd(band_count, (unsigned long long)nb);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < RS_WARPS; ++w) {
+                const int c = wcnt[w];
+                wcnt[w] = run;
+                run += c;
+            }
+            base_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
+        }
+        __syncthreads();
+        if (my_emit && !count_only) {
+            const unsigned long long pos = base_s + wcnt[warp] + __popc(m & ((1u << lane) - 1u));
+            if (pos < out_cap) {
+                ejoin_pair p;
+                p.i = my_i;
+                p.j = my_j;
+                p.sim = my_sim;
+                out[pos] = p;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Batched re-score: candidate (a, b) holds rows of the concatenated operands;
+// job j owns a in [a_off[j], a_off[j+1]) and b in [b_off[j], b_off[j+1]).  The
+// FP32 rows are read from the job's own input (row a - a_off[j] of R_j, row
+// b - b_off[j] of S_j) and the job's eps decides; records are (job, i, j, sim).
+// V > 0: rows gathered as V float4 per lane (16-byte aligned inputs, d % 4 == 0,
+// d <= 128 V); V == 0: scalar loop for any d and alignment.
+template <int V>
+__global__ void __launch_bounds__(RS_WARPS * 32) rescore_batch_kernel(
+    const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
+    const BatchRows br, int d, const float *__restrict__ invA, const float *__restrict__ invB, float fp64_band,
+    BatchPair *__restrict__ out, uint64_t out_cap, unsigned long long *out_count, unsigned long long *band_count)
+{
+    __shared__ int wcnt[RS_WARPS];
+    __shared__ unsigned long long base_s;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t n = *cand_count;
+    if (n > cand_cap) n = cand_cap;
+    const int d4 = d >> 2;
+
+    for (uint64_t blk = (uint64_t)blockIdx.x * RS_PER_BLOCK; blk < n; blk += (uint64_t)gridDim.x * RS_PER_BLOCK) {
+        bool my_emit = false;
+        BatchPair my{};
+        int my_band = 0;
+        const uint64_t wbase = blk + (uint64_t)warp * RS_PER_WARP;
+        // lanes 0..RS_PER_WARP-1 resolve the warp's candidates: job, local ids, scale, eps
+        uint32_t gi = 0, gj = 0, job = 0;
+        float sc = 0.f, ej = 0.f;
+        bool valid = false;
+        if (lane < RS_PER_WARP && wbase + lane < n) {
+            const uint2 c = cand[wbase + lane];
+            int lo = 0, hi = br.n_jobs;  // a_off[lo] <= c.x < a_off[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(br.a_off + mid) <= (long long)c.x) lo = mid;
+                else hi = mid;
+            }
+            job = (uint32_t)lo;
+            gi = (uint32_t)(c.x - __ldg(br.a_off + lo));
+            gj = (uint32_t)(c.y - __ldg(br.b_off + lo));
+            sc = invA[c.x] * invB[c.y];
+            ej = __ldg(br.eps + lo);
+            valid = true;
+        }
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+#pragma unroll 1
+        for (int q = 0; q < RS_PER_WARP; ++q) {
+            if (!((vmask >> q) & 1u)) break;  // warp-uniform
+            const uint32_t jb = __shfl_sync(0xffffffffu, job, q);
+            const uint32_t ii = __shfl_sync(0xffffffffu, gi, q);
+            const uint32_t jj = __shfl_sync(0xffffffffu, gj, q);
+            const float eps = __shfl_sync(0xffffffffu, ej, q);
+            const float *r = br.R[jb] + (int64_t)ii * br.ldR[jb];
+            const float *s = br.S[jb] + (int64_t)jj * br.ldS[jb];
+            float acc = 0.f;
+            if constexpr (V > 0) {
+                float4 a[V], b[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int g = lane + 32 * v;
+                    a[v] = g < d4 ? __ldg(reinterpret_cast<const float4 *>(r) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    b[v] = g < d4 ? __ldg(reinterpret_cast<const float4 *>(s) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    acc = fmaf(a[v].x, b[v].x, acc);
+                    acc = fmaf(a[v].y, b[v].y, acc);
+                    acc = fmaf(a[v].z, b[v].z, acc);
+                    acc = fmaf(a[v].w, b[v].w, acc);
+                }
+            } else {
+                for (int kk = lane; kk < d; kk += 32) acc = fmaf(__ldg(r + kk), __ldg(s + kk), acc);
+            }
+            acc = warp_sum_f(acc);
+            float sim = fminf(1.f, fmaxf(-1.f, acc * __shfl_sync(0xffffffffu, sc, q)));
+            bool emit = sim >= eps;
+            int band = 0;
+            if (fabsf(sim - eps) < fp64_band) {
+                double dd = 0.0, nr = 0.0, ns = 0.0;
+                for (int kk = lane; kk < d; kk += 32) {
+                    const double x = (double)__ldg(r + kk), y = (double)__ldg(s + kk);
+                    dd = fma(x, y, dd);
+                    nr = fma(x, x, nr);
+                    ns = fma(y, y, ns);
+                }
+                dd = warp_sum_d(dd);
+                nr = warp_sum_d(nr);
+                ns = warp_sum_d(ns);
+                double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
+                s64 = fmin(1.0, fmax(-1.0, s64));
+                emit = s64 >= (double)eps;
+                sim = (float)s64;
+                band = 1;
+            }
+            if (lane == q) {
+                my_emit = emit;
+                my.job = jb;
+                my.i = ii;
+                my.j = jj;
+                my.sim = sim;
+                my_band = band;
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, my_emit);
+        const int nb = __popc(__ballot_sync(0xffffffffu, my_band != 0));
+        if (lane == 0) {
+            wcnt[warp] = __popc(m);
+            if (nb) atomicAdd(band_count, (unsigned long long)nb);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int w = 0; w < RS_WARPS; ++w) {
+                const int c = wcnt[w];
+                wcnt[w] = run;
+                run += c;
+            }
+            base_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
+        }
+        __syncthreads();
+        if (my_emit) {
+            const unsigned long long pos = base_s + wcnt[warp] + __popc(m & ((1u << lane) - 1u));
+            if (pos < out_cap) out[pos] = my;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_rescore_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                 const BatchRows &br, int d, const float *invA, const float *invB, float fp64_band,
+                                 BatchPair *out, uint64_t out_cap, unsigned long long *out_count,
+                                 unsigned long long *band_count, bool aligned, int num_sms, cudaStream_t st)
+{
+    if (cand_cap == 0) return cudaSuccess;
+    uint64_t blocks = (cand_cap + RS_PER_BLOCK - 1) / RS_PER_BLOCK;
+    const uint64_t lim = (uint64_t)num_sms * 8;
+    if (blocks > lim) blocks = lim;
+    const unsigned g = (unsigned)blocks;
+    const int T = RS_WARPS * 32;
+    // `aligned`: every job's rows start on 16 bytes and d % 4 == 0 (checked by the host)
+#define EJ_RB_ARGS cand, cand_count, cand_cap, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count
+    if (aligned && d <= 128) rescore_batch_kernel<1><<<g, T, 0, st>>>(EJ_RB_ARGS);
+    else if (aligned && d <= 256) rescore_batch_kernel<2><<<g, T, 0, st>>>(EJ_RB_ARGS);
+    else if (aligned && d <= 384) rescore_batch_kernel<3><<<g, T, 0, st>>>(EJ_RB_ARGS);
+    else if (aligned && d <= 512) rescore_batch_kernel<4><<<g, T, 0, st>>>(EJ_RB_ARGS);
+    else if (aligned && d <= 768) rescore_batch_kernel<6><<<g, T, 0, st>>>(EJ_RB_ARGS);
+    else if (aligned && d <= 1024) rescore_batch_kernel<8><<<g, T, 0, st>>>(EJ_RB_ARGS);
+    else rescore_batch_kernel<0><<<g, T, 0, st>>>(EJ_RB_ARGS);
+#undef EJ_RB_ARGS
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap, const float *R,
                            int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
                            const uint32_t *idsS, const float *invR, const float *invS, float eps, float fp64_band,
@@ -148,9 +443,29 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
     uint64_t blocks = (cand_cap + RS_PER_BLOCK - 1) / RS_PER_BLOCK;
     const uint64_t lim = (uint64_t)num_sms * 8;
     if (blocks > lim) blocks = lim;
-    rescore_kernel<<<(unsigned)blocks, RS_WARPS * 32, 0, st>>>(cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR,
-                                                               idsS, invR, invS, eps, fp64_band, out, out_cap,
-                                                               out_count, band_count, count_only);
+    const bool aligned = (d % 4 == 0) && (ldR % 4 == 0) && (ldS % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(R) % 16 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
+    const unsigned g = (unsigned)blocks;
+    const int T = RS_WARPS * 32;
+#define EJ_RESCORE_ARGS                                                                                              \
+    cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap, out_count, \
+        band_count, count_only
+    if (aligned && d <= 128) {
+        rescore_mlp_kernel<1, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    } else if (aligned && d <= 256) {
+        rescore_mlp_kernel<2, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    } else if (aligned && d <= 384) {
+        rescore_mlp_kernel<3, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    } else if (aligned && d <= 512) {
+        rescore_mlp_kernel<4, 2><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    } else if (aligned && d <= 768) {
+        rescore_mlp_kernel<6, 2><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    } else if (aligned && d <= 1024) {
+        rescore_mlp_kernel<8, 2><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    } else {
+        rescore_kernel<<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    }
+#undef EJ_RESCORE_ARGS
     return cudaGetLastError();
 }
 

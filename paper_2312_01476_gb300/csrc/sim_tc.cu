@@ -9,15 +9,16 @@
 // partition offsets m0, n0).  D never leaves the chip (Sec. V-B: the
 // "buffer" of a partition pair is a TMEM accumulator here).
 //
-// Structure (one persistent CTA per SM, 192 threads):
+// Structure (one persistent CTA per SM, 320 threads):
 //   warp 0      TMA producer: 128-byte-swizzled K-slices of the R tile
 //               (128 rows) and S tile (256 rows) into a 4-stage smem ring.
 //   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma per stage into one
 //               of two 128 x 256 FP32 accumulators (512 TMEM columns).
-//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, max-reduce for a
-//               fast reject, ballot-free per-lane masks, warp prefix sums,
-//               staging in shared memory, one global atomic per 1024
-//               candidates (or fewer at the end).
+//   warps 2..9  epilogue, two warps per TMEM lane quarter, each on 128 of the
+//               256 accumulator columns: software-pipelined tcgen05.ld of 32
+//               columns, tree max-reduce for a fast reject, per-lane match
+//               masks, warp prefix sums, staging in shared memory, one global
+//               atomic per flush of up to 512 candidates.
 // Every wait is bounded by `timeout` SM cycles; on expiry the CTA raises an
 // abort flag, records ERR_TIMEOUT, drains its in-flight copies and MMAs,
 // frees TMEM and exits.
@@ -31,16 +32,17 @@ constexpr int STAGES = 4;
 constexpr int ROW_BYTES = 128;  // K bytes of one stage row = one 128-byte swizzle atom
 constexpr int A_STAGE = BM * ROW_BYTES;
 constexpr int B_STAGE = BN * ROW_BYTES;
-constexpr int STAGING = 1024;  // candidate slots per epilogue warp
-constexpr int EPI_WARPS = 4;
+constexpr int STAGING = 512;  // candidate slots per epilogue warp
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, 128 accumulator columns each
+constexpr int EPI_CHUNKS = BN / 2 / 32;  // 32-column chunks per epilogue warp
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int GROUP_M = 16;
 
 constexpr int OFF_A = 0;
 constexpr int OFF_B = OFF_A + STAGES * A_STAGE;
 constexpr int OFF_STG = OFF_B + STAGES * B_STAGE;
-constexpr int OFF_BAR = OFF_STG + EPI_WARPS * STAGING * 8;
+constexpr int OFF_CTR = OFF_STG + EPI_WARPS * STAGING * 8;
+constexpr int OFF_BAR = OFF_CTR + EPI_WARPS * 4;
 constexpr int N_BARS = 2 * STAGES + 2 + 2 + 1;
 constexpr int OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr int SMEM_USED = OFF_MISC + 16;
@@ -90,19 +92,60 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
     }
 }
 
-// Tile t -> (m, n): groups of GROUP_M row tiles sweep all column tiles, so the
-// CTAs running concurrently share operand tiles in L2.
-__device__ __forceinline__ void tile_coords(long long t, long long tiles_m, long long tiles_n, long long &m,
-                                            long long &n)
+// Tile t -> (m, n): groups of group_m row tiles sweep all column tiles, so the
+// CTAs running concurrently share operand tiles in L2, and the candidates they
+// emit (which the re-score gathers in emission order) touch a bounded set of
+// FP32 input rows.
+__device__ __forceinline__ void tile_coords(long long t, long long tiles_m, long long tiles_n, int group_m,
+                                            long long &m, long long &n)
 {
-    const long long per_group = (long long)GROUP_M * tiles_n;
+    const long long per_group = (long long)group_m * tiles_n;
     const long long g = t / per_group;
-    const long long first = g * GROUP_M;
+    const long long first = g * group_m;
     long long gsz = tiles_m - first;
-    if (gsz > GROUP_M) gsz = GROUP_M;
+    if (gsz > group_m) gsz = group_m;
     const long long u = t - g * per_group;
     m = first + u % gsz;
     n = u / gsz;
+}
+
+// Where a tile of the global tile space lives: first operand rows of R and S,
+// valid extents inside the tile, threshold.
+struct TileInfo {
+    long long rowA, rowB;
+    int limA, limB;
+    float thr;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &bt, long long tiles_m,
+                                                long long tiles_n, long long nA, long long nB, float thr, int group_m)
+{
+    TileInfo ti;
+    long long m, n;
+    if constexpr (BATCH) {
+        int lo = 0, hi = bt.n_jobs;  // tile_off[lo] <= t < tile_off[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(bt.tile_off + mid) <= t) lo = mid;
+            else hi = mid;
+        }
+        const long long na = __ldg(bt.nA + lo), nb = __ldg(bt.nB + lo);
+        tile_coords(t - __ldg(bt.tile_off + lo), (na + BM - 1) / BM, (nb + BN - 1) / BN, group_m, m, n);
+        ti.rowA = __ldg(bt.a_off + lo) + m * BM;
+        ti.rowB = __ldg(bt.b_off + lo) + n * BN;
+        ti.limA = (int)min((long long)BM, na - m * BM);
+        ti.limB = (int)min((long long)BN, nb - n * BN);
+        ti.thr = __ldg(bt.thr + lo);
+    } else {
+        tile_coords(t, tiles_m, tiles_n, group_m, m, n);
+        ti.rowA = m * BM;
+        ti.rowB = n * BN;
+        ti.limA = (int)min((long long)BM, nA - m * BM);
+        ti.limB = (int)min((long long)BN, nB - n * BN);
+        ti.thr = thr;
+    }
+    return ti;
 }
 
 // Wait without the abort shortcut (used only to drain in-flight work at exit).
@@ -118,12 +161,13 @@ __device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity, u
 }
 }  // namespace
 
-template <int KIND>
+template <int KIND, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1)
     sim_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kp,
                   const long long *__restrict__ nA_ptr, const long long *__restrict__ nB_ptr, float thr,
                   const float *__restrict__ scaleA, const float *__restrict__ scaleB, uint2 *__restrict__ cand,
-                  uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only)
+                  uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only,
+                  int group_m, const BatchTables bt)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -138,9 +182,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_MISC + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long nA = *nA_ptr, nB = *nB_ptr;
+    const long long nA = BATCH ? 0 : *nA_ptr, nB = BATCH ? 0 : *nB_ptr;
     const long long tiles_m = (nA + BM - 1) / BM, tiles_n = (nB + BN - 1) / BN;
-    const long long total = tiles_m * tiles_n;
+    const long long total = BATCH ? __ldg(bt.tile_off + bt.n_jobs) : tiles_m * tiles_n;
     const int num_kb = kp / Kind<KIND>::ELEMS;
 
     if (threadIdx.x == 0) {
@@ -174,8 +218,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint64_t issued = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                long long m, n;
-                tile_coords(t, tiles_m, tiles_n, m, n);
+                const TileInfo ti = decode_tile<BATCH>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, timeout, abort_flag, status)) {
                         ok = false;
@@ -183,9 +226,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                     }
                     mbar_arrive_expect_tx(full_bar(stage), A_STAGE + B_STAGE);
                     tma_load_2d(sbase + OFF_A + stage * A_STAGE, &tmA, full_bar(stage), kb * Kind<KIND>::ELEMS,
-                                (int)(m * BM));
+                                (int)ti.rowA);
                     tma_load_2d(sbase + OFF_B + stage * B_STAGE, &tmB, full_bar(stage), kb * Kind<KIND>::ELEMS,
-                                (int)(n * BN));
+                                (int)ti.rowB);
                     ++issued;
                     if (++stage == STAGES) {
                         stage = 0;
@@ -247,9 +290,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
     } else {
         // ------------------------------------------------------------ epilogue
-        const int e = warp - 2;
-        const int q = warp & 3;  // TMEM lane quarter this warp may access
+        const int e = warp - 2;      // 0 .. EPI_WARPS-1
+        const int q = warp & 3;      // TMEM lane quarter this warp may access
+        const int half = e >> 2;     // which 128 accumulator columns
         uint2 *stg = reinterpret_cast<uint2 *>(smem + OFF_STG) + e * STAGING;
+        int *stg_ctr = reinterpret_cast<int *>(smem + OFF_CTR) + e;  // mirrors stg_cnt for slot claims
+        if (lane == 0) *stg_ctr = 0;
+        __syncwarp();
         int stg_cnt = 0;
         unsigned long long counted = 0;
         int acc = 0;
@@ -264,73 +311,134 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const unsigned long long p = base + (unsigned long long)x;
                 if (p < cap) cand[p] = stg[x];
             }
+            if (lane == 0) *stg_ctr = 0;
             __syncwarp();
             stg_cnt = 0;
         };
 
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-            long long m, n;
-            tile_coords(t, tiles_m, tiles_n, m, n);
+            const TileInfo ti = decode_tile<BATCH>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
+            const float thr_t = ti.thr;
             int ok = 0;
             if (lane == 0) ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, timeout, abort_flag, status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
 
-            const long long row = m * BM + q * 32 + lane;
-            const bool row_ok = row < nA;
+            const int row_local = q * 32 + lane;
+            const bool row_ok = row_local < ti.limA;
+            const long long row = ti.rowA + row_local;  // emitted operand row
+            const int colbase_local = half * (BN / 2);
+            const long long colbase = ti.rowB + colbase_local;
+            const uint32_t tbase =
+                tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN) + (uint32_t)(half * (BN / 2));
             float rs = 1.f;
-            if (KIND == 1) rs = row_ok ? scaleA[row] : 0.f;
-            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-
-#pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                const long long col0 = n * BN + c * 32;
-                uint32_t v[32];
-                tmem_ld_32cols(tbase + (uint32_t)(c * 32), v);
-                float csc = 1.f;
-                if (KIND == 1) {
-                    const long long cl = col0 + lane;
-                    csc = cl < nB ? scaleB[cl] : 0.f;
+            float csc[EPI_CHUNKS];
+#pragma unroll
+            for (int c = 0; c < EPI_CHUNKS; ++c) csc[c] = 1.f;
+            if (KIND == 1) {
+                rs = row_ok ? scaleA[row] : 0.f;
+#pragma unroll
+                for (int c = 0; c < EPI_CHUNKS; ++c) {
+                    const int cl = colbase_local + c * 32 + lane;
+                    csc[c] = cl < ti.limB ? scaleB[ti.rowB + cl] : 0.f;
                 }
-                tmem_wait_ld();
+            }
+
+            auto process = [&](uint32_t (&v)[32], int c) {
+                const long long col0 = colbase + c * 32;
+                const int left = ti.limB - (colbase_local + c * 32);  // valid columns in this chunk
                 float f[32];
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
                     f[k] = __uint_as_float(v[k]);
-                    if (KIND == 1) f[k] *= rs * __shfl_sync(0xffffffffu, csc, k);
+                    if (KIND == 1) f[k] *= rs * __shfl_sync(0xffffffffu, csc[c], k);
                 }
-                float mx = f[0];
+                // max tree: a8[g] = max of f[8g .. 8g+7]
+                float a8[4];
+                {
+                    float t[16], u[8];
 #pragma unroll
-                for (int k = 1; k < 32; ++k) mx = fmaxf(mx, f[k]);
-                const bool hit = row_ok && (mx >= thr);
-                if (__any_sync(0xffffffffu, hit)) {
-                    unsigned mask = 0u;
-                    if (row_ok) {
+                    for (int k = 0; k < 16; ++k) t[k] = fmaxf(f[2 * k], f[2 * k + 1]);
 #pragma unroll
-                        for (int k = 0; k < 32; ++k)
-                            if (f[k] >= thr && col0 + k < nB) mask |= 1u << k;
+                    for (int k = 0; k < 8; ++k) u[k] = fmaxf(t[2 * k], t[2 * k + 1]);
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) a8[g] = fmaxf(u[2 * g], u[2 * g + 1]);
+                }
+                const float mx = fmaxf(fmaxf(a8[0], a8[1]), fmaxf(a8[2], a8[3]));
+                if (!__any_sync(0xffffffffu, row_ok && mx >= thr_t)) return;
+                // slow path: per-lane match mask, built only for 8-column groups that hold a match
+                unsigned mask = 0u;
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if (__any_sync(0xffffffffu, row_ok && a8[g] >= thr_t)) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) mask |= (f[8 * g + k] >= thr_t ? 1u : 0u) << (8 * g + k);
                     }
-                    const int cnt = __popc(mask);
+                }
+                if (left < 32) mask &= left <= 0 ? 0u : ((1u << left) - 1u);
+                if (!row_ok) mask = 0u;
+                const int cnt = __popc(mask);
+                const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+                if (count_only) {
+                    counted += (unsigned long long)tot;
+                    return;
+                }
+                if (tot == 0) return;
+                if (tot > STAGING) {
+                    // denser than the staging area: claim space and write directly
                     int incl = cnt;
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const int y = __shfl_up_sync(0xffffffffu, incl, o);
                         if (lane >= o) incl += y;
                     }
-                    const int tot = __shfl_sync(0xffffffffu, incl, 31);
-                    if (count_only) {
-                        counted += (unsigned long long)tot;
-                    } else if (tot) {
-                        if (stg_cnt + tot > STAGING) flush();
-                        int pos = stg_cnt + incl - cnt;
-                        while (mask) {
-                            const int k = __ffs(mask) - 1;
-                            mask &= mask - 1u;
-                            stg[pos++] = make_uint2((uint32_t)row, (uint32_t)(col0 + k));
-                        }
-                        stg_cnt += tot;
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)tot);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    unsigned long long p = base + (unsigned long long)(incl - cnt);
+                    while (mask) {
+                        const int k = __ffs(mask) - 1;
+                        mask &= mask - 1u;
+                        if (p < cap) cand[p] = make_uint2((uint32_t)row, (uint32_t)(col0 + k));
+                        ++p;
                     }
+                    return;
+                }
+                if (stg_cnt + tot > STAGING) flush();
+                if (cnt) {
+                    int pos = atomicAdd(stg_ctr, cnt);  // shared-memory slot claim
+                    while (mask) {
+                        const int k = __ffs(mask) - 1;
+                        mask &= mask - 1u;
+                        stg[pos++] = make_uint2((uint32_t)row, (uint32_t)(col0 + k));
+                    }
+                }
+                stg_cnt += tot;
+                __syncwarp();
+            };
+
+            // software pipeline: the load of chunk c+1 is in flight while chunk c is scanned
+            uint32_t va[32], vb[32];
+            tmem_ld_32cols(tbase, va);
+            tmem_wait_ld_regs(va);
+#pragma unroll
+            for (int c = 0; c < EPI_CHUNKS; ++c) {
+                if (c + 1 < EPI_CHUNKS) {
+                    if (c & 1)
+                        tmem_ld_32cols(tbase + (uint32_t)((c + 1) * 32), va);
+                    else
+                        tmem_ld_32cols(tbase + (uint32_t)((c + 1) * 32), vb);
+                }
+                if (c & 1)
+                    process(vb, c);
+                else
+                    process(va, c);
+                if (c + 1 < EPI_CHUNKS) {
+                    if (c & 1)
+                        tmem_wait_ld_regs(va);
+                    else
+                        tmem_wait_ld_regs(vb);
                 }
             }
             tc_fence_before();
@@ -353,34 +461,67 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 size_t sim_tc_smem_bytes() { return (size_t)SMEM_BYTES; }
 
+template <int KIND, bool BATCH>
+static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                              const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
+                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                              int count_only, int grid, int group_m, const BatchTables &bt, cudaStream_t st)
+{
+    // the shared-memory opt-in is set once per device (and therefore never inside a stream capture
+    // that follows a first eager launch)
+    static unsigned long long configured = 0ull;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!((configured >> dev) & 1ull)) {
+        e = cudaFuncSetAttribute(sim_tc_kernel<KIND, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        configured |= 1ull << dev;
+    }
+    sim_tc_kernel<KIND, BATCH><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand,
+                                                                  cap, cand_count, status, timeout, count_only,
+                                                                  group_m < 1 ? 1 : group_m, bt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
                           const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
                           uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                          int count_only, int grid, cudaStream_t st)
+                          int count_only, int grid, int group_m, cudaStream_t st)
 {
-    cudaError_t e = cudaSuccess;
+    const BatchTables none{};
     switch (kind) {
     case 0:
-        e = cudaFuncSetAttribute(sim_tc_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        sim_tc_kernel<0><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap,
-                                                            cand_count, status, timeout, count_only);
-        break;
+        return launch_one<0, false>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
+                                    count_only, grid, group_m, none, st);
     case 1:
-        e = cudaFuncSetAttribute(sim_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        sim_tc_kernel<1><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap,
-                                                            cand_count, status, timeout, count_only);
-        break;
+        return launch_one<1, false>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
+                                    count_only, grid, group_m, none, st);
     case 2:
-        e = cudaFuncSetAttribute(sim_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        sim_tc_kernel<2><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap,
-                                                            cand_count, status, timeout, count_only);
-        break;
+        return launch_one<2, false>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
+                                    count_only, grid, group_m, none, st);
     default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+}
+
+cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                                const BatchTables &bt, const float *scaleA, const float *scaleB, uint2 *cand,
+                                uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                                int grid, int group_m, cudaStream_t st)
+{
+    switch (kind) {
+    case 0:
+        return launch_one<0, true>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
+                                   timeout, 0, grid, group_m, bt, st);
+    case 1:
+        return launch_one<1, true>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
+                                   timeout, 0, grid, group_m, bt, st);
+    case 2:
+        return launch_one<2, true>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
+                                   timeout, 0, grid, group_m, bt, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace ej

@@ -158,7 +158,7 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
     if (!encode_bf16_tmap(&tmA, A, kp, rowsA, 128) || !encode_bf16_tmap(&tmB, B, kp, rowsB, 256)) return EJOIN_ECUDA;
     if ((e = launch_sim_tc(0, &tmA, &tmB, (int)kp, &dm->n_sel[0], &dm->n_sel[1], eps - band, nullptr, nullptr, cand,
                            EJOIN_STATIC_MAX_CANDIDATES, &dm->cand_count, &dm->status, 1ull << 31, 0, ds->num_sms,
-                           s)) != cudaSuccess)
+                           default_group_m(kp), s)) != cudaSuccess)
         return st_of(e);
     if ((e = launch_rescore(cand, &dm->cand_count, EJOIN_STATIC_MAX_CANDIDATES, R.x, R.ld, S.x, S.ld, R.d, nullptr,
                             nullptr, invA, invB, eps, 2e-5f, d_pairs, capacity, &dm->pair_count, &dm->band_count, 0,

@@ -28,7 +28,7 @@ PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJ
 class ejoin_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("stream", ctypes.c_void_p), ("prec", ctypes.c_int32),
                 ("band", ctypes.c_float), ("fp64_band", ctypes.c_float), ("capacity_hint", ctypes.c_uint64),
-                ("flags", ctypes.c_uint32), ("timeout_cycles", ctypes.c_uint64)]
+                ("flags", ctypes.c_uint32), ("timeout_cycles", ctypes.c_uint64), ("group_m", ctypes.c_int32)]
 
 
 class ejoin_rel(ctypes.Structure):
@@ -56,6 +56,19 @@ class ejoin_stats(ctypes.Structure):
                 ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_h2d", ctypes.c_float), ("ms_d2h", ctypes.c_float), ("contract_retries", ctypes.c_int32)]
 
+
+class ejoin_job(ctypes.Structure):
+    _fields_ = [("R", ejoin_rel), ("S", ejoin_rel), ("eps", ctypes.c_float)]
+
+
+class ejoin_batch_stats(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_int32), ("total_tiles", ctypes.c_int64), ("rows_r", ctypes.c_int64),
+                ("rows_s", ctypes.c_int64), ("group_m", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("candidate_capacity", ctypes.c_uint64), ("pair_capacity", ctypes.c_uint64),
+                ("band", ctypes.c_float)]
+
+
+EJOIN_BATCH_GRAPH, EJOIN_BATCH_AUTOTUNE = 0x1, 0x2
 
 _lib = None
 
@@ -98,6 +111,19 @@ def load_library(path: str = LIB_PATH):
     lib.ejoin_strerror.argtypes = [ctypes.c_int]
     lib.ejoin_version.restype = ctypes.c_char_p
     lib.ejoin_version.argtypes = []
+    lib.ejoin_batch_create.restype = ctypes.c_int
+    lib.ejoin_batch_create.argtypes = [ctypes.c_void_p, P(ejoin_job), ctypes.c_int32, ctypes.c_uint32,
+                                       P(ctypes.c_void_p)]
+    lib.ejoin_batch_run.restype = ctypes.c_int
+    lib.ejoin_batch_run.argtypes = [ctypes.c_void_p]
+    lib.ejoin_batch_wait.restype = ctypes.c_int
+    lib.ejoin_batch_wait.argtypes = [ctypes.c_void_p, P(ctypes.c_uint64)]
+    lib.ejoin_batch_result.restype = ctypes.c_int
+    lib.ejoin_batch_result.argtypes = [ctypes.c_void_p, P(ctypes.c_void_p), P(ctypes.c_uint64)]
+    lib.ejoin_batch_info.restype = ctypes.c_int
+    lib.ejoin_batch_info.argtypes = [ctypes.c_void_p, P(ejoin_batch_stats)]
+    lib.ejoin_batch_destroy.restype = None
+    lib.ejoin_batch_destroy.argtypes = [ctypes.c_void_p]
     if path == LIB_PATH:
         _lib = lib
     return lib
@@ -139,11 +165,12 @@ class Ctx:
     """An ejoin context: device, stream, precision, bands, flags."""
 
     def __init__(self, device: int = 0, stream: Optional[int] = None, prec="bf16", band: float = -1.0,
-                 fp64_band: float = -1.0, capacity_hint: int = 0, flags: int = 0, timeout_cycles: int = 0):
+                 fp64_band: float = -1.0, capacity_hint: int = 0, flags: int = 0, timeout_cycles: int = 0,
+                 group_m: int = 0):
         lib = load_library()
         self.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
         cfg = ejoin_config(int(device), ctypes.c_void_p(stream or 0), self.prec, float(band), float(fp64_band),
-                           int(capacity_hint), int(flags), int(timeout_cycles))
+                           int(capacity_hint), int(flags), int(timeout_cycles), int(group_m))
         h = ctypes.c_void_p()
         _check(lib.ejoin_create(ctypes.byref(h), ctypes.byref(cfg)), "ejoin_create")
         self.handle = h
@@ -180,9 +207,12 @@ def _dev_rel(x) -> ejoin_rel:
     import torch
     if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
         raise TypeError("relation must be a 2-D float32 CUDA tensor")
-    if x.stride(1) != 1:
+    if x.shape[0] == 0 or x.shape[1] == 0:
+        return ejoin_rel(ctypes.c_void_p(x.data_ptr() or 0), x.shape[0], x.shape[1], x.shape[1])
+    if x.stride(1) != 1 and x.shape[1] > 1:
         raise TypeError("relation rows must be contiguous")
-    return ejoin_rel(ctypes.c_void_p(x.data_ptr()), x.shape[0], x.shape[1], x.stride(0))
+    ld = x.stride(0) if x.shape[0] > 1 else x.shape[1]
+    return ejoin_rel(ctypes.c_void_p(x.data_ptr()), x.shape[0], x.shape[1], ld)
 
 
 def _dev_sel(s: Optional[Sel]):
@@ -315,3 +345,80 @@ def ejoin_last_stats(ctx: Ctx) -> dict:
     st = ejoin_stats()
     _check(load_library().ejoin_last_stats(ctx.handle, ctypes.byref(st)), "ejoin_last_stats")
     return {name: getattr(st, name) for name, _ in ejoin_stats._fields_}
+
+
+class Batch:
+    """A planned batch of independent E-joins (ejoin_batch_create); runs replay a CUDA graph
+    when ``graph`` is set.  ``jobs``: list of (R, S, eps) with R, S float32 CUDA tensors."""
+
+    def __init__(self, ctx: Ctx, jobs, graph: bool = True, autotune: bool = False):
+        lib = load_library()
+        self.ctx = ctx
+        self._keep = [(R, S) for R, S, _ in jobs]
+        arr = (ejoin_job * len(jobs))()
+        for k, (R, S, eps) in enumerate(jobs):
+            arr[k].R = _dev_rel(R)
+            arr[k].S = _dev_rel(S)
+            arr[k].eps = float(eps)
+        flags = (EJOIN_BATCH_GRAPH if graph else 0) | (EJOIN_BATCH_AUTOTUNE if autotune else 0)
+        h = ctypes.c_void_p()
+        _check(lib.ejoin_batch_create(ctx.handle, arr, len(jobs), flags, ctypes.byref(h)), "ejoin_batch_create")
+        self.handle = h
+
+    def run(self):
+        _check(load_library().ejoin_batch_run(self.handle), "ejoin_batch_run")
+
+    def wait(self) -> int:
+        cnt = ctypes.c_uint64(0)
+        _check(load_library().ejoin_batch_wait(self.handle, ctypes.byref(cnt)), "ejoin_batch_wait")
+        return int(cnt.value)
+
+    def result(self, count: int):
+        """(job, i, j, sim) as torch tensors viewing the plan's device buffer."""
+        import torch
+        p = ctypes.c_void_p()
+        cap = ctypes.c_uint64(0)
+        _check(load_library().ejoin_batch_result(self.handle, ctypes.byref(p), ctypes.byref(cap)),
+               "ejoin_batch_result")
+        n = min(int(count), int(cap.value))
+        if n == 0:
+            z = torch.zeros(0, dtype=torch.int32, device="cuda")
+            return z, z, z, z.view(torch.float32)
+        # wrap the device buffer without copying it: 4 x 32-bit words per record
+        buf = _DevBuf(p.value, n * 16)
+        t = torch.as_tensor(buf, device="cuda").view(torch.int32).view(n, 4)
+        return t[:, 0], t[:, 1], t[:, 2], t[:, 3].view(torch.float32)
+
+    def info(self) -> dict:
+        st = ejoin_batch_stats()
+        _check(load_library().ejoin_batch_info(self.handle, ctypes.byref(st)), "ejoin_batch_info")
+        return {name: getattr(st, name) for name, _ in ejoin_batch_stats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().ejoin_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DevBuf:
+    """Minimal __cuda_array_interface__ over a device buffer owned by the library."""
+
+    def __init__(self, ptr: int, nbytes: int):
+        self.__cuda_array_interface__ = {"shape": (nbytes,), "typestr": "|u1", "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def ejoin_batch(ctx: Ctx, jobs, graph: bool = True, autotune: bool = False):
+    """One-shot batched join: plan, run, wait; returns (job, i, j, sim) host numpy arrays."""
+    b = Batch(ctx, jobs, graph=graph, autotune=autotune)
+    b.run()
+    n = b.wait()
+    job, i, j, sim = (x.cpu().numpy() for x in b.result(n))
+    b.close()
+    return job, i, j, sim

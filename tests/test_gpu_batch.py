@@ -1,0 +1,108 @@
+"""Batched E-joins (one persistent launch over a job table, CUDA-graph replay,
+autotuned raster): every job's pairs equal the FP64 oracle's for that job
+under the parity rule of parity_util."""
+import numpy as np
+import pytest
+
+import ejoin_inputs as inputs
+import oracle
+from parity_util import compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2312_01476_gb300 as pkg  # noqa: E402
+
+
+def make_jobs(seed, sizes, d, eps_lo=0.3, eps_hi=0.6, planted=True):
+    rng = np.random.default_rng(seed)
+    jobs_np = []
+    for k, (nR, nS) in enumerate(sizes):
+        R = rng.standard_normal((nR, d)).astype(np.float32)
+        S = rng.standard_normal((nS, d)).astype(np.float32)
+        if planted and nR and nS:
+            m = min(nR, nS, 20)
+            S[:m] = R[:m] + np.float32(0.4) * rng.standard_normal((m, d)).astype(np.float32)
+        eps = float(rng.uniform(eps_lo, eps_hi))
+        jobs_np.append((R, S, eps))
+    return jobs_np
+
+
+def check_batch(jobs_np, job, gi, gj, gs):
+    for k, (R, S, eps) in enumerate(jobs_np):
+        sel = job == k
+        oi, oj, os_ = oracle.join(R, S, eps)
+        compare(R, S, eps, gi[sel], gj[sel], gs[sel], oi, oj, os_)
+
+
+def to_dev(jobs_np):
+    return [(torch.from_numpy(R).cuda(), torch.from_numpy(S).cuda(), eps) for R, S, eps in jobs_np]
+
+
+SIZES = [(300, 700), (0, 50), (40, 0), (1, 1), (129, 257), (1000, 513), (37, 2000), (256, 256), (5, 900),
+         (777, 31)]
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "tf32"])
+def test_batch_matches_oracle_per_job(prec):
+    jobs_np = make_jobs(1, SIZES, 96)
+    with pkg.Ctx(device=0, prec=prec) as ctx:
+        job, gi, gj, gs = pkg.ejoin_batch(ctx, to_dev(jobs_np), graph=True)
+    assert len(job) > 100
+    check_batch(jobs_np, job, gi.view(np.uint32), gj.view(np.uint32), gs)
+
+
+def test_batch_graph_replay_is_stable_and_autotuned():
+    jobs_np = make_jobs(2, SIZES[::-1] + [(2000, 1500)], 128, 0.2, 0.5)
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        b = pkg.Batch(ctx, to_dev(jobs_np), graph=True, autotune=True)
+        info = b.info()
+        assert info["graph"] == 1 and info["group_m"] in (4, 8, 16, 32, 64, 128)
+        sets = []
+        for _ in range(3):
+            b.run()
+        n = b.wait()
+        for _ in range(2):
+            b.run()
+            n2 = b.wait()
+            assert n2 == n
+            job, gi, gj, gs = (x.cpu().numpy() for x in b.result(n2))
+            sets.append(set(zip(job.tolist(), gi.tolist(), gj.tolist())))
+        assert sets[0] == sets[1]
+        check_batch(jobs_np, job, gi.view(np.uint32), gj.view(np.uint32), gs)
+        b.close()
+
+
+def test_batch_unaligned_rows_use_the_generic_rescore():
+    rng = np.random.default_rng(3)
+    jobs_np = []
+    jobs_dev = []
+    for nR, nS in [(200, 300), (150, 90)]:
+        Rw = rng.standard_normal((nR, 67)).astype(np.float32)
+        Sw = rng.standard_normal((nS, 67)).astype(np.float32)
+        # d = 66 with ld = 67: rows are not 16-byte aligned
+        jobs_np.append((np.ascontiguousarray(Rw[:, :66]), np.ascontiguousarray(Sw[:, :66]), 0.3))
+        jobs_dev.append((torch.from_numpy(Rw).cuda()[:, :66], torch.from_numpy(Sw).cuda()[:, :66], 0.3))
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        job, gi, gj, gs = pkg.ejoin_batch(ctx, jobs_dev, graph=False)
+    check_batch(jobs_np, job, gi.view(np.uint32), gj.view(np.uint32), gs)
+
+
+def test_batch_clustered_lognormal_small():
+    # the shape of the batched workload at a scale the oracle finishes in seconds
+    rng = np.random.default_rng(inputs.seed_for(4))
+    d = 384
+    centres = inputs.sphere_centres(50, d, inputs.seed_for(4))
+    jobs_np = []
+    for k in range(16):
+        nR, nS = np.clip(np.round(np.exp(rng.normal(np.log(300), 1.0, 2))), 20, 3000).astype(int)
+        R = inputs.clustered(int(nR), d, centres, 0.3, inputs.seed_for(4) * 1000 + 2 * k, threads=1)
+        S = inputs.clustered(int(nS), d, centres, 0.3, inputs.seed_for(4) * 1000 + 2 * k + 1, threads=1)
+        jobs_np.append((R, S, float(rng.uniform(0.8, 0.95))))
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        job, gi, gj, gs = pkg.ejoin_batch(ctx, to_dev(jobs_np), graph=True)
+    assert len(job) > 1000
+    check_batch(jobs_np, job, gi.view(np.uint32), gj.view(np.uint32), gs)

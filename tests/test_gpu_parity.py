@@ -222,3 +222,16 @@ def test_normalize_entry_point():
             assert np.all(rows[:, 300:] == 0)
             exact = [1.0 / oracle.norm(X[r]) for r in np.nonzero(attr == 3)[0]]
             assert np.allclose(inv[:n].cpu().numpy(), exact, rtol=1e-6)
+
+
+@pytest.mark.parametrize("d", [4, 200, 384, 512, 700, 768, 1024, 1030])
+@pytest.mark.parametrize("prec", ["bf16", "f32"])
+def test_dims_cover_every_rescore_variant(prec, d):
+    # d picks the re-score kernel variant (row gathers of 1..8 float4 per lane, or the generic loop)
+    R, S = gauss(30 + d, 260, d), gauss(31 + d, 300, d)
+    S[:50] = R[:50] + np.float32(0.3) * gauss(32 + d, 50, d)
+    eps = 0.5 if d > 8 else 0.7
+    gi, gj, gs, st = run(prec, R, S, eps)
+    oi, oj, os_ = oracle.join(R, S, eps)
+    assert len(oi) >= 40
+    compare(R, S, eps, gi, gj, gs, oi, oj, os_)
