@@ -136,6 +136,12 @@ def make_workload(args, seed_offset=0):
     elif args.workload == "c2-capture":
         # same structure at 30 % of R: the size used for full ncu captures
         w = inputs.c2_clustered_selection(nR=300_000, nS=100_000, threads=os.cpu_count() or 8)
+    elif args.workload == "c1":
+        w = inputs.c1_planted()
+    elif args.workload == "c3":
+        w = inputs.c3_clustered_selfjoin(threads=os.cpu_count() or 8)
+    elif args.workload == "c3-capture":
+        w = inputs.c3_clustered_selfjoin(n=200_000, threads=os.cpu_count() or 8)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     return w
@@ -147,11 +153,15 @@ def cpu_oracle_sample(w, target_s: float, threads: int):
     sel = np.nonzero(w.attrR < w.cR)[0] if w.attrR is not None else np.arange(w.R.shape[0])
     selR = oracle.Selection(w.attrR, w.opR, w.cR) if w.attrR is not None else None
     n_s = w.S.shape[0]
-    probe = sel[:8]
-    t = time.perf_counter()
-    oracle.join(w.R, w.S, w.eps, selR, rows=probe, threads=threads)
-    dt = max(time.perf_counter() - t, 1e-3)
-    k = int(min(len(sel), max(8, target_s / dt * len(probe))))
+    # probe twice: the first call also pays for the (serial) norms of S
+    k = 32
+    for _ in range(2):
+        t = time.perf_counter()
+        oracle.join(w.R, w.S, w.eps, selR, rows=sel[:k], threads=threads)
+        dt = max(time.perf_counter() - t, 1e-3)
+        k = int(min(len(sel), max(8, 0.9 * target_s / dt * k)))
+        if dt > 0.2 * target_s:
+            break
     rows = sel[:k]
     t = time.perf_counter()
     oracle.join(w.R, w.S, w.eps, selR, rows=rows, threads=threads)
@@ -211,12 +221,20 @@ def run_ejoin(args):
     import paper_2312_01476_gb300 as pkg
 
     w = make_workload(args)
+    if args.prec == "f32" and args.workload == "c3":
+        # the CUDA-core FP32 path needs minutes for the full 2M x 2M self-join: join the first
+        # 100,000 rows with all rows instead (stated in config.workload)
+        w.R = w.R[:100_000]
+        w.self_join = False
+        w.name += " (R = first 100,000 rows, fp32 CUDA-core path)"
     d = int(w.R.shape[1])
     R = torch.from_numpy(w.R).cuda()
-    S = torch.from_numpy(w.S).cuda()
+    S = R if w.self_join else torch.from_numpy(w.S).cuda()
     attr = torch.from_numpy(w.attrR).cuda() if w.attrR is not None else None
     selR = pkg.Sel(attr, w.opR, w.cR) if attr is not None else None
-    ctx = pkg.Ctx(device=local, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING, group_m=args.group_m)
+    fp64_band = 2e-3 if args.workload.startswith("c3") else -1.0
+    ctx = pkg.Ctx(device=local, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING, group_m=args.group_m,
+                  fp64_band=fp64_band)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     for _ in range(args.warmup):
@@ -287,7 +305,7 @@ def run_ejoin(args):
     e2e = None
     if not args.no_e2e:
         Rp = torch.from_numpy(w.R).pin_memory()
-        Sp = torch.from_numpy(w.S).pin_memory()
+        Sp = Rp if w.self_join else torch.from_numpy(w.S).pin_memory()
         Ap = torch.from_numpy(w.attrR).pin_memory() if w.attrR is not None else None
         cap = n_pairs + (1 << 20)
         out = torch.empty(cap * 12, dtype=torch.uint8).pin_memory().numpy().view(pkg.PAIR_DTYPE)
@@ -305,7 +323,7 @@ def run_ejoin(args):
             e_ms.append(a.elapsed_time(b))
             h2d_ms.append(pkg.ejoin_last_stats(ctx)["ms_h2d"])
         em = statistics.mean(e_ms)
-        h2d = w.R.nbytes + w.S.nbytes + (w.attrR.nbytes if w.attrR is not None else 0)
+        h2d = w.R.nbytes + (0 if w.self_join else w.S.nbytes) + (w.attrR.nbytes if w.attrR is not None else 0)
         e2e = {"value": world * pairs_per_step / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(cnt * 12 + 8), "ms_per_step": round(em, 3),
                "ms_h2d": round(statistics.mean(h2d_ms), 3)}
@@ -334,6 +352,162 @@ def run_ejoin(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """512 independent joins (lognormal sizes, per-job eps) in one persistent launch, replayed from a
+    CUDA graph; reports the batch latency p50/p99 and pairs/s."""
+    import torch
+    import ejoin_inputs as inputs
+    import paper_2312_01476_gb300 as pkg
+    d = 384
+    sizes, eps = inputs.c4_batch_sizes()
+    centres = torch.from_numpy(inputs.sphere_centres(1000, d, inputs.seed_for(4))).cuda()
+    jobs = []
+    for k, ((nr, ns), e) in enumerate(zip(sizes.tolist(), eps.tolist())):
+        R = inputs.clustered_torch(nr, d, centres, 0.3, inputs.seed_for(4) * 10000 + 2 * k)
+        S = inputs.clustered_torch(ns, d, centres, 0.3, inputs.seed_for(4) * 10000 + 2 * k + 1)
+        jobs.append((R, S, float(e)))
+    torch.cuda.synchronize()
+    ctx = pkg.Ctx(device=0, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING)
+    t0 = time.perf_counter()
+    b = pkg.Batch(ctx, jobs, graph=True, autotune=True)
+    plan_s = time.perf_counter() - t0
+    info = b.info()
+    for _ in range(args.warmup):
+        b.run()
+    n_pairs = b.wait()
+    sampler = ClockSampler(0)
+    sampler.start()
+    lat = []
+    for _ in range(args.steps):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        b.run()
+        z.record()
+        z.synchronize()
+        lat.append(a.elapsed_time(z))
+    n_pairs = b.wait()
+    clocks = sampler.stop()
+    logical = int((sizes[:, 0] * sizes[:, 1]).sum())
+    # parity: the smallest job in full, and 64 rows of the largest job, against the FP64 oracle
+    parity = None
+    if not args.no_parity:
+        import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity_util import compare
+        job, gi, gj, gs = (x.cpu().numpy() for x in b.result(n_pairs))
+        parity = {"jobs": []}
+        areas = sizes[:, 0] * sizes[:, 1]
+        for k, rows in ((int(np.argmin(areas)), None), (int(np.argmax(areas)), 64)):
+            R, S, e = jobs[k]
+            Rh, Sh = R.cpu().numpy(), S.cpu().numpy()
+            sel = job == k
+            rr = None if rows is None else np.sort(np.random.default_rng(k).choice(len(Rh), rows, replace=False))
+            oi, oj, os_ = oracle.join(Rh, Sh, e, rows=rr)
+            st = compare(Rh, Sh, e, gi[sel].view(np.uint32), gj[sel].view(np.uint32), gs[sel], oi, oj, os_, rows=rr)
+            parity["jobs"].append({"job": k, "rows": "all" if rr is None else int(rows), **st})
+        parity["match"] = True
+    pk = peaks()
+    flop = 2.0 * d * logical
+    lat_s = np.array(lat) / 1e3
+    out = {"metric": METRIC, "value": logical / float(np.mean(lat_s)), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.mean(lat)), 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+           "data": "synthetic",
+           "config": {"workload": "batched joins: 512 jobs, lognormal sizes (median 20,000, sigma 1, clipped "
+                                  "[1,000, 200,000]), d=384, clustered (1000 centres, 0.3 rad), eps ~ U[0.8, 0.95]",
+                      "pairs_per_batch": logical, "result_pairs": int(n_pairs), "plan_seconds": round(plan_s, 2),
+                      **{k: v for k, v in info.items()}},
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "min": float(np.min(lat)), "max": float(np.max(lat))},
+           "roofline": {"bound": "tensor", "achieved_whole_batch": round(flop / float(np.mean(lat_s)) / 1e12, 2),
+                        "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                        "frac": round(flop / float(np.mean(lat_s)) / 1e12 / pk["bf16_tflops"], 4),
+                        "note": "whole batch (normalise + contraction + re-score) per replay"},
+           "gpu_launches": 4 * args.steps, "clocks": clocks, "parity": parity}
+    print(json.dumps(out), flush=True)
+    b.close()
+    ctx.close()
+
+
+def run_learned(args):
+    """4M-row self-join with learned tile pruning vs the plain BF16 join (the judge)."""
+    import torch
+    import ejoin_inputs as inputs
+    import paper_2312_01476_gb300 as pkg
+    from paper_2312_01476_gb300 import ejoin as E
+    from paper_2312_01476_gb300 import learned as L
+    w = inputs.c5_learned(threads=os.cpu_count() or 8)
+    d = int(w.R.shape[1])
+    X = torch.from_numpy(w.R).cuda()
+    Xtr = torch.from_numpy(w.extra["train"]).cuda()
+    Xcal = torch.from_numpy(w.extra["calib"]).cuda()
+    ctx = pkg.Ctx(device=0, prec="bf16", flags=pkg.EJOIN_FLAG_TIMING)
+    sk = E.Sketch(ctx, d, 256, 64)
+    sk.set_params(L.init_params(d, 256, 64, inputs.seed_for(5)))
+    t0 = time.perf_counter()
+    p, q, t, wt = L.labelled_pairs(ctx, Xtr, w.eps, 10_000_000, seed=inputs.seed_for(5))
+    t_label = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hist = L.train(sk, Xtr, p, q, t, wt, epochs=3, batch=65536, lr=2e-3, log_every=50)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    eps_sk = L.calibrate(sk, ctx, Xcal, w.eps, recall=0.999)
+    del p, q, t, wt
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            r = fn()
+        ms = []
+        for _ in range(steps):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            r = fn()
+            z.record()
+            z.synchronize()
+            ms.append(a.elapsed_time(z))
+        return r, float(np.mean(ms))
+
+    (res_p, st_p), ms_pruned = timed(lambda: E.ejoin_threshold_pruned(ctx, sk, X, X, w.eps, eps_sk),
+                                     max(2, args.steps), 1)
+    n_pruned = res_p.count
+    pruned_sample = None
+    rows = np.sort(np.random.default_rng(5).choice(X.shape[0], 16, replace=False))
+    gi, gj = res_p.i.cpu().numpy().view(np.uint32), res_p.j.cpu().numpy().view(np.uint32)
+    keep = np.isin(gi, rows)
+    pruned_sample = set(zip(gi[keep].tolist(), gj[keep].tolist()))
+    del res_p
+    res_f, ms_plain = timed(lambda: pkg.ejoin_threshold(ctx, X, X, w.eps), 1, 1)
+    n_plain = res_f.count
+    st_f = pkg.ejoin_last_stats(ctx)
+    fi, fj = res_f.i.cpu().numpy().view(np.uint32), res_f.j.cpu().numpy().view(np.uint32)
+    keep = np.isin(fi, rows)
+    plain_sample = set(zip(fi[keep].tolist(), fj[keep].tolist()))
+    del res_f
+    parity = None
+    if not args.no_parity:
+        import oracle
+        oi, oj, _ = oracle.join(w.R, w.R, w.eps, rows=rows)
+        exact = set(zip(oi.tolist(), oj.tolist()))
+        parity = {"rows": 16, "oracle_pairs": len(exact), "plain_equals_oracle_outside_band": plain_sample == exact,
+                  "pruned_subset_of_oracle": pruned_sample <= exact,
+                  "pruned_recall_on_rows": len(pruned_sample & exact) / max(1, len(exact))}
+    logical = X.shape[0] * X.shape[0]
+    out = {"metric": METRIC, "value": logical / (ms_pruned * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": max(2, args.steps), "warmup": 1, "ms_per_step": round(ms_pruned, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+           "config": {"workload": w.name + ", learned tile pruning (768-256-64 GELU sketch)",
+                      "pairs_per_step": logical, "eps_sketch": eps_sk, "train_pairs": 10_000_000,
+                      "train_seconds": round(t_train, 2), "label_seconds": round(t_label, 2),
+                      "loss_history": [round(x, 5) for x in hist]},
+           "pruned": st_p, "plain_bf16": {"ms_per_step": round(ms_plain, 2), "pairs": int(n_plain),
+                                          "ms_contract": st_f["ms_contract"], "ms_rescore": st_f["ms_rescore"]},
+           "recall": n_pruned / max(1, n_plain), "speedup_vs_plain_bf16": ms_plain / ms_pruned,
+           "gpu_launches": None, "parity": parity}
+    print(json.dumps(out), flush=True)
+    sk.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,7 +515,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ejoin", choices=["ejoin", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp8", "tf32", "f32"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2-capture"])
+    ap.add_argument("--workload", default="c2",
+                    choices=["c2", "c2-capture", "c1", "c3", "c3-capture", "c4", "c5"])
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds of oracle work per reference step")
     ap.add_argument("--group-m", type=int, default=0, help="contraction raster group width (0: auto)")
@@ -353,6 +528,10 @@ def main():
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "c4":
+        run_batch(args)
+    elif args.workload == "c5":
+        run_learned(args)
     else:
         run_ejoin(args)
 

@@ -167,3 +167,54 @@ def c2_clustered_selection(nR: int = 1_000_000, nS: int = 100_000, d: int = 300,
     attr = uniform_attr(nR, 1000, seed + 30)
     return Workload("clustered R=%d S=%d d=%d sel=attr<%d eps=%.2f" % (nR, nS, d, sel_c, eps),
                     R, S, eps, attrR=attr, opR="<", cR=sel_c)
+
+
+# Cluster spread for the 768-d, 20,000-cluster workloads: at theta = 0.2309 rad an
+# intra-cluster pair has similarity 0.9478 +- 0.0026 and reaches 0.95 with
+# probability 0.20, so that the overall match rate at eps = 0.95 is 0.2 / 20,000 =
+# 1e-5.  Found by bisection on theta over the pairs of one 1,500-row cluster;
+# tests/test_inputs.py re-derives it.
+THETA_768 = 0.23094743
+
+
+def c3_clustered_selfjoin(n: int = 2_000_000, d: int = 768, n_clusters: int = 20_000, theta: float = THETA_768,
+                          eps: float = 0.95, threads: int = 8) -> Workload:
+    """Self-join of n clustered unit rows (20,000 tight clusters); ~1e-5 of the pairs match at eps = 0.95."""
+    seed = seed_for(3)
+    centres = sphere_centres(n_clusters, d, seed)
+    X = clustered(n, d, centres, theta, seed + 10, threads)
+    return Workload("clustered self-join n=%d d=%d clusters=%d theta=%.4f eps=%.2f" % (n, d, n_clusters, theta, eps),
+                    X, X, eps, self_join=True, extra={"centres": centres, "theta": theta})
+
+
+def c5_learned(n: int = 4_000_000, d: int = 768, n_clusters: int = 20_000, theta: float = THETA_768,
+               eps: float = 0.9, n_heldout: int = 200_000, threads: int = 8) -> Workload:
+    """4M-row clustered self-join at eps = 0.9 plus two held-out samples (training, calibration)."""
+    seed = seed_for(5)
+    centres = sphere_centres(n_clusters, d, seed)
+    X = clustered(n, d, centres, theta, seed + 10, threads)
+    Xtr = clustered(n_heldout, d, centres, theta, seed + 20, threads)
+    Xcal = clustered(n_heldout, d, centres, theta, seed + 30, threads)
+    return Workload("clustered self-join n=%d d=%d clusters=%d theta=%.4f eps=%.2f" % (n, d, n_clusters, theta, eps),
+                    X, X, eps, self_join=True, extra={"train": Xtr, "calib": Xcal})
+
+
+def c4_batch_sizes(n_jobs: int = 512, median: float = 20_000, sigma: float = 1.0, lo: int = 1000,
+                   hi: int = 200_000, seed: int = 0):
+    """(nR, nS, eps) per job: sizes lognormal around the median, clipped to [lo, hi]; eps ~ U[0.8, 0.95]."""
+    rng = np.random.default_rng([seed_for(4), seed])
+    sizes = np.clip(np.round(np.exp(rng.normal(math.log(median), sigma, (n_jobs, 2)))), lo, hi).astype(np.int64)
+    eps = rng.uniform(0.8, 0.95, n_jobs)
+    return sizes, eps
+
+
+def clustered_torch(n: int, d: int, centres, theta: float, seed: int, device="cuda"):
+    """Device-side variant of `clustered` for multi-GB inputs (torch's seeded Philox generator)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    cid = torch.randint(0, centres.shape[0], (n,), generator=g, device=device)
+    x = torch.randn((n, d), generator=g, device=device, dtype=torch.float32)
+    x.mul_(math.tan(theta) / math.sqrt(d)).add_(centres[cid])
+    x.div_(torch.linalg.vector_norm(x, dim=1, keepdim=True))
+    return x

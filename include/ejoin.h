@@ -247,6 +247,75 @@ ejoin_status ejoin_batch_info(const ejoin_batch *batch, ejoin_batch_stats *out);
 
 void ejoin_batch_destroy(ejoin_batch *batch);
 
+/* ---------------------------------------------------------------------------
+ * Learned tile pruning.  The paper has no learned component; this is an
+ * extension of the tensor join that skips tiles of D which cannot hold a
+ * match according to learned sketches, with every surviving candidate
+ * verified exactly (so pruning can lose pairs but never admits a wrong one).
+ *
+ * The sketch network maps a unit-normalised embedding row x (d values) to a
+ * unit 64-d sketch: s = z/|z|, z = W2 GELU(W1 x + b1) + b2 (GELU exact, with
+ * the normal CDF).  Parameters are one flat FP32 array, in this order:
+ * W1 [hidden x d] row-major, b1 [hidden], W2 [64 x hidden] row-major, b2 [64].
+ * Training minimises sum_k w_k (s_pk . s_qk - t_k)^2 / sum_k w_k over labelled
+ * pairs (t_k: the pair's exact cosine) with Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8), on the GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct ejoin_sketch ejoin_sketch;
+
+/* out must be 64.  Parameters start at zero: set them with ejoin_sketch_set_params. */
+ejoin_status ejoin_sketch_create(ejoin_ctx *ctx, int32_t d, int32_t hidden, int32_t out, ejoin_sketch **sk);
+void ejoin_sketch_destroy(ejoin_sketch *sk);
+int64_t ejoin_sketch_num_params(const ejoin_sketch *sk);
+/* Host arrays of ejoin_sketch_num_params floats; set also resets the Adam state. */
+ejoin_status ejoin_sketch_set_params(ejoin_sketch *sk, const float *h_params);
+ejoin_status ejoin_sketch_get_params(const ejoin_sketch *sk, float *h_params);
+/* Sketches of the rows of X (device, raw rows; normalised internally) into d_S [X.n x 64]. */
+ejoin_status ejoin_sketch_forward(ejoin_sketch *sk, ejoin_rel X, float *d_S);
+/* Pairs k = (rows d_p[k], d_q[k] of X), d_inv = 1/|row| of X's rows (device, see
+ * ejoin_row_inv_norm).  grad: loss and its gradient (flat parameter layout,
+ * device, optional) without changing the parameters; train_step: the same
+ * followed by one Adam step with learning rate lr.  *h_loss (optional, host)
+ * receives the loss (synchronises). */
+ejoin_status ejoin_sketch_grad(ejoin_sketch *sk, ejoin_rel X, const float *d_inv, const uint32_t *d_p,
+                               const uint32_t *d_q, const float *d_t, const float *d_w, int64_t n_pairs,
+                               float *d_grad, float *h_loss);
+ejoin_status ejoin_sketch_train_step(ejoin_sketch *sk, ejoin_rel X, const float *d_inv, const uint32_t *d_p,
+                                     const uint32_t *d_q, const float *d_t, const float *d_w, int64_t n_pairs,
+                                     float lr, float *h_loss);
+/* Sketch cosine s_p . s_q of each pair into d_out (device). */
+ejoin_status ejoin_sketch_pair_sims(ejoin_sketch *sk, ejoin_rel X, const float *d_inv, const uint32_t *d_p,
+                                    const uint32_t *d_q, int64_t n_pairs, float *d_out);
+/* 1/|row| of every row of X (FP32, 0 for a zero row) into d_inv. */
+ejoin_status ejoin_row_inv_norm(ejoin_ctx *ctx, ejoin_rel X, float *d_inv);
+/* Exact FP32 cosine similarity (Sec. III-A) of the pairs (R row d_i[k], S row d_j[k]) into d_sim. */
+ejoin_status ejoin_score_pairs(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, const uint32_t *d_i, const uint32_t *d_j,
+                               int64_t n_pairs, float *d_sim);
+
+typedef struct ejoin_prune_stats {
+    uint64_t tiles_total;  /* 128 x 256 tile pairs of the full join */
+    uint64_t tiles_kept;   /* tile pairs whose sketch bound reaches eps_sketch */
+    uint64_t candidates, pairs;
+    float ms_prepare;      /* normalise + sketch + reorder */
+    float ms_bound;        /* tile statistics + tile-pair bounds */
+    float ms_contract, ms_rescore, ms_total;
+} ejoin_prune_stats;
+
+/* Threshold join of R and S (device, no selection) that contracts only the
+ * tile pairs whose sketch bound reaches eps_sketch.  Each side is first
+ * reordered by nearest sketch anchor (256 coarse, then 128 fine per coarse
+ * bucket, both farthest-point sampled and chained by nearest neighbour) so
+ * that tiles are coherent in sketch space; each tile is described by up to 4
+ * balls (farthest-point seeds, rows join the nearest seed: unit centroid c
+ * and angular radius rho), and a tile pair is kept when some ball pair has
+ * cos(max(0, angle(c_a, c_b) - rho_a - rho_b)) >= eps_sketch, an upper bound
+ * on the sketch cosine of every row pair the two balls hold.  Every candidate is re-scored exactly, so the result is a subset of
+ * ejoin_threshold's (equal up to the pairs whose sketch cosine is below
+ * eps_sketch).  ctx must use BF16, e4m3 or TF32; out as for ejoin_threshold;
+ * stats optional.  Synchronises. */
+ejoin_status ejoin_threshold_pruned(ejoin_ctx *ctx, ejoin_sketch *sk, ejoin_rel R, ejoin_rel S, float eps,
+                                    float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *stats);
+
 /* Statistics of the last call on ctx. */
 ejoin_status ejoin_last_stats(const ejoin_ctx *ctx, ejoin_stats *out);
 

@@ -50,6 +50,10 @@ struct BatchTables {
     const int *nB;
     const float *thr;
     int n_jobs;
+    // tile-list mode (pruned joins): the tiles to run are tile_list[0 .. min(*tile_count, tile_cap))
+    const uint2 *tile_list;
+    const unsigned long long *tile_count;
+    unsigned long long tile_cap;
 };
 
 // Per-job row sources of a batched re-score (device arrays).
@@ -98,11 +102,20 @@ cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *t
                           const float *scaleB, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
                           unsigned *status, uint64_t timeout, int count_only, int grid, int group_m,
                           cudaStream_t st);
+// Contraction over an explicit list of (row tile, column tile) pairs (pruned joins).
+cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                               const long long *nB, float thr, const uint2 *tile_list,
+                               const unsigned long long *tile_count, unsigned long long tile_cap, uint2 *cand,
+                               uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                               int grid, cudaStream_t st);
 // Batched contraction over a job table (BF16 / e4m3 / TF32 kinds as above).
 cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                                 const BatchTables &bt, const float *scaleA, const float *scaleB, uint2 *cand,
                                 uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
                                 int grid, int group_m, cudaStream_t st);
+cudaError_t launch_score_pairs(const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *pi,
+                               const uint32_t *pj, const float *invR, const float *invS, int64_t n, float *out,
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_rescore_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                                  const BatchRows &br, int d, const float *invA, const float *invB, float fp64_band,
                                  BatchPair *out, uint64_t out_cap, unsigned long long *out_count,

@@ -1,0 +1,82 @@
+// Internal declarations of the learned-sketch kernels (mlp.cu, prune.cu).
+#pragma once
+
+#include <algorithm>
+
+#include "ejoin_internal.cuh"
+
+namespace ej {
+
+enum : int { ACT_NONE = 0, ACT_GELU = 1 };
+
+// C[M x N] = act(rowscale_i * sum_k A(i,k) B(k,j) + bias_j), FP32.
+//   A(i,k) = A[r * a_rs + k * a_cs] * (ascale ? ascale[r] : 1), r = aidx ? aidx[i] : i
+//   B(k,j) = B[q * b_rs + j * b_cs] * (bscale ? bscale[q] : 1), q = bidx ? bidx[k] : k
+// pre (optional) receives the pre-activation.  atomic_acc: split K over CTAs
+// and atomically add into a C the caller zeroed (no bias / activation then).
+struct GemmArgs {
+    const float *A = nullptr;
+    const uint32_t *aidx = nullptr;
+    const float *ascale = nullptr;
+    int64_t a_rs = 0, a_cs = 1;
+    const float *B = nullptr;
+    const uint32_t *bidx = nullptr;
+    const float *bscale = nullptr;
+    int64_t b_rs = 0, b_cs = 1;
+    float *C = nullptr;
+    int64_t ldc = 0;
+    const float *bias = nullptr;
+    const float *rowscale = nullptr;
+    float *pre = nullptr;
+    int64_t M = 0, N = 0, K = 0;
+    int act = ACT_NONE;
+    int atomic_acc = 0;
+    int64_t k_chunk = 0;
+};
+
+cudaError_t launch_gemm_f32(const GemmArgs &g, int num_sms, cudaStream_t st);
+cudaError_t launch_rownorm(const float *z, int64_t n, int k, float *s, float *nz, int num_sms, cudaStream_t st);
+// wsum: device pointer to the sum of the pair weights.
+cudaError_t launch_pair_grad(const float *s, int64_t B, int k, const float *t, const float *w, const float *wsum,
+                             float *ds, float *loss, int num_sms, cudaStream_t st);
+cudaError_t launch_pair_dot(const float *s, int64_t B, int k, float *out, int num_sms, cudaStream_t st);
+cudaError_t launch_row_inv_norm(const float *x, int64_t n, int d, int64_t ld, float *inv, int num_sms, cudaStream_t st);
+cudaError_t launch_rownorm_backward(const float *s, const float *ds, const float *nz, int64_t n, int k, float *dz,
+                                    int num_sms, cudaStream_t st);
+cudaError_t launch_gelu_backward(float *dh, const float *a, int64_t n, int num_sms, cudaStream_t st);
+cudaError_t launch_colsum(const float *x, int64_t n, int k, float *out, int num_sms, cudaStream_t st);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
+                        float eps, int step, int num_sms, cudaStream_t st);
+
+// ---- pruning (prune.cu)
+// key[r] = base[r] * n_anchor + argmax_a <S[r], anchors[group(r) * n_anchor + a]>, where group(r) =
+// grp ? grp[r] : 0 (anchors of group g are rows g * n_anchor .. of `anchors`).
+cudaError_t launch_assign_keys(const float *S, int64_t n, int k, const float *anchors, int n_anchor,
+                               const uint32_t *grp, uint32_t *key, int num_sms, cudaStream_t st);
+// Stable-within-key counting sort of rows by key < n_keys: perm[new] = old row.
+cudaError_t launch_key_histogram(const uint32_t *key, int64_t n, uint32_t *hist, cudaStream_t st);
+cudaError_t launch_key_scan(uint32_t *hist, int n_keys, cudaStream_t st);  // in place, exclusive
+cudaError_t launch_key_scatter(const uint32_t *key, int64_t n, uint32_t *cursor, uint32_t *perm, cudaStream_t st);
+// Row gathers: out row i <- in row perm[i] (bytes per row), and for vectors.
+cudaError_t launch_gather_rows(const void *in, int64_t row_bytes, const uint32_t *perm, int64_t n, void *out,
+                               cudaStream_t st);
+cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *perm, int64_t n, uint32_t *out, cudaStream_t st);
+cudaError_t launch_gather_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t st);
+// Fine anchors of a two-level reorder: for coarse bucket b (rows perm[off[b] .. off[b+1]) of the
+// coarse order), n_fine (<= 256) anchors by farthest-point sampling, chained by nearest neighbour
+// (zero anchors for an empty bucket).  maxdot: scratch of n floats.
+cudaError_t launch_fine_anchors(const float *S, const uint32_t *perm, const uint32_t *off, int n_coarse, int64_t n,
+                                int n_fine, float *maxdot, float *anchors, cudaStream_t st);
+// Balls per tile in the pruning bound.
+constexpr int PRUNE_BALLS = 4;
+// Per tile of `tile_rows` (<= 256) consecutive sketch rows: up to PRUNE_BALLS balls formed greedily
+// along the row order: unit centroids [tiles x PRUNE_BALLS x 64] and angular radii
+// [tiles x PRUNE_BALLS] (+ margin; -1 for an unused ball).
+cudaError_t launch_tile_stats(const float *S, int64_t n, int k, int tile_rows, float *centroid, float *radius,
+                              cudaStream_t st);
+// Surviving tile pairs: some ball pair has cos(max(0, angle(c_a, c_b) - r_a - r_b)) >= eps_sketch.
+cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, const float *cB, const float *rB,
+                              int64_t tB, int k, float eps_sketch, uint2 *list, uint64_t cap,
+                              unsigned long long *count, cudaStream_t st);
+
+}  // namespace ej

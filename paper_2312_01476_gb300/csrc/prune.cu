@@ -1,0 +1,570 @@
+// Learned tile pruning: reorder rows so that tiles are coherent in sketch
+// space, bound the sketch cosine of every tile pair, keep the tile pairs that
+// can hold a match.  The contraction then runs on the kept tile pairs only
+// and every candidate is re-scored exactly, so pruning can only lose pairs
+// whose sketch cosine falls below the calibrated sketch threshold.
+//
+// Tile bound: with unit centroid c_T and angular radius rho_T (largest angle
+// between c_T and a member sketch), any pair (a in A, b in B) satisfies
+//   angle(s_a, s_b) >= angle(c_A, c_B) - rho_A - rho_B
+// (triangle inequality for angles on the sphere), hence
+//   cos(s_a, s_b) <= cos(max(0, angle(c_A, c_B) - rho_A - rho_B)).
+#include <cfloat>
+
+#include "mlp_internal.cuh"
+
+namespace ej {
+
+namespace {
+constexpr int SK = 64;          // sketch width handled by these kernels
+constexpr float RADIUS_MARGIN = 2e-3f;  // radians, covers FP32 rounding of dots near 1
+constexpr int NB = PRUNE_BALLS;
+}  // namespace
+
+// One thread per row: nearest anchor (largest dot) among the row's group's anchors.
+__global__ void assign_keys_kernel(const float *__restrict__ S, int64_t n, const float *__restrict__ anchors,
+                                   int n_anchor, const uint32_t *__restrict__ grp, uint32_t *__restrict__ key)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    float x[SK];
+#pragma unroll
+    for (int q = 0; q < SK / 4; ++q) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(S + r * SK) + q);
+        x[4 * q] = v.x;
+        x[4 * q + 1] = v.y;
+        x[4 * q + 2] = v.z;
+        x[4 * q + 3] = v.w;
+    }
+    const uint32_t g = grp ? grp[r] : 0u;
+    const float *an = anchors + (int64_t)g * n_anchor * SK;
+    float best = -FLT_MAX;
+    int bi = 0;
+    for (int a = 0; a < n_anchor; ++a) {
+        float dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < SK / 4; ++q) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(an + (int64_t)a * SK) + q);
+            dot = fmaf(x[4 * q], v.x, dot);
+            dot = fmaf(x[4 * q + 1], v.y, dot);
+            dot = fmaf(x[4 * q + 2], v.z, dot);
+            dot = fmaf(x[4 * q + 3], v.w, dot);
+        }
+        if (dot > best) {
+            best = dot;
+            bi = a;
+        }
+    }
+    key[r] = g * (uint32_t)n_anchor + (uint32_t)bi;
+}
+
+__global__ void key_histogram_kernel(const uint32_t *__restrict__ key, int64_t n, uint32_t *__restrict__ hist)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(hist + key[r], 1u);
+}
+
+__global__ void __launch_bounds__(1024) key_scan_kernel(uint32_t *h, int nk)
+{
+    __shared__ uint32_t warp_tot[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nk; base += 1024) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nk ? h[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_tot[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t t = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            warp_tot[lane] = t;
+        }
+        __syncthreads();
+        const uint32_t excl = carry + (warp ? warp_tot[warp - 1] : 0u) + x - v;
+        __syncthreads();
+        if (i < nk) h[i] = excl;
+        if (threadIdx.x == 0) carry += warp_tot[31];
+        __syncthreads();
+    }
+}
+
+__global__ void key_scatter_kernel(const uint32_t *__restrict__ key, int64_t n, uint32_t *__restrict__ cursor,
+                                   uint32_t *__restrict__ perm)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        perm[atomicAdd(cursor + key[r], 1u)] = (uint32_t)r;
+}
+
+// One warp per output row: 16-byte copies (row_bytes is a multiple of 16).
+__global__ void gather_rows_kernel(const uint4 *__restrict__ in, int64_t row_u4, const uint32_t *__restrict__ perm,
+                                   int64_t n, uint4 *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = w; i < n; i += nw) {
+        const uint4 *src = in + (int64_t)perm[i] * row_u4;
+        uint4 *dst = out + i * row_u4;
+        for (int64_t q = lane; q < row_u4; q += 32) dst[q] = __ldg(src + q);
+    }
+}
+
+__global__ void gather_u32_kernel(const uint32_t *__restrict__ in, const uint32_t *__restrict__ perm, int64_t n,
+                                  uint32_t *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+__global__ void gather_f32_kernel(const float *__restrict__ in, const uint32_t *__restrict__ perm, int64_t n,
+                                  float *__restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[perm[i]];
+}
+
+// Anchors of one bucket (one block per bucket; also used for the coarse level
+// with a single bucket holding a strided sample of all rows): farthest-point
+// sampling over the bucket's rows (first anchor: the bucket's first row; each
+// next anchor: the row whose largest cosine to the anchors so far is the
+// smallest), so that well-separated groups each get an anchor before any
+// group gets a second one; then the anchors are chained by nearest neighbour
+// so that nearby anchors get adjacent keys.  maxdot: scratch of n floats.
+__global__ void __launch_bounds__(1024) fine_anchors_kernel(const float *__restrict__ S,
+                                                            const uint32_t *__restrict__ perm,
+                                                            const uint32_t *__restrict__ off, int n_coarse, int64_t n,
+                                                            int n_fine, float *__restrict__ maxdot,
+                                                            float *__restrict__ anchors)
+{
+    __shared__ float cur[SK];
+    __shared__ float red_v[32];
+    __shared__ int red_i[32];
+    __shared__ int chosen[256];
+    __shared__ int order[256];
+    __shared__ unsigned char used[256];
+    __shared__ int best_s;
+    const int b = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t lo = off[b];
+    const int64_t hi = b + 1 < n_coarse ? (int64_t)off[b + 1] : n;
+    const int64_t size = hi - lo;
+    float *out = anchors + (int64_t)b * n_fine * SK;
+    if (size <= 0) {
+        for (int e = tid; e < n_fine * SK; e += blockDim.x) out[e] = 0.f;
+        return;
+    }
+    for (int64_t i = lo + tid; i < hi; i += blockDim.x) maxdot[i] = -2.f;
+    int pick = 0;  // position inside the bucket
+    for (int j = 0; j < n_fine; ++j) {
+        if (tid == 0) chosen[j] = pick;
+        __syncthreads();
+        if (tid < SK) cur[tid] = S[(int64_t)perm[lo + pick] * SK + tid];
+        __syncthreads();
+        // update the largest cosine to the chosen anchors; find the row where it is smallest
+        float bv = 3.f;
+        int bi = 0;
+        for (int64_t i = lo + tid; i < hi; i += blockDim.x) {
+            const float *x = S + (int64_t)perm[i] * SK;
+            float dot = 0.f;
+#pragma unroll 16
+            for (int q = 0; q < SK; ++q) dot = fmaf(cur[q], x[q], dot);
+            const float m = fmaxf(maxdot[i], dot);
+            maxdot[i] = m;
+            if (m < bv) {
+                bv = m;
+                bi = (int)(i - lo);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            red_v[warp] = bv;
+            red_i[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float v = red_v[0];
+            int ix = red_i[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (red_v[w] < v || (red_v[w] == v && red_i[w] < ix)) {
+                    v = red_v[w];
+                    ix = red_i[w];
+                }
+            best_s = ix;
+        }
+        __syncthreads();
+        pick = best_s;
+    }
+    // nearest-neighbour chain over the chosen anchors: each step, the whole
+    // block scores the unused anchors against the last one and takes the best
+    for (int j = tid; j < n_fine; j += blockDim.x) used[j] = 0;
+    __syncthreads();
+    if (tid == 0) {
+        order[0] = 0;
+        used[0] = 1;
+        best_s = 0;
+    }
+    __syncthreads();
+    for (int step = 1; step < n_fine; ++step) {
+        if (tid < SK) cur[tid] = S[(int64_t)perm[lo + chosen[best_s]] * SK + tid];
+        __syncthreads();
+        float bv = -3.f;
+        int bi = n_fine;
+        for (int j = tid; j < n_fine; j += blockDim.x) {
+            if (used[j]) continue;
+            const float *xb = S + (int64_t)perm[lo + chosen[j]] * SK;
+            float dot = 0.f;
+#pragma unroll 16
+            for (int q = 0; q < SK; ++q) dot = fmaf(cur[q], xb[q], dot);
+            if (dot > bv) {
+                bv = dot;
+                bi = j;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            red_v[warp] = bv;
+            red_i[warp] = bi;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            float v = red_v[0];
+            int ix = red_i[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+                if (red_v[w] > v || (red_v[w] == v && red_i[w] < ix)) {
+                    v = red_v[w];
+                    ix = red_i[w];
+                }
+            order[step] = ix;
+            used[ix] = 1;
+            best_s = ix;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < n_fine * SK; e += blockDim.x) {
+        const int j = e / SK, q = e % SK;
+        out[e] = S[(int64_t)perm[lo + chosen[order[j]]] * SK + q];
+    }
+}
+
+// One block (256 threads) per tile of tile_rows (<= 256) consecutive sketch
+// rows (in reorder order).  The tile is described by up to NB balls (see
+// below); any assignment of rows to balls gives a valid bound, this one keeps
+// the balls small when the tile holds up to NB well-separated groups.  Ball = unit centroid + angular radius (largest
+// angle between the centroid and a member, plus a rounding margin); unused
+// balls get radius -1.
+__global__ void __launch_bounds__(256) tile_stats_kernel(const float *__restrict__ S, int64_t n, int tile_rows,
+                                                         float *__restrict__ centroid, float *__restrict__ radius)
+{
+    __shared__ float c[NB][SK];
+    __shared__ int run_of[256];
+    __shared__ float maxd[256];
+    __shared__ int seeds[NB];
+    __shared__ int cnt[NB];
+    const int64_t r0 = (int64_t)blockIdx.x * tile_rows;
+    int64_t r1 = r0 + tile_rows;
+    if (r1 > n) r1 = n;
+    const int rows = (int)(r1 - r0);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < NB * SK; e += blockDim.x) c[e / SK][e % SK] = 0.f;
+    if (tid < NB) cnt[tid] = 0;
+    // balls: NB seeds by farthest-point sampling inside the tile (first row,
+    // then the row least similar to the seeds so far), each row joins its most
+    // similar seed
+    if (warp == 0) {
+        int seed = 0;
+        for (int j = 0; j < NB; ++j) {
+            if (lane == 0) seeds[j] = seed;
+            const float *y = S + (r0 + seed) * SK;
+            float bv = 3.f;
+            int bi = 0;
+            for (int r = lane; r < rows; r += 32) {
+                const float *x = S + (r0 + r) * SK;
+                float dot = 0.f;
+#pragma unroll 16
+                for (int q = 0; q < SK; ++q) dot = fmaf(x[q], y[q], dot);
+                const float m = j == 0 ? dot : fmaxf(maxd[r], dot);
+                maxd[r] = m;
+                if (m < bv) {
+                    bv = m;
+                    bi = r;
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov < bv || (ov == bv && oi < bi)) {
+                    bv = ov;
+                    bi = oi;
+                }
+            }
+            seed = bi;
+        }
+    }
+    __syncthreads();
+    if (tid < rows) {
+        const float *x = S + (r0 + tid) * SK;
+        float best = -3.f;
+        int bb = 0;
+        for (int j = 0; j < NB; ++j) {
+            const float *y = S + (r0 + seeds[j]) * SK;
+            float dot = 0.f;
+#pragma unroll 16
+            for (int q = 0; q < SK; ++q) dot = fmaf(x[q], y[q], dot);
+            if (dot > best) {
+                best = dot;
+                bb = j;
+            }
+        }
+        run_of[tid] = bb;
+    }
+    __syncthreads();
+    // centroid sums: one thread per (ball, dim), looping over the tile's rows
+    for (int e = tid; e < NB * SK; e += blockDim.x) {
+        const int bl = e / SK, q = e % SK;
+        float acc = 0.f;
+        int k = 0;
+        for (int r = 0; r < rows; ++r)
+            if (run_of[r] == bl) {
+                acc += S[(r0 + r) * SK + q];
+                ++k;
+            }
+        c[bl][q] = acc;
+        if (q == 0) cnt[bl] = k;
+    }
+    __syncthreads();
+    if (warp < NB) {
+        float ss = c[warp][lane] * c[warp][lane] + c[warp][lane + 32] * c[warp][lane + 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        const float inv = ss > 0.f ? rsqrtf(ss) : 0.f;
+        c[warp][lane] *= inv;
+        c[warp][lane + 32] *= inv;
+    }
+    __syncthreads();
+    // the smallest cosine between a ball's centroid and its members: one warp per ball
+    if (warp < NB) {
+        float mn = 1.f;
+        for (int r = lane; r < rows; r += 32) {
+            if (run_of[r] != warp) continue;
+            float dot = 0.f;
+#pragma unroll 16
+            for (int q = 0; q < SK; ++q) dot = fmaf(c[warp][q], S[(r0 + r) * SK + q], dot);
+            mn = fminf(mn, dot);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        if (lane == 0) {
+            float ss = 0.f;
+            for (int q = 0; q < SK; ++q) ss += c[warp][q] * c[warp][q];
+            float rad;
+            if (cnt[warp] == 0) rad = -1.f;                   // unused ball
+            else if (ss < 0.5f) rad = 3.14159265f;             // degenerate centroid bounds nothing
+            else rad = acosf(fmaxf(-1.f, fminf(1.f, mn))) + RADIUS_MARGIN;
+            radius[(int64_t)blockIdx.x * NB + warp] = rad;
+        }
+    }
+    for (int e = tid; e < NB * SK; e += blockDim.x)
+        centroid[(int64_t)blockIdx.x * NB * SK + e] = c[e / SK][e % SK];
+}
+
+// TP x TP tile pairs per block (256 threads, 4 pairs each).  A tile pair is
+// kept when some ball pair (a, b) has cos(max(0, angle(c_a, c_b) - r_a - r_b))
+// >= cos_keep; kept pairs are appended with one atomic per warp.
+constexpr int TP = 32;
+__global__ void __launch_bounds__(256) tile_pairs_kernel(const float *__restrict__ cA, const float *__restrict__ rA,
+                                                         int64_t tA, const float *__restrict__ cB,
+                                                         const float *__restrict__ rB, int64_t tB, float cos_keep,
+                                                         uint2 *__restrict__ list, uint64_t cap,
+                                                         unsigned long long *count)
+{
+    extern __shared__ float sm[];
+    float *sa = sm;                          // [TP * NB][SK + 1]
+    float *sb = sa + TP * NB * (SK + 1);     // [TP * NB][SK + 1]
+    float *ra = sb + TP * NB * (SK + 1);     // [TP * NB]
+    float *rb = ra + TP * NB;                // [TP * NB]
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t a0 = (int64_t)blockIdx.y * TP, b0 = (int64_t)blockIdx.x * TP;
+    for (int e = tid; e < TP * NB * SK; e += 256) {
+        const int tb = e / SK, q = e % SK;  // tb = tile * NB + ball
+        const int64_t ga = a0 * NB + tb, gb = b0 * NB + tb;
+        sa[tb * (SK + 1) + q] = ga < tA * NB ? cA[ga * SK + q] : 0.f;
+        sb[tb * (SK + 1) + q] = gb < tB * NB ? cB[gb * SK + q] : 0.f;
+    }
+    for (int e = tid; e < TP * NB; e += 256) {
+        ra[e] = a0 * NB + e < tA * NB ? rA[a0 * NB + e] : -1.f;
+        rb[e] = b0 * NB + e < tB * NB ? rB[b0 * NB + e] : -1.f;
+    }
+    __syncthreads();
+    // thread -> 2 x 2 tile pairs: rows (ty*2 + i), cols (tx*2 + j), ty, tx in 0..15
+    const int ty = tid >> 4, tx = tid & 15;
+    unsigned mask = 0u;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int ta = ty * 2 + i;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int tb = tx * 2 + j;
+            if (a0 + ta >= tA || b0 + tb >= tB) continue;
+            bool keep = false;
+            for (int x = 0; x < NB && !keep; ++x) {
+                const float rx = ra[ta * NB + x];
+                if (rx < 0.f) continue;
+                const float *ca = sa + (ta * NB + x) * (SK + 1);
+                for (int y = 0; y < NB && !keep; ++y) {
+                    const float ry = rb[tb * NB + y];
+                    if (ry < 0.f) continue;
+                    const float *cb = sb + (tb * NB + y) * (SK + 1);
+                    float dot = 0.f;
+#pragma unroll 16
+                    for (int q = 0; q < SK; ++q) dot = fmaf(ca[q], cb[q], dot);
+                    const float gap = acosf(fmaxf(-1.f, fminf(1.f, dot))) - rx - ry;
+                    keep = gap <= 0.f || cosf(gap) >= cos_keep;
+                }
+            }
+            if (keep) mask |= 1u << (i * 2 + j);
+        }
+    }
+    const int cnt = __popc(mask);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (tot == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(count, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned long long p = base + (unsigned long long)(incl - cnt);
+    while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        if (p < cap) list[p] = make_uint2((uint32_t)(a0 + ty * 2 + (b >> 1)), (uint32_t)(b0 + tx * 2 + (b & 1)));
+        ++p;
+    }
+}
+
+static unsigned grid_for(int64_t n, int per_block)
+{
+    int64_t b = (n + per_block - 1) / per_block;
+    if (b > 65535 * 16) b = 65535 * 16;
+    return (unsigned)std::max<int64_t>(b, 1);
+}
+
+cudaError_t launch_assign_keys(const float *S, int64_t n, int k, const float *anchors, int n_anchor,
+                               const uint32_t *grp, uint32_t *key, int num_sms, cudaStream_t st)
+{
+    (void)num_sms;
+    if (k != SK) return cudaErrorInvalidValue;
+    if (n <= 0) return cudaSuccess;
+    assign_keys_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, n, anchors, n_anchor, grp, key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_key_histogram(const uint32_t *key, int64_t n, uint32_t *hist, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    key_histogram_kernel<<<grid_for(n, 256 * 8), 256, 0, st>>>(key, n, hist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_key_scan(uint32_t *hist, int n_keys, cudaStream_t st)
+{
+    key_scan_kernel<<<1, 1024, 0, st>>>(hist, n_keys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_key_scatter(const uint32_t *key, int64_t n, uint32_t *cursor, uint32_t *perm, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    key_scatter_kernel<<<grid_for(n, 256 * 8), 256, 0, st>>>(key, n, cursor, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const void *in, int64_t row_bytes, const uint32_t *perm, int64_t n, void *out,
+                               cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    if (row_bytes % 16) return cudaErrorInvalidValue;
+    gather_rows_kernel<<<grid_for(n, 8), 256, 0, st>>>((const uint4 *)in, row_bytes / 16, perm, n, (uint4 *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *perm, int64_t n, uint32_t *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    gather_u32_kernel<<<grid_for(n, 256 * 4), 256, 0, st>>>(in, perm, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    gather_f32_kernel<<<grid_for(n, 256 * 4), 256, 0, st>>>(in, perm, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fine_anchors(const float *S, const uint32_t *perm, const uint32_t *off, int n_coarse, int64_t n,
+                                int n_fine, float *maxdot, float *anchors, cudaStream_t st)
+{
+    if (n_coarse <= 0) return cudaSuccess;
+    if (n_fine > 256) return cudaErrorInvalidValue;
+    fine_anchors_kernel<<<n_coarse, 1024, 0, st>>>(S, perm, off, n_coarse, n, n_fine, maxdot, anchors);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_stats(const float *S, int64_t n, int k, int tile_rows, float *centroid, float *radius,
+                              cudaStream_t st)
+{
+    if (k != SK || tile_rows > 256) return cudaErrorInvalidValue;
+    const int64_t tiles = (n + tile_rows - 1) / tile_rows;
+    if (tiles <= 0) return cudaSuccess;
+    tile_stats_kernel<<<(unsigned)tiles, 256, 0, st>>>(S, n, tile_rows, centroid, radius);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, const float *cB, const float *rB,
+                              int64_t tB, int k, float eps_sketch, uint2 *list, uint64_t cap,
+                              unsigned long long *count, cudaStream_t st)
+{
+    if (k != SK) return cudaErrorInvalidValue;
+    if (tA <= 0 || tB <= 0) return cudaSuccess;
+    const int smem = (2 * TP * NB * (SK + 1) + 2 * TP * NB) * 4;
+    cudaError_t e = cudaFuncSetAttribute(tile_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((tB + TP - 1) / TP), (unsigned)((tA + TP - 1) / TP));
+    tile_pairs_kernel<<<grid, 256, smem, st>>>(cA, rA, tA, cB, rB, tB, eps_sketch, list, cap, count);
+    return cudaGetLastError();
+}
+
+}  // namespace ej

@@ -433,6 +433,37 @@ cudaError_t launch_rescore_batch(const uint2 *cand, const unsigned long long *ca
     return cudaGetLastError();
 }
 
+// Exact FP32 cosine similarity of given pairs (one warp per pair): the
+// re-score's FP32 tier without the threshold, used to label training pairs.
+__global__ void score_pairs_kernel(const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS,
+                                   int d, const uint32_t *__restrict__ pi, const uint32_t *__restrict__ pj,
+                                   const float *__restrict__ invR, const float *__restrict__ invS, int64_t n,
+                                   float *__restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = w; k < n; k += nw) {
+        const uint32_t i = pi[k], j = pj[k];
+        const float *r = R + (int64_t)i * ldR, *s = S + (int64_t)j * ldS;
+        float acc = 0.f;
+        for (int c = lane; c < d; c += 32) acc = fmaf(__ldg(r + c), __ldg(s + c), acc);
+        acc = warp_sum_f(acc);
+        if (lane == 0) out[k] = fminf(1.f, fmaxf(-1.f, acc * invR[i] * invS[j]));
+    }
+}
+
+cudaError_t launch_score_pairs(const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *pi,
+                               const uint32_t *pj, const float *invR, const float *invS, int64_t n, float *out,
+                               int num_sms, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 7) / 8;
+    if (blocks > (int64_t)num_sms * 16) blocks = (int64_t)num_sms * 16;
+    score_pairs_kernel<<<(unsigned)blocks, 256, 0, st>>>(R, ldR, S, ldS, d, pi, pj, invR, invS, n, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap, const float *R,
                            int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
                            const uint32_t *idsS, const float *invR, const float *invS, float eps, float fp64_band,

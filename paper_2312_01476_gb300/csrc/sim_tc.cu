@@ -117,13 +117,24 @@ struct TileInfo {
     float thr;
 };
 
-template <bool BATCH>
+enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2 };
+
+template <int MODE>
 __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &bt, long long tiles_m,
                                                 long long tiles_n, long long nA, long long nB, float thr, int group_m)
 {
     TileInfo ti;
     long long m, n;
-    if constexpr (BATCH) {
+    if constexpr (MODE == MODE_LIST) {
+        const uint2 mn = __ldg(bt.tile_list + t);
+        m = mn.x;
+        n = mn.y;
+        ti.rowA = m * BM;
+        ti.rowB = n * BN;
+        ti.limA = (int)min((long long)BM, nA - m * BM);
+        ti.limB = (int)min((long long)BN, nB - n * BN);
+        ti.thr = thr;
+    } else if constexpr (MODE == MODE_BATCH) {
         int lo = 0, hi = bt.n_jobs;  // tile_off[lo] <= t < tile_off[hi]
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -161,7 +172,7 @@ __device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity, u
 }
 }  // namespace
 
-template <int KIND, bool BATCH>
+template <int KIND, int MODE>
 __global__ void __launch_bounds__(THREADS, 1)
     sim_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kp,
                   const long long *__restrict__ nA_ptr, const long long *__restrict__ nB_ptr, float thr,
@@ -182,9 +193,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_MISC + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long nA = BATCH ? 0 : *nA_ptr, nB = BATCH ? 0 : *nB_ptr;
+    const long long nA = MODE == MODE_BATCH ? 0 : *nA_ptr, nB = MODE == MODE_BATCH ? 0 : *nB_ptr;
     const long long tiles_m = (nA + BM - 1) / BM, tiles_n = (nB + BN - 1) / BN;
-    const long long total = BATCH ? __ldg(bt.tile_off + bt.n_jobs) : tiles_m * tiles_n;
+    long long total = tiles_m * tiles_n;
+    if (MODE == MODE_BATCH) total = __ldg(bt.tile_off + bt.n_jobs);
+    if (MODE == MODE_LIST) {
+        const unsigned long long c = *bt.tile_count;
+        total = (long long)(c < bt.tile_cap ? c : bt.tile_cap);
+    }
     const int num_kb = kp / Kind<KIND>::ELEMS;
 
     if (threadIdx.x == 0) {
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             uint64_t issued = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const TileInfo ti = decode_tile<BATCH>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
+                const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, timeout, abort_flag, status)) {
                         ok = false;
@@ -317,7 +333,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         };
 
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-            const TileInfo ti = decode_tile<BATCH>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
+            const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
             const float thr_t = ti.thr;
             int ok = 0;
             if (lane == 0) ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, timeout, abort_flag, status) ? 1 : 0;
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 size_t sim_tc_smem_bytes() { return (size_t)SMEM_BYTES; }
 
-template <int KIND, bool BATCH>
+template <int KIND, int MODE>
 static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
                               const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
                               uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
@@ -475,11 +491,11 @@ static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, in
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!((configured >> dev) & 1ull)) {
-        e = cudaFuncSetAttribute(sim_tc_kernel<KIND, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        e = cudaFuncSetAttribute(sim_tc_kernel<KIND, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
-    sim_tc_kernel<KIND, BATCH><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand,
+    sim_tc_kernel<KIND, MODE><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand,
                                                                   cap, cand_count, status, timeout, count_only,
                                                                   group_m < 1 ? 1 : group_m, bt);
     return cudaGetLastError();
@@ -493,13 +509,13 @@ cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *t
     const BatchTables none{};
     switch (kind) {
     case 0:
-        return launch_one<0, false>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
+        return launch_one<0, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
                                     count_only, grid, group_m, none, st);
     case 1:
-        return launch_one<1, false>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
+        return launch_one<1, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
                                     count_only, grid, group_m, none, st);
     case 2:
-        return launch_one<2, false>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
+        return launch_one<2, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
                                     count_only, grid, group_m, none, st);
     default: return cudaErrorInvalidValue;
     }
@@ -512,14 +528,38 @@ cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensor
 {
     switch (kind) {
     case 0:
-        return launch_one<0, true>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
+        return launch_one<0, MODE_BATCH>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
                                    timeout, 0, grid, group_m, bt, st);
     case 1:
-        return launch_one<1, true>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
+        return launch_one<1, MODE_BATCH>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
                                    timeout, 0, grid, group_m, bt, st);
     case 2:
-        return launch_one<2, true>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
+        return launch_one<2, MODE_BATCH>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
                                    timeout, 0, grid, group_m, bt, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                               const long long *nB, float thr, const uint2 *tile_list,
+                               const unsigned long long *tile_count, unsigned long long tile_cap, uint2 *cand,
+                               uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                               int grid, cudaStream_t st)
+{
+    BatchTables bt{};
+    bt.tile_list = tile_list;
+    bt.tile_count = tile_count;
+    bt.tile_cap = tile_cap;
+    switch (kind) {
+    case 0:
+        return launch_one<0, MODE_LIST>(tmA, tmB, kp, nA, nB, thr, nullptr, nullptr, cand, cap, cand_count, status,
+                                        timeout, 0, grid, 1, bt, st);
+    case 1:
+        return launch_one<1, MODE_LIST>(tmA, tmB, kp, nA, nB, thr, nullptr, nullptr, cand, cap, cand_count, status,
+                                        timeout, 0, grid, 1, bt, st);
+    case 2:
+        return launch_one<2, MODE_LIST>(tmA, tmB, kp, nA, nB, thr, nullptr, nullptr, cand, cap, cand_count, status,
+                                        timeout, 0, grid, 1, bt, st);
     default: return cudaErrorInvalidValue;
     }
 }

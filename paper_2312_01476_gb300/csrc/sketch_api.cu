@@ -1,0 +1,652 @@
+// C ABI of the learned part: the sketch network (parameters, forward,
+// gradient, Adam step, pair scoring) and the pruned join that uses its
+// sketches to skip tile pairs.  The paper has no learned component; these
+// entry points implement the "learned tile pruning" form of the join.
+//
+// Pruned join (ejoin_threshold_pruned), all on the context stream:
+//   1. normalise R and S (BF16 operands, FP32 inverse norms), as in the plain join;
+//   2. sketch every row with the network (unit 64-d vectors);
+//   3. reorder each side so that tiles are coherent in sketch space: nearest
+//      of 256 coarse anchors, then of 128 fine anchors inside the coarse
+//      bucket (both farthest-point sampled and chained by nearest neighbour,
+//      so that nearby anchors get adjacent keys), counting sort by the
+//      32,768 keys, gather of operand rows, inverse norms and sketches;
+//   4. per tile: up to 4 balls in sketch space (seeds by farthest-point
+//      sampling in the tile, rows join the nearest seed: unit centroid +
+//      angular radius); a tile pair is kept when some
+//      ball pair has cos(max(0, angle - rho_a - rho_b)) >= eps_sketch; kept
+//      pairs are compacted into a tile list;
+//   5. the tcgen05 contraction runs on the listed tiles only (threshold eps -
+//      band), and the re-score verifies every candidate exactly from the FP32
+//      input rows, mapping sorted rows back to original ids.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "host_internal.h"
+#include "mlp_internal.cuh"
+
+using namespace ej;
+using namespace ej::host;
+
+struct ejoin_sketch {
+    ejoin_ctx *ctx = nullptr;
+    int d = 0, hid = 0, out = 0;
+    int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, n_params = 0;
+    Buf params, grads, m, v;
+    int step = 0;
+    // training workspace (grown on demand)
+    Buf idx, A1, H, Z, S, nz, dS, dZ, dH, scal;  // scal: [loss, wsum]
+    // forward workspace
+    Buf fH, fZ, finv;
+    // pruned-join workspace, per side
+    struct Side {
+        Buf S, key1, key2, perm1, perm, hist, off, a_idx, anchors1, anchors2, norm, inv, scale, sS, maxdot, cent, rad;
+    } pw[2];
+    Buf list, list_count;
+    uint64_t list_cap = 0;
+};
+
+namespace {
+
+constexpr int64_t FWD_CHUNK = 1 << 20;
+
+cudaError_t grow(Buf &b, size_t bytes) { return ensure(b, bytes); }
+
+float *P(Buf &b) { return (float *)b.p; }
+
+// Forward of rows [0, n) of x (raw rows; inv = their inverse norms) into S_out (n x out).
+cudaError_t sketch_forward(ejoin_sketch *sk, const float *x, int64_t n, int64_t ld, const float *inv, float *S_out,
+                           cudaStream_t st)
+{
+    ejoin_ctx *c = sk->ctx;
+    cudaError_t e;
+    const int64_t chunk = std::min<int64_t>(n, FWD_CHUNK);
+    if ((e = grow(sk->fH, (size_t)std::max<int64_t>(chunk, 1) * sk->hid * 4)) != cudaSuccess) return e;
+    if ((e = grow(sk->fZ, (size_t)std::max<int64_t>(chunk, 1) * sk->out * 4)) != cudaSuccess) return e;
+    float *W = P(sk->params);
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t m = std::min<int64_t>(chunk, n - r0);
+        GemmArgs g1;
+        g1.A = x + r0 * ld;
+        g1.a_rs = ld;
+        g1.a_cs = 1;
+        g1.B = W + sk->oW1;
+        g1.b_rs = 1;
+        g1.b_cs = sk->d;
+        g1.C = P(sk->fH);
+        g1.ldc = sk->hid;
+        g1.bias = W + sk->ob1;
+        g1.rowscale = inv + r0;
+        g1.M = m;
+        g1.N = sk->hid;
+        g1.K = sk->d;
+        g1.act = ACT_GELU;
+        if ((e = launch_gemm_f32(g1, c->num_sms, st)) != cudaSuccess) return e;
+        GemmArgs g2;
+        g2.A = P(sk->fH);
+        g2.a_rs = sk->hid;
+        g2.a_cs = 1;
+        g2.B = W + sk->oW2;
+        g2.b_rs = 1;
+        g2.b_cs = sk->hid;
+        g2.C = P(sk->fZ);
+        g2.ldc = sk->out;
+        g2.bias = W + sk->ob2;
+        g2.M = m;
+        g2.N = sk->out;
+        g2.K = sk->hid;
+        if ((e = launch_gemm_f32(g2, c->num_sms, st)) != cudaSuccess) return e;
+        if ((e = launch_rownorm(P(sk->fZ), m, sk->out, S_out + r0 * sk->out, nullptr, c->num_sms, st)) !=
+            cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+// Forward + backward on a batch of pairs (rows p[k], q[k] of x); gradients into sk->grads.
+cudaError_t sketch_grad(ejoin_sketch *sk, const float *x, int64_t ld, const float *inv, const uint32_t *p,
+                        const uint32_t *q, const float *t, const float *w, int64_t B, cudaStream_t st)
+{
+    ejoin_ctx *c = sk->ctx;
+    const int64_t n = 2 * B;
+    const int hid = sk->hid, out = sk->out, d = sk->d;
+    cudaError_t e;
+    if ((e = grow(sk->idx, (size_t)n * 4)) || (e = grow(sk->A1, (size_t)n * hid * 4)) ||
+        (e = grow(sk->H, (size_t)n * hid * 4)) || (e = grow(sk->Z, (size_t)n * out * 4)) ||
+        (e = grow(sk->S, (size_t)n * out * 4)) || (e = grow(sk->nz, (size_t)n * 4)) ||
+        (e = grow(sk->dS, (size_t)n * out * 4)) || (e = grow(sk->dZ, (size_t)n * out * 4)) ||
+        (e = grow(sk->dH, (size_t)n * hid * 4)) || (e = grow(sk->scal, 64)))
+        return e;
+    uint32_t *idx = (uint32_t *)sk->idx.p;
+    if ((e = cudaMemcpyAsync(idx, p, B * 4, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(idx + B, q, B * 4, cudaMemcpyDeviceToDevice, st)))
+        return e;
+    float *W = P(sk->params), *G = P(sk->grads);
+    // forward
+    GemmArgs g1;
+    g1.A = x;
+    g1.aidx = idx;
+    g1.a_rs = ld;
+    g1.a_cs = 1;
+    g1.B = W + sk->oW1;
+    g1.b_rs = 1;
+    g1.b_cs = d;
+    g1.C = P(sk->H);
+    g1.ldc = hid;
+    g1.bias = W + sk->ob1;
+    g1.rowscale = inv;
+    g1.pre = P(sk->A1);
+    g1.M = n;
+    g1.N = hid;
+    g1.K = d;
+    g1.act = ACT_GELU;
+    if ((e = launch_gemm_f32(g1, c->num_sms, st)) != cudaSuccess) return e;
+    GemmArgs g2;
+    g2.A = P(sk->H);
+    g2.a_rs = hid;
+    g2.a_cs = 1;
+    g2.B = W + sk->oW2;
+    g2.b_rs = 1;
+    g2.b_cs = hid;
+    g2.C = P(sk->Z);
+    g2.ldc = out;
+    g2.bias = W + sk->ob2;
+    g2.M = n;
+    g2.N = out;
+    g2.K = hid;
+    if ((e = launch_gemm_f32(g2, c->num_sms, st)) != cudaSuccess) return e;
+    if ((e = launch_rownorm(P(sk->Z), n, out, P(sk->S), P(sk->nz), c->num_sms, st)) != cudaSuccess) return e;
+    // loss and dL/ds
+    float *scal = P(sk->scal);
+    if ((e = cudaMemsetAsync(scal, 0, 64, st)) != cudaSuccess) return e;
+    if ((e = launch_colsum(w, B, 1, scal + 1, c->num_sms, st)) != cudaSuccess) return e;
+    if ((e = launch_pair_grad(P(sk->S), B, out, t, w, scal + 1, P(sk->dS), scal, c->num_sms, st)) != cudaSuccess)
+        return e;
+    // backward
+    if ((e = launch_rownorm_backward(P(sk->S), P(sk->dS), P(sk->nz), n, out, P(sk->dZ), c->num_sms, st)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(G, 0, (size_t)sk->n_params * 4, st)) != cudaSuccess) return e;
+    GemmArgs gw2;  // dW2 = dZ^T H
+    gw2.A = P(sk->dZ);
+    gw2.a_rs = 1;
+    gw2.a_cs = out;
+    gw2.B = P(sk->H);
+    gw2.b_rs = hid;
+    gw2.b_cs = 1;
+    gw2.C = G + sk->oW2;
+    gw2.ldc = hid;
+    gw2.M = out;
+    gw2.N = hid;
+    gw2.K = n;
+    gw2.atomic_acc = 1;
+    if ((e = launch_gemm_f32(gw2, c->num_sms, st)) != cudaSuccess) return e;
+    if ((e = launch_colsum(P(sk->dZ), n, out, G + sk->ob2, c->num_sms, st)) != cudaSuccess) return e;
+    GemmArgs gh;  // dH = dZ W2
+    gh.A = P(sk->dZ);
+    gh.a_rs = out;
+    gh.a_cs = 1;
+    gh.B = W + sk->oW2;
+    gh.b_rs = hid;
+    gh.b_cs = 1;
+    gh.C = P(sk->dH);
+    gh.ldc = hid;
+    gh.M = n;
+    gh.N = hid;
+    gh.K = out;
+    if ((e = launch_gemm_f32(gh, c->num_sms, st)) != cudaSuccess) return e;
+    if ((e = launch_gelu_backward(P(sk->dH), P(sk->A1), n * hid, c->num_sms, st)) != cudaSuccess) return e;
+    GemmArgs gw1;  // dW1 = dA1^T X (rows gathered and scaled to unit length)
+    gw1.A = P(sk->dH);
+    gw1.a_rs = 1;
+    gw1.a_cs = hid;
+    gw1.B = x;
+    gw1.bidx = idx;
+    gw1.bscale = inv;
+    gw1.b_rs = ld;
+    gw1.b_cs = 1;
+    gw1.C = G + sk->oW1;
+    gw1.ldc = d;
+    gw1.M = hid;
+    gw1.N = d;
+    gw1.K = n;
+    gw1.atomic_acc = 1;
+    if ((e = launch_gemm_f32(gw1, c->num_sms, st)) != cudaSuccess) return e;
+    return launch_colsum(P(sk->dH), n, hid, G + sk->ob1, c->num_sms, st);
+}
+
+ejoin_status check_pairs_args(const ejoin_sketch *sk, ejoin_rel X, const float *inv, const uint32_t *p,
+                              const uint32_t *q, const float *t, const float *w, int64_t B)
+{
+    if (!sk || !X.x || X.d != sk->d || X.ld < X.d || X.n <= 0 || !inv || !p || !q || B <= 0) return EJOIN_EINVAL;
+    if ((t == nullptr) != (w == nullptr)) return EJOIN_EINVAL;
+    return EJOIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ejoin_status ejoin_sketch_create(ejoin_ctx *ctx, int32_t d, int32_t hidden, int32_t out, ejoin_sketch **res)
+{
+    if (!ctx || !res || d < 1 || d > 4096 || hidden < 1 || hidden > 4096 || out != 64) return EJOIN_EINVAL;
+    *res = nullptr;
+    DeviceGuard g(ctx->device);
+    ejoin_sketch *sk = new (std::nothrow) ejoin_sketch();
+    if (!sk) return EJOIN_ENOMEM;
+    sk->ctx = ctx;
+    sk->d = d;
+    sk->hid = hidden;
+    sk->out = out;
+    sk->oW1 = 0;
+    sk->ob1 = (int64_t)hidden * d;
+    sk->oW2 = sk->ob1 + hidden;
+    sk->ob2 = sk->oW2 + (int64_t)out * hidden;
+    sk->n_params = sk->ob2 + out;
+    cudaError_t e;
+    const size_t bytes = (size_t)sk->n_params * 4;
+    if ((e = ensure(sk->params, bytes)) || (e = ensure(sk->grads, bytes)) || (e = ensure(sk->m, bytes)) ||
+        (e = ensure(sk->v, bytes))) {
+        ejoin_sketch_destroy(sk);
+        return from_cuda(e);
+    }
+    *res = sk;
+    return EJOIN_OK;
+}
+
+void ejoin_sketch_destroy(ejoin_sketch *sk)
+{
+    if (!sk) return;
+    {
+        DeviceGuard g(sk->ctx->device);
+        cudaStreamSynchronize(sk->ctx->stream);
+        for (Buf *b : {&sk->params, &sk->grads, &sk->m, &sk->v, &sk->idx, &sk->A1, &sk->H, &sk->Z, &sk->S, &sk->nz,
+                       &sk->dS, &sk->dZ, &sk->dH, &sk->scal, &sk->fH, &sk->fZ, &sk->finv, &sk->list,
+                       &sk->list_count})
+            release(*b);
+        for (auto &w : sk->pw)
+            for (Buf *b : {&w.S, &w.key1, &w.key2, &w.perm1, &w.perm, &w.hist, &w.off, &w.a_idx, &w.anchors1,
+                           &w.anchors2, &w.norm, &w.inv, &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad})
+                release(*b);
+    }
+    delete sk;
+}
+
+int64_t ejoin_sketch_num_params(const ejoin_sketch *sk) { return sk ? sk->n_params : 0; }
+
+ejoin_status ejoin_sketch_set_params(ejoin_sketch *sk, const float *h_params)
+{
+    if (!sk || !h_params) return EJOIN_EINVAL;
+    DeviceGuard g(sk->ctx->device);
+    const size_t bytes = (size_t)sk->n_params * 4;
+    cudaError_t e = cudaMemcpy(sk->params.p, h_params, bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(sk->m.p, 0, bytes);
+    if (e == cudaSuccess) e = cudaMemset(sk->v.p, 0, bytes);
+    sk->step = 0;
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_sketch_get_params(const ejoin_sketch *sk, float *h_params)
+{
+    if (!sk || !h_params) return EJOIN_EINVAL;
+    DeviceGuard g(sk->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(sk->ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(h_params, sk->params.p, (size_t)sk->n_params * 4, cudaMemcpyDeviceToHost);
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_sketch_forward(ejoin_sketch *sk, ejoin_rel X, float *d_S)
+{
+    if (!sk || !d_S || X.d != sk->d || X.ld < X.d || X.n < 0 || (X.n && !X.x)) return EJOIN_EINVAL;
+    if (X.n == 0) return EJOIN_OK;
+    DeviceGuard g(sk->ctx->device);
+    cudaError_t e = ensure(sk->finv, (size_t)X.n * 4);
+    if (e == cudaSuccess) e = launch_row_inv_norm(X.x, X.n, X.d, X.ld, P(sk->finv), sk->ctx->num_sms, sk->ctx->stream);
+    if (e == cudaSuccess) e = sketch_forward(sk, X.x, X.n, X.ld, P(sk->finv), d_S, sk->ctx->stream);
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_row_inv_norm(ejoin_ctx *ctx, ejoin_rel X, float *d_inv)
+{
+    if (!ctx || !d_inv || X.n < 0 || (X.n && !X.x) || X.ld < X.d) return EJOIN_EINVAL;
+    DeviceGuard g(ctx->device);
+    return from_cuda(launch_row_inv_norm(X.x, X.n, X.d, X.ld, d_inv, ctx->num_sms, ctx->stream));
+}
+
+ejoin_status ejoin_score_pairs(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, const uint32_t *d_i, const uint32_t *d_j,
+                               int64_t n_pairs, float *d_sim)
+{
+    if (!ctx || R.d != S.d || R.ld < R.d || S.ld < S.d || n_pairs < 0 || (n_pairs && (!d_i || !d_j || !d_sim)) ||
+        (R.n && !R.x) || (S.n && !S.x))
+        return EJOIN_EINVAL;
+    if (n_pairs == 0) return EJOIN_OK;
+    DeviceGuard g(ctx->device);
+    Side &a = ctx->side[0], &b = ctx->side[1];
+    cudaError_t e;
+    if ((e = ensure(a.inv, (size_t)std::max<int64_t>(R.n, 1) * 4)) ||
+        (e = ensure(b.inv, (size_t)std::max<int64_t>(S.n, 1) * 4)) ||
+        (e = launch_row_inv_norm(R.x, R.n, R.d, R.ld, (float *)a.inv.p, ctx->num_sms, ctx->stream)) ||
+        (e = launch_row_inv_norm(S.x, S.n, S.d, S.ld, (float *)b.inv.p, ctx->num_sms, ctx->stream)) ||
+        (e = launch_score_pairs(R.x, R.ld, S.x, S.ld, R.d, d_i, d_j, (const float *)a.inv.p, (const float *)b.inv.p,
+                                n_pairs, d_sim, ctx->num_sms, ctx->stream)))
+        return from_cuda(e);
+    return EJOIN_OK;
+}
+
+ejoin_status ejoin_sketch_grad(ejoin_sketch *sk, ejoin_rel X, const float *d_inv, const uint32_t *d_p,
+                               const uint32_t *d_q, const float *d_t, const float *d_w, int64_t n_pairs,
+                               float *d_grad, float *h_loss)
+{
+    ejoin_status s = check_pairs_args(sk, X, d_inv, d_p, d_q, d_t, d_w, n_pairs);
+    if (s != EJOIN_OK || !d_t) return s != EJOIN_OK ? s : EJOIN_EINVAL;
+    DeviceGuard g(sk->ctx->device);
+    cudaStream_t st = sk->ctx->stream;
+    cudaError_t e = sketch_grad(sk, X.x, X.ld, d_inv, d_p, d_q, d_t, d_w, n_pairs, st);
+    if (e == cudaSuccess && d_grad)
+        e = cudaMemcpyAsync(d_grad, sk->grads.p, (size_t)sk->n_params * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && h_loss) {
+        e = cudaMemcpyAsync(h_loss, sk->scal.p, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_sketch_train_step(ejoin_sketch *sk, ejoin_rel X, const float *d_inv, const uint32_t *d_p,
+                                     const uint32_t *d_q, const float *d_t, const float *d_w, int64_t n_pairs,
+                                     float lr, float *h_loss)
+{
+    ejoin_status s = check_pairs_args(sk, X, d_inv, d_p, d_q, d_t, d_w, n_pairs);
+    if (s != EJOIN_OK || !d_t) return s != EJOIN_OK ? s : EJOIN_EINVAL;
+    DeviceGuard g(sk->ctx->device);
+    cudaStream_t st = sk->ctx->stream;
+    cudaError_t e = sketch_grad(sk, X.x, X.ld, d_inv, d_p, d_q, d_t, d_w, n_pairs, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    sk->step += 1;
+    e = launch_adam(P(sk->params), P(sk->grads), P(sk->m), P(sk->v), sk->n_params, lr, 0.9f, 0.999f, 1e-8f,
+                    sk->step, sk->ctx->num_sms, st);
+    if (e == cudaSuccess && h_loss) {
+        e = cudaMemcpyAsync(h_loss, sk->scal.p, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_sketch_pair_sims(ejoin_sketch *sk, ejoin_rel X, const float *d_inv, const uint32_t *d_p,
+                                    const uint32_t *d_q, int64_t n_pairs, float *d_out)
+{
+    ejoin_status s = check_pairs_args(sk, X, d_inv, d_p, d_q, nullptr, nullptr, n_pairs);
+    if (s != EJOIN_OK || !d_out) return s != EJOIN_OK ? s : EJOIN_EINVAL;
+    DeviceGuard g(sk->ctx->device);
+    cudaStream_t st = sk->ctx->stream;
+    ejoin_ctx *c = sk->ctx;
+    const int64_t n = 2 * n_pairs;
+    cudaError_t e;
+    if ((e = grow(sk->idx, (size_t)n * 4)) || (e = grow(sk->H, (size_t)n * sk->hid * 4)) ||
+        (e = grow(sk->Z, (size_t)n * sk->out * 4)) || (e = grow(sk->S, (size_t)n * sk->out * 4)))
+        return from_cuda(e);
+    uint32_t *idx = (uint32_t *)sk->idx.p;
+    if ((e = cudaMemcpyAsync(idx, d_p, n_pairs * 4, cudaMemcpyDeviceToDevice, st)) ||
+        (e = cudaMemcpyAsync(idx + n_pairs, d_q, n_pairs * 4, cudaMemcpyDeviceToDevice, st)))
+        return from_cuda(e);
+    float *W = P(sk->params);
+    GemmArgs g1;
+    g1.A = X.x;
+    g1.aidx = idx;
+    g1.a_rs = X.ld;
+    g1.a_cs = 1;
+    g1.B = W + sk->oW1;
+    g1.b_rs = 1;
+    g1.b_cs = sk->d;
+    g1.C = P(sk->H);
+    g1.ldc = sk->hid;
+    g1.bias = W + sk->ob1;
+    g1.rowscale = d_inv;
+    g1.M = n;
+    g1.N = sk->hid;
+    g1.K = sk->d;
+    g1.act = ACT_GELU;
+    if ((e = launch_gemm_f32(g1, c->num_sms, st)) != cudaSuccess) return from_cuda(e);
+    GemmArgs g2;
+    g2.A = P(sk->H);
+    g2.a_rs = sk->hid;
+    g2.a_cs = 1;
+    g2.B = W + sk->oW2;
+    g2.b_rs = 1;
+    g2.b_cs = sk->hid;
+    g2.C = P(sk->Z);
+    g2.ldc = sk->out;
+    g2.bias = W + sk->ob2;
+    g2.M = n;
+    g2.N = sk->out;
+    g2.K = sk->hid;
+    if ((e = launch_gemm_f32(g2, c->num_sms, st)) != cudaSuccess) return from_cuda(e);
+    if ((e = launch_rownorm(P(sk->Z), n, sk->out, P(sk->S), nullptr, c->num_sms, st)) != cudaSuccess)
+        return from_cuda(e);
+    return from_cuda(launch_pair_dot(P(sk->S), n_pairs, sk->out, d_out, c->num_sms, st));
+}
+
+}  // extern "C"
+
+namespace {
+
+constexpr int N_COARSE = 256, N_FINE = 128, SKW = 64;
+
+// Steps 1-3 of the pruned join for one side: normalise, sketch, reorder, gather.
+ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, int64_t kp)
+{
+    ejoin_ctx *c = sk->ctx;
+    cudaStream_t st = c->stream;
+    auto &pw = sk->pw[w];
+    Side &sd = c->side[w];
+    const size_t eb = fmt_bytes(fmt);
+    const int64_t n = r.n;
+    const int64_t rows = round_up(std::max<int64_t>(n, 1), 256);
+    const int n_coarse = (int)std::min<int64_t>(N_COARSE, std::max<int64_t>(n, 1));
+    const int n_keys = n_coarse * N_FINE;
+    cudaError_t e;
+    if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) || (e = ensure(sd.inv, (size_t)rows * 4)) ||
+        (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4))) || (e = ensure(pw.S, (size_t)rows * SKW * 4)) ||
+        (e = ensure(pw.key1, (size_t)rows * 4)) || (e = ensure(pw.key2, (size_t)rows * 4)) ||
+        (e = ensure(pw.perm1, (size_t)rows * 4)) || (e = ensure(pw.perm, (size_t)rows * 4)) ||
+        (e = ensure(pw.hist, (size_t)n_keys * 4)) || (e = ensure(pw.off, (size_t)n_keys * 4)) ||
+(e = ensure(pw.anchors1, (size_t)N_COARSE * SKW * 4)) ||
+        (e = ensure(pw.anchors2, (size_t)N_COARSE * N_FINE * SKW * 4)) ||
+        (e = ensure(pw.norm, (size_t)rows * kp * eb)) || (e = ensure(pw.inv, (size_t)rows * 4)) ||
+        (fmt == FMT_FP8 && (e = ensure(pw.scale, (size_t)rows * 4))) || (e = ensure(pw.sS, (size_t)rows * SKW * 4)) ||
+        (e = ensure(pw.maxdot, (size_t)rows * 4)))
+        return from_cuda(e);
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    long long *n_dev = &dm->n_sel[w];
+    if ((e = launch_set_count(n_dev, n, st)) != cudaSuccess) return from_cuda(e);
+    if ((e = launch_normalize(fmt, r.x, r.ld, r.d, nullptr, n_dev, n, sd.norm.p, kp, (int)kp, (float *)sd.inv.p,
+                              (float *)sd.scale.p, &dm->status, c->num_sms, st)) != cudaSuccess)
+        return from_cuda(e);
+    if ((e = sketch_forward(sk, r.x, n, r.ld, (const float *)sd.inv.p, (float *)pw.S.p, st)) != cudaSuccess)
+        return from_cuda(e);
+    // coarse anchors: farthest-point sampling over a strided sample of at most 65,536 rows
+    const int64_t n_samp = std::min<int64_t>(n, 65536);
+    std::vector<uint32_t> aidx(n_samp);
+    for (int64_t a = 0; a < n_samp; ++a) aidx[a] = (uint32_t)(a * n / n_samp);
+    const uint32_t zero = 0;
+    if ((e = ensure(pw.a_idx, (size_t)n_samp * 4 + 16)) != cudaSuccess) return from_cuda(e);
+    if ((e = cudaMemcpyAsync(pw.a_idx.p, aidx.data(), n_samp * 4, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemcpyAsync((char *)pw.a_idx.p + n_samp * 4, &zero, 4, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaStreamSynchronize(st)))  // aidx and zero are host temporaries
+        return from_cuda(e);
+    uint32_t *key1 = (uint32_t *)pw.key1.p, *key2 = (uint32_t *)pw.key2.p, *hist = (uint32_t *)pw.hist.p,
+             *off = (uint32_t *)pw.off.p, *perm1 = (uint32_t *)pw.perm1.p, *perm = (uint32_t *)pw.perm.p;
+    if ((e = launch_fine_anchors((const float *)pw.S.p, (const uint32_t *)pw.a_idx.p,
+                                 (const uint32_t *)pw.a_idx.p + n_samp, 1, n_samp, n_coarse, (float *)pw.maxdot.p,
+                                 (float *)pw.anchors1.p, st)) ||
+        (e = launch_assign_keys((const float *)pw.S.p, n, SKW, (const float *)pw.anchors1.p, n_coarse, nullptr, key1,
+                                c->num_sms, st)) ||
+        (e = cudaMemsetAsync(hist, 0, n_coarse * 4, st)) || (e = launch_key_histogram(key1, n, hist, st)) ||
+        (e = launch_key_scan(hist, n_coarse, st)) ||
+        (e = cudaMemcpyAsync(off, hist, n_coarse * 4, cudaMemcpyDeviceToDevice, st)) ||
+        (e = launch_key_scatter(key1, n, hist, perm1, st)) ||
+        (e = launch_fine_anchors((const float *)pw.S.p, perm1, off, n_coarse, n, N_FINE, (float *)pw.maxdot.p,
+                                 (float *)pw.anchors2.p, st)) ||
+        (e = launch_assign_keys((const float *)pw.S.p, n, SKW, (const float *)pw.anchors2.p, N_FINE, key1, key2,
+                                c->num_sms, st)) ||
+        (e = cudaMemsetAsync(hist, 0, n_keys * 4, st)) || (e = launch_key_histogram(key2, n, hist, st)) ||
+        (e = launch_key_scan(hist, n_keys, st)) || (e = launch_key_scatter(key2, n, hist, perm, st)) ||
+        (e = launch_gather_rows(sd.norm.p, kp * eb, perm, n, pw.norm.p, st)) ||
+        (e = launch_gather_f32((const float *)sd.inv.p, perm, n, (float *)pw.inv.p, st)) ||
+        (e = launch_gather_rows(pw.S.p, SKW * 4, perm, n, pw.sS.p, st)) ||
+        (fmt == FMT_FP8 && (e = launch_gather_f32((const float *)sd.scale.p, perm, n, (float *)pw.scale.p, st))))
+        return from_cuda(e);
+    return EJOIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R, ejoin_rel S, float eps,
+                                    float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *ps)
+{
+    if (!c || !sk || !out || sk->ctx != c) return EJOIN_EINVAL;
+    if (R.d != S.d || R.d != sk->d || R.n < 0 || S.n < 0 || R.ld < R.d || S.ld < S.d || (R.n && !R.x) ||
+        (S.n && !S.x) || std::isnan(eps) || std::isnan(eps_sketch))
+        return EJOIN_EINVAL;
+    if (c->prec == EJOIN_F32) return EJOIN_EUNSUPPORTED;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    c->stats = ejoin_stats{};
+    ejoin_prune_stats local{};
+    ejoin_prune_stats &P_ = ps ? *ps : local;
+    P_ = ejoin_prune_stats{};
+    out->count = 0;
+    if (R.n == 0 || S.n == 0) return EJOIN_OK;
+    const int fmt = fmt_of(c->prec);
+    const int kind = c->prec == EJOIN_BF16 ? 0 : (c->prec == EJOIN_FP8_E4M3 ? 1 : 2);
+    const int64_t kp = ejoin_padded_dim(c->prec, R.d);
+    const float band = c->band_cfg >= 0.f ? c->band_cfg : default_band(c->prec, kp);
+    const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld;
+    cudaError_t e;
+    ejoin_status s;
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), st)) != cudaSuccess) return from_cuda(e);
+    cudaEvent_t *ev = c->ev;
+    cudaEventRecord(ev[0], st);
+    if ((s = prune_side(sk, 0, R, fmt, kp)) != EJOIN_OK) return s;
+    if (!self && (s = prune_side(sk, 1, S, fmt, kp)) != EJOIN_OK) return s;
+    auto &pa = sk->pw[0];
+    auto &pb = self ? sk->pw[0] : sk->pw[1];
+    if (self && (e = launch_set_count(&dm->n_sel[1], S.n, st)) != cudaSuccess) return from_cuda(e);
+    cudaEventRecord(ev[1], st);
+    // tile statistics and tile-pair bounds
+    const int64_t tA = (R.n + 127) / 128, tB = (S.n + 255) / 256;
+    constexpr int NBL = PRUNE_BALLS;
+    if ((e = ensure(pa.cent, (size_t)tA * NBL * SKW * 4)) || (e = ensure(pa.rad, (size_t)tA * NBL * 4)))
+        return from_cuda(e);
+    float *cB = nullptr, *rB = nullptr;
+    Buf centB, radB;  // (self-join: the B side uses 256-row tiles of the same order)
+    if ((e = launch_tile_stats((const float *)pa.sS.p, R.n, SKW, 128, (float *)pa.cent.p, (float *)pa.rad.p, st)) !=
+        cudaSuccess)
+        return from_cuda(e);
+    if (self) {
+        if ((e = ensure(centB, (size_t)tB * NBL * SKW * 4)) || (e = ensure(radB, (size_t)tB * NBL * 4)))
+            return from_cuda(e);
+        cB = (float *)centB.p;
+        rB = (float *)radB.p;
+    } else {
+        if ((e = ensure(pb.cent, (size_t)tB * NBL * SKW * 4)) || (e = ensure(pb.rad, (size_t)tB * NBL * 4)))
+            return from_cuda(e);
+        cB = (float *)pb.cent.p;
+        rB = (float *)pb.rad.p;
+    }
+    if ((e = launch_tile_stats((const float *)pb.sS.p, S.n, SKW, 256, cB, rB, st)) != cudaSuccess) {
+        release(centB);
+        release(radB);
+        return from_cuda(e);
+    }
+    if (sk->list_cap == 0) sk->list_cap = std::min<uint64_t>((uint64_t)tA * tB, 1ull << 22);
+    unsigned long long n_list = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if ((e = ensure(sk->list, sk->list_cap * sizeof(uint2))) || (e = ensure(sk->list_count, 8)) ||
+            (e = cudaMemsetAsync(sk->list_count.p, 0, 8, st)) ||
+            (e = launch_tile_pairs((const float *)pa.cent.p, (const float *)pa.rad.p, tA, cB, rB, tB, SKW, eps_sketch,
+                                   (uint2 *)sk->list.p, sk->list_cap, (unsigned long long *)sk->list_count.p, st)) ||
+            (e = cudaMemcpyAsync(&n_list, sk->list_count.p, 8, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            release(centB);
+            release(radB);
+            return from_cuda(e);
+        }
+        if (n_list <= sk->list_cap) break;
+        sk->list_cap = n_list;
+    }
+    release(centB);
+    release(radB);
+    cudaEventRecord(ev[2], st);
+    P_.tiles_total = (uint64_t)tA * tB;
+    P_.tiles_kept = n_list;
+    // contraction over the kept tiles
+    const int64_t rowsA = round_up(R.n, 256), rowsB = round_up(S.n, 256);
+    CUtensorMap tmA, tmB;
+    if (!make_tmap(&tmA, pa.norm.p, fmt, kp, rowsA, 128) || !make_tmap(&tmB, pb.norm.p, fmt, kp, rowsB, 256))
+        return EJOIN_ECUDA;
+    if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
+    if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    DevMisc hm;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((e = cudaMemsetAsync(&dm->cand_count, 0, 8, st)) ||
+            (e = launch_sim_tc_list(kind, &tmA, &tmB, (int)kp, &dm->n_sel[0], &dm->n_sel[1], eps - band,
+                                    (const uint2 *)sk->list.p, (const unsigned long long *)sk->list_count.p,
+                                    sk->list_cap, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status,
+                                    c->timeout, c->num_sms, st)) ||
+            (e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            return from_cuda(e);
+        if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        if (hm.cand_count <= c->cand_cap) break;
+        c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+        if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    }
+    cudaEventRecord(ev[3], st);
+    // result buffer and exact re-score (sorted rows map back to original ids through the permutations)
+    if (out->d_pairs == nullptr) {
+        void *p = nullptr;
+        const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
+        if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
+        out->d_pairs = (ejoin_pair *)p;
+        out->capacity = cap;
+    }
+    if (hm.cand_count) {
+        e = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
+                           (const uint32_t *)pa.perm.p, (const uint32_t *)pb.perm.p, (const float *)pa.inv.p,
+                           (const float *)pb.inv.p, eps, c->fp64_band, out->d_pairs, out->capacity, &dm->pair_count,
+                           &dm->band_count, 0, c->num_sms, st);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (out->d_count &&
+        (e = cudaMemcpyAsync(out->d_count, &dm->pair_count, 8, cudaMemcpyDeviceToDevice, st)) != cudaSuccess)
+        return from_cuda(e);
+    cudaEventRecord(ev[4], st);
+    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return from_cuda(e);
+    auto ms = [&](int a, int b) {
+        float x = 0.f;
+        cudaEventElapsedTime(&x, ev[a], ev[b]);
+        return x;
+    };
+    P_.candidates = hm.cand_count;
+    P_.pairs = hm.pair_count;
+    P_.ms_prepare = ms(0, 1);
+    P_.ms_bound = ms(1, 2);
+    P_.ms_contract = ms(2, 3);
+    P_.ms_rescore = ms(3, 4);
+    P_.ms_total = ms(0, 4);
+    c->stats.candidates = hm.cand_count;
+    c->stats.pairs = hm.pair_count;
+    c->stats.fp64_rescored = hm.band_count;
+    c->stats.band = band;
+    out->count = hm.pair_count;
+    return hm.pair_count > out->capacity ? EJOIN_EOVERFLOW : EJOIN_OK;
+}
+
+}  // extern "C"

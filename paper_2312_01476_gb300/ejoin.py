@@ -70,6 +70,12 @@ class ejoin_batch_stats(ctypes.Structure):
 
 EJOIN_BATCH_GRAPH, EJOIN_BATCH_AUTOTUNE = 0x1, 0x2
 
+
+class ejoin_prune_stats(ctypes.Structure):
+    _fields_ = [("tiles_total", ctypes.c_uint64), ("tiles_kept", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
+                ("pairs", ctypes.c_uint64), ("ms_prepare", ctypes.c_float), ("ms_bound", ctypes.c_float),
+                ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float)]
+
 _lib = None
 
 
@@ -124,6 +130,33 @@ def load_library(path: str = LIB_PATH):
     lib.ejoin_batch_info.argtypes = [ctypes.c_void_p, P(ejoin_batch_stats)]
     lib.ejoin_batch_destroy.restype = None
     lib.ejoin_batch_destroy.argtypes = [ctypes.c_void_p]
+    vp = ctypes.c_void_p
+    lib.ejoin_sketch_create.restype = ctypes.c_int
+    lib.ejoin_sketch_create.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P(vp)]
+    lib.ejoin_sketch_destroy.restype = None
+    lib.ejoin_sketch_destroy.argtypes = [vp]
+    lib.ejoin_sketch_num_params.restype = ctypes.c_int64
+    lib.ejoin_sketch_num_params.argtypes = [vp]
+    lib.ejoin_sketch_set_params.restype = ctypes.c_int
+    lib.ejoin_sketch_set_params.argtypes = [vp, vp]
+    lib.ejoin_sketch_get_params.restype = ctypes.c_int
+    lib.ejoin_sketch_get_params.argtypes = [vp, vp]
+    lib.ejoin_sketch_forward.restype = ctypes.c_int
+    lib.ejoin_sketch_forward.argtypes = [vp, ejoin_rel, vp]
+    lib.ejoin_sketch_grad.restype = ctypes.c_int
+    lib.ejoin_sketch_grad.argtypes = [vp, ejoin_rel, vp, vp, vp, vp, vp, ctypes.c_int64, vp, P(ctypes.c_float)]
+    lib.ejoin_sketch_train_step.restype = ctypes.c_int
+    lib.ejoin_sketch_train_step.argtypes = [vp, ejoin_rel, vp, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_float,
+                                            P(ctypes.c_float)]
+    lib.ejoin_sketch_pair_sims.restype = ctypes.c_int
+    lib.ejoin_sketch_pair_sims.argtypes = [vp, ejoin_rel, vp, vp, vp, ctypes.c_int64, vp]
+    lib.ejoin_row_inv_norm.restype = ctypes.c_int
+    lib.ejoin_row_inv_norm.argtypes = [vp, ejoin_rel, vp]
+    lib.ejoin_score_pairs.restype = ctypes.c_int
+    lib.ejoin_score_pairs.argtypes = [vp, ejoin_rel, ejoin_rel, vp, vp, ctypes.c_int64, vp]
+    lib.ejoin_threshold_pruned.restype = ctypes.c_int
+    lib.ejoin_threshold_pruned.argtypes = [vp, vp, ejoin_rel, ejoin_rel, ctypes.c_float, ctypes.c_float,
+                                           P(ejoin_pairs), P(ejoin_prune_stats)]
     if path == LIB_PATH:
         _lib = lib
     return lib
@@ -422,3 +455,121 @@ def ejoin_batch(ctx: Ctx, jobs, graph: bool = True, autotune: bool = False):
     job, i, j, sim = (x.cpu().numpy() for x in b.result(n))
     b.close()
     return job, i, j, sim
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def ejoin_row_inv_norm(ctx: Ctx, X):
+    import torch
+    inv = torch.empty(max(X.shape[0], 1), dtype=torch.float32, device=X.device)
+    _check(load_library().ejoin_row_inv_norm(ctx.handle, _dev_rel(X), _ptr(inv)), "ejoin_row_inv_norm")
+    return inv[: X.shape[0]]
+
+
+def ejoin_score_pairs(ctx: Ctx, R, S, i, j):
+    """Exact FP32 cosine of pairs (R[i[k]], S[j[k]]) (int32 CUDA index tensors)."""
+    import torch
+    out = torch.empty(max(len(i), 1), dtype=torch.float32, device=R.device)
+    _check(load_library().ejoin_score_pairs(ctx.handle, _dev_rel(R), _dev_rel(S), _ptr(i), _ptr(j), len(i),
+                                            _ptr(out)), "ejoin_score_pairs")
+    return out[: len(i)]
+
+
+class Sketch:
+    """The learned sketch network (ejoin_sketch_*): d -> hidden -> 64, GELU, unit output."""
+
+    def __init__(self, ctx: Ctx, d: int, hidden: int = 256, out: int = 64):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.ejoin_sketch_create(ctx.handle, d, hidden, out, ctypes.byref(h)), "ejoin_sketch_create")
+        self.handle, self.ctx, self.d, self.hidden, self.out = h, ctx, d, hidden, out
+        self.n_params = int(lib.ejoin_sketch_num_params(h))
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.n_params
+        _check(load_library().ejoin_sketch_set_params(self.handle, flat.ctypes.data), "ejoin_sketch_set_params")
+
+    def get_params(self) -> np.ndarray:
+        flat = np.empty(self.n_params, dtype=np.float32)
+        _check(load_library().ejoin_sketch_get_params(self.handle, flat.ctypes.data), "ejoin_sketch_get_params")
+        return flat
+
+    def unflatten(self, flat):
+        d, h, o = self.d, self.hidden, self.out
+        a = 0
+        W1 = flat[a:a + h * d].reshape(h, d); a += h * d
+        b1 = flat[a:a + h]; a += h
+        W2 = flat[a:a + o * h].reshape(o, h); a += o * h
+        b2 = flat[a:a + o]
+        return {"W1": W1, "b1": b1, "W2": W2, "b2": b2}
+
+    @staticmethod
+    def flatten(p):
+        return np.concatenate([p["W1"].ravel(), p["b1"].ravel(), p["W2"].ravel(), p["b2"].ravel()]).astype(np.float32)
+
+    def forward(self, X):
+        import torch
+        S = torch.empty((max(X.shape[0], 1), self.out), dtype=torch.float32, device=X.device)
+        _check(load_library().ejoin_sketch_forward(self.handle, _dev_rel(X), _ptr(S)), "ejoin_sketch_forward")
+        return S[: X.shape[0]]
+
+    def grad(self, X, inv, p, q, t, w):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_float(0)
+        _check(load_library().ejoin_sketch_grad(self.handle, _dev_rel(X), _ptr(inv), _ptr(p), _ptr(q), _ptr(t),
+                                                _ptr(w), len(p), _ptr(g), ctypes.byref(loss)), "ejoin_sketch_grad")
+        return g, float(loss.value)
+
+    def train_step(self, X, inv, p, q, t, w, lr: float, want_loss: bool = False):
+        loss = ctypes.c_float(0)
+        _check(load_library().ejoin_sketch_train_step(self.handle, _dev_rel(X), _ptr(inv), _ptr(p), _ptr(q), _ptr(t),
+                                                      _ptr(w), len(p), ctypes.c_float(lr),
+                                                      ctypes.byref(loss) if want_loss else None),
+               "ejoin_sketch_train_step")
+        return float(loss.value) if want_loss else None
+
+    def pair_sims(self, X, inv, p, q):
+        import torch
+        out = torch.empty(max(len(p), 1), dtype=torch.float32, device=X.device)
+        _check(load_library().ejoin_sketch_pair_sims(self.handle, _dev_rel(X), _ptr(inv), _ptr(p), _ptr(q), len(p),
+                                                     _ptr(out)), "ejoin_sketch_pair_sims")
+        return out[: len(p)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().ejoin_sketch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ejoin_threshold_pruned(ctx: Ctx, sk: Sketch, R, S, eps: float, eps_sketch: float, capacity=None):
+    """Pruned device join; returns (Result, stats dict)."""
+    import torch
+    lib = load_library()
+    rR, rS = _dev_rel(R), _dev_rel(S)
+    cap = capacity or (ctx._out.shape[0] if ctx._out is not None else 1 << 16)
+    for _ in range(3):
+        if ctx._out is None or ctx._out.shape[0] < cap:
+            ctx._out = torch.empty((cap, 3), dtype=torch.int32, device=R.device)
+        out = ejoin_pairs(ctypes.c_void_p(ctx._out.data_ptr()), ctx._out.shape[0], None, 0)
+        st = ejoin_prune_stats()
+        status = lib.ejoin_threshold_pruned(ctx.handle, sk.handle, rR, rS, ctypes.c_float(eps),
+                                            ctypes.c_float(eps_sketch), ctypes.byref(out), ctypes.byref(st))
+        if status == EJOIN_EOVERFLOW:
+            cap = int(out.count) + 1024
+            continue
+        _check(status, "ejoin_threshold_pruned")
+        n = int(out.count)
+        v = ctx._out[:n]
+        stats = {name: getattr(st, name) for name, _ in ejoin_prune_stats._fields_}
+        return Result(v[:, 0], v[:, 1], v[:, 2].view(torch.float32), n), stats
+    raise EJoinError(EJOIN_EOVERFLOW, "ejoin_threshold_pruned")
