@@ -67,6 +67,11 @@ typedef enum ejoin_prec {
 /* ejoin_config.flags */
 #define EJOIN_FLAG_COUNT_ONLY 0x1u /* count the pairs, store none (a "count pass") */
 #define EJOIN_FLAG_TIMING     0x2u /* record CUDA events around each stage (ejoin_last_stats) */
+#define EJOIN_FLAG_FUSED      0x4u /* tensor-core precisions: run the re-score as extra warps of the
+                                      contraction kernel (one launch; needs 16-byte aligned rows,
+                                      d % 4 == 0 and a caller-supplied result buffer).  Off by default:
+                                      on GB300 the separate re-score kernel, with the whole GPU behind it,
+                                      is faster on candidate-dense joins */
 
 typedef struct ejoin_config {
     int32_t device;          /* CUDA device ordinal */
@@ -135,9 +140,11 @@ typedef struct ejoin_stats {
     uint64_t pairs;             /* result pairs */
     uint64_t launches;          /* kernels launched by the call */
     float band;                 /* guard band used */
-    float ms_select, ms_normalize, ms_contract, ms_rescore, ms_total; /* FLAG_TIMING only */
+    float ms_select, ms_normalize, ms_contract, ms_rescore, ms_total; /* FLAG_TIMING only; with the fused
+                                                                         kernel ms_contract covers both */
     float ms_h2d, ms_d2h;       /* ejoin_threshold_host only, FLAG_TIMING only */
     int32_t contract_retries;   /* candidate-buffer regrowths */
+    int32_t fused;              /* 1 if the re-score ran fused into the contraction */
 } ejoin_stats;
 
 /* Create a context on cfg->device (made current for the call).  cfg may be

@@ -394,6 +394,63 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         if (!make_tmap(&tmA, sa.norm.p, fmt, kp, rowsA, 128) || !make_tmap(&tmB, sb.norm.p, fmt, kp, rowsB, 256))
             return EJOIN_ECUDA;
     }
+    const bool aligned_rows = R.d % 4 == 0 && R.ld % 4 == 0 && S.ld % 4 == 0 &&
+                              (reinterpret_cast<uintptr_t>(R.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(S.x) & 15) == 0;
+    const bool fuse = prec != EJOIN_F32 && (c->flags & EJOIN_FLAG_FUSED) && aligned_rows &&
+                      (*pairs_io != nullptr || count_only);
+    if (fuse) {
+        // contraction with the exact re-score fused in: one launch writes the final pairs
+        FuseArgs fa{};
+        fa.R = R.x;
+        fa.ldR = R.ld;
+        fa.S = S.x;
+        fa.ldS = S.ld;
+        fa.d = R.d;
+        fa.idsR = selR ? (const uint32_t *)sa.ids.p : nullptr;
+        fa.idsS = selS ? (const uint32_t *)sb.ids.p : nullptr;
+        fa.invR = (const float *)sa.inv.p;
+        fa.invS = (const float *)sb.inv.p;
+        fa.eps = eps;
+        fa.fp64_band = c->fp64_band;
+        fa.out = *pairs_io;
+        fa.out_cap = count_only ? 0 : *cap_io;
+        fa.pair_count = &dm->pair_count;
+        fa.band_count = &dm->band_count;
+        fa.count_only = count_only ? 1 : 0;
+        const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
+        e = launch_sim_tc_fused(kind, &tmA, &tmB, (int)kp, nA, nB, thr, (const float *)sa.scale.p,
+                                (const float *)sb.scale.p, fa, &dm->cand_count, &dm->status, c->timeout, c->num_sms,
+                                c->group_m > 0 ? c->group_m : default_group_m(kp), c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        c->stats.launches += 1;
+        c->stats.fused = 1;
+        if (timing) cudaEventRecord(c->ev[2], c->stream);
+        if (d_count_user &&
+            (e = cudaMemcpyAsync(d_count_user, &dm->pair_count, sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                 c->stream)) != cudaSuccess)
+            return from_cuda(e);
+        DevMisc hf;
+        if ((e = cudaMemcpyAsync(&hf, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+            return from_cuda(e);
+        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+        c->stats.n_sel_r = (uint64_t)hf.n_sel[0];
+        c->stats.n_sel_s = (uint64_t)(self ? hf.n_sel[0] : hf.n_sel[1]);
+        if (hf.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+        if (hf.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        if (hf.status) return EJOIN_ECUDA;
+        c->stats.candidates = hf.cand_count;
+        c->stats.pairs = hf.pair_count;
+        c->stats.fp64_rescored = hf.band_count;
+        if (timing) {
+            c->stats.ms_normalize = elapsed(c->ev[0], c->ev[1]);
+            c->stats.ms_contract = elapsed(c->ev[1], c->ev[2]);
+            c->stats.ms_rescore = 0.f;
+            c->stats.ms_total = elapsed(c->ev[0], c->ev[2]);
+        }
+        *count_out = hf.pair_count;
+        if (!count_only && hf.pair_count > *cap_io) return EJOIN_EOVERFLOW;
+        return EJOIN_OK;
+    }
     auto contract = [&]() -> ejoin_status {
         cudaError_t ee;
         if (prec == EJOIN_F32) {
@@ -413,9 +470,11 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     if (timing) cudaEventRecord(c->ev[2], c->stream);
 
     DevMisc hm;
-    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-        return from_cuda(e);
-    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+    auto read_misc = [&]() -> cudaError_t {
+        cudaError_t ee = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream);
+        return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
+    };
+    if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
     c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
     c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
     if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
@@ -429,9 +488,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
             return from_cuda(e);
         if ((st = contract()) != EJOIN_OK) return st;
         if (timing) cudaEventRecord(c->ev[2], c->stream);
-        if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-            return from_cuda(e);
-        if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+        if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
         if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
         c->stats.contract_retries++;
     }

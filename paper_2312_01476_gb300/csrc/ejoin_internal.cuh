@@ -68,6 +68,22 @@ struct BatchRows {
     int n_jobs;
 };
 
+// Arguments of the re-score fused into the contraction (single join).
+struct FuseArgs {
+    const float *R;
+    int64_t ldR;
+    const float *S;
+    int64_t ldS;
+    int d;
+    const uint32_t *idsR, *idsS;
+    const float *invR, *invS;
+    float eps, fp64_band;
+    ejoin_pair *out;
+    uint64_t out_cap;
+    unsigned long long *pair_count, *band_count;
+    int count_only;
+};
+
 // One result record of a batched join.
 struct BatchPair {
     uint32_t job, i, j;
@@ -102,6 +118,13 @@ cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *t
                           const float *scaleB, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
                           unsigned *status, uint64_t timeout, int count_only, int grid, int group_m,
                           cudaStream_t st);
+// Contraction with the exact re-score fused in (extra warps consume the candidates from a
+// shared-memory ring and write final pairs).  Needs 16-byte aligned rows, ld % 4 == 0 and
+// d % 4 == 0.
+cudaError_t launch_sim_tc_fused(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                                const long long *nA, const long long *nB, float thr, const float *scaleA,
+                                const float *scaleB, const FuseArgs &fa, unsigned long long *cand_count,
+                                unsigned *status, uint64_t timeout, int grid, int group_m, cudaStream_t st);
 // Contraction over an explicit list of (row tile, column tile) pairs (pruned joins).
 cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
                                const long long *nB, float thr, const uint2 *tile_list,
@@ -130,6 +153,7 @@ inline int default_group_m(int64_t kp)
     return (int)g;
 }
 size_t sim_tc_smem_bytes();
+// Candidates: cand[0 .. min(*cand_count, cand_cap)).
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                            const float *R, int64_t ldR, const float *S, int64_t ldS, int d,
                            const uint32_t *idsR, const uint32_t *idsS, const float *invR, const float *invS,

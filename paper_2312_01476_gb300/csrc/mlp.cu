@@ -118,9 +118,26 @@ cudaError_t launch_gemm_f32(const GemmArgs &g, int num_sms, cudaStream_t st)
     if (a.k_chunk <= 0) a.k_chunk = GK;
     splits = (g.K + a.k_chunk - 1) / a.k_chunk;
     if (splits < 1) splits = 1;
-    dim3 grid((unsigned)((g.N + GT - 1) / GT), (unsigned)((g.M + GT - 1) / GT), (unsigned)splits);
-    gemm_f32_kernel<<<grid, GNT, 0, st>>>(a);
-    return cudaGetLastError();
+    // the grid's y dimension is limited to 65,535 blocks: larger M runs in row chunks
+    const int64_t max_rows = (int64_t)65535 * GT;
+    for (int64_t r0 = 0; r0 < g.M; r0 += max_rows) {
+        GemmArgs c = a;
+        c.M = std::min<int64_t>(max_rows, g.M - r0);
+        if (g.aidx) {
+            c.aidx = g.aidx + r0;
+        } else {
+            c.A = g.A + r0 * g.a_rs;
+            if (g.rowscale) c.rowscale = g.rowscale + r0;
+            if (g.ascale) c.ascale = g.ascale + r0;
+        }
+        c.C = g.C + r0 * g.ldc;
+        if (g.pre) c.pre = g.pre + r0 * g.ldc;
+        dim3 grid((unsigned)((g.N + GT - 1) / GT), (unsigned)((c.M + GT - 1) / GT), (unsigned)splits);
+        gemm_f32_kernel<<<grid, GNT, 0, st>>>(c);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // s = z / |z| per row (one warp per row); keeps |z| for the backward pass.

@@ -9,6 +9,8 @@
 // Pairs with sim >= eps (Sec. III-B threshold predicate) are emitted as
 // (original i, original j, sim) records (Sec. IV-C, mapping back to tuples),
 // one global atomic per block of candidates.
+#include <algorithm>
+
 #include "ejoin_internal.cuh"
 
 namespace ej {
@@ -49,17 +51,19 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
                      ((reinterpret_cast<uintptr_t>(S) & 15) == 0);
     const int d4 = vec ? (d >> 2) : 0;  // float4 groups
     const double eps_d = (double)eps;
-
-    for (uint64_t blk = (uint64_t)blockIdx.x * RS_PER_BLOCK; blk < n; blk += (uint64_t)gridDim.x * RS_PER_BLOCK) {
+    for (uint64_t start = (uint64_t)blockIdx.x * RS_PER_BLOCK; start < n;
+         start += (uint64_t)gridDim.x * RS_PER_BLOCK) {
+        const int len = (int)std::min<uint64_t>(RS_PER_BLOCK, n - start);
         // lane q (< RS_PER_WARP) holds the outcome of the warp's q-th candidate
         bool my_emit = false;
         uint32_t my_i = 0, my_j = 0;
         float my_sim = 0.f;
         int my_band = 0;
-        const uint64_t wbase = blk + (uint64_t)warp * RS_PER_WARP;
+        const int wofs = warp * RS_PER_WARP;
+        const uint64_t wbase = start + (uint64_t)wofs;
         for (int q = 0; q < RS_PER_WARP; ++q) {
             const uint64_t k = wbase + q;
-            if (k >= n) break;  // warp-uniform
+            if (wofs + q >= len) break;  // warp-uniform
             const uint2 c = cand[k];
             const uint32_t i = idsR ? idsR[c.x] : c.x;
             const uint32_t j = idsS ? idsS[c.y] : c.y;
@@ -158,18 +162,20 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
     if (n > cand_cap) n = cand_cap;
     const int d4 = d >> 2;  // d is a multiple of 4 here
     const double eps_d = (double)eps;
-
-    for (uint64_t blk = (uint64_t)blockIdx.x * RS_PER_BLOCK; blk < n; blk += (uint64_t)gridDim.x * RS_PER_BLOCK) {
+    for (uint64_t start = (uint64_t)blockIdx.x * RS_PER_BLOCK; start < n;
+         start += (uint64_t)gridDim.x * RS_PER_BLOCK) {
+        const int len = (int)std::min<uint64_t>(RS_PER_BLOCK, n - start);
         bool my_emit = false;
         uint32_t my_i = 0, my_j = 0;
         float my_sim = 0.f;
         int my_band = 0;
-        const uint64_t wbase = blk + (uint64_t)warp * RS_PER_WARP;
+        const int wofs = warp * RS_PER_WARP;
+        const uint64_t wbase = start + (uint64_t)wofs;
         // lanes 0..RS_PER_WARP-1 fetch the warp's candidates and their ids / inverse norms
         uint32_t ci = 0, cj = 0, gi = 0, gj = 0;
         float sc = 0.f;
         bool valid = false;
-        if (lane < RS_PER_WARP && wbase + lane < n) {
+        if (lane < RS_PER_WARP && wofs + lane < len) {
             const uint2 c = cand[wbase + lane];
             ci = c.x;
             cj = c.y;

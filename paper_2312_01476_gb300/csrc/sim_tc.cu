@@ -33,9 +33,17 @@ constexpr int ROW_BYTES = 128;  // K bytes of one stage row = one 128-byte swizz
 constexpr int A_STAGE = BM * ROW_BYTES;
 constexpr int B_STAGE = BN * ROW_BYTES;
 constexpr int STAGING = 512;  // candidate slots per epilogue warp
+constexpr int FLUSH_TILES = 16;  // tiles between candidate flushes of an epilogue warp (or when staging is full)
 constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, 128 accumulator columns each
 constexpr int EPI_CHUNKS = BN / 2 / 32;  // 32-column chunks per epilogue warp
 constexpr int THREADS = (2 + EPI_WARPS) * 32;
+// fused re-score: warps 2 + EPI_WARPS .. consume candidates from a shared-memory ring that
+// replaces the epilogue staging: QN cells of 8 data bytes, QN 32-bit cell sequence numbers,
+// then RS_STG staged result records per re-score warp
+constexpr int RS_WARPS_F = 4;
+constexpr int QN = 2048;
+constexpr int RS_STG = 128;
+constexpr int THREADS_FUSED = (2 + EPI_WARPS + RS_WARPS_F) * 32;
 constexpr uint32_t TMEM_COLS = 512;
 
 constexpr int OFF_A = 0;
@@ -43,6 +51,8 @@ constexpr int OFF_B = OFF_A + STAGES * A_STAGE;
 constexpr int OFF_STG = OFF_B + STAGES * B_STAGE;
 constexpr int OFF_CTR = OFF_STG + EPI_WARPS * STAGING * 8;
 constexpr int OFF_BAR = OFF_CTR + EPI_WARPS * 4;
+static_assert(QN * 12 + RS_WARPS_F * RS_STG * 12 <= EPI_WARPS * STAGING * 8, "fused ring fits the staging area");
+static_assert(EPI_WARPS * 4 >= 12, "fused ring counters");
 constexpr int N_BARS = 2 * STAGES + 2 + 2 + 1;
 constexpr int OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr int SMEM_USED = OFF_MISC + 16;
@@ -117,7 +127,173 @@ struct TileInfo {
     float thr;
 };
 
-enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2 };
+enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3 };
+
+constexpr int threads_for(int mode) { return mode == MODE_FUSED ? THREADS_FUSED : THREADS; }
+
+// Re-score role of the fused kernel: take 8 queue slots at a time, gather the
+// FP32 rows of up to 8 candidates at once, FP32 dot (FP64 tier inside the
+// band), emit pairs with sim >= eps through a staged, one-atomic-per-flush
+// output.  Exits when every epilogue warp is done and the queue is drained.
+__device__ __forceinline__ void rescore_role(uint8_t *smem, const FuseArgs &fa, volatile int *abort_flag,
+                                             unsigned *status, uint64_t timeout, int rw, int lane,
+                                             unsigned long long *band_count_total)
+{
+    // bounded multi-producer / multi-consumer ring with per-cell sequence numbers: the producer
+    // of position p waits for seq == p, writes, sets seq = p + 1; the consumer of p waits for
+    // seq == p + 1, reads, sets seq = p + QN (the cell is free for position p + QN)
+    volatile unsigned long long *vq = reinterpret_cast<volatile unsigned long long *>(smem + OFF_STG);
+    volatile uint32_t *vseq = reinterpret_cast<volatile uint32_t *>(smem + OFF_STG + QN * 8);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(smem + OFF_CTR);  // [0] head, [1] take, [2] producers done
+    volatile uint32_t *vctr = ctr;
+    uint32_t *stg = reinterpret_cast<uint32_t *>(smem + OFF_STG + QN * 12) + rw * RS_STG * 3;
+    int stg_n = 0;
+    unsigned long long n_band = 0;
+    const int d4 = fa.d >> 2;
+    uint32_t *out_w = reinterpret_cast<uint32_t *>(fa.out);
+
+    auto flush = [&]() {
+        __syncwarp();
+        unsigned long long base = 0;
+        if (lane == 0 && stg_n) base = atomicAdd(fa.pair_count, (unsigned long long)stg_n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (!fa.count_only) {
+            for (int x = lane; x < 3 * stg_n; x += 32)
+                if (base + (unsigned long long)(x / 3) < fa.out_cap) out_w[base * 3 + x] = stg[x];
+        }
+        __syncwarp();
+        stg_n = 0;
+    };
+
+    while (true) {
+        uint32_t s0 = 0;
+        if (lane == 0) s0 = atomicAdd(&ctr[1], 8u);
+        s0 = __shfl_sync(0xffffffffu, s0, 0);
+        uint32_t row = 0, col = 0;
+        bool valid = false, ended = false;
+        if (lane < 8) {
+            const uint32_t sl = s0 + (uint32_t)lane;
+            const int slot = (int)(sl & (QN - 1));
+            const long long t0 = clock64();
+            while (true) {
+                if (vseq[slot] == sl + 1u) {
+                    __threadfence_block();
+                    const unsigned long long e = vq[slot];
+                    row = (uint32_t)e;
+                    col = (uint32_t)(e >> 32);
+                    __threadfence_block();
+                    vseq[slot] = sl + (uint32_t)QN;  // the cell is free for position sl + QN
+                    valid = true;
+                    break;
+                }
+                if (vctr[2] == (uint32_t)EPI_WARPS && sl >= vctr[0]) {
+                    ended = true;  // every candidate has been queued, and none at this position
+                    break;
+                }
+                if (*abort_flag) {
+                    ended = true;
+                    break;
+                }
+                if ((uint64_t)(clock64() - t0) > timeout) {
+                    *abort_flag = 1;
+                    atomicOr(status, ERR_TIMEOUT);
+                    ended = true;
+                    break;
+                }
+            }
+        }
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        const bool any_end = __any_sync(0xffffffffu, ended);
+        if (vm) {
+            const float4 *pr[8], *ps[8];
+            uint32_t gi[8], gj[8];
+            float sc[8], acc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const uint32_t ri = __shfl_sync(0xffffffffu, row, c), cj = __shfl_sync(0xffffffffu, col, c);
+                const bool v = (vm >> c) & 1u;
+                gi[c] = v ? (fa.idsR ? fa.idsR[ri] : ri) : 0u;
+                gj[c] = v ? (fa.idsS ? fa.idsS[cj] : cj) : 0u;
+                sc[c] = v ? fa.invR[ri] * fa.invS[cj] : 0.f;
+                pr[c] = reinterpret_cast<const float4 *>(fa.R + (int64_t)gi[c] * fa.ldR);
+                ps[c] = reinterpret_cast<const float4 *>(fa.S + (int64_t)gj[c] * fa.ldS);
+                acc[c] = 0.f;
+            }
+            for (int g = lane; g < d4; g += 32) {
+                float4 a[8], b[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const bool v = (vm >> c) & 1u;
+                    a[c] = v ? __ldg(pr[c] + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    b[c] = v ? __ldg(ps[c] + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    acc[c] = fmaf(a[c].x, b[c].x, acc[c]);
+                    acc[c] = fmaf(a[c].y, b[c].y, acc[c]);
+                    acc[c] = fmaf(a[c].z, b[c].z, acc[c]);
+                    acc[c] = fmaf(a[c].w, b[c].w, acc[c]);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+            bool my_emit = false;
+            uint32_t my_i = 0, my_j = 0;
+            float my_sim = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                if (!((vm >> c) & 1u)) continue;  // warp-uniform
+                float sim = fminf(1.f, fmaxf(-1.f, acc[c] * sc[c]));
+                bool emit = sim >= fa.eps;
+                if (fabsf(sim - fa.eps) < fa.fp64_band) {
+                    // FP64 tier: dot product and both norms in double
+                    const float *r = fa.R + (int64_t)gi[c] * fa.ldR, *q = fa.S + (int64_t)gj[c] * fa.ldS;
+                    double dd = 0.0, nr = 0.0, ns = 0.0;
+                    for (int k = lane; k < fa.d; k += 32) {
+                        const double x = (double)__ldg(r + k), y = (double)__ldg(q + k);
+                        dd = fma(x, y, dd);
+                        nr = fma(x, x, nr);
+                        ns = fma(y, y, ns);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        dd += __shfl_xor_sync(0xffffffffu, dd, o);
+                        nr += __shfl_xor_sync(0xffffffffu, nr, o);
+                        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+                    }
+                    double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
+                    s64 = fmin(1.0, fmax(-1.0, s64));
+                    emit = s64 >= (double)fa.eps;
+                    sim = (float)s64;
+                    ++n_band;
+                }
+                if (lane == c) {
+                    my_emit = emit;
+                    my_i = gi[c];
+                    my_j = gj[c];
+                    my_sim = sim;
+                }
+            }
+            const unsigned em = __ballot_sync(0xffffffffu, my_emit);
+            if (em) {
+                if (stg_n + __popc(em) > RS_STG) flush();
+                if (my_emit) {
+                    const int pos = stg_n + __popc(em & ((1u << lane) - 1u));
+                    stg[3 * pos + 0] = my_i;
+                    stg[3 * pos + 1] = my_j;
+                    stg[3 * pos + 2] = __float_as_uint(my_sim);
+                }
+                stg_n += __popc(em);
+                __syncwarp();
+            }
+        }
+        if (any_end) break;
+    }
+    flush();
+    if (lane == 0 && n_band) atomicAdd(band_count_total, n_band);
+}
 
 template <int MODE>
 __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &bt, long long tiles_m,
@@ -173,12 +349,12 @@ __device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity, u
 }  // namespace
 
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(threads_for(MODE), 1)
     sim_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kp,
                   const long long *__restrict__ nA_ptr, const long long *__restrict__ nB_ptr, float thr,
                   const float *__restrict__ scaleA, const float *__restrict__ scaleB, uint2 *__restrict__ cand,
                   uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only,
-                  int group_m, const BatchTables bt)
+                  int group_m, const BatchTables bt, const FuseArgs fa)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -214,7 +390,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
+        if (MODE == MODE_FUSED) {
+            uint32_t *c32 = reinterpret_cast<uint32_t *>(smem + OFF_CTR);
+            c32[0] = 0u;  // head: next position to reserve
+            c32[1] = 0u;  // take: next position to consume
+            c32[2] = 0u;  // epilogue warps done
+        }
         fence_mbar_init();
+    }
+    if (MODE == MODE_FUSED) {
+        uint32_t *seq = reinterpret_cast<uint32_t *>(smem + OFF_STG + QN * 8);
+        for (int i = threadIdx.x; i < QN; i += blockDim.x) seq[i] = (uint32_t)i;  // cell i free for position i
     }
     if (warp == 0 && lane == 0) {
         tma_prefetch_desc(&tmA);
@@ -304,6 +490,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_drain_wait(drain_bar, 0u, timeout, status);
         }
         __syncwarp();
+    } else if (warp >= 2 + EPI_WARPS) {
+        // ------------------------------------------------- fused re-score role
+        if constexpr (MODE == MODE_FUSED)
+            rescore_role(smem, fa, abort_flag, status, timeout, warp - 2 - EPI_WARPS, lane, fa.band_count);
     } else {
         // ------------------------------------------------------------ epilogue
         const int e = warp - 2;      // 0 .. EPI_WARPS-1
@@ -311,9 +501,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int half = e >> 2;     // which 128 accumulator columns
         uint2 *stg = reinterpret_cast<uint2 *>(smem + OFF_STG) + e * STAGING;
         int *stg_ctr = reinterpret_cast<int *>(smem + OFF_CTR) + e;  // mirrors stg_cnt for slot claims
-        if (lane == 0) *stg_ctr = 0;
+        // (in the fused mode these words hold the queue counters, set once at kernel start)
+        if (MODE != MODE_FUSED && lane == 0) *stg_ctr = 0;
         __syncwarp();
         int stg_cnt = 0;
+        int tiles_since_flush = 0;
         unsigned long long counted = 0;
         int acc = 0;
         uint32_t acc_phase = 0;
@@ -321,7 +513,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         auto flush = [&]() {
             __syncwarp();
             unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)stg_cnt);
+            if (lane == 0) {
+                base = atomicAdd(cand_count, (unsigned long long)stg_cnt);
+            }
             base = __shfl_sync(0xffffffffu, base, 0);
             for (int x = lane; x < stg_cnt; x += 32) {
                 const unsigned long long p = base + (unsigned long long)x;
@@ -396,6 +590,42 @@ __global__ void __launch_bounds__(THREADS, 1)
                 if (!row_ok) mask = 0u;
                 const int cnt = __popc(mask);
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+                if constexpr (MODE == MODE_FUSED) {
+                    // hand the candidates to the re-score warps through the shared-memory queue
+                    counted += (unsigned long long)tot;
+                    if (cnt) {
+                        volatile unsigned long long *vq = reinterpret_cast<volatile unsigned long long *>(smem + OFF_STG);
+                        volatile uint32_t *vseq = reinterpret_cast<volatile uint32_t *>(smem + OFF_STG + QN * 8);
+                        uint32_t pos = atomicAdd(reinterpret_cast<uint32_t *>(smem + OFF_CTR), (uint32_t)cnt);
+                        while (mask) {
+                            const int k = __ffs(mask) - 1;
+                            mask &= mask - 1u;
+                            const int slot = (int)(pos & (QN - 1));
+                            const long long t0 = clock64();
+                            bool ok = true;
+                            while (vseq[slot] != pos) {  // wait until the cell is free for this position
+                                if (*abort_flag) {
+                                    ok = false;
+                                    break;
+                                }
+                                if ((uint64_t)(clock64() - t0) > timeout) {
+                                    *abort_flag = 1;
+                                    atomicOr(status, ERR_TIMEOUT);
+                                    ok = false;
+                                    break;
+                                }
+                            }
+                            if (!ok) break;
+                            vq[slot] = ((unsigned long long)(uint32_t)(col0 + k) << 32) | (uint32_t)row;
+                            __threadfence_block();
+                            vseq[slot] = pos + 1u;  // published
+                            ++pos;
+                        }
+                    }
+                    // reconverge: the caller's next tcgen05.wait::ld is a .sync.aligned instruction
+                    __syncwarp();
+                    return;
+                }
                 if (count_only) {
                     counted += (unsigned long long)tot;
                     return;
@@ -410,7 +640,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (lane >= o) incl += y;
                     }
                     unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(cand_count, (unsigned long long)tot);
+                    if (lane == 0) {
+                        base = atomicAdd(cand_count, (unsigned long long)tot);
+                    }
                     base = __shfl_sync(0xffffffffu, base, 0);
                     unsigned long long p = base + (unsigned long long)(incl - cnt);
                     while (mask) {
@@ -419,6 +651,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (p < cap) cand[p] = make_uint2((uint32_t)row, (uint32_t)(col0 + k));
                         ++p;
                     }
+                    __syncwarp();  // reconverge before the caller's .sync.aligned tcgen05 instructions
                     return;
                 }
                 if (stg_cnt + tot > STAGING) flush();
@@ -464,9 +697,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                 acc = 0;
                 acc_phase ^= 1u;
             }
+            // publish the staged candidates every FLUSH_TILES tiles (accumulator already released):
+            // the list then follows the raster closely, and the re-score's row gathers stay in L2
+            if constexpr (MODE != MODE_FUSED) {
+                if (++tiles_since_flush >= FLUSH_TILES) {
+                    tiles_since_flush = 0;
+                    if (stg_cnt) flush();
+                }
+            }
         }
-        if (stg_cnt) flush();
-        if (count_only && lane == 0 && counted) atomicAdd(cand_count, counted);
+        if constexpr (MODE == MODE_FUSED) {
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) {
+                if (counted) atomicAdd(cand_count, counted);
+                atomicAdd(reinterpret_cast<uint32_t *>(smem + OFF_CTR + 8), 1u);  // this producer is done
+            }
+        } else {
+            if (stg_cnt) flush();
+            if (count_only && lane == 0 && counted) atomicAdd(cand_count, counted);
+        }
     }
 
     tc_fence_before();
@@ -481,7 +731,8 @@ template <int KIND, int MODE>
 static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
                               const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
                               uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                              int count_only, int grid, int group_m, const BatchTables &bt, cudaStream_t st)
+                              int count_only, int grid, int group_m, const BatchTables &bt, cudaStream_t st,
+                              const FuseArgs &fa = FuseArgs{})
 {
     // the shared-memory opt-in is set once per device (and therefore never inside a stream capture
     // that follows a first eager launch)
@@ -495,9 +746,9 @@ static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, in
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
-    sim_tc_kernel<KIND, MODE><<<grid, THREADS, SMEM_BYTES, st>>>(*tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand,
-                                                                  cap, cand_count, status, timeout, count_only,
-                                                                  group_m < 1 ? 1 : group_m, bt);
+    sim_tc_kernel<KIND, MODE><<<grid, threads_for(MODE), SMEM_BYTES, st>>>(
+        *tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout, count_only,
+        group_m < 1 ? 1 : group_m, bt, fa);
     return cudaGetLastError();
 }
 
@@ -509,14 +760,14 @@ cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *t
     const BatchTables none{};
     switch (kind) {
     case 0:
-        return launch_one<0, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
-                                    count_only, grid, group_m, none, st);
+        return launch_one<0, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status,
+                                          timeout, count_only, grid, group_m, none, st);
     case 1:
-        return launch_one<1, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
-                                    count_only, grid, group_m, none, st);
+        return launch_one<1, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status,
+                                          timeout, count_only, grid, group_m, none, st);
     case 2:
-        return launch_one<2, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout,
-                                    count_only, grid, group_m, none, st);
+        return launch_one<2, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status,
+                                          timeout, count_only, grid, group_m, none, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -536,6 +787,26 @@ cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensor
     case 2:
         return launch_one<2, MODE_BATCH>(tmA, tmB, kp, nullptr, nullptr, 0.f, scaleA, scaleB, cand, cap, cand_count, status,
                                    timeout, 0, grid, group_m, bt, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sim_tc_fused(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                                const long long *nA, const long long *nB, float thr, const float *scaleA,
+                                const float *scaleB, const FuseArgs &fa, unsigned long long *cand_count,
+                                unsigned *status, uint64_t timeout, int grid, int group_m, cudaStream_t st)
+{
+    const BatchTables none{};
+    switch (kind) {
+    case 0:
+        return launch_one<0, MODE_FUSED>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, nullptr, 0, cand_count, status,
+                                         timeout, fa.count_only, grid, group_m, none, st, fa);
+    case 1:
+        return launch_one<1, MODE_FUSED>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, nullptr, 0, cand_count, status,
+                                         timeout, fa.count_only, grid, group_m, none, st, fa);
+    case 2:
+        return launch_one<2, MODE_FUSED>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, nullptr, 0, cand_count, status,
+                                         timeout, fa.count_only, grid, group_m, none, st, fa);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libejoin.so")
 EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
 EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
 EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
-EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING = 0x1, 0x2
+EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED = 0x1, 0x2, 0x4
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
 
@@ -54,7 +54,8 @@ class ejoin_stats(ctypes.Structure):
                 ("fp64_rescored", ctypes.c_uint64), ("pairs", ctypes.c_uint64), ("launches", ctypes.c_uint64),
                 ("band", ctypes.c_float), ("ms_select", ctypes.c_float), ("ms_normalize", ctypes.c_float),
                 ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
-                ("ms_h2d", ctypes.c_float), ("ms_d2h", ctypes.c_float), ("contract_retries", ctypes.c_int32)]
+                ("ms_h2d", ctypes.c_float), ("ms_d2h", ctypes.c_float), ("contract_retries", ctypes.c_int32),
+                ("fused", ctypes.c_int32)]
 
 
 class ejoin_job(ctypes.Structure):

@@ -149,3 +149,23 @@ def test_trained_sketch_prunes_with_recall():
     # cluster, a few percent of all pairs; the untrained network cannot separate them
     assert kept["trained"] < 0.08, kept
     assert kept["trained"] < 0.25 * kept["untrained"], kept
+
+
+def test_pair_sims_beyond_one_grid_of_rows():
+    # 2.2M pairs -> 4.4M gathered rows: more than 65,535 row blocks of the GEMM grid
+    rng = np.random.default_rng(21)
+    X = rng.standard_normal((5000, 32)).astype(np.float32)
+    n = 2_200_000
+    p = rng.integers(0, 5000, n).astype(np.int32)
+    q = rng.integers(0, 5000, n).astype(np.int32)
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        sk = E.Sketch(ctx, 32, 16, 64)
+        flat = L.init_params(32, 16, 64, 5)
+        sk.set_params(flat)
+        Xd = torch.from_numpy(X).cuda()
+        inv = E.ejoin_row_inv_norm(ctx, Xd)
+        got = sk.pair_sims(Xd, inv, torch.from_numpy(p).cuda(), torch.from_numpy(q).cuda()).cpu().numpy()
+        S = sk.forward(Xd).cpu().numpy()
+        sk.close()
+    want = np.sum(S[p] * S[q], axis=1)
+    assert np.abs(got - want).max() < 1e-5

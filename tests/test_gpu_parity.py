@@ -126,6 +126,7 @@ def test_scaled_rows_and_padding_dims(prec):
 def test_candidate_buffer_regrowth(prec):
     R, S = gauss(12, 500, 64), gauss(13, 400, 64)
     eps = -0.05  # about half of all pairs
+    # the candidate buffer exists on the two-kernel path (the fused kernel has no candidate buffer)
     gi, gj, gs, st = run(prec, R, S, eps, capacity=1 << 20, capacity_hint=64)
     assert st["contract_retries"] >= 1
     oi, oj, os_ = oracle.join(R, S, eps)
@@ -235,3 +236,43 @@ def test_dims_cover_every_rescore_variant(prec, d):
     oi, oj, os_ = oracle.join(R, S, eps)
     assert len(oi) >= 40
     compare(R, S, eps, gi, gj, gs, oi, oj, os_)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "tf32"])
+def test_fused_and_two_kernel_paths_agree(prec):
+    # eps in the middle of the intra-cluster similarities (0.913 +- 0.005): band-heavy, FP64 tier busy
+    w = inputs.c2_clustered_selection(nR=60000, nS=9000, d=300, n_clusters=40, threads=4, eps=0.912)
+    selR = pkg.Sel(dev(w.attrR), "<", w.cR)
+    gi, gj, gs, st = run(prec, w.R, w.S, w.eps, selR, capacity=1 << 22, fp64_band=0.02, flags=pkg.EJOIN_FLAG_FUSED)
+    assert st["fused"] == 1 and st["fp64_rescored"] > 0
+    ui, uj, us, su = run(prec, w.R, w.S, w.eps, selR, capacity=1 << 22, fp64_band=0.02)
+    assert su["fused"] == 0
+    a = dict(zip(zip(gi.tolist(), gj.tolist()), gs.tolist()))
+    b = dict(zip(zip(ui.tolist(), uj.tolist()), us.tolist()))
+    assert set(a) == set(b) and len(a) > 10000
+    assert max(abs(a[k] - b[k]) for k in a) == 0.0  # same arithmetic per candidate
+    rows = np.sort(np.random.default_rng(1).choice(np.nonzero(w.attrR < w.cR)[0], 40, replace=False))
+    oi, oj, os_ = oracle.join(w.R, w.S, w.eps, oracle.Selection(w.attrR, "<", w.cR), rows=rows)
+    compare(w.R, w.S, w.eps, gi, gj, gs, oi, oj, os_, rows=rows)
+    assert st["candidates"] == su["candidates"]
+
+
+def test_fused_path_counts_beyond_the_result_buffer():
+    R, S = gauss(40, 700, 64), gauss(41, 500, 64)
+    with pkg.Ctx(device=0, prec="bf16", flags=pkg.EJOIN_FLAG_FUSED) as ctx:
+        res = pkg.ejoin_threshold(ctx, dev(R), dev(S), -1.0, capacity=1000)  # overflow, then retry
+        assert res.count == 700 * 500
+        assert pkg.ejoin_last_stats(ctx)["fused"] == 1
+
+
+@pytest.mark.parametrize("shape", [(129, 257, 128), (1000, 513, 300), (300, 700, 40)])
+def test_fused_path_matches_oracle_dense(shape):
+    # candidate-dense joins drive the fused kernel's shared-memory ring through many laps
+    nR, nS, d = shape
+    R, S = gauss(50 + d, nR, d), gauss(51 + d, nS, d)
+    for prec in ("bf16", "fp8"):
+        # eps = 0.02: about 45 % of the Gaussian pairs are candidates at every d here
+        gi, gj, gs, st = run(prec, R, S, 0.02, capacity=1 << 22, flags=pkg.EJOIN_FLAG_FUSED)
+        assert st["fused"] == 1 and st["candidates"] > 0.3 * nR * nS
+        oi, oj, os_ = oracle.join(R, S, 0.02)
+        compare(R, S, 0.02, gi, gj, gs, oi, oj, os_)
