@@ -86,7 +86,7 @@ typedef struct ejoin_config {
     uint64_t timeout_cycles; /* bound on every device-side spin-wait, in SM clock cycles
                                 (0: 2^31, about one second) */
     int32_t group_m;         /* tensor-core contraction raster: row tiles per group (0: sized so
-                                that one group's FP32 rows take about 16 MB) */
+                                that one group's FP32 rows take about 40 MB) */
 } ejoin_config;
 
 /* A relation: n rows of d FP32 values, row r at x + r * ld (ld >= d).

@@ -144,10 +144,11 @@ cudaError_t launch_rescore_batch(const uint2 *cand, const unsigned long long *ca
                                  BatchPair *out, uint64_t out_cap, unsigned long long *out_count,
                                  unsigned long long *band_count, bool aligned, int num_sms, cudaStream_t st);
 // Default row-tile group width of the contraction's raster for operands of
-// padded dimension kp: about 16 MB of FP32 input rows per group.
+// padded dimension kp: about 40 MB of FP32 input rows per group (the R rows the
+// re-score gathers while the group's candidates are processed stay in L2).
 inline int default_group_m(int64_t kp)
 {
-    int64_t g = (16ll << 20) / (128 * 4 * (kp > 0 ? kp : 1));
+    int64_t g = (40ll << 20) / (128 * 4 * (kp > 0 ? kp : 1));
     if (g < 8) g = 8;
     if (g > 256) g = 256;
     return (int)g;
