@@ -73,6 +73,11 @@ typedef enum ejoin_prec {
                                       on GB300 the separate re-score kernel, with the whole GPU behind it,
                                       is faster on candidate-dense joins */
 
+#define EJOIN_FLAG_NO_SYMMETRY 0x8u /* evaluate a self-join over the full square of pairs.  By default a
+                                      self-join on the tensor cores contracts only the 256-row block
+                                      pairs on and above the diagonal and writes every pair (i, j),
+                                      i != j, in both orders; the result is the same set */
+
 typedef struct ejoin_config {
     int32_t device;          /* CUDA device ordinal */
     void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
@@ -135,7 +140,8 @@ typedef struct ejoin_ctx ejoin_ctx;
 /* Per-call statistics of the last ejoin_threshold / ejoin_threshold_host call. */
 typedef struct ejoin_stats {
     uint64_t n_sel_r, n_sel_s;  /* rows kept by the selections */
-    uint64_t candidates;        /* pairs at or above eps - band in the bulk precision */
+    uint64_t candidates;        /* pairs at or above eps - band in the bulk precision (a symmetric
+                                   self-join counts each unordered pair once) */
     uint64_t fp64_rescored;     /* candidates re-scored in FP64 */
     uint64_t pairs;             /* result pairs */
     uint64_t launches;          /* kernels launched by the call */
@@ -252,6 +258,7 @@ ejoin_status ejoin_batch_result(const ejoin_batch *batch, const ejoin_batch_pair
 
 ejoin_status ejoin_batch_info(const ejoin_batch *batch, ejoin_batch_stats *out);
 
+/* Release the plan (synchronises its device; does not use the context, so it may come after ejoin_destroy). */
 void ejoin_batch_destroy(ejoin_batch *batch);
 
 /* ---------------------------------------------------------------------------
@@ -272,6 +279,7 @@ typedef struct ejoin_sketch ejoin_sketch;
 
 /* out must be 64.  Parameters start at zero: set them with ejoin_sketch_set_params. */
 ejoin_status ejoin_sketch_create(ejoin_ctx *ctx, int32_t d, int32_t hidden, int32_t out, ejoin_sketch **sk);
+/* Release the network (synchronises its device; does not use the context, so it may come after ejoin_destroy). */
 void ejoin_sketch_destroy(ejoin_sketch *sk);
 int64_t ejoin_sketch_num_params(const ejoin_sketch *sk);
 /* Host arrays of ejoin_sketch_num_params floats; set also resets the Adam state. */
@@ -306,13 +314,20 @@ typedef struct ejoin_prune_stats {
     float ms_prepare;      /* normalise + sketch + reorder */
     float ms_bound;        /* tile statistics + tile-pair bounds */
     float ms_contract, ms_rescore, ms_total;
+    /* diagnostics of the tile bounds (filled when stats is given): mean angular radius (rad) of the
+       used balls of the R tiles (a) and of the S tiles (b), the fraction of used balls wider than
+       0.5 rad, the covering anchors of R and the rows of the largest anchor group of R */
+    float ball_radius_mean_a, ball_radius_mean_b;
+    float wide_ball_frac_a, wide_ball_frac_b;
+    uint64_t anchors_a, max_group_rows_a;
 } ejoin_prune_stats;
 
 /* Threshold join of R and S (device, no selection) that contracts only the
  * tile pairs whose sketch bound reaches eps_sketch.  Each side is first
- * reordered by nearest sketch anchor (256 coarse, then 128 fine per coarse
- * bucket, both farthest-point sampled and chained by nearest neighbour) so
- * that tiles are coherent in sketch space; each tile is described by up to 4
+ * reordered by nearest covering anchor (anchors drawn in rounds from the rows
+ * of a sample that no anchor covers yet at sketch cosine 0.85, so that every
+ * group of similar rows gets an anchor of its own) so that tiles are coherent
+ * in sketch space; each tile is described by up to 4
  * balls (farthest-point seeds, rows join the nearest seed: unit centroid c
  * and angular radius rho), and a tile pair is kept when some ball pair has
  * cos(max(0, angle(c_a, c_b) - rho_a - rho_b)) >= eps_sketch, an upper bound

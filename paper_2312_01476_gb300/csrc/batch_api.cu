@@ -28,6 +28,7 @@ using namespace ej::host;
 
 struct ejoin_batch {
     ejoin_ctx *ctx = nullptr;
+    int device = 0;  // the context's device, kept for teardown
     int n_jobs = 0;
     int d = 0;
     int64_t kp = 0;
@@ -200,9 +201,9 @@ ejoin_status autotune(ejoin_batch *b)
 void destroy_batch(ejoin_batch *b)
 {
     if (!b) return;
-    DeviceGuard g(b->ctx->device);
-    if (b->cap_stream) cudaStreamSynchronize(b->cap_stream);
-    cudaStreamSynchronize(b->ctx->stream);
+    // the context may already be gone: wait for the device, not for its stream
+    DeviceGuard g(b->device);
+    cudaDeviceSynchronize();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -243,6 +244,7 @@ ejoin_status ejoin_batch_create(ejoin_ctx *c, const ejoin_job *jobs, int32_t n_j
     ejoin_batch *b = new (std::nothrow) ejoin_batch();
     if (!b) return EJOIN_ENOMEM;
     b->ctx = c;
+    b->device = c->device;
     b->n_jobs = n_jobs;
     b->d = d;
     b->flags = flags;

@@ -451,9 +451,16 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         if (!count_only && hf.pair_count > *cap_io) return EJOIN_EOVERFLOW;
         return EJOIN_OK;
     }
+    // a self-join on the tensor cores contracts the upper triangle only (mirrored in the re-score)
+    const bool sym = self && prec != EJOIN_F32 && !(c->flags & EJOIN_FLAG_NO_SYMMETRY);
     auto contract = [&]() -> ejoin_status {
         cudaError_t ee;
-        if (prec == EJOIN_F32) {
+        if (sym) {
+            const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
+            ee = launch_sim_tc_sym(kind, &tmA, &tmB, (int)kp, nA, thr, (const float *)sa.scale.p, (uint2 *)c->cand.p,
+                                   c->cand_cap, &dm->cand_count, &dm->status, c->timeout, 0, c->num_sms,
+                                   c->group_m > 0 ? c->group_m : default_group_m(kp), c->stream);
+        } else if (prec == EJOIN_F32) {
             ee = launch_sim_simt((const float *)sa.norm.p, (const float *)sb.norm.p, (int)kp, nA, nB, thr,
                                  (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, 0, c->num_sms, c->stream);
         } else {
@@ -509,7 +516,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
                        selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
                        (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
                        count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0, c->num_sms,
-                       c->stream);
+                       c->stream, sym ? 1 : 0);
     if (e != cudaSuccess) return from_cuda(e);
     c->stats.launches += hm.cand_count ? 1 : 0;
     if (timing) cudaEventRecord(c->ev[3], c->stream);

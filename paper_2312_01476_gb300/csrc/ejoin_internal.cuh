@@ -118,6 +118,12 @@ cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *t
                           const float *scaleB, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
                           unsigned *status, uint64_t timeout, int count_only, int grid, int group_m,
                           cudaStream_t st);
+// Self-join contraction (one operand, nA rows): only the block pairs on and above the
+// diagonal of 256-row blocks; candidates (r, c) have r <= c.
+cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                              float thr, const float *scale, uint2 *cand, uint64_t cap,
+                              unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only,
+                              int grid, int group_m, cudaStream_t st);
 // Contraction with the exact re-score fused in (extra warps consume the candidates from a
 // shared-memory ring and write final pairs).  Needs 16-byte aligned rows, ld % 4 == 0 and
 // d % 4 == 0.
@@ -154,13 +160,15 @@ inline int default_group_m(int64_t kp)
     return (int)g;
 }
 size_t sim_tc_smem_bytes();
-// Candidates: cand[0 .. min(*cand_count, cand_cap)).
+// Candidates: cand[0 .. min(*cand_count, cand_cap)).  mirror: the candidates come
+// from the upper triangle of a self-join; each pair (i, j), i != j, is written in
+// both orders.
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                            const float *R, int64_t ldR, const float *S, int64_t ldS, int d,
                            const uint32_t *idsR, const uint32_t *idsS, const float *invR, const float *invS,
                            float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                            unsigned long long *out_count, unsigned long long *band_count, int count_only,
-                           int num_sms, cudaStream_t st);
+                           int num_sms, cudaStream_t st, int mirror = 0);
 
 // ------------------------------------------------------- device PTX helpers
 #if defined(__CUDACC__)
@@ -306,6 +314,72 @@ __device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&v)[32])
                    "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
                  :
                  : "memory");
+}
+
+// ---------------------------------------------------- compensated dot products
+// The accurate tier of the re-score: x.y, x.x and y.y of two FP32 rows with the
+// compensated dot product "Dot2" of Ogita, Rump and Oishi (SIAM J. Sci.
+// Comput. 26(6), 2005): every product is split exactly into p + e with one
+// FMA, every running sum into s + t with the branch-free two-sum, and the
+// error terms are summed alongside.  The result carries the accuracy of an
+// evaluation in twice the working precision, |err| <= u |dot| + gamma_n^2
+// sum |x_k y_k| (u = 2^-24, gamma_n = n u / (1 - n u)); here the high and low
+// parts are added in FP64, so the u |dot| rounding term is not incurred.  For
+// d = 768 the relative error is below 3e-9 of |x| |y|, and on GB300 it costs a
+// fraction of a plain FP64 dot product.  The lanes of a warp each take the
+// elements k = lane, lane + 32, ...; partial (sum, error) pairs are combined
+// with the same two-sum.
+struct Dot2Acc {
+    float s, c;  // running sum and accumulated error
+};
+
+// (the _rn intrinsics keep the compiler from contracting or reassociating these steps)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+__device__ __forceinline__ void dot2_add(Dot2Acc &a, float x, float y)
+{
+    const float p = __fmul_rn(x, y);
+    const float ep = fmaf(x, y, -p);  // exact: x y = p + ep
+    float s, es;
+    two_sum(a.s, p, s, es);
+    a.s = s;
+    a.c = __fadd_rn(a.c, __fadd_rn(es, ep));
+}
+
+__device__ __forceinline__ double dot2_warp_total(Dot2Acc a)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float os = __shfl_xor_sync(0xffffffffu, a.s, o);
+        const float oc = __shfl_xor_sync(0xffffffffu, a.c, o);
+        float s, e;
+        two_sum(a.s, os, s, e);
+        a.s = s;
+        a.c = __fadd_rn(a.c, __fadd_rn(oc, e));
+    }
+    return (double)a.s + (double)a.c;
+}
+
+// Accurate cosine of two raw FP32 rows (one warp): Dot2 for x.y, x.x, y.y,
+// finished in FP64; 0 when a row is zero; clamped to [-1, 1].
+__device__ __forceinline__ double accurate_cosine(const float *__restrict__ r, const float *__restrict__ s, int d,
+                                                  int lane)
+{
+    Dot2Acc xy{0.f, 0.f}, xx{0.f, 0.f}, yy{0.f, 0.f};
+    for (int k = lane; k < d; k += 32) {
+        const float x = __ldg(r + k), y = __ldg(s + k);
+        dot2_add(xy, x, y);
+        dot2_add(xx, x, x);
+        dot2_add(yy, y, y);
+    }
+    const double dd = dot2_warp_total(xy), nr = dot2_warp_total(xx), ns = dot2_warp_total(yy);
+    double c = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
+    return fmin(1.0, fmax(-1.0, c));
 }
 
 #endif  // __CUDACC__

@@ -62,11 +62,12 @@ cudaError_t launch_gather_rows(const void *in, int64_t row_bytes, const uint32_t
                                cudaStream_t st);
 cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *perm, int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_gather_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t st);
-// Fine anchors of a two-level reorder: for coarse bucket b (rows perm[off[b] .. off[b+1]) of the
-// coarse order), n_fine (<= 256) anchors by farthest-point sampling, chained by nearest neighbour
-// (zero anchors for an empty bucket).  maxdot: scratch of n floats.
-cudaError_t launch_fine_anchors(const float *S, const uint32_t *perm, const uint32_t *off, int n_coarse, int64_t n,
-                                int n_fine, float *maxdot, float *anchors, cudaStream_t st);
+// Covering anchors: drop[a] = 1 when an earlier candidate b < a has sketch cosine >= tau with
+// candidate a (rows cand[] of S), and covered[i] |= (some anchor has cosine >= tau with row rows[i]).
+cudaError_t launch_cover_drop(const float *S, const uint32_t *cand, int nc, float tau, unsigned char *drop,
+                              cudaStream_t st);
+cudaError_t launch_cover_update(const float *S, const uint32_t *rows, int64_t m, const float *anchors, int n_anchor,
+                                float tau, unsigned char *covered, cudaStream_t st);
 // Balls per tile in the pruning bound.
 constexpr int PRUNE_BALLS = 4;
 // Per tile of `tile_rows` (<= 256) consecutive sketch rows: up to PRUNE_BALLS balls formed greedily

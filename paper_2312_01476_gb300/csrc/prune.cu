@@ -135,142 +135,65 @@ __global__ void gather_f32_kernel(const float *__restrict__ in, const uint32_t *
         out[i] = in[perm[i]];
 }
 
-// Anchors of one bucket (one block per bucket; also used for the coarse level
-// with a single bucket holding a strided sample of all rows): farthest-point
-// sampling over the bucket's rows (first anchor: the bucket's first row; each
-// next anchor: the row whose largest cosine to the anchors so far is the
-// smallest), so that well-separated groups each get an anchor before any
-// group gets a second one; then the anchors are chained by nearest neighbour
-// so that nearby anchors get adjacent keys.  maxdot: scratch of n floats.
-__global__ void __launch_bounds__(1024) fine_anchors_kernel(const float *__restrict__ S,
-                                                            const uint32_t *__restrict__ perm,
-                                                            const uint32_t *__restrict__ off, int n_coarse, int64_t n,
-                                                            int n_fine, float *__restrict__ maxdot,
-                                                            float *__restrict__ anchors)
+// Covering anchors (the reorder of the pruned join).  Rows are grouped by the
+// anchor they are most similar to in sketch space; for the groups to be
+// coherent, every group of mutually similar rows needs an anchor of its own
+// (with fewer anchors than groups, nearest-anchor assignment splits groups
+// between unrelated anchors).  Anchors are therefore drawn, in rounds, from
+// the rows of a sample that no anchor covers yet (cosine >= tau), in a fixed
+// pseudo-random order; a candidate covered by an earlier candidate of the
+// same round is dropped, so that each group gets about one anchor.
+
+// drop[a] = 1 when some earlier candidate b < a has <S[cand[a]], S[cand[b]]> >= tau
+// (one warp per candidate).
+__global__ void cover_drop_kernel(const float *__restrict__ S, const uint32_t *__restrict__ cand, int nc, float tau,
+                                  unsigned char *__restrict__ drop)
 {
-    __shared__ float cur[SK];
-    __shared__ float red_v[32];
-    __shared__ int red_i[32];
-    __shared__ int chosen[256];
-    __shared__ int order[256];
-    __shared__ unsigned char used[256];
-    __shared__ int best_s;
-    const int b = blockIdx.x;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t lo = off[b];
-    const int64_t hi = b + 1 < n_coarse ? (int64_t)off[b + 1] : n;
-    const int64_t size = hi - lo;
-    float *out = anchors + (int64_t)b * n_fine * SK;
-    if (size <= 0) {
-        for (int e = tid; e < n_fine * SK; e += blockDim.x) out[e] = 0.f;
-        return;
-    }
-    for (int64_t i = lo + tid; i < hi; i += blockDim.x) maxdot[i] = -2.f;
-    int pick = 0;  // position inside the bucket
-    for (int j = 0; j < n_fine; ++j) {
-        if (tid == 0) chosen[j] = pick;
-        __syncthreads();
-        if (tid < SK) cur[tid] = S[(int64_t)perm[lo + pick] * SK + tid];
-        __syncthreads();
-        // update the largest cosine to the chosen anchors; find the row where it is smallest
-        float bv = 3.f;
-        int bi = 0;
-        for (int64_t i = lo + tid; i < hi; i += blockDim.x) {
-            const float *x = S + (int64_t)perm[i] * SK;
-            float dot = 0.f;
-#pragma unroll 16
-            for (int q = 0; q < SK; ++q) dot = fmaf(cur[q], x[q], dot);
-            const float m = fmaxf(maxdot[i], dot);
-            maxdot[i] = m;
-            if (m < bv) {
-                bv = m;
-                bi = (int)(i - lo);
-            }
-        }
+    const int lane = threadIdx.x & 31;
+    const int a = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (a >= nc) return;
+    const float2 x = __ldg(reinterpret_cast<const float2 *>(S + (int64_t)cand[a] * SK) + lane);
+    bool hit = false;
+    for (int b = 0; b < a && !hit; ++b) {
+        const float2 y = __ldg(reinterpret_cast<const float2 *>(S + (int64_t)cand[b] * SK) + lane);
+        float dot = fmaf(x.x, y.x, x.y * y.y);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov < bv || (ov == bv && oi < bi)) {
-                bv = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            red_v[warp] = bv;
-            red_i[warp] = bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            float v = red_v[0];
-            int ix = red_i[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (red_v[w] < v || (red_v[w] == v && red_i[w] < ix)) {
-                    v = red_v[w];
-                    ix = red_i[w];
-                }
-            best_s = ix;
-        }
-        __syncthreads();
-        pick = best_s;
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        hit = dot >= tau;  // warp-uniform
     }
-    // nearest-neighbour chain over the chosen anchors: each step, the whole
-    // block scores the unused anchors against the last one and takes the best
-    for (int j = tid; j < n_fine; j += blockDim.x) used[j] = 0;
-    __syncthreads();
-    if (tid == 0) {
-        order[0] = 0;
-        used[0] = 1;
-        best_s = 0;
-    }
-    __syncthreads();
-    for (int step = 1; step < n_fine; ++step) {
-        if (tid < SK) cur[tid] = S[(int64_t)perm[lo + chosen[best_s]] * SK + tid];
-        __syncthreads();
-        float bv = -3.f;
-        int bi = n_fine;
-        for (int j = tid; j < n_fine; j += blockDim.x) {
-            if (used[j]) continue;
-            const float *xb = S + (int64_t)perm[lo + chosen[j]] * SK;
-            float dot = 0.f;
-#pragma unroll 16
-            for (int q = 0; q < SK; ++q) dot = fmaf(cur[q], xb[q], dot);
-            if (dot > bv) {
-                bv = dot;
-                bi = j;
-            }
-        }
+    if (lane == 0) drop[a] = hit ? 1 : 0;
+}
+
+// covered[i] |= max over the anchors of <S[rows[i]], anchor> >= tau (one thread per row).
+__global__ void cover_update_kernel(const float *__restrict__ S, const uint32_t *__restrict__ rows, int64_t m,
+                                    const float *__restrict__ anchors, int n_anchor, float tau,
+                                    unsigned char *__restrict__ covered)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || covered[i]) return;
+    float x[SK];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ov > bv || (ov == bv && oi < bi)) {
-                bv = ov;
-                bi = oi;
-            }
-        }
-        if (lane == 0) {
-            red_v[warp] = bv;
-            red_i[warp] = bi;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            float v = red_v[0];
-            int ix = red_i[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
-                if (red_v[w] > v || (red_v[w] == v && red_i[w] < ix)) {
-                    v = red_v[w];
-                    ix = red_i[w];
-                }
-            order[step] = ix;
-            used[ix] = 1;
-            best_s = ix;
-        }
-        __syncthreads();
+    for (int q = 0; q < SK / 4; ++q) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(S + (int64_t)rows[i] * SK) + q);
+        x[4 * q] = v.x;
+        x[4 * q + 1] = v.y;
+        x[4 * q + 2] = v.z;
+        x[4 * q + 3] = v.w;
     }
-    for (int e = tid; e < n_fine * SK; e += blockDim.x) {
-        const int j = e / SK, q = e % SK;
-        out[e] = S[(int64_t)perm[lo + chosen[order[j]]] * SK + q];
+    for (int a = 0; a < n_anchor; ++a) {
+        float dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < SK / 4; ++q) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(anchors + (int64_t)a * SK) + q);
+            dot = fmaf(x[4 * q], v.x, dot);
+            dot = fmaf(x[4 * q + 1], v.y, dot);
+            dot = fmaf(x[4 * q + 2], v.z, dot);
+            dot = fmaf(x[4 * q + 3], v.w, dot);
+        }
+        if (dot >= tau) {
+            covered[i] = 1;
+            return;
+        }
     }
 }
 
@@ -534,12 +457,19 @@ cudaError_t launch_gather_f32(const float *in, const uint32_t *perm, int64_t n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_fine_anchors(const float *S, const uint32_t *perm, const uint32_t *off, int n_coarse, int64_t n,
-                                int n_fine, float *maxdot, float *anchors, cudaStream_t st)
+cudaError_t launch_cover_drop(const float *S, const uint32_t *cand, int nc, float tau, unsigned char *drop,
+                              cudaStream_t st)
 {
-    if (n_coarse <= 0) return cudaSuccess;
-    if (n_fine > 256) return cudaErrorInvalidValue;
-    fine_anchors_kernel<<<n_coarse, 1024, 0, st>>>(S, perm, off, n_coarse, n, n_fine, maxdot, anchors);
+    if (nc <= 0) return cudaSuccess;
+    cover_drop_kernel<<<(unsigned)((nc + 7) / 8), 256, 0, st>>>(S, cand, nc, tau, drop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cover_update(const float *S, const uint32_t *rows, int64_t m, const float *anchors, int n_anchor,
+                                float tau, unsigned char *covered, cudaStream_t st)
+{
+    if (m <= 0 || n_anchor <= 0) return cudaSuccess;
+    cover_update_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(S, rows, m, anchors, n_anchor, tau, covered);
     return cudaGetLastError();
 }
 

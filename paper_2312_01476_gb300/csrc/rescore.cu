@@ -5,7 +5,8 @@
 // Eq. (Cosine Similarity)): an FP32 dot product, lane-parallel with a
 // butterfly reduction, scaled by the two FP32 inverse norms from the
 // normalisation pass.  A candidate whose FP32 similarity lies within
-// fp64_band of eps is recomputed again in FP64 (dot product and both norms).
+// fp64_band of eps is recomputed by the accurate tier (compensated dot
+// product and both norms, finished in FP64; accurate_cosine).
 // Pairs with sim >= eps (Sec. III-B threshold predicate) are emitted as
 // (original i, original j, sim) records (Sec. IV-C, mapping back to tuples),
 // one global atomic per block of candidates.
@@ -28,11 +29,61 @@ __device__ __forceinline__ float warp_sum_f(float v)
     return v;
 }
 
-__device__ __forceinline__ double warp_sum_d(double v)
+
+// Block-level aggregation of the re-score's outcomes (lane q of each warp holds
+// one candidate's result): one global atomic per block step.  mirror (a
+// self-join evaluated on the upper triangle only): a pair (i, j) with i != j
+// is written as (i, j) and (j, i), both with the same similarity, which is
+// exact because the FP32 dot product and the accurate tier are symmetric in
+// their two rows.
+__device__ __forceinline__ void emit_block(bool my_emit, uint32_t my_i, uint32_t my_j, float my_sim, int my_band,
+                                           int mirror, int *wcnt, unsigned long long *base_s,
+                                           unsigned long long *out_count, unsigned long long *band_count,
+                                           ejoin_pair *__restrict__ out, uint64_t out_cap, int count_only, int lane,
+                                           int warp)
 {
+    const int mine = my_emit ? ((mirror && my_i != my_j) ? 2 : 1) : 0;
+    int incl = mine;  // warp inclusive scan of the record counts
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+    const int nb = __popc(__ballot_sync(0xffffffffu, my_band != 0));
+    if (lane == 0) {
+        wcnt[warp] = wtot;
+        if (nb) atomicAdd(band_count, (unsigned long long)nb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int w = 0; w < RS_WARPS; ++w) {
+            const int c = wcnt[w];
+            wcnt[w] = run;
+            run += c;
+        }
+        *base_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
+    }
+    __syncthreads();
+    if (mine && !count_only) {
+        const unsigned long long pos = *base_s + (unsigned long long)(wcnt[warp] + incl - mine);
+        if (pos < out_cap) {
+            ejoin_pair p;
+            p.i = my_i;
+            p.j = my_j;
+            p.sim = my_sim;
+            out[pos] = p;
+        }
+        if (mine == 2 && pos + 1 < out_cap) {
+            ejoin_pair p;
+            p.i = my_j;
+            p.j = my_i;
+            p.sim = my_sim;
+            out[pos + 1] = p;
+        }
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
@@ -40,7 +91,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
     const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
     const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
     const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
-    unsigned long long *out_count, unsigned long long *band_count, int count_only)
+    unsigned long long *out_count, unsigned long long *band_count, int count_only, int mirror)
 {
     __shared__ int wcnt[RS_WARPS];
     __shared__ unsigned long long base_s;
@@ -85,19 +136,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
             bool emit = sim >= eps;
             int band = 0;
             if (fabsf(sim - eps) < fp64_band) {
-                // FP64 tier: dot product and both norms in double
-                double dd = 0.0, nr = 0.0, ns = 0.0;
-                for (int kk = lane; kk < d; kk += 32) {
-                    const double a = (double)__ldg(r + kk), b = (double)__ldg(s + kk);
-                    dd = fma(a, b, dd);
-                    nr = fma(a, a, nr);
-                    ns = fma(b, b, ns);
-                }
-                dd = warp_sum_d(dd);
-                nr = warp_sum_d(nr);
-                ns = warp_sum_d(ns);
-                double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
-                s64 = fmin(1.0, fmax(-1.0, s64));
+                // accurate tier: compensated dot product and norms, finished in FP64
+                const double s64 = accurate_cosine(r, s, d, lane);
                 emit = s64 >= eps_d;
                 sim = (float)s64;
                 band = 1;
@@ -110,35 +150,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
                 my_band = band;
             }
         }
-        // block-level aggregation of the emitted pairs: one atomic per block step
-        const unsigned m = __ballot_sync(0xffffffffu, my_emit);
-        const int nb = __popc(__ballot_sync(0xffffffffu, my_band != 0));
-        if (lane == 0) {
-            wcnt[warp] = __popc(m);
-            if (nb) atomicAdd(band_count, (unsigned long long)nb);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int w = 0; w < RS_WARPS; ++w) {
-                const int c = wcnt[w];
-                wcnt[w] = run;
-                run += c;
-            }
-            base_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
-        }
-        __syncthreads();
-        if (my_emit && !count_only) {
-            const unsigned long long pos = base_s + wcnt[warp] + __popc(m & ((1u << lane) - 1u));
-            if (pos < out_cap) {
-                ejoin_pair p;
-                p.i = my_i;
-                p.j = my_j;
-                p.sim = my_sim;
-                out[pos] = p;
-            }
-        }
-        __syncthreads();
+        emit_block(my_emit, my_i, my_j, my_sim, my_band, mirror, wcnt, &base_s, out_count, band_count, out, out_cap,
+                   count_only, lane, warp);
     }
 }
 
@@ -152,7 +165,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
     const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
     const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
     const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
-    unsigned long long *out_count, unsigned long long *band_count, int count_only)
+    unsigned long long *out_count, unsigned long long *band_count, int count_only, int mirror)
 {
     static_assert(RS_PER_WARP % C == 0, "candidates per warp step");
     __shared__ int wcnt[RS_WARPS];
@@ -230,20 +243,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
                 bool emit = sim >= eps;
                 int band = 0;
                 if (fabsf(sim - eps) < fp64_band) {
-                    const float *r = R + (int64_t)ii[c] * ldR;
-                    const float *s = S + (int64_t)jj[c] * ldS;
-                    double dd = 0.0, nr = 0.0, ns = 0.0;
-                    for (int kk = lane; kk < d; kk += 32) {
-                        const double x = (double)__ldg(r + kk), y = (double)__ldg(s + kk);
-                        dd = fma(x, y, dd);
-                        nr = fma(x, x, nr);
-                        ns = fma(y, y, ns);
-                    }
-                    dd = warp_sum_d(dd);
-                    nr = warp_sum_d(nr);
-                    ns = warp_sum_d(ns);
-                    double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
-                    s64 = fmin(1.0, fmax(-1.0, s64));
+                    // accurate tier: compensated dot product and norms, finished in FP64
+                    const double s64 = accurate_cosine(R + (int64_t)ii[c] * ldR, S + (int64_t)jj[c] * ldS, d, lane);
                     emit = s64 >= eps_d;
                     sim = (float)s64;
                     band = 1;
@@ -257,34 +258,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
                 }
             }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, my_emit);
-        const int nb = __popc(__ballot_sync(0xffffffffu, my_band != 0));
-        if (lane == 0) {
-            wcnt[warp] = __popc(m);
-            if (nb) atomicAdd(band_count, (unsigned long long)nb);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int run = 0;
-            for (int w = 0; w < RS_WARPS; ++w) {
-                const int c = wcnt[w];
-                wcnt[w] = run;
-                run += c;
-            }
-            base_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
-        }
-        __syncthreads();
-        if (my_emit && !count_only) {
-            const unsigned long long pos = base_s + wcnt[warp] + __popc(m & ((1u << lane) - 1u));
-            if (pos < out_cap) {
-                ejoin_pair p;
-                p.i = my_i;
-                p.j = my_j;
-                p.sim = my_sim;
-                out[pos] = p;
-            }
-        }
-        __syncthreads();
+        emit_block(my_emit, my_i, my_j, my_sim, my_band, mirror, wcnt, &base_s, out_count, band_count, out, out_cap,
+                   count_only, lane, warp);
     }
 }
 
@@ -365,18 +340,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_batch_kernel(
             bool emit = sim >= eps;
             int band = 0;
             if (fabsf(sim - eps) < fp64_band) {
-                double dd = 0.0, nr = 0.0, ns = 0.0;
-                for (int kk = lane; kk < d; kk += 32) {
-                    const double x = (double)__ldg(r + kk), y = (double)__ldg(s + kk);
-                    dd = fma(x, y, dd);
-                    nr = fma(x, x, nr);
-                    ns = fma(y, y, ns);
-                }
-                dd = warp_sum_d(dd);
-                nr = warp_sum_d(nr);
-                ns = warp_sum_d(ns);
-                double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
-                s64 = fmin(1.0, fmax(-1.0, s64));
+                // accurate tier: compensated dot product and norms, finished in FP64
+                const double s64 = accurate_cosine(r, s, d, lane);
                 emit = s64 >= (double)eps;
                 sim = (float)s64;
                 band = 1;
@@ -474,7 +439,8 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
                            int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
                            const uint32_t *idsS, const float *invR, const float *invS, float eps, float fp64_band,
                            ejoin_pair *out, uint64_t out_cap, unsigned long long *out_count,
-                           unsigned long long *band_count, int count_only, int num_sms, cudaStream_t st)
+                           unsigned long long *band_count, int count_only, int num_sms, cudaStream_t st,
+                           int mirror)
 {
     if (cand_cap == 0) return cudaSuccess;
     uint64_t blocks = (cand_cap + RS_PER_BLOCK - 1) / RS_PER_BLOCK;
@@ -486,7 +452,7 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
     const int T = RS_WARPS * 32;
 #define EJ_RESCORE_ARGS                                                                                              \
     cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap, out_count, \
-        band_count, count_only
+        band_count, count_only, mirror
     if (aligned && d <= 128) {
         rescore_mlp_kernel<1, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
     } else if (aligned && d <= 256) {

@@ -125,9 +125,68 @@ struct TileInfo {
     long long rowA, rowB;
     int limA, limB;
     float thr;
+    bool diag;  // MODE_SYM: a tile of a diagonal block (keep col >= row only)
 };
 
-enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3 };
+enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3, MODE_SYM = 4 };
+
+// MODE_SYM (self-join, R == S): only the block pairs (I, J), I <= J, of
+// 256-row blocks are contracted, each as its two 128-row tiles (2I, J) and
+// (2I + 1, J); inside a diagonal block (I == J) only the positions with
+// col >= row are kept.  Every unordered pair is found once and the re-score
+// emits it in both orders.  Raster: groups of G block rows; inside a group,
+// column blocks J = I0 .. nb - 1 in order, and for each J the group's block
+// rows I0 .. min(I0 + G, J + 1) - 1.
+struct SymRaster {
+    long long nb;  // 256-row blocks
+    long long G;   // block rows per group
+};
+
+// Tiles (two per block pair) of the full groups 0 .. g - 1 (each with nb - I0 >= G columns).
+__device__ __forceinline__ long long sym_group_start(long long g, const SymRaster &sr)
+{
+    const long long G = sr.G;
+    return g * G * (G + 1) + 2 * G * (g * (sr.nb - G) - G * (g * (g - 1) / 2));
+}
+
+__device__ __forceinline__ long long sym_total(const SymRaster &sr) { return sr.nb * (sr.nb + 1); }
+
+// Tile t of the symmetric raster -> (m, n, diagonal block?)
+__device__ __forceinline__ void sym_coords(long long t, const SymRaster &sr, long long &m, long long &n, bool &diag)
+{
+    const long long G = sr.G;
+    const long long n_groups = (sr.nb + G - 1) / G;
+    // group: the last g with start(g) <= t (starts of the full groups grow with g)
+    long long lo = 0, hi = n_groups;  // start(lo) <= t < start(hi) (start(n_groups) taken as +inf)
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) >> 1;
+        if (sym_group_start(mid, sr) <= t) lo = mid;
+        else hi = mid;
+    }
+    const long long I0 = lo * G;
+    const long long Gg = min(G, sr.nb - I0);
+    const long long u = t - sym_group_start(lo, sr);
+    const long long b = u >> 1;  // block pair inside the group
+    const long long h = u & 1;   // which 128-row half of the block row
+    const long long L = sr.nb - I0;
+    const long long tri_cols = min(L, Gg);
+    const long long tri = tri_cols * (tri_cols + 1) / 2;
+    long long x, y;
+    if (b < tri) {
+        // column x holds x + 1 block rows: largest x with x (x + 1) / 2 <= b
+        x = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+        while (x * (x + 1) / 2 > b) --x;
+        while ((x + 1) * (x + 2) / 2 <= b) ++x;
+        y = b - x * (x + 1) / 2;
+    } else {
+        const long long r = b - tri;
+        x = tri_cols + r / Gg;
+        y = r % Gg;
+    }
+    m = 2 * (I0 + y) + h;
+    n = I0 + x;
+    diag = x == y;
+}
 
 constexpr int threads_for(int mode) { return mode == MODE_FUSED ? THREADS_FUSED : THREADS; }
 
@@ -248,23 +307,9 @@ __device__ __forceinline__ void rescore_role(uint8_t *smem, const FuseArgs &fa, 
                 float sim = fminf(1.f, fmaxf(-1.f, acc[c] * sc[c]));
                 bool emit = sim >= fa.eps;
                 if (fabsf(sim - fa.eps) < fa.fp64_band) {
-                    // FP64 tier: dot product and both norms in double
-                    const float *r = fa.R + (int64_t)gi[c] * fa.ldR, *q = fa.S + (int64_t)gj[c] * fa.ldS;
-                    double dd = 0.0, nr = 0.0, ns = 0.0;
-                    for (int k = lane; k < fa.d; k += 32) {
-                        const double x = (double)__ldg(r + k), y = (double)__ldg(q + k);
-                        dd = fma(x, y, dd);
-                        nr = fma(x, x, nr);
-                        ns = fma(y, y, ns);
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        dd += __shfl_xor_sync(0xffffffffu, dd, o);
-                        nr += __shfl_xor_sync(0xffffffffu, nr, o);
-                        ns += __shfl_xor_sync(0xffffffffu, ns, o);
-                    }
-                    double s64 = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
-                    s64 = fmin(1.0, fmax(-1.0, s64));
+                    // accurate tier: compensated dot product and norms, finished in FP64
+                    const double s64 = accurate_cosine(fa.R + (int64_t)gi[c] * fa.ldR, fa.S + (int64_t)gj[c] * fa.ldS,
+                                                       fa.d, lane);
                     emit = s64 >= (double)fa.eps;
                     sim = (float)s64;
                     ++n_band;
@@ -300,8 +345,17 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
                                                 long long tiles_n, long long nA, long long nB, float thr, int group_m)
 {
     TileInfo ti;
+    ti.diag = false;
     long long m, n;
-    if constexpr (MODE == MODE_LIST) {
+    if constexpr (MODE == MODE_SYM) {
+        const SymRaster sr{(nA + 2 * BM - 1) / (2 * BM), group_m > 2 ? (long long)(group_m / 2) : 1ll};
+        sym_coords(t, sr, m, n, ti.diag);
+        ti.rowA = m * BM;
+        ti.rowB = n * BN;
+        ti.limA = (int)max(-1ll, min((long long)BM, nA - m * BM));  // <= 0: the empty half of a last block
+        ti.limB = (int)min((long long)BN, nB - n * BN);
+        ti.thr = thr;
+    } else if constexpr (MODE == MODE_LIST) {
         const uint2 mn = __ldg(bt.tile_list + t);
         m = mn.x;
         n = mn.y;
@@ -373,6 +427,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
     const long long tiles_m = (nA + BM - 1) / BM, tiles_n = (nB + BN - 1) / BN;
     long long total = tiles_m * tiles_n;
     if (MODE == MODE_BATCH) total = __ldg(bt.tile_off + bt.n_jobs);
+    if (MODE == MODE_SYM) total = sym_total(SymRaster{(nA + 2 * BM - 1) / (2 * BM), 1});
     if (MODE == MODE_LIST) {
         const unsigned long long c = *bt.tile_count;
         total = (long long)(c < bt.tile_cap ? c : bt.tile_cap);
@@ -587,6 +642,13 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                     }
                 }
                 if (left < 32) mask &= left <= 0 ? 0u : ((1u << left) - 1u);
+                if constexpr (MODE == MODE_SYM) {
+                    // diagonal block: keep col >= row (the mirror is emitted by the re-score)
+                    if (ti.diag) {
+                        const long long skip = row - col0;  // columns of this chunk left of the diagonal
+                        mask &= skip <= 0 ? 0xffffffffu : (skip >= 32 ? 0u : ~((1u << skip) - 1u));
+                    }
+                }
                 if (!row_ok) mask = 0u;
                 const int cnt = __popc(mask);
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
@@ -768,6 +830,26 @@ cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *t
     case 2:
         return launch_one<2, MODE_SINGLE>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status,
                                           timeout, count_only, grid, group_m, none, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                              float thr, const float *scale, uint2 *cand, uint64_t cap,
+                              unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only,
+                              int grid, int group_m, cudaStream_t st)
+{
+    const BatchTables none{};
+    switch (kind) {
+    case 0:
+        return launch_one<0, MODE_SYM>(tmA, tmB, kp, nA, nA, thr, scale, scale, cand, cap, cand_count, status, timeout,
+                                       count_only, grid, group_m, none, st);
+    case 1:
+        return launch_one<1, MODE_SYM>(tmA, tmB, kp, nA, nA, thr, scale, scale, cand, cap, cand_count, status, timeout,
+                                       count_only, grid, group_m, none, st);
+    case 2:
+        return launch_one<2, MODE_SYM>(tmA, tmB, kp, nA, nA, thr, scale, scale, cand, cap, cand_count, status, timeout,
+                                       count_only, grid, group_m, none, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -6,11 +6,10 @@
 // Pruned join (ejoin_threshold_pruned), all on the context stream:
 //   1. normalise R and S (BF16 operands, FP32 inverse norms), as in the plain join;
 //   2. sketch every row with the network (unit 64-d vectors);
-//   3. reorder each side so that tiles are coherent in sketch space: nearest
-//      of 256 coarse anchors, then of 128 fine anchors inside the coarse
-//      bucket (both farthest-point sampled and chained by nearest neighbour,
-//      so that nearby anchors get adjacent keys), counting sort by the
-//      32,768 keys, gather of operand rows, inverse norms and sketches;
+//   3. reorder each side so that tiles are coherent in sketch space: covering
+//      anchors drawn in rounds from a sample (prune.cu), every row joins its
+//      most similar anchor, counting sort by anchor, gather of operand rows,
+//      inverse norms and sketches;
 //   4. per tile: up to 4 balls in sketch space (seeds by farthest-point
 //      sampling in the tile, rows join the nearest seed: unit centroid +
 //      angular radius); a tile pair is kept when some
@@ -31,6 +30,7 @@ using namespace ej::host;
 
 struct ejoin_sketch {
     ejoin_ctx *ctx = nullptr;
+    int device = 0;  // the context's device, kept for teardown
     int d = 0, hid = 0, out = 0;
     int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, n_params = 0;
     Buf params, grads, m, v;
@@ -41,7 +41,8 @@ struct ejoin_sketch {
     Buf fH, fZ, finv;
     // pruned-join workspace, per side
     struct Side {
-        Buf S, key1, key2, perm1, perm, hist, off, a_idx, anchors1, anchors2, norm, inv, scale, sS, maxdot, cent, rad;
+        Buf S, key1, perm1, perm, hist, a_idx, anchors2, norm, inv, scale, sS, maxdot, cent, rad;
+        int n_anchor = 0;  // covering anchors of the last reorder
     } pw[2];
     Buf list, list_count;
     uint64_t list_cap = 0;
@@ -236,6 +237,7 @@ ejoin_status ejoin_sketch_create(ejoin_ctx *ctx, int32_t d, int32_t hidden, int3
     ejoin_sketch *sk = new (std::nothrow) ejoin_sketch();
     if (!sk) return EJOIN_ENOMEM;
     sk->ctx = ctx;
+    sk->device = ctx->device;
     sk->d = d;
     sk->hid = hidden;
     sk->out = out;
@@ -259,15 +261,16 @@ void ejoin_sketch_destroy(ejoin_sketch *sk)
 {
     if (!sk) return;
     {
-        DeviceGuard g(sk->ctx->device);
-        cudaStreamSynchronize(sk->ctx->stream);
+        // the context may already be gone: wait for the device, not for its stream
+        DeviceGuard g(sk->device);
+        cudaDeviceSynchronize();
         for (Buf *b : {&sk->params, &sk->grads, &sk->m, &sk->v, &sk->idx, &sk->A1, &sk->H, &sk->Z, &sk->S, &sk->nz,
                        &sk->dS, &sk->dZ, &sk->dH, &sk->scal, &sk->fH, &sk->fZ, &sk->finv, &sk->list,
                        &sk->list_count})
             release(*b);
         for (auto &w : sk->pw)
-            for (Buf *b : {&w.S, &w.key1, &w.key2, &w.perm1, &w.perm, &w.hist, &w.off, &w.a_idx, &w.anchors1,
-                           &w.anchors2, &w.norm, &w.inv, &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad})
+            for (Buf *b : {&w.S, &w.key1, &w.perm1, &w.perm, &w.hist, &w.a_idx, &w.anchors2, &w.norm, &w.inv,
+                           &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad})
                 release(*b);
     }
     delete sk;
@@ -430,7 +433,12 @@ ejoin_status ejoin_sketch_pair_sims(ejoin_sketch *sk, ejoin_rel X, const float *
 
 namespace {
 
-constexpr int N_COARSE = 256, N_FINE = 128, SKW = 64;
+constexpr int SKW = 64;
+// covering anchors (see prune.cu): sample size, candidates per round, anchor limit, coverage cosine
+constexpr int64_t COVER_SAMPLE = 262144;
+constexpr int COVER_ROUND = 4096;
+constexpr int COVER_MAX_ANCHORS = 32768;
+constexpr float COVER_TAU = 0.85f;
 
 // Steps 1-3 of the pruned join for one side: normalise, sketch, reorder, gather.
 ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, int64_t kp)
@@ -442,19 +450,17 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
     const size_t eb = fmt_bytes(fmt);
     const int64_t n = r.n;
     const int64_t rows = round_up(std::max<int64_t>(n, 1), 256);
-    const int n_coarse = (int)std::min<int64_t>(N_COARSE, std::max<int64_t>(n, 1));
-    const int n_keys = n_coarse * N_FINE;
+    const int64_t m = std::min<int64_t>(n, COVER_SAMPLE);
     cudaError_t e;
     if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) || (e = ensure(sd.inv, (size_t)rows * 4)) ||
         (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4))) || (e = ensure(pw.S, (size_t)rows * SKW * 4)) ||
-        (e = ensure(pw.key1, (size_t)rows * 4)) || (e = ensure(pw.key2, (size_t)rows * 4)) ||
-        (e = ensure(pw.perm1, (size_t)rows * 4)) || (e = ensure(pw.perm, (size_t)rows * 4)) ||
-        (e = ensure(pw.hist, (size_t)n_keys * 4)) || (e = ensure(pw.off, (size_t)n_keys * 4)) ||
-(e = ensure(pw.anchors1, (size_t)N_COARSE * SKW * 4)) ||
-        (e = ensure(pw.anchors2, (size_t)N_COARSE * N_FINE * SKW * 4)) ||
+        (e = ensure(pw.key1, (size_t)rows * 4)) || (e = ensure(pw.perm, (size_t)rows * 4)) ||
+        (e = ensure(pw.hist, (size_t)COVER_MAX_ANCHORS * 4)) ||
+        (e = ensure(pw.a_idx, (size_t)(m + COVER_ROUND) * 4)) || (e = ensure(pw.perm1, (size_t)COVER_ROUND)) ||
+        (e = ensure(pw.anchors2, (size_t)COVER_MAX_ANCHORS * SKW * 4)) ||
         (e = ensure(pw.norm, (size_t)rows * kp * eb)) || (e = ensure(pw.inv, (size_t)rows * 4)) ||
         (fmt == FMT_FP8 && (e = ensure(pw.scale, (size_t)rows * 4))) || (e = ensure(pw.sS, (size_t)rows * SKW * 4)) ||
-        (e = ensure(pw.maxdot, (size_t)rows * 4)))
+        (e = ensure(pw.maxdot, (size_t)std::max<int64_t>(m, 1))))
         return from_cuda(e);
     DevMisc *dm = (DevMisc *)c->misc.p;
     long long *n_dev = &dm->n_sel[w];
@@ -464,33 +470,58 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
         return from_cuda(e);
     if ((e = sketch_forward(sk, r.x, n, r.ld, (const float *)sd.inv.p, (float *)pw.S.p, st)) != cudaSuccess)
         return from_cuda(e);
-    // coarse anchors: farthest-point sampling over a strided sample of at most 65,536 rows
-    const int64_t n_samp = std::min<int64_t>(n, 65536);
-    std::vector<uint32_t> aidx(n_samp);
-    for (int64_t a = 0; a < n_samp; ++a) aidx[a] = (uint32_t)(a * n / n_samp);
-    const uint32_t zero = 0;
-    if ((e = ensure(pw.a_idx, (size_t)n_samp * 4 + 16)) != cudaSuccess) return from_cuda(e);
-    if ((e = cudaMemcpyAsync(pw.a_idx.p, aidx.data(), n_samp * 4, cudaMemcpyHostToDevice, st)) ||
-        (e = cudaMemcpyAsync((char *)pw.a_idx.p + n_samp * 4, &zero, 4, cudaMemcpyHostToDevice, st)) ||
-        (e = cudaStreamSynchronize(st)))  // aidx and zero are host temporaries
+
+    // covering anchors over a strided sample of m rows, candidates taken in a fixed pseudo-random order
+    const float *S = (const float *)pw.S.p;
+    uint32_t *samp = (uint32_t *)pw.a_idx.p;   // sample rows [m]
+    uint32_t *cand_dev = samp + m;             // this round's candidates / kept anchors
+    unsigned char *drop_dev = (unsigned char *)pw.perm1.p;
+    unsigned char *cov_dev = (unsigned char *)pw.maxdot.p;
+    float *anchors = (float *)pw.anchors2.p;
+    std::vector<uint32_t> aidx(m), order(m), cand;
+    for (int64_t a = 0; a < m; ++a) aidx[a] = (uint32_t)(a * n / m), order[a] = (uint32_t)a;
+    uint64_t rs = 0x9E3779B97F4A7C15ull ^ (uint64_t)(w + 1);  // splitmix64 stream for the shuffle
+    auto next = [&rs]() {
+        uint64_t z = (rs += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int64_t a = m - 1; a > 0; --a) std::swap(order[a], order[next() % (uint64_t)(a + 1)]);
+    std::vector<unsigned char> cov(m, 0), drop(COVER_ROUND);
+    if ((e = cudaMemcpyAsync(samp, aidx.data(), m * 4, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaMemsetAsync(cov_dev, 0, (size_t)std::max<int64_t>(m, 1), st)))
         return from_cuda(e);
-    uint32_t *key1 = (uint32_t *)pw.key1.p, *key2 = (uint32_t *)pw.key2.p, *hist = (uint32_t *)pw.hist.p,
-             *off = (uint32_t *)pw.off.p, *perm1 = (uint32_t *)pw.perm1.p, *perm = (uint32_t *)pw.perm.p;
-    if ((e = launch_fine_anchors((const float *)pw.S.p, (const uint32_t *)pw.a_idx.p,
-                                 (const uint32_t *)pw.a_idx.p + n_samp, 1, n_samp, n_coarse, (float *)pw.maxdot.p,
-                                 (float *)pw.anchors1.p, st)) ||
-        (e = launch_assign_keys((const float *)pw.S.p, n, SKW, (const float *)pw.anchors1.p, n_coarse, nullptr, key1,
-                                c->num_sms, st)) ||
-        (e = cudaMemsetAsync(hist, 0, n_coarse * 4, st)) || (e = launch_key_histogram(key1, n, hist, st)) ||
-        (e = launch_key_scan(hist, n_coarse, st)) ||
-        (e = cudaMemcpyAsync(off, hist, n_coarse * 4, cudaMemcpyDeviceToDevice, st)) ||
-        (e = launch_key_scatter(key1, n, hist, perm1, st)) ||
-        (e = launch_fine_anchors((const float *)pw.S.p, perm1, off, n_coarse, n, N_FINE, (float *)pw.maxdot.p,
-                                 (float *)pw.anchors2.p, st)) ||
-        (e = launch_assign_keys((const float *)pw.S.p, n, SKW, (const float *)pw.anchors2.p, N_FINE, key1, key2,
-                                c->num_sms, st)) ||
-        (e = cudaMemsetAsync(hist, 0, n_keys * 4, st)) || (e = launch_key_histogram(key2, n, hist, st)) ||
-        (e = launch_key_scan(hist, n_keys, st)) || (e = launch_key_scatter(key2, n, hist, perm, st)) ||
+    int n_anchor = 0;
+    while (n_anchor < COVER_MAX_ANCHORS) {
+        cand.clear();
+        for (int64_t a = 0; a < m && (int)cand.size() < COVER_ROUND; ++a)
+            if (!cov[order[a]]) cand.push_back(aidx[order[a]]);
+        if (cand.empty()) break;
+        const int nc = (int)cand.size();
+        if ((e = cudaMemcpyAsync(cand_dev, cand.data(), nc * 4, cudaMemcpyHostToDevice, st)) ||
+            (e = launch_cover_drop(S, cand_dev, nc, COVER_TAU, drop_dev, st)) ||
+            (e = cudaMemcpyAsync(drop.data(), drop_dev, nc, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))  // cand and drop are host vectors
+            return from_cuda(e);
+        std::vector<uint32_t> kept;
+        for (int a = 0; a < nc && n_anchor + (int)kept.size() < COVER_MAX_ANCHORS; ++a)
+            if (!drop[a]) kept.push_back(cand[a]);
+        const int nk = (int)kept.size();
+        if ((e = cudaMemcpyAsync(cand_dev, kept.data(), nk * 4, cudaMemcpyHostToDevice, st)) ||
+            (e = launch_gather_rows(pw.S.p, SKW * 4, cand_dev, nk, anchors + (int64_t)n_anchor * SKW, st)) ||
+            (e = launch_cover_update(S, samp, m, anchors + (int64_t)n_anchor * SKW, nk, COVER_TAU, cov_dev, st)) ||
+            (e = cudaMemcpyAsync(cov.data(), cov_dev, m, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))  // kept and cov are host vectors
+            return from_cuda(e);
+        n_anchor += nk;
+    }
+    pw.n_anchor = n_anchor;
+    // every row joins its most similar anchor; counting sort by anchor
+    uint32_t *key = (uint32_t *)pw.key1.p, *hist = (uint32_t *)pw.hist.p, *perm = (uint32_t *)pw.perm.p;
+    if ((e = launch_assign_keys(S, n, SKW, anchors, n_anchor, nullptr, key, c->num_sms, st)) ||
+        (e = cudaMemsetAsync(hist, 0, (size_t)n_anchor * 4, st)) || (e = launch_key_histogram(key, n, hist, st)) ||
+        (e = launch_key_scan(hist, n_anchor, st)) || (e = launch_key_scatter(key, n, hist, perm, st)) ||
         (e = launch_gather_rows(sd.norm.p, kp * eb, perm, n, pw.norm.p, st)) ||
         (e = launch_gather_f32((const float *)sd.inv.p, perm, n, (float *)pw.inv.p, st)) ||
         (e = launch_gather_rows(pw.S.p, SKW * 4, perm, n, pw.sS.p, st)) ||
@@ -577,6 +608,38 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
         }
         if (n_list <= sk->list_cap) break;
         sk->list_cap = n_list;
+    }
+    if (ps) {
+        // diagnostics: ball radii of both sides, covering anchors and the largest anchor group of R
+        std::vector<float> ra((size_t)tA * NBL), rb((size_t)tB * NBL);
+        std::vector<uint32_t> co((size_t)std::max(pa.n_anchor, 1));
+        if ((e = cudaMemcpyAsync(ra.data(), pa.rad.p, ra.size() * 4, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(rb.data(), rB, rb.size() * 4, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(co.data(), pa.hist.p, co.size() * 4, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st))) {
+            release(centB);
+            release(radB);
+            return from_cuda(e);
+        }
+        auto summarise = [](const std::vector<float> &r, float &mean, float &wide) {
+            double sum = 0.0;
+            uint64_t used = 0, w = 0;
+            for (float x : r)
+                if (x >= 0.f) {
+                    sum += x;
+                    ++used;
+                    w += x > 0.5f;
+                }
+            mean = used ? (float)(sum / used) : 0.f;
+            wide = used ? (float)w / (float)used : 0.f;
+        };
+        summarise(ra, P_.ball_radius_mean_a, P_.wide_ball_frac_a);
+        summarise(rb, P_.ball_radius_mean_b, P_.wide_ball_frac_b);
+        // the scatter left hist[k] at the end of anchor group k: group k holds hist[k] - hist[k - 1] rows
+        uint64_t mx = 0;
+        for (size_t b = 0; b < co.size(); ++b) mx = std::max<uint64_t>(mx, co[b] - (b ? co[b - 1] : 0u));
+        P_.max_group_rows_a = mx;
+        P_.anchors_a = (uint64_t)pa.n_anchor;
     }
     release(centB);
     release(radB);

@@ -7,7 +7,9 @@ library is missing, loading raises: there is no CPU fallback.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
+import weakref
 import os
 from dataclasses import dataclass
 from typing import Optional
@@ -20,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libejoin.so")
 EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
 EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
 EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
-EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED = 0x1, 0x2, 0x4
+EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED, EJOIN_FLAG_NO_SYMMETRY = 0x1, 0x2, 0x4, 0x8
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
 
@@ -75,7 +77,10 @@ EJOIN_BATCH_GRAPH, EJOIN_BATCH_AUTOTUNE = 0x1, 0x2
 class ejoin_prune_stats(ctypes.Structure):
     _fields_ = [("tiles_total", ctypes.c_uint64), ("tiles_kept", ctypes.c_uint64), ("candidates", ctypes.c_uint64),
                 ("pairs", ctypes.c_uint64), ("ms_prepare", ctypes.c_float), ("ms_bound", ctypes.c_float),
-                ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float)]
+                ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
+                ("ball_radius_mean_a", ctypes.c_float), ("ball_radius_mean_b", ctypes.c_float),
+                ("wide_ball_frac_a", ctypes.c_float), ("wide_ball_frac_b", ctypes.c_float),
+                ("anchors_a", ctypes.c_uint64), ("max_group_rows_a", ctypes.c_uint64)]
 
 _lib = None
 
@@ -163,6 +168,23 @@ def load_library(path: str = LIB_PATH):
     return lib
 
 
+# Live handles, closed in dependency order when the interpreter exits (sketches and batches
+# before the contexts they were created on), so that no handle is released after the
+# objects it refers to, whatever order the interpreter tears its objects down in.
+_live_dependents = weakref.WeakSet()
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_live_handles():
+    for group in (_live_dependents, _live_contexts):
+        for obj in list(group):
+            try:
+                obj.close()
+            except Exception:
+                pass
+
+
 class EJoinError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -210,6 +232,7 @@ class Ctx:
         self.handle = h
         self.device = device
         self._out = None  # cached device result buffer (torch int32 [cap, 3])
+        _live_contexts.add(self)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -398,6 +421,7 @@ class Batch:
         h = ctypes.c_void_p()
         _check(lib.ejoin_batch_create(ctx.handle, arr, len(jobs), flags, ctypes.byref(h)), "ejoin_batch_create")
         self.handle = h
+        _live_dependents.add(self)
 
     def run(self):
         _check(load_library().ejoin_batch_run(self.handle), "ejoin_batch_run")
@@ -487,6 +511,7 @@ class Sketch:
         _check(lib.ejoin_sketch_create(ctx.handle, d, hidden, out, ctypes.byref(h)), "ejoin_sketch_create")
         self.handle, self.ctx, self.d, self.hidden, self.out = h, ctx, d, hidden, out
         self.n_params = int(lib.ejoin_sketch_num_params(h))
+        _live_dependents.add(self)
 
     def set_params(self, flat: np.ndarray):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

@@ -276,3 +276,47 @@ def test_fused_path_matches_oracle_dense(shape):
         assert st["fused"] == 1 and st["candidates"] > 0.3 * nR * nS
         oi, oj, os_ = oracle.join(R, S, 0.02)
         compare(R, S, 0.02, gi, gj, gs, oi, oj, os_)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "tf32"])
+@pytest.mark.parametrize("n", [300, 256, 513, 1500])
+def test_symmetric_self_join_equals_full_square(prec, n):
+    # the upper-triangle evaluation (default for tensor-core self-joins) returns the same set as the
+    # full square, every off-diagonal pair in both orders with one similarity, and matches the oracle
+    X = gauss(60 + n, n, 96)
+    X[n // 2:] = X[: n - n // 2] + np.float32(0.4) * gauss(61 + n, n - n // 2, 96)
+    eps = 0.3
+    Xd = dev(X)  # one tensor for both sides: a self-join is recognised by identical relations
+
+    def run_self(flags=0):
+        with pkg.Ctx(device=0, prec=prec, flags=flags) as ctx:
+            res = pkg.ejoin_threshold(ctx, Xd, Xd, eps)
+            return (res.i.cpu().numpy().view(np.uint32), res.j.cpu().numpy().view(np.uint32),
+                    res.sim.cpu().numpy(), pkg.ejoin_last_stats(ctx))
+
+    gi, gj, gs, st = run_self()
+    fi, fj, fs, sf = run_self(pkg.EJOIN_FLAG_NO_SYMMETRY)
+    assert st["candidates"] < sf["candidates"]
+    a = dict(zip(zip(gi.tolist(), gj.tolist()), gs.tolist()))
+    b = dict(zip(zip(fi.tolist(), fj.tolist()), fs.tolist()))
+    assert len(a) == len(gi) and set(a) == set(b)
+    assert all(a[(i, j)] == a[(j, i)] for (i, j) in a)
+    assert all((i, i) in a for i in range(n))
+    oi, oj, os_ = oracle.join(X, X, eps)
+    compare(X, X, eps, gi, gj, gs, oi, oj, os_)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "f32"])
+def test_accurate_tier_matches_fp64(prec):
+    # fp64_band = 2 sends every candidate through the accurate tier (compensated dot products finished
+    # in FP64): its similarities then agree with the FP64 oracle to FP32 rounding of the result
+    # (|err| <= 2^-24 for |sim| <= 1) plus the tier's own bound (< 3e-9 at d = 768)
+    R, S = gauss(70, 700, 768), gauss(71, 900, 768)
+    S[:300] = R[:300] + np.float32(0.35) * gauss(72, 300, 768)
+    R[:5] *= np.float32(1e-3)  # rows far from unit length
+    S[5:10] *= np.float32(1e3)
+    eps = 0.2
+    gi, gj, gs, st = run(prec, R, S, eps, fp64_band=2.0)
+    assert st["fp64_rescored"] == st["candidates"] > 0
+    oi, oj, os_ = oracle.join(R, S, eps)
+    compare(R, S, eps, gi, gj, gs, oi, oj, os_, band=1e-7, tol=1.2e-7)
