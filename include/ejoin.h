@@ -380,7 +380,7 @@ const char *ejoin_version(void);
 #define EJOIN_STATIC_MAX_OPERAND_ELEMS (1u << 24)
 #define EJOIN_STATIC_MAX_CANDIDATES (1u << 20)
 #define EJOIN_STATIC_SCRATCH_BYTES \
-    (1024u + 2u * 4u * EJOIN_STATIC_MAX_ROWS + 8u * EJOIN_STATIC_MAX_CANDIDATES + 2u * EJOIN_STATIC_MAX_OPERAND_ELEMS)
+    (1024u + 2u * 4u * EJOIN_STATIC_MAX_ROWS + 2u * 8u * EJOIN_STATIC_MAX_CANDIDATES + 2u * EJOIN_STATIC_MAX_OPERAND_ELEMS)
 ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float eps, ejoin_pair *d_pairs, uint64_t capacity,
                                     uint64_t *count, void *stream);
 

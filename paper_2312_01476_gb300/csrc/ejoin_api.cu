@@ -239,6 +239,7 @@ void ejoin_destroy(ejoin_ctx *c)
         }
         release(c->misc);
         release(c->cand);
+        release(c->band);
         for (auto &b : c->host_in) release(b);
         release(c->host_pairs);
         if (c->events)
@@ -298,7 +299,7 @@ bool same_sel(const ejoin_sel *a, const ejoin_sel *b)
 // Selection + normalisation of one relation into side buffers (or caller buffers).
 ejoin_status prepare_side(ejoin_ctx *c, int which, const ejoin_rel &r, const ejoin_sel *sel, int fmt, int64_t kp,
                           void *out, int64_t ld_out, float *inv, float *scale, uint32_t *ids, long long *n_sel,
-                          unsigned *status, bool timing_split)
+                          unsigned *status, bool timing_split, int scale_group = 0)
 {
     Side &sd = c->side[which];
     cudaError_t e;
@@ -320,10 +321,16 @@ ejoin_status prepare_side(ejoin_ctx *c, int which, const ejoin_rel &r, const ejo
     }
     if (timing_split && (c->flags & EJOIN_FLAG_TIMING)) cudaEventRecord(c->ev[1 + which], c->stream);
     if (r.n > 0) {
-        e = launch_normalize(fmt, r.x, r.ld, r.d, sel ? ids : nullptr, n_sel, r.n, out, ld_out, (int)kp, inv, scale,
-                             status, c->num_sms, c->stream);
+        if (fmt == FMT_FP8 && scale_group > 0) {
+            e = launch_normalize_fp8_grouped(r.x, r.ld, r.d, sel ? ids : nullptr, n_sel, r.n, out, ld_out, (int)kp, inv,
+                                             scale, scale_group, status, c->num_sms, c->stream);
+            c->stats.launches += 3;
+        } else {
+            e = launch_normalize(fmt, r.x, r.ld, r.d, sel ? ids : nullptr, n_sel, r.n, out, ld_out, (int)kp, inv,
+                                 scale, status, c->num_sms, c->stream);
+            c->stats.launches += 1;
+        }
         if (e != cudaSuccess) return from_cuda(e);
-        c->stats.launches += 1;
     }
     return EJOIN_OK;
 }
@@ -373,12 +380,14 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     if (timing) cudaEventRecord(c->ev[0], c->stream);
     Side &sa = c->side[0];
     Side &sb = self ? c->side[0] : c->side[1];
+    // e4m3: the S operand's scales are shared per 256-row column tile (a self-join's single operand too),
+    // so the contraction folds them into its threshold; R keeps per-row scales
     ejoin_status st = prepare_side(c, 0, R, selR, fmt, kp, sa.norm.p, kp, (float *)sa.inv.p, (float *)sa.scale.p,
-                                   (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false);
+                                   (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false, self ? 256 : 0);
     if (st != EJOIN_OK) return st;
     if (!self) {
         st = prepare_side(c, 1, S, selS, fmt, kp, sb.norm.p, kp, (float *)sb.inv.p, (float *)sb.scale.p,
-                          (uint32_t *)sb.ids.p, &dm->n_sel[1], &dm->status, false);
+                          (uint32_t *)sb.ids.p, &dm->n_sel[1], &dm->status, false, 256);
         if (st != EJOIN_OK) return st;
     }
     const long long *nA = &dm->n_sel[0];
@@ -512,13 +521,14 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     if (*pairs_io == nullptr && !count_only) *cap_io = 0;
 
     // exact re-score of the candidates
+    if ((e = ensure(c->band, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
     e = hm.cand_count == 0 ? cudaSuccess : launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
                        selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
                        (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
                        count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0, c->num_sms,
-                       c->stream, sym ? 1 : 0);
+                       c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0);
     if (e != cudaSuccess) return from_cuda(e);
-    c->stats.launches += hm.cand_count ? 1 : 0;
+    c->stats.launches += hm.cand_count ? (c->fp64_band > 0.f ? 2 : 1) : 0;
     if (timing) cudaEventRecord(c->ev[3], c->stream);
     if (d_count_user) {
         if ((e = cudaMemcpyAsync(d_count_user, &dm->pair_count, sizeof(uint64_t), cudaMemcpyDeviceToDevice,

@@ -54,6 +54,9 @@ struct BatchTables {
     const uint2 *tile_list;
     const unsigned long long *tile_count;
     unsigned long long tile_cap;
+    // tile-list mode of a self-join listing only block pairs on and above the diagonal of 256-row
+    // blocks: inside a diagonal block (row tile m, column tile n, m / 2 == n) keep col >= row
+    int sym;
 };
 
 // Per-job row sources of a batched re-score (device arrays).
@@ -106,6 +109,12 @@ cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const u
                              const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
                              int kp, float *inv_norm, float *scale, unsigned *status, int num_sms,
                              cudaStream_t st);
+// e4m3 normalisation whose scales are shared by each aligned group of `group` output rows
+// (scale[c] = the largest per-row scale of c's group); 3 kernels.
+cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, const uint32_t *ids,
+                                         const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
+                                         int kp, float *inv_norm, float *scale, int group, unsigned *status,
+                                         int num_sms, cudaStream_t st);
 cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
                                    int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
                                    float *scale, unsigned *status, int num_sms, cudaStream_t st);
@@ -131,12 +140,13 @@ cudaError_t launch_sim_tc_fused(int kind, const CUtensorMap *tmA, const CUtensor
                                 const long long *nA, const long long *nB, float thr, const float *scaleA,
                                 const float *scaleB, const FuseArgs &fa, unsigned long long *cand_count,
                                 unsigned *status, uint64_t timeout, int grid, int group_m, cudaStream_t st);
-// Contraction over an explicit list of (row tile, column tile) pairs (pruned joins).
+// Contraction over an explicit list of (row tile, column tile) pairs (pruned joins); sym: see
+// BatchTables::sym.
 cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
                                const long long *nB, float thr, const uint2 *tile_list,
                                const unsigned long long *tile_count, unsigned long long tile_cap, uint2 *cand,
                                uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                               int grid, cudaStream_t st);
+                               int grid, cudaStream_t st, int sym = 0);
 // Batched contraction over a job table (BF16 / e4m3 / TF32 kinds as above).
 cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                                 const BatchTables &bt, const float *scaleA, const float *scaleB, uint2 *cand,
@@ -160,15 +170,17 @@ inline int default_group_m(int64_t kp)
     return (int)g;
 }
 size_t sim_tc_smem_bytes();
-// Candidates: cand[0 .. min(*cand_count, cand_cap)).  mirror: the candidates come
-// from the upper triangle of a self-join; each pair (i, j), i != j, is written in
-// both orders.
+// Candidates: cand[0 .. min(*cand_count, cand_cap)).  Candidates whose FP32 similarity
+// lies within fp64_band of eps are listed in band_list (capacity band_cap >= cand_cap,
+// counted in *band_count) and decided by a second kernel, the accurate tier.  mirror: the
+// candidates come from the upper triangle of a self-join; each pair (i, j), i != j, is
+// written in both orders.
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                            const float *R, int64_t ldR, const float *S, int64_t ldS, int d,
                            const uint32_t *idsR, const uint32_t *idsS, const float *invR, const float *invS,
                            float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                            unsigned long long *out_count, unsigned long long *band_count, int count_only,
-                           int num_sms, cudaStream_t st, int mirror = 0);
+                           int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror = 0);
 
 // ------------------------------------------------------- device PTX helpers
 #if defined(__CUDACC__)
@@ -366,8 +378,10 @@ __device__ __forceinline__ double dot2_warp_total(Dot2Acc a)
 }
 
 // Accurate cosine of two raw FP32 rows (one warp): Dot2 for x.y, x.x, y.y,
-// finished in FP64; 0 when a row is zero; clamped to [-1, 1].
-__device__ __forceinline__ double accurate_cosine(const float *__restrict__ r, const float *__restrict__ s, int d,
+// finished in FP64; 0 when a row is zero; clamped to [-1, 1].  Not inlined:
+// the callers take it rarely, and its registers must not count against their
+// occupancy.
+static __device__ __noinline__ double accurate_cosine(const float *__restrict__ r, const float *__restrict__ s, int d,
                                                   int lane)
 {
     Dot2Acc xy{0.f, 0.f}, xx{0.f, 0.f}, yy{0.f, 0.f};
@@ -378,6 +392,54 @@ __device__ __forceinline__ double accurate_cosine(const float *__restrict__ r, c
         dot2_add(yy, y, y);
     }
     const double dd = dot2_warp_total(xy), nr = dot2_warp_total(xx), ns = dot2_warp_total(yy);
+    double c = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
+    return fmin(1.0, fmax(-1.0, c));
+}
+
+// The same for 16-byte aligned rows with d % 4 == 0: float4 loads, two sets of
+// accumulators (even and odd float4 groups of a lane) combined at the end.
+static __device__ __noinline__ double accurate_cosine4(const float *__restrict__ r, const float *__restrict__ s, int d,
+                                                       int lane)
+{
+    Dot2Acc xy[2] = {{0.f, 0.f}, {0.f, 0.f}}, xx[2] = {{0.f, 0.f}, {0.f, 0.f}}, yy[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    const float4 *r4 = reinterpret_cast<const float4 *>(r), *s4 = reinterpret_cast<const float4 *>(s);
+    const int d4 = d >> 2;
+    int g = lane;
+    for (; g + 32 < d4; g += 64) {
+        const float4 a0 = __ldg(r4 + g), b0 = __ldg(s4 + g), a1 = __ldg(r4 + g + 32), b1 = __ldg(s4 + g + 32);
+        dot2_add(xy[0], a0.x, b0.x), dot2_add(xy[1], a1.x, b1.x);
+        dot2_add(xy[0], a0.y, b0.y), dot2_add(xy[1], a1.y, b1.y);
+        dot2_add(xy[0], a0.z, b0.z), dot2_add(xy[1], a1.z, b1.z);
+        dot2_add(xy[0], a0.w, b0.w), dot2_add(xy[1], a1.w, b1.w);
+        dot2_add(xx[0], a0.x, a0.x), dot2_add(xx[1], a1.x, a1.x);
+        dot2_add(xx[0], a0.y, a0.y), dot2_add(xx[1], a1.y, a1.y);
+        dot2_add(xx[0], a0.z, a0.z), dot2_add(xx[1], a1.z, a1.z);
+        dot2_add(xx[0], a0.w, a0.w), dot2_add(xx[1], a1.w, a1.w);
+        dot2_add(yy[0], b0.x, b0.x), dot2_add(yy[1], b1.x, b1.x);
+        dot2_add(yy[0], b0.y, b0.y), dot2_add(yy[1], b1.y, b1.y);
+        dot2_add(yy[0], b0.z, b0.z), dot2_add(yy[1], b1.z, b1.z);
+        dot2_add(yy[0], b0.w, b0.w), dot2_add(yy[1], b1.w, b1.w);
+    }
+    if (g < d4) {
+        const float4 a0 = __ldg(r4 + g), b0 = __ldg(s4 + g);
+        dot2_add(xy[0], a0.x, b0.x), dot2_add(xy[0], a0.y, b0.y), dot2_add(xy[0], a0.z, b0.z),
+            dot2_add(xy[0], a0.w, b0.w);
+        dot2_add(xx[0], a0.x, a0.x), dot2_add(xx[0], a0.y, a0.y), dot2_add(xx[0], a0.z, a0.z),
+            dot2_add(xx[0], a0.w, a0.w);
+        dot2_add(yy[0], b0.x, b0.x), dot2_add(yy[0], b0.y, b0.y), dot2_add(yy[0], b0.z, b0.z),
+            dot2_add(yy[0], b0.w, b0.w);
+    }
+    // fold the second set into the first (two-sum of the sums, errors added)
+    auto fold = [](Dot2Acc &a, const Dot2Acc &b) {
+        float t, e;
+        two_sum(a.s, b.s, t, e);
+        a.s = t;
+        a.c = __fadd_rn(a.c, __fadd_rn(b.c, e));
+    };
+    fold(xy[0], xy[1]);
+    fold(xx[0], xx[1]);
+    fold(yy[0], yy[1]);
+    const double dd = dot2_warp_total(xy[0]), nr = dot2_warp_total(xx[0]), ns = dot2_warp_total(yy[0]);
     double c = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
     return fmin(1.0, fmax(-1.0, c));
 }

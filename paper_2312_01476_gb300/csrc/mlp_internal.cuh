@@ -68,6 +68,14 @@ cudaError_t launch_cover_drop(const float *S, const uint32_t *cand, int nc, floa
                               cudaStream_t st);
 cudaError_t launch_cover_update(const float *S, const uint32_t *rows, int64_t m, const float *anchors, int n_anchor,
                                 float tau, unsigned char *covered, cudaStream_t st);
+// Assignment of rows to covering anchors from the candidates (row, anchor) of a threshold
+// contraction of the sketches against the anchors: best[r] = max over r's candidates of
+// (cosine bits << 32 | anchor) (best zeroed by the caller); key[r] = its anchor, or n_anchor
+// when no candidate reached row r.
+cudaError_t launch_anchor_argmax(const uint2 *cand, const unsigned long long *cand_count, uint64_t cap, const float *S,
+                                 const float *anchors, unsigned long long *best, int num_sms, cudaStream_t st);
+cudaError_t launch_anchor_keys(const unsigned long long *best, int64_t n, int n_anchor, uint32_t *key, int num_sms,
+                               cudaStream_t st);
 // Balls per tile in the pruning bound.
 constexpr int PRUNE_BALLS = 4;
 // Per tile of `tile_rows` (<= 256) consecutive sketch rows: up to PRUNE_BALLS balls formed greedily
@@ -76,8 +84,9 @@ constexpr int PRUNE_BALLS = 4;
 cudaError_t launch_tile_stats(const float *S, int64_t n, int k, int tile_rows, float *centroid, float *radius,
                               cudaStream_t st);
 // Surviving tile pairs: some ball pair has cos(max(0, angle(c_a, c_b) - r_a - r_b)) >= eps_sketch.
+// sym (self-join, A tiles of 128 and B tiles of 256 rows of one order): only pairs with a / 2 <= b.
 cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, const float *cB, const float *rB,
                               int64_t tB, int k, float eps_sketch, uint2 *list, uint64_t cap,
-                              unsigned long long *count, cudaStream_t st);
+                              unsigned long long *count, cudaStream_t st, int sym = 0);
 
 }  // namespace ej

@@ -200,7 +200,8 @@ __device__ __forceinline__ void normalize_row(const float *__restrict__ src, int
     }
     if (lane == 0 && inv_norm) inv_norm[c] = inv;
 
-    // pass 2: write the normalised row, zero padded to kp
+    // pass 2: write the normalised row, zero padded to kp (out == nullptr: norms and scales only)
+    if (!out) return;
     for (int g = lane; g < groups; g += 32) {
         const int k = 4 * g;
         float4 v = k < d ? load4(k) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -277,6 +278,88 @@ __global__ void __launch_bounds__(256) normalize_batch_kernel(const float *const
         const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
         normalize_row<FMT>(x + (g - row_off[lo]) * ld, d, vec, out, g, kp, kp, inv_norm, scale, status, lane);
     }
+}
+
+// e4m3 with a scale shared by each group of G consecutive output rows (the
+// rows of one column tile of the contraction): scale[c] = the largest per-row
+// scale max|y|/448 of c's group, so the epilogue can fold one column scale per
+// tile into its threshold.  Unit rows have |y| <= 1, so every shared scale is
+// still at most 1/448 and the guard band of the per-row form covers it.
+__global__ void scale_group_max_kernel(float *__restrict__ scale, const long long *__restrict__ n_rows_dev,
+                                       int64_t n_rows_max, int G)
+{
+    int64_t n = *n_rows_dev;
+    if (n > n_rows_max) n = n_rows_max;
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g0 = w * G; g0 < n; g0 += nw * G) {
+        const int64_t g1 = g0 + G < n ? g0 + G : n;
+        float m = 0.f;
+        for (int64_t c = g0 + lane; c < g1; c += 32) m = fmaxf(m, scale[c]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        for (int64_t c = g0 + lane; c < g1; c += 32) scale[c] = m;
+    }
+}
+
+// Quantise kept row c (one warp): q = rn_satfinite(x_r * inv[c] / scale[c]) in
+// e4m3, zero padded to kp.
+__global__ void __launch_bounds__(256) fp8_quantize_kernel(const float *__restrict__ x, int64_t ld, int d,
+                                                           const uint32_t *__restrict__ ids,
+                                                           const long long *__restrict__ n_rows_dev,
+                                                           int64_t n_rows_max, __nv_fp8_storage_t *__restrict__ out,
+                                                           int64_t ld_out, int kp, const float *__restrict__ inv_norm,
+                                                           const float *__restrict__ scale)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int64_t n_rows = *n_rows_dev;
+    if (n_rows > n_rows_max) n_rows = n_rows_max;
+    const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    for (int64_t c = warp_global; c < n_rows; c += n_warps) {
+        const float *src = x + (ids ? (int64_t)ids[c] : c) * ld;
+        const float m = inv_norm[c] / scale[c];
+        for (int g = lane; g < (kp >> 2); g += 32) {
+            const int k = 4 * g;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (vec && k + 3 < d) {
+                v = __ldg(reinterpret_cast<const float4 *>(src + k));
+            } else {
+                if (k + 0 < d) v.x = __ldg(src + k + 0);
+                if (k + 1 < d) v.y = __ldg(src + k + 1);
+                if (k + 2 < d) v.z = __ldg(src + k + 2);
+                if (k + 3 < d) v.w = __ldg(src + k + 3);
+            }
+            const __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v.x * m, v.y * m), __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v.z * m, v.w * m), __NV_SATFINITE, __NV_E4M3);
+            *reinterpret_cast<uint32_t *>(out + c * ld_out + k) = (uint32_t)lo | ((uint32_t)hi << 16);
+        }
+    }
+}
+
+cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, const uint32_t *ids,
+                                         const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
+                                         int kp, float *inv_norm, float *scale, int group, unsigned *status,
+                                         int num_sms, cudaStream_t st)
+{
+    if (n_rows_max <= 0) return cudaSuccess;
+    if (!inv_norm || !scale || group < 1) return cudaErrorInvalidValue;
+    int64_t blocks = (n_rows_max + 7) / 8;
+    const int64_t cap = (int64_t)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    // norms and per-row scales, then the group maxima, then the quantised rows
+    normalize_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, nullptr,
+                                                                ld_out, kp, inv_norm, scale, status);
+    int64_t gblocks = ((n_rows_max + group - 1) / group + 7) / 8;
+    if (gblocks > cap) gblocks = cap;
+    if (gblocks < 1) gblocks = 1;
+    scale_group_max_kernel<<<(unsigned)gblocks, 256, 0, st>>>(scale, n_rows_dev, n_rows_max, group);
+    fp8_quantize_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max,
+                                                          reinterpret_cast<__nv_fp8_storage_t *>(out), ld_out, kp,
+                                                          inv_norm, scale);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_sel_count(const SelArgs &s, int64_t n, uint32_t *block_counts, cudaStream_t st)

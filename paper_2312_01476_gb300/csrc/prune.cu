@@ -9,6 +9,7 @@
 //   angle(s_a, s_b) >= angle(c_A, c_B) - rho_A - rho_B
 // (triangle inequality for angles on the sphere), hence
 //   cos(s_a, s_b) <= cos(max(0, angle(c_A, c_B) - rho_A - rho_B)).
+#include <algorithm>
 #include <cfloat>
 
 #include "mlp_internal.cuh"
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(256) tile_pairs_kernel(const float *__restrict
                                                          int64_t tA, const float *__restrict__ cB,
                                                          const float *__restrict__ rB, int64_t tB, float cos_keep,
                                                          uint2 *__restrict__ list, uint64_t cap,
-                                                         unsigned long long *count)
+                                                         unsigned long long *count, int sym)
 {
     extern __shared__ float sm[];
     float *sa = sm;                          // [TP * NB][SK + 1]
@@ -357,6 +358,7 @@ __global__ void __launch_bounds__(256) tile_pairs_kernel(const float *__restrict
         for (int j = 0; j < 2; ++j) {
             const int tb = tx * 2 + j;
             if (a0 + ta >= tA || b0 + tb >= tB) continue;
+            if (sym && ((a0 + ta) >> 1) > b0 + tb) continue;  // self-join: block pairs on or above the diagonal
             bool keep = false;
             for (int x = 0; x < NB && !keep; ++x) {
                 const float rx = ra[ta * NB + x];
@@ -485,7 +487,7 @@ cudaError_t launch_tile_stats(const float *S, int64_t n, int k, int tile_rows, f
 
 cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, const float *cB, const float *rB,
                               int64_t tB, int k, float eps_sketch, uint2 *list, uint64_t cap,
-                              unsigned long long *count, cudaStream_t st)
+                              unsigned long long *count, cudaStream_t st, int sym)
 {
     if (k != SK) return cudaErrorInvalidValue;
     if (tA <= 0 || tB <= 0) return cudaSuccess;
@@ -493,7 +495,63 @@ cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, cons
     cudaError_t e = cudaFuncSetAttribute(tile_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((tB + TP - 1) / TP), (unsigned)((tA + TP - 1) / TP));
-    tile_pairs_kernel<<<grid, 256, smem, st>>>(cA, rA, tA, cB, rB, tB, eps_sketch, list, cap, count);
+    tile_pairs_kernel<<<grid, 256, smem, st>>>(cA, rA, tA, cB, rB, tB, eps_sketch, list, cap, count, sym);
+    return cudaGetLastError();
+}
+
+}  // namespace ej
+
+namespace ej {
+
+// Argmax over the (row, anchor) candidates of the assignment contraction: the
+// exact FP32 sketch cosine of each candidate, packed above the anchor index,
+// kept per row with a 64-bit atomicMax (the candidates' cosines are positive,
+// so their bit patterns order like the values).
+__global__ void anchor_argmax_kernel(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count,
+                                     uint64_t cap, const float *__restrict__ S, const float *__restrict__ anchors,
+                                     unsigned long long *__restrict__ best)
+{
+    uint64_t n = *cand_count;
+    if (n > cap) n = cap;
+    const int lane = threadIdx.x & 31;
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t k = w; k < n; k += nw) {
+        const uint2 c = cand[k];
+        const float2 x = __ldg(reinterpret_cast<const float2 *>(S + (int64_t)c.x * SK) + lane);
+        const float2 y = __ldg(reinterpret_cast<const float2 *>(anchors + (int64_t)c.y * SK) + lane);
+        float dot = fmaf(x.x, y.x, x.y * y.y);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0 && dot > 0.f)
+            atomicMax(best + c.x, ((unsigned long long)__float_as_uint(dot) << 32) | (unsigned long long)c.y);
+    }
+}
+
+// key[r] = anchor of best[r], or n_anchor (the group of rows no anchor reached) when best[r] == 0.
+__global__ void anchor_keys_kernel(const unsigned long long *__restrict__ best, int64_t n, int n_anchor,
+                                   uint32_t *__restrict__ key)
+{
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = best[r];
+        key[r] = b ? (uint32_t)(b & 0xffffffffull) : (uint32_t)n_anchor;
+    }
+}
+
+cudaError_t launch_anchor_argmax(const uint2 *cand, const unsigned long long *cand_count, uint64_t cap, const float *S,
+                                 const float *anchors, unsigned long long *best, int num_sms, cudaStream_t st)
+{
+    if (cap == 0) return cudaSuccess;
+    anchor_argmax_kernel<<<(unsigned)num_sms * 8, 256, 0, st>>>(cand, cand_count, cap, S, anchors, best);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_anchor_keys(const unsigned long long *best, int64_t n, int n_anchor, uint32_t *key, int num_sms,
+                               cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16);
+    anchor_keys_kernel<<<(unsigned)blocks, 256, 0, st>>>(best, n, n_anchor, key);
     return cudaGetLastError();
 }
 

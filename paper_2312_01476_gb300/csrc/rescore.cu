@@ -36,24 +36,32 @@ __device__ __forceinline__ float warp_sum_f(float v)
 // is written as (i, j) and (j, i), both with the same similarity, which is
 // exact because the FP32 dot product and the accurate tier are symmetric in
 // their two rows.
-__device__ __forceinline__ void emit_block(bool my_emit, uint32_t my_i, uint32_t my_j, float my_sim, int my_band,
-                                           int mirror, int *wcnt, unsigned long long *base_s,
-                                           unsigned long long *out_count, unsigned long long *band_count,
+template <bool MIRROR>
+__device__ __forceinline__ void emit_block(bool my_emit, uint32_t my_i, uint32_t my_j, float my_sim, int *wcnt,
+                                           unsigned long long *base_s, unsigned long long *out_count,
                                            ejoin_pair *__restrict__ out, uint64_t out_cap, int count_only, int lane,
                                            int warp)
 {
-    const int mine = my_emit ? ((mirror && my_i != my_j) ? 2 : 1) : 0;
-    int incl = mine;  // warp inclusive scan of the record counts
+    int mine, incl;
+    if constexpr (MIRROR) {
+        mine = my_emit ? (my_i != my_j ? 2 : 1) : 0;
+        incl = mine;  // warp inclusive scan of the record counts
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
     }
-    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
-    const int nb = __popc(__ballot_sync(0xffffffffu, my_band != 0));
+    const unsigned m = __ballot_sync(0xffffffffu, my_emit);
     if (lane == 0) {
-        wcnt[warp] = wtot;
-        if (nb) atomicAdd(band_count, (unsigned long long)nb);
+        if constexpr (MIRROR) {
+            wcnt[warp] = 0;
+        } else {
+            wcnt[warp] = __popc(m);
+        }
+    }
+    if constexpr (MIRROR) {
+        if (lane == 31) wcnt[warp] = incl;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -66,8 +74,10 @@ __device__ __forceinline__ void emit_block(bool my_emit, uint32_t my_i, uint32_t
         *base_s = run ? atomicAdd(out_count, (unsigned long long)run) : 0ull;
     }
     __syncthreads();
-    if (mine && !count_only) {
-        const unsigned long long pos = *base_s + (unsigned long long)(wcnt[warp] + incl - mine);
+    if (my_emit && !count_only) {
+        unsigned long long pos;
+        if constexpr (MIRROR) pos = *base_s + (unsigned long long)(wcnt[warp] + incl - mine);
+        else pos = *base_s + wcnt[warp] + __popc(m & ((1u << lane) - 1u));
         if (pos < out_cap) {
             ejoin_pair p;
             p.i = my_i;
@@ -75,23 +85,27 @@ __device__ __forceinline__ void emit_block(bool my_emit, uint32_t my_i, uint32_t
             p.sim = my_sim;
             out[pos] = p;
         }
-        if (mine == 2 && pos + 1 < out_cap) {
-            ejoin_pair p;
-            p.i = my_j;
-            p.j = my_i;
-            p.sim = my_sim;
-            out[pos + 1] = p;
+        if constexpr (MIRROR) {
+            if (mine == 2 && pos + 1 < out_cap) {
+                ejoin_pair p;
+                p.i = my_j;
+                p.j = my_i;
+                p.sim = my_sim;
+                out[pos + 1] = p;
+            }
         }
     }
     __syncthreads();
 }
 
+template <bool MIRROR>
 __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
     const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
     const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
     const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
     const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
-    unsigned long long *out_count, unsigned long long *band_count, int count_only, int mirror)
+    unsigned long long *out_count, unsigned long long *band_count, int count_only, uint2 *__restrict__ band_list,
+    uint64_t band_cap)
 {
     __shared__ int wcnt[RS_WARPS];
     __shared__ unsigned long long base_s;
@@ -101,7 +115,6 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
     const bool vec = ((ldR & 3) == 0) && ((ldS & 3) == 0) && ((reinterpret_cast<uintptr_t>(R) & 15) == 0) &&
                      ((reinterpret_cast<uintptr_t>(S) & 15) == 0);
     const int d4 = vec ? (d >> 2) : 0;  // float4 groups
-    const double eps_d = (double)eps;
     for (uint64_t start = (uint64_t)blockIdx.x * RS_PER_BLOCK; start < n;
          start += (uint64_t)gridDim.x * RS_PER_BLOCK) {
         const int len = (int)std::min<uint64_t>(RS_PER_BLOCK, n - start);
@@ -109,7 +122,6 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
         bool my_emit = false;
         uint32_t my_i = 0, my_j = 0;
         float my_sim = 0.f;
-        int my_band = 0;
         const int wofs = warp * RS_PER_WARP;
         const uint64_t wbase = start + (uint64_t)wofs;
         for (int q = 0; q < RS_PER_WARP; ++q) {
@@ -134,24 +146,23 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
             float sim = acc * invR[c.x] * invS[c.y];
             sim = fminf(1.f, fmaxf(-1.f, sim));
             bool emit = sim >= eps;
-            int band = 0;
             if (fabsf(sim - eps) < fp64_band) {
-                // accurate tier: compensated dot product and norms, finished in FP64
-                const double s64 = accurate_cosine(r, s, d, lane);
-                emit = s64 >= eps_d;
-                sim = (float)s64;
-                band = 1;
+                // near eps: decided by the accurate tier (rescore_band_kernel)
+                if (lane == 0) {
+                    const unsigned long long p = atomicAdd(band_count, 1ull);
+                    if (p < band_cap) band_list[p] = make_uint2(i, j);
+                }
+                emit = false;
             }
             if (lane == q) {
                 my_emit = emit;
                 my_i = i;
                 my_j = j;
                 my_sim = sim;
-                my_band = band;
             }
         }
-        emit_block(my_emit, my_i, my_j, my_sim, my_band, mirror, wcnt, &base_s, out_count, band_count, out, out_cap,
-                   count_only, lane, warp);
+        emit_block<MIRROR>(my_emit, my_i, my_j, my_sim, wcnt, &base_s, out_count, out, out_cap, count_only, lane,
+                           warp);
     }
 }
 
@@ -159,13 +170,14 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_kernel(
 // rows of C candidates at once (V float4 per lane per row, all loads issued
 // before the first FMA), so that 2*C*V independent loads are in flight per
 // lane instead of a dependent chain per candidate.
-template <int V, int C>
+template <int V, int C, bool MIRROR>
 __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
     const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
     const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
     const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
     const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
-    unsigned long long *out_count, unsigned long long *band_count, int count_only, int mirror)
+    unsigned long long *out_count, unsigned long long *band_count, int count_only, uint2 *__restrict__ band_list,
+    uint64_t band_cap)
 {
     static_assert(RS_PER_WARP % C == 0, "candidates per warp step");
     __shared__ int wcnt[RS_WARPS];
@@ -174,14 +186,12 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
     uint64_t n = *cand_count;
     if (n > cand_cap) n = cand_cap;
     const int d4 = d >> 2;  // d is a multiple of 4 here
-    const double eps_d = (double)eps;
     for (uint64_t start = (uint64_t)blockIdx.x * RS_PER_BLOCK; start < n;
          start += (uint64_t)gridDim.x * RS_PER_BLOCK) {
         const int len = (int)std::min<uint64_t>(RS_PER_BLOCK, n - start);
         bool my_emit = false;
         uint32_t my_i = 0, my_j = 0;
         float my_sim = 0.f;
-        int my_band = 0;
         const int wofs = warp * RS_PER_WARP;
         const uint64_t wbase = start + (uint64_t)wofs;
         // lanes 0..RS_PER_WARP-1 fetch the warp's candidates and their ids / inverse norms
@@ -241,25 +251,83 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
                 float sim = acc[c] * __shfl_sync(0xffffffffu, sc, q);
                 sim = fminf(1.f, fmaxf(-1.f, sim));
                 bool emit = sim >= eps;
-                int band = 0;
                 if (fabsf(sim - eps) < fp64_band) {
-                    // accurate tier: compensated dot product and norms, finished in FP64
-                    const double s64 = accurate_cosine(R + (int64_t)ii[c] * ldR, S + (int64_t)jj[c] * ldS, d, lane);
-                    emit = s64 >= eps_d;
-                    sim = (float)s64;
-                    band = 1;
+                    // near eps: decided by the accurate tier (rescore_band_kernel)
+                    if (lane == 0) {
+                        const unsigned long long p = atomicAdd(band_count, 1ull);
+                        if (p < band_cap) band_list[p] = make_uint2(ii[c], jj[c]);
+                    }
+                    emit = false;
                 }
                 if (lane == q) {
                     my_emit = emit;
                     my_i = ii[c];
                     my_j = jj[c];
                     my_sim = sim;
-                    my_band = band;
                 }
             }
         }
-        emit_block(my_emit, my_i, my_j, my_sim, my_band, mirror, wcnt, &base_s, out_count, band_count, out, out_cap,
-                   count_only, lane, warp);
+        emit_block<MIRROR>(my_emit, my_i, my_j, my_sim, wcnt, &base_s, out_count, out, out_cap, count_only, lane,
+                           warp);
+    }
+}
+
+// Accurate tier of the re-score: the candidates that the FP32 tier found within
+// fp64_band of eps, listed as (original i, original j), decided by
+// accurate_cosine (compensated dot products finished in FP64).  One warp per
+// entry, 32 entries per warp step, one global atomic per step.
+template <bool MIRROR, bool VEC>
+__global__ void __launch_bounds__(256) rescore_band_kernel(const uint2 *__restrict__ band_list,
+                                                           const unsigned long long *__restrict__ band_count,
+                                                           uint64_t band_cap, const float *__restrict__ R, int64_t ldR,
+                                                           const float *__restrict__ S, int64_t ldS, int d, float eps,
+                                                           ejoin_pair *__restrict__ out, uint64_t out_cap,
+                                                           unsigned long long *out_count, int count_only)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t n = *band_count;
+    if (n > band_cap) n = band_cap;
+    const double eps_d = (double)eps;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = w0 * 32; base < n; base += nw * 32) {
+        const int len = (int)(n - base < 32 ? n - base : 32);
+        const uint2 mine_e = lane < len ? band_list[base + lane] : make_uint2(0u, 0u);
+        bool my_emit = false;
+        float my_sim = 0.f;
+        for (int q = 0; q < len; ++q) {
+            const uint32_t i = __shfl_sync(0xffffffffu, mine_e.x, q), j = __shfl_sync(0xffffffffu, mine_e.y, q);
+            const double s64 = VEC ? accurate_cosine4(R + (int64_t)i * ldR, S + (int64_t)j * ldS, d, lane)
+                                   : accurate_cosine(R + (int64_t)i * ldR, S + (int64_t)j * ldS, d, lane);
+            if (lane == q) {
+                my_emit = s64 >= eps_d;
+                my_sim = (float)s64;
+            }
+        }
+        const int mine = my_emit ? ((MIRROR && mine_e.x != mine_e.y) ? 2 : 1) : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long pos0 = 0;
+        if (lane == 0 && tot) pos0 = atomicAdd(out_count, (unsigned long long)tot);
+        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+        if (mine && !count_only) {
+            const unsigned long long pos = pos0 + (unsigned long long)(incl - mine);
+            ejoin_pair p;
+            p.i = mine_e.x;
+            p.j = mine_e.y;
+            p.sim = my_sim;
+            if (pos < out_cap) out[pos] = p;
+            if (mine == 2 && pos + 1 < out_cap) {
+                p.i = mine_e.y;
+                p.j = mine_e.x;
+                out[pos + 1] = p;
+            }
+        }
     }
 }
 
@@ -440,9 +508,11 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
                            const uint32_t *idsS, const float *invR, const float *invS, float eps, float fp64_band,
                            ejoin_pair *out, uint64_t out_cap, unsigned long long *out_count,
                            unsigned long long *band_count, int count_only, int num_sms, cudaStream_t st,
-                           int mirror)
+                           uint2 *band_list, uint64_t band_cap, int mirror)
 {
     if (cand_cap == 0) return cudaSuccess;
+    // every candidate may fall in the band: the list must hold them all
+    if (fp64_band > 0.f && (!band_list || band_cap < cand_cap)) return cudaErrorInvalidValue;
     uint64_t blocks = (cand_cap + RS_PER_BLOCK - 1) / RS_PER_BLOCK;
     const uint64_t lim = (uint64_t)num_sms * 8;
     if (blocks > lim) blocks = lim;
@@ -452,22 +522,36 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
     const int T = RS_WARPS * 32;
 #define EJ_RESCORE_ARGS                                                                                              \
     cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap, out_count, \
-        band_count, count_only, mirror
-    if (aligned && d <= 128) {
-        rescore_mlp_kernel<1, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-    } else if (aligned && d <= 256) {
-        rescore_mlp_kernel<2, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-    } else if (aligned && d <= 384) {
-        rescore_mlp_kernel<3, 4><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-    } else if (aligned && d <= 512) {
-        rescore_mlp_kernel<4, 2><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-    } else if (aligned && d <= 768) {
-        rescore_mlp_kernel<6, 2><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-    } else if (aligned && d <= 1024) {
-        rescore_mlp_kernel<8, 2><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+        band_count, count_only, band_list, band_cap
+#define EJ_DISPATCH(M)                                                                                              \
+    if (aligned && d <= 128) rescore_mlp_kernel<1, 4, M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                       \
+    else if (aligned && d <= 256) rescore_mlp_kernel<2, 4, M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                  \
+    else if (aligned && d <= 384) rescore_mlp_kernel<3, 4, M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                  \
+    else if (aligned && d <= 512) rescore_mlp_kernel<4, 2, M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                  \
+    else if (aligned && d <= 768) rescore_mlp_kernel<6, 2, M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                  \
+    else if (aligned && d <= 1024) rescore_mlp_kernel<8, 2, M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                 \
+    else rescore_kernel<M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+    if (mirror) {
+        EJ_DISPATCH(true)
     } else {
-        rescore_kernel<<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+        EJ_DISPATCH(false)
     }
+#undef EJ_DISPATCH
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || fp64_band <= 0.f) return e;
+    // the accurate tier over the candidates listed near eps (stream order: after the FP32 tier)
+    const unsigned gb = (unsigned)std::min<uint64_t>((band_cap + 255) / 256, (uint64_t)num_sms * 8);
+#define EJ_BAND(M, V)                                                                                               \
+    rescore_band_kernel<M, V><<<gb, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, \
+                                                  out_count, count_only)
+    if (mirror) {
+        if (aligned) EJ_BAND(true, true);
+        else EJ_BAND(true, false);
+    } else {
+        if (aligned) EJ_BAND(false, true);
+        else EJ_BAND(false, false);
+    }
+#undef EJ_BAND
 #undef EJ_RESCORE_ARGS
     return cudaGetLastError();
 }

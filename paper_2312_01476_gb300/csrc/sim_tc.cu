@@ -359,6 +359,7 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
         const uint2 mn = __ldg(bt.tile_list + t);
         m = mn.x;
         n = mn.y;
+        ti.diag = bt.sym && (m >> 1) == n;
         ti.rowA = m * BM;
         ti.rowB = n * BN;
         ti.limA = (int)min((long long)BM, nA - m * BM);
@@ -597,11 +598,19 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             const long long colbase = ti.rowB + colbase_local;
             const uint32_t tbase =
                 tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN) + (uint32_t)(half * (BN / 2));
+            // e4m3: similarity = acc * s_row * s_col.  In the single and self-join modes the rows of a
+            // 256-row column tile share one scale (launch_normalize_fp8_grouped), so the two scales fold
+            // into a per-lane threshold on the raw accumulator; the other modes scale every element
+            constexpr bool TILE_SCALE = KIND == 1 && (MODE == MODE_SINGLE || MODE == MODE_SYM);
             float rs = 1.f;
+            float thr_lane = thr_t;
             float csc[EPI_CHUNKS];
 #pragma unroll
             for (int c = 0; c < EPI_CHUNKS; ++c) csc[c] = 1.f;
-            if (KIND == 1) {
+            if constexpr (TILE_SCALE) {
+                const float sc = row_ok ? scaleA[row] * __ldg(scaleB + ti.rowB) : 0.f;
+                thr_lane = sc > 0.f ? __fdiv_rn(thr_t, sc) : (thr_t <= 0.f ? -INFINITY : INFINITY);
+            } else if constexpr (KIND == 1) {
                 rs = row_ok ? scaleA[row] : 0.f;
 #pragma unroll
                 for (int c = 0; c < EPI_CHUNKS; ++c) {
@@ -617,7 +626,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
                     f[k] = __uint_as_float(v[k]);
-                    if (KIND == 1) f[k] *= rs * __shfl_sync(0xffffffffu, csc[c], k);
+                    if (KIND == 1 && !TILE_SCALE) f[k] *= rs * __shfl_sync(0xffffffffu, csc[c], k);
                 }
                 // max tree: a8[g] = max of f[8g .. 8g+7]
                 float a8[4];
@@ -631,19 +640,20 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                     for (int g = 0; g < 4; ++g) a8[g] = fmaxf(u[2 * g], u[2 * g + 1]);
                 }
                 const float mx = fmaxf(fmaxf(a8[0], a8[1]), fmaxf(a8[2], a8[3]));
-                if (!__any_sync(0xffffffffu, row_ok && mx >= thr_t)) return;
+                if (!__any_sync(0xffffffffu, row_ok && mx >= thr_lane)) return;
                 // slow path: per-lane match mask, built only for 8-column groups that hold a match
                 unsigned mask = 0u;
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
-                    if (__any_sync(0xffffffffu, row_ok && a8[g] >= thr_t)) {
+                    if (__any_sync(0xffffffffu, row_ok && a8[g] >= thr_lane)) {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) mask |= (f[8 * g + k] >= thr_t ? 1u : 0u) << (8 * g + k);
+                        for (int k = 0; k < 8; ++k) mask |= (f[8 * g + k] >= thr_lane ? 1u : 0u) << (8 * g + k);
                     }
                 }
                 if (left < 32) mask &= left <= 0 ? 0u : ((1u << left) - 1u);
-                if constexpr (MODE == MODE_SYM) {
-                    // diagonal block: keep col >= row (the mirror is emitted by the re-score)
+                if constexpr (MODE == MODE_SYM || MODE == MODE_LIST) {
+                    // diagonal block of a symmetric evaluation: keep col >= row (the mirror is emitted by
+                    // the re-score)
                     if (ti.diag) {
                         const long long skip = row - col0;  // columns of this chunk left of the diagonal
                         mask &= skip <= 0 ? 0xffffffffu : (skip >= 32 ? 0u : ~((1u << skip) - 1u));
@@ -897,12 +907,13 @@ cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorM
                                const long long *nB, float thr, const uint2 *tile_list,
                                const unsigned long long *tile_count, unsigned long long tile_cap, uint2 *cand,
                                uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                               int grid, cudaStream_t st)
+                               int grid, cudaStream_t st, int sym)
 {
     BatchTables bt{};
     bt.tile_list = tile_list;
     bt.tile_count = tile_count;
     bt.tile_cap = tile_cap;
+    bt.sym = sym;
     switch (kind) {
     case 0:
         return launch_one<0, MODE_LIST>(tmA, tmB, kp, nA, nB, thr, nullptr, nullptr, cand, cap, cand_count, status,

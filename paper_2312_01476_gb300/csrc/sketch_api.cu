@@ -42,7 +42,8 @@ struct ejoin_sketch {
     // pruned-join workspace, per side
     struct Side {
         Buf S, key1, perm1, perm, hist, a_idx, anchors2, norm, inv, scale, sS, maxdot, cent, rad;
-        int n_anchor = 0;  // covering anchors of the last reorder
+        Buf skb, anb, tinv, best, cnt;  // assignment contraction: BF16 sketches and anchors, argmax
+        int n_anchor = 0;               // covering anchors of the last reorder
     } pw[2];
     Buf list, list_count;
     uint64_t list_cap = 0;
@@ -270,7 +271,7 @@ void ejoin_sketch_destroy(ejoin_sketch *sk)
             release(*b);
         for (auto &w : sk->pw)
             for (Buf *b : {&w.S, &w.key1, &w.perm1, &w.perm, &w.hist, &w.a_idx, &w.anchors2, &w.norm, &w.inv,
-                           &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad})
+                           &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad, &w.skb, &w.anb, &w.tinv, &w.best, &w.cnt})
                 release(*b);
     }
     delete sk;
@@ -455,7 +456,7 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
     if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) || (e = ensure(sd.inv, (size_t)rows * 4)) ||
         (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4))) || (e = ensure(pw.S, (size_t)rows * SKW * 4)) ||
         (e = ensure(pw.key1, (size_t)rows * 4)) || (e = ensure(pw.perm, (size_t)rows * 4)) ||
-        (e = ensure(pw.hist, (size_t)COVER_MAX_ANCHORS * 4)) ||
+        (e = ensure(pw.hist, (size_t)(COVER_MAX_ANCHORS + 1) * 4)) ||
         (e = ensure(pw.a_idx, (size_t)(m + COVER_ROUND) * 4)) || (e = ensure(pw.perm1, (size_t)COVER_ROUND)) ||
         (e = ensure(pw.anchors2, (size_t)COVER_MAX_ANCHORS * SKW * 4)) ||
         (e = ensure(pw.norm, (size_t)rows * kp * eb)) || (e = ensure(pw.inv, (size_t)rows * 4)) ||
@@ -517,11 +518,53 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
         n_anchor += nk;
     }
     pw.n_anchor = n_anchor;
-    // every row joins its most similar anchor; counting sort by anchor
+
+    // every row joins its most similar anchor: a BF16 threshold contraction of the sketches against
+    // the anchors on the tensor cores finds, for each row, the anchors within sketch cosine 0.6, and an
+    // argmax of their exact FP32 cosines picks one; rows that no anchor reaches form a last group
+    const int64_t rowsK = round_up(n_anchor, 256);
+    if ((e = ensure(pw.skb, (size_t)rows * SKW * 2)) || (e = ensure(pw.anb, (size_t)rowsK * SKW * 2)) ||
+        (e = ensure(pw.tinv, (size_t)std::max(rows, rowsK) * 4)) || (e = ensure(pw.best, (size_t)rows * 8)) ||
+        (e = ensure(pw.cnt, 16)))
+        return from_cuda(e);
+    long long *cnt = (long long *)pw.cnt.p;
+    float *tinv = (float *)pw.tinv.p;
+    if ((e = launch_set_count(cnt, n, st)) || (e = launch_set_count(cnt + 1, n_anchor, st)) ||
+        (e = launch_normalize(FMT_BF16, S, SKW, SKW, nullptr, cnt, n, pw.skb.p, SKW, SKW, tinv, nullptr, &dm->status,
+                              c->num_sms, st)) ||
+        (e = launch_normalize(FMT_BF16, anchors, SKW, SKW, nullptr, cnt + 1, n_anchor, pw.anb.p, SKW, SKW, tinv,
+                              nullptr, &dm->status, c->num_sms, st)) ||
+        (e = cudaMemsetAsync(pw.best.p, 0, (size_t)n * 8, st)))
+        return from_cuda(e);
+    CUtensorMap tmS, tmAn;
+    if (!make_tmap(&tmS, pw.skb.p, FMT_BF16, SKW, rows, 128) || !make_tmap(&tmAn, pw.anb.p, FMT_BF16, SKW, rowsK, 256))
+        return EJOIN_ECUDA;
+    const float thr = 0.6f - default_band(EJOIN_BF16, SKW);
+    if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
+    if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    for (int attempt = 0;; ++attempt) {
+        DevMisc hm;
+        if ((e = cudaMemsetAsync(&dm->cand_count, 0, 8, st)) ||
+            (e = launch_sim_tc(0, &tmS, &tmAn, SKW, cnt, cnt + 1, thr, nullptr, nullptr, (uint2 *)c->cand.p,
+                               c->cand_cap, &dm->cand_count, &dm->status, c->timeout, 0, c->num_sms,
+                               default_group_m(SKW), st)) ||
+            (e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            return from_cuda(e);
+        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+        if (hm.cand_count <= c->cand_cap) break;
+        if (attempt == 3) return EJOIN_ECUDA;
+        c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+        if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    }
+    // counting sort by anchor (n_anchor + 1 groups)
     uint32_t *key = (uint32_t *)pw.key1.p, *hist = (uint32_t *)pw.hist.p, *perm = (uint32_t *)pw.perm.p;
-    if ((e = launch_assign_keys(S, n, SKW, anchors, n_anchor, nullptr, key, c->num_sms, st)) ||
-        (e = cudaMemsetAsync(hist, 0, (size_t)n_anchor * 4, st)) || (e = launch_key_histogram(key, n, hist, st)) ||
-        (e = launch_key_scan(hist, n_anchor, st)) || (e = launch_key_scatter(key, n, hist, perm, st)) ||
+    if ((e = launch_anchor_argmax((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, S, anchors,
+                                  (unsigned long long *)pw.best.p, c->num_sms, st)) ||
+        (e = launch_anchor_keys((const unsigned long long *)pw.best.p, n, n_anchor, key, c->num_sms, st)) ||
+        (e = cudaMemsetAsync(hist, 0, (size_t)(n_anchor + 1) * 4, st)) || (e = launch_key_histogram(key, n, hist, st)) ||
+        (e = launch_key_scan(hist, n_anchor + 1, st)) || (e = launch_key_scatter(key, n, hist, perm, st)) ||
         (e = launch_gather_rows(sd.norm.p, kp * eb, perm, n, pw.norm.p, st)) ||
         (e = launch_gather_f32((const float *)sd.inv.p, perm, n, (float *)pw.inv.p, st)) ||
         (e = launch_gather_rows(pw.S.p, SKW * 4, perm, n, pw.sS.p, st)) ||
@@ -599,7 +642,8 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
         if ((e = ensure(sk->list, sk->list_cap * sizeof(uint2))) || (e = ensure(sk->list_count, 8)) ||
             (e = cudaMemsetAsync(sk->list_count.p, 0, 8, st)) ||
             (e = launch_tile_pairs((const float *)pa.cent.p, (const float *)pa.rad.p, tA, cB, rB, tB, SKW, eps_sketch,
-                                   (uint2 *)sk->list.p, sk->list_cap, (unsigned long long *)sk->list_count.p, st)) ||
+                                   (uint2 *)sk->list.p, sk->list_cap, (unsigned long long *)sk->list_count.p, st,
+                                   self ? 1 : 0)) ||
             (e = cudaMemcpyAsync(&n_list, sk->list_count.p, 8, cudaMemcpyDeviceToHost, st)) ||
             (e = cudaStreamSynchronize(st))) {
             release(centB);
@@ -612,7 +656,7 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     if (ps) {
         // diagnostics: ball radii of both sides, covering anchors and the largest anchor group of R
         std::vector<float> ra((size_t)tA * NBL), rb((size_t)tB * NBL);
-        std::vector<uint32_t> co((size_t)std::max(pa.n_anchor, 1));
+        std::vector<uint32_t> co((size_t)pa.n_anchor + 1);
         if ((e = cudaMemcpyAsync(ra.data(), pa.rad.p, ra.size() * 4, cudaMemcpyDeviceToHost, st)) ||
             (e = cudaMemcpyAsync(rb.data(), rB, rb.size() * 4, cudaMemcpyDeviceToHost, st)) ||
             (e = cudaMemcpyAsync(co.data(), pa.hist.p, co.size() * 4, cudaMemcpyDeviceToHost, st)) ||
@@ -659,7 +703,7 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
             (e = launch_sim_tc_list(kind, &tmA, &tmB, (int)kp, &dm->n_sel[0], &dm->n_sel[1], eps - band,
                                     (const uint2 *)sk->list.p, (const unsigned long long *)sk->list_count.p,
                                     sk->list_cap, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status,
-                                    c->timeout, c->num_sms, st)) ||
+                                    c->timeout, c->num_sms, st, self ? 1 : 0)) ||
             (e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, st)) ||
             (e = cudaStreamSynchronize(st)))
             return from_cuda(e);
@@ -679,10 +723,11 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
         out->capacity = cap;
     }
     if (hm.cand_count) {
+        if ((e = ensure(c->band, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
         e = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
                            (const uint32_t *)pa.perm.p, (const uint32_t *)pb.perm.p, (const float *)pa.inv.p,
                            (const float *)pb.inv.p, eps, c->fp64_band, out->d_pairs, out->capacity, &dm->pair_count,
-                           &dm->band_count, 0, c->num_sms, st);
+                           &dm->band_count, 0, c->num_sms, st, (uint2 *)c->band.p, c->cand_cap, self ? 1 : 0);
         if (e != cudaSuccess) return from_cuda(e);
     }
     if (out->d_count &&

@@ -34,7 +34,8 @@ constexpr size_t OFF_MISC = 0;
 constexpr size_t OFF_INV_A = OFF_MISC + MISC_BYTES;
 constexpr size_t OFF_INV_B = OFF_INV_A + INV_BYTES;
 constexpr size_t OFF_CAND = OFF_INV_B + INV_BYTES;
-constexpr size_t OFF_OPER = OFF_CAND + CAND_BYTES;
+constexpr size_t OFF_BAND = OFF_CAND + CAND_BYTES;  // candidates near eps for the accurate tier
+constexpr size_t OFF_OPER = OFF_BAND + CAND_BYTES;
 constexpr size_t SCRATCH_BYTES = OFF_OPER + OPER_BYTES;
 static_assert(SCRATCH_BYTES == EJOIN_STATIC_SCRATCH_BYTES, "scratch size stated in ejoin.h");
 static_assert(OFF_OPER % 1024 == 0, "operand area alignment for TMA");
@@ -136,6 +137,7 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
     float *invA = reinterpret_cast<float *>(base + OFF_INV_A);
     float *invB = reinterpret_cast<float *>(base + OFF_INV_B);
     uint2 *cand = reinterpret_cast<uint2 *>(base + OFF_CAND);
+    uint2 *band_list = reinterpret_cast<uint2 *>(base + OFF_BAND);
     void *A = base + OFF_OPER;
     void *B = base + OFF_OPER + (size_t)rowsA * kp * 2;
     const float band = [&] {
@@ -162,7 +164,7 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
         return st_of(e);
     if ((e = launch_rescore(cand, &dm->cand_count, EJOIN_STATIC_MAX_CANDIDATES, R.x, R.ld, S.x, S.ld, R.d, nullptr,
                             nullptr, invA, invB, eps, 2e-5f, d_pairs, capacity, &dm->pair_count, &dm->band_count, 0,
-                            ds->num_sms, s)) != cudaSuccess)
+                            ds->num_sms, s, band_list, EJOIN_STATIC_MAX_CANDIDATES)) != cudaSuccess)
         return st_of(e);
     DevMisc hm;
     if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return st_of(e);

@@ -87,8 +87,9 @@ def report(name, w, precs, n_rows=32, n_pairs=200_000, fp64_band=-1.0):
         line = {"workload": name, "prec": prec, "pairs_sampled": int(len(pi)),
                 "bulk_err_max": float(err.max()), "bulk_err_p999": float(np.quantile(err, 0.999)),
                 "band": band, "err_over_band": float(err.max() / band)}
-        # the real kernels with band = 0: what the bulk precision alone gets wrong
-        with pkg.Ctx(device=0, prec=prec, band=0.0, fp64_band=fp64_band) as ctx:
+        # the real kernels with band = 0: what the bulk precision alone gets wrong (a self-join over the
+        # full square, so that candidates and pairs both count ordered pairs)
+        with pkg.Ctx(device=0, prec=prec, band=0.0, fp64_band=fp64_band, flags=pkg.EJOIN_FLAG_NO_SYMMETRY) as ctx:
             res = pkg.ejoin_threshold(ctx, R, S, w.eps, selR)
             st = pkg.ejoin_last_stats(ctx)
             gi, gj = res.i.cpu().numpy().view(np.uint32), res.j.cpu().numpy().view(np.uint32)

@@ -118,6 +118,30 @@ def test_pruning_disabled_equals_plain_join():
     compare(X, S, eps, gi, gj, np.array([sims[(a, b)] for a, b in zip(gi, gj)]), oi, oj, os_)
 
 
+def test_pruned_self_join_equals_plain_join():
+    # self-join: the pruned path lists only tile pairs on or above the block diagonal and mirrors the
+    # pairs; with nothing pruned it must return the plain join's set (every (i, i), both orders)
+    X, flat = _tiny(5, n=2300, d=96, hid=64)
+    X[1200:1500] = X[:300] + np.float32(0.3) * np.random.default_rng(8).standard_normal((300, 96)).astype(np.float32)
+    eps = 0.3
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        sk = E.Sketch(ctx, 96, 64, 64)
+        sk.set_params(L.init_params(96, 64, 64, 5))
+        Xd = torch.from_numpy(X).cuda()
+        res, st = E.ejoin_threshold_pruned(ctx, sk, Xd, Xd, eps, -2.0)
+        got = dict(zip(zip(res.i.cpu().numpy().tolist(), res.j.cpu().numpy().tolist()), res.sim.cpu().numpy().tolist()))
+        plain = pkg.ejoin_threshold(ctx, Xd, Xd, eps)
+        want = set(zip(plain.i.cpu().numpy().tolist(), plain.j.cpu().numpy().tolist()))
+        sk.close()
+    assert len(got) == res.count and set(got) == want
+    assert all((j, i) in got and got[(j, i)] == got[(i, j)] for (i, j) in got)
+    assert all((i, i) in got for i in range(len(X)))
+    oi, oj, os_ = oracle.join(X, X, eps)
+    keys = sorted(got)
+    compare(X, X, eps, np.array([a for a, b in keys], dtype=np.uint32), np.array([b for a, b in keys], dtype=np.uint32),
+            np.array([got[k] for k in keys]), oi, oj, os_)
+
+
 def test_trained_sketch_prunes_with_recall():
     d, eps, theta = 128, 0.8, 0.3
     centres = inputs.sphere_centres(120, d, 1234)  # ~200 rows per cluster, as in the 4M-row workload

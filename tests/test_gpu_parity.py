@@ -307,12 +307,14 @@ def test_symmetric_self_join_equals_full_square(prec, n):
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8", "f32"])
-def test_accurate_tier_matches_fp64(prec):
+@pytest.mark.parametrize("d", [768, 299])
+def test_accurate_tier_matches_fp64(prec, d):
     # fp64_band = 2 sends every candidate through the accurate tier (compensated dot products finished
     # in FP64): its similarities then agree with the FP64 oracle to FP32 rounding of the result
-    # (|err| <= 2^-24 for |sim| <= 1) plus the tier's own bound (< 3e-9 at d = 768)
-    R, S = gauss(70, 700, 768), gauss(71, 900, 768)
-    S[:300] = R[:300] + np.float32(0.35) * gauss(72, 300, 768)
+    # (|err| <= 2^-24 for |sim| <= 1) plus the tier's own bound (< 3e-9 at d = 768); d = 299 takes the
+    # scalar-load variant of the tier
+    R, S = gauss(70, 700, d), gauss(71, 900, d)
+    S[:300] = R[:300] + np.float32(0.35) * gauss(72, 300, d)
     R[:5] *= np.float32(1e-3)  # rows far from unit length
     S[5:10] *= np.float32(1e3)
     eps = 0.2
