@@ -270,3 +270,73 @@ int64_t oracle_count_selected(const int32_t *attr, int32_t op, int32_t c, int64_
     for (int64_t i = 0; i < n; ++i) k += keep_row(attr, op, c, i);
     return k;
 }
+
+/*
+ * The top-1 join condition (Sec. VI-E, "top-k" join predicate with k = 1):
+ * for every kept row i of R, the kept row j of S with the largest similarity,
+ * ties broken towards the smaller j.  Same arithmetic as oracle_join.
+ *
+ *   rows/n_rows  optional ascending list of R rows to evaluate (NULL: all rows)
+ *   out_*        room for one record per evaluated row
+ *
+ * Writes one record (i, j, sim) per kept R row, in ascending i, when S has at
+ * least one kept row; returns the number written, or -1 on allocation failure.
+ */
+int64_t oracle_top1(const float *R, int64_t nR, int64_t ldR,
+                    const float *S, int64_t nS, int64_t ldS, int32_t d,
+                    const int32_t *attrR, int32_t opR, int32_t cR,
+                    const int32_t *attrS, int32_t opS, int32_t cS,
+                    const int64_t *rows, int64_t n_rows,
+                    uint32_t *out_i, uint32_t *out_j, double *out_sim, int32_t n_threads)
+{
+    const int64_t n_eval = rows ? n_rows : nR;
+    if (n_eval <= 0 || nS <= 0) return 0;
+    double *ns = (double *)malloc((size_t)nS * sizeof(double));
+    int64_t *best_j = (int64_t *)malloc((size_t)n_eval * sizeof(int64_t));
+    double *best_s = (double *)malloc((size_t)n_eval * sizeof(double));
+    if (!ns || !best_j || !best_s) {
+        free(ns);
+        free(best_j);
+        free(best_s);
+        return -1;
+    }
+    for (int64_t j = 0; j < nS; ++j) ns[j] = oracle_norm(S + j * ldS, d);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+#endif
+    for (int64_t q = 0; q < n_eval; ++q) {
+        const int64_t i = rows ? rows[q] : q;
+        best_j[q] = -1;
+        best_s[q] = 0.0;
+        if (!keep_row(attrR, opR, cR, i)) continue;
+        const float *r = R + i * ldR;
+        const double nr = oracle_norm(r, d);
+        for (int64_t j = 0; j < nS; ++j) {
+            if (!keep_row(attrS, opS, cS, j)) continue;
+            const double sim = cosine_from(oracle_dot(r, S + j * ldS, d), nr, ns[j]);
+#if ORACLE_MUTANT == 7
+            if (best_j[q] < 0 || sim >= best_s[q]) { /* mutant 7: a tie goes to the larger j */
+#else
+            if (best_j[q] < 0 || sim > best_s[q]) { /* strict: the smaller j keeps a tie */
+#endif
+                best_j[q] = j;
+                best_s[q] = sim;
+            }
+        }
+    }
+    (void)nt;
+    int64_t n_out = 0;
+    for (int64_t q = 0; q < n_eval; ++q) {
+        if (best_j[q] < 0) continue;
+        out_i[n_out] = (uint32_t)(rows ? rows[q] : q);
+        out_j[n_out] = (uint32_t)best_j[q];
+        out_sim[n_out] = best_s[q];
+        ++n_out;
+    }
+    free(ns);
+    free(best_j);
+    free(best_s);
+    return n_out;
+}

@@ -551,6 +551,139 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     return EJOIN_OK;
 }
 
+// Top-1 join condition (Sec. VI-E, top-k with k = 1) on the tensor cores: pass 0 takes every R row's
+// largest bulk similarity, pass 1 keeps the columns within 2 * band of it (the exact argmax among them,
+// since the bulk error is at most band), and the FP32 re-score picks the best of those per row.
+ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, const ejoin_sel *selR,
+                      const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
+                      uint64_t *count_out)
+{
+    c->stats = ejoin_stats{};
+    if (!rel_ok(R) || !rel_ok(S) || R.d != S.d || !sel_ok(selR) || !sel_ok(selS)) return EJOIN_EINVAL;
+    const int prec = c->prec;
+    if (prec == EJOIN_F32) return EJOIN_EUNSUPPORTED;
+    const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
+    const int fmt = fmt_of(prec);
+    const int64_t kp = ejoin_padded_dim(prec, R.d);
+    const size_t eb = fmt_bytes(fmt);
+    const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld && same_sel(selR, selS);
+    const float band = c->band_cfg >= 0.f ? c->band_cfg : default_band(prec, kp);
+    c->stats.band = band;
+    cudaError_t e;
+    const ejoin_rel *rels[2] = {&R, &S};
+    const ejoin_sel *sels[2] = {selR, selS};
+    for (int w = 0; w < (self ? 1 : 2); ++w) {
+        const int64_t rows = round_up(std::max<int64_t>(rels[w]->n, 1), 256);
+        Side &sd = c->side[w];
+        if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) != cudaSuccess) return from_cuda(e);
+        if ((e = ensure(sd.inv, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+        if (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+        if (sels[w] && (e = ensure(sd.ids, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+    }
+    const int64_t rowsA = round_up(std::max<int64_t>(R.n, 1), 256);
+    const int64_t rowsB = round_up(std::max<int64_t>(S.n, 1), 256);
+    if ((e = ensure(c->top, (size_t)rowsA * 12)) != cudaSuccess) return from_cuda(e);
+    unsigned long long *best = (unsigned long long *)c->top.p;
+    unsigned *row_best = (unsigned *)(best + rowsA);
+    if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
+    if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), c->stream)) != cudaSuccess) return from_cuda(e);
+    if ((e = cudaMemsetAsync(c->top.p, 0, (size_t)rowsA * 12, c->stream)) != cudaSuccess) return from_cuda(e);
+
+    if (timing) cudaEventRecord(c->ev[0], c->stream);
+    Side &sa = c->side[0];
+    Side &sb = self ? c->side[0] : c->side[1];
+    // e4m3: both operands' scales shared per 256-row tile (S's fold into the epilogue threshold)
+    ejoin_status st = prepare_side(c, 0, R, selR, fmt, kp, sa.norm.p, kp, (float *)sa.inv.p, (float *)sa.scale.p,
+                                   (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false, self ? 256 : 0);
+    if (st != EJOIN_OK) return st;
+    if (!self) {
+        st = prepare_side(c, 1, S, selS, fmt, kp, sb.norm.p, kp, (float *)sb.inv.p, (float *)sb.scale.p,
+                          (uint32_t *)sb.ids.p, &dm->n_sel[1], &dm->status, false, 256);
+        if (st != EJOIN_OK) return st;
+    }
+    const long long *nA = &dm->n_sel[0];
+    const long long *nB = self ? &dm->n_sel[0] : &dm->n_sel[1];
+    if (timing) cudaEventRecord(c->ev[1], c->stream);
+
+    CUtensorMap tmA, tmB;
+    if (!make_tmap(&tmA, sa.norm.p, fmt, kp, rowsA, 128) || !make_tmap(&tmB, sb.norm.p, fmt, kp, rowsB, 256))
+        return EJOIN_ECUDA;
+    const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
+    const int gm = c->group_m > 0 ? c->group_m : default_group_m(kp);
+    const float margin = 2.f * band;
+    e = launch_sim_tc_top(kind, 0, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p, (const float *)sb.scale.p,
+                          row_best, margin, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status, c->timeout,
+                          c->num_sms, gm, c->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    auto pass1 = [&]() -> cudaError_t {
+        c->stats.launches += 1;
+        return launch_sim_tc_top(kind, 1, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
+                                 (const float *)sb.scale.p, row_best, margin, (uint2 *)c->cand.p, c->cand_cap,
+                                 &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
+    };
+    c->stats.launches += 1;
+    if ((e = pass1()) != cudaSuccess) return from_cuda(e);
+    if (timing) cudaEventRecord(c->ev[2], c->stream);
+    DevMisc hm;
+    auto read_misc = [&]() -> cudaError_t {
+        cudaError_t ee = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream);
+        return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
+    };
+    if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+    c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
+    c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
+    if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+    if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+    if (hm.status) return EJOIN_ECUDA;
+    while (hm.cand_count > c->cand_cap) {
+        // candidate buffer too small: grow it and run pass 1 again (the row maxima stay)
+        c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+        if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+        if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+            return from_cuda(e);
+        if ((e = pass1()) != cudaSuccess) return from_cuda(e);
+        if (timing) cudaEventRecord(c->ev[2], c->stream);
+        if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        if (hm.status) return EJOIN_ECUDA;
+        c->stats.contract_retries++;
+    }
+    c->stats.candidates = hm.cand_count;
+    const uint64_t n_out = c->stats.n_sel_s > 0 ? c->stats.n_sel_r : 0;
+    if (*pairs_io == nullptr && may_alloc && n_out > 0) {
+        void *p = nullptr;
+        if ((e = cudaMalloc(&p, n_out * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
+        *pairs_io = (ejoin_pair *)p;
+        *cap_io = n_out;
+    }
+    if (*pairs_io == nullptr) *cap_io = 0;
+    if (hm.cand_count > 0) {
+        e = launch_top1_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
+                                selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
+                                (const float *)sa.inv.p, (const float *)sb.inv.p, best, c->num_sms, c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        e = launch_top1_emit(best, nA, rowsA, selR ? (const uint32_t *)sa.ids.p : nullptr, *pairs_io, *cap_io,
+                             &dm->pair_count, c->num_sms, c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        c->stats.launches += 2;
+    }
+    if (timing) cudaEventRecord(c->ev[3], c->stream);
+    if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+    if (hm.pair_count) return EJOIN_ECUDA;  // a kept row without a best pair
+    c->stats.pairs = n_out;
+    if (timing) {
+        c->stats.ms_normalize = elapsed(c->ev[0], c->ev[1]);
+        c->stats.ms_contract = elapsed(c->ev[1], c->ev[2]);
+        c->stats.ms_rescore = elapsed(c->ev[2], c->ev[3]);
+        c->stats.ms_total = elapsed(c->ev[0], c->ev[3]);
+    }
+    *count_out = n_out;
+    if (n_out > *cap_io) return EJOIN_EOVERFLOW;
+    return EJOIN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -570,6 +703,30 @@ ejoin_status ejoin_threshold(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float eps, 
         out->capacity = cap;
     }
     out->count = count;
+    return st;
+}
+
+ejoin_status ejoin_top1(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, const ejoin_sel *selR, const ejoin_sel *selS,
+                        ejoin_pairs *out)
+{
+    if (!c || !out) return EJOIN_EINVAL;
+    DeviceGuard g(c->device);
+    uint64_t count = 0;
+    ejoin_pair *p = out->d_pairs;
+    uint64_t cap = out->capacity;
+    const bool alloc = p == nullptr;
+    ejoin_status st = run_top1(c, R, S, selR, selS, &p, &cap, alloc, &count);
+    if (alloc && p) {
+        out->d_pairs = p;
+        out->capacity = cap;
+    }
+    out->count = count;
+    if (out->d_count && (st == EJOIN_OK || st == EJOIN_EOVERFLOW)) {
+        const uint64_t cnt = count;
+        if (cudaMemcpyAsync(out->d_count, &cnt, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return EJOIN_ECUDA;
+    }
     return st;
 }
 

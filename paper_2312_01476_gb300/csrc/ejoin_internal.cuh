@@ -57,7 +57,36 @@ struct BatchTables {
     // tile-list mode of a self-join listing only block pairs on and above the diagonal of 256-row
     // blocks: inside a diagonal block (row tile m, column tile n, m / 2 == n) keep col >= row
     int sym;
+    // top-1 passes: per operand row of A, the largest bulk similarity (order-preserving bits,
+    // f2ord), and the margin below it that the candidate pass keeps
+    unsigned *row_best;
+    float top_margin;
 };
+
+// Order-preserving map of floats to unsigned integers (and back): a < b iff f2ord(a) < f2ord(b)
+// for non-NaN a, b; 0 lies below the image of every float.
+__host__ __device__ __forceinline__ unsigned f2ord(float f)
+{
+#if defined(__CUDA_ARCH__)
+    const unsigned u = __float_as_uint(f);
+#else
+    unsigned u;
+    __builtin_memcpy(&u, &f, 4);
+#endif
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__host__ __device__ __forceinline__ float ord2f(unsigned o)
+{
+    const unsigned u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+#if defined(__CUDA_ARCH__)
+    return __uint_as_float(u);
+#else
+    float f;
+    __builtin_memcpy(&f, &u, 4);
+    return f;
+#endif
+}
 
 // Per-job row sources of a batched re-score (device arrays).
 struct BatchRows {
@@ -133,6 +162,14 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
                               float thr, const float *scale, uint2 *cand, uint64_t cap,
                               unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only,
                               int grid, int group_m, cudaStream_t st);
+// Top-1 passes of the contraction (single join): pass 0 records in row_best[r] the largest bulk
+// similarity of operand row r of A (atomicMax on f2ord; row_best zeroed by the caller); pass 1
+// emits the candidates (r, c) with bulk similarity >= ord2f(row_best[r]) - margin.
+cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                              const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
+                              unsigned *row_best, float margin, uint2 *cand, uint64_t cap,
+                              unsigned long long *cand_count, unsigned *status, uint64_t timeout, int grid,
+                              int group_m, cudaStream_t st);
 // Contraction with the exact re-score fused in (extra warps consume the candidates from a
 // shared-memory ring and write final pairs).  Needs 16-byte aligned rows, ld % 4 == 0 and
 // d % 4 == 0.
@@ -170,6 +207,16 @@ inline int default_group_m(int64_t kp)
     return (int)g;
 }
 size_t sim_tc_smem_bytes();
+// Top-1: best[r] = max over the candidates (r, c) of (f2ord(FP32 sim) << 32 | ~original j) (best
+// zeroed by the caller); then out[r] = (i, j, sim) for every operand row r of A (rows without a
+// best are counted in *missing).
+cudaError_t launch_top1_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
+                                const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *best,
+                                int num_sms, cudaStream_t st);
+cudaError_t launch_top1_emit(const unsigned long long *best, const long long *nA_dev, int64_t nA_max,
+                             const uint32_t *idsR, ejoin_pair *out, uint64_t out_cap, unsigned long long *missing,
+                             int num_sms, cudaStream_t st);
 // Candidates: cand[0 .. min(*cand_count, cand_cap)).  Candidates whose FP32 similarity
 // lies within fp64_band of eps are listed in band_list (capacity band_cap >= cand_cap,
 // counted in *band_count) and decided by a second kernel, the accurate tier.  mirror: the

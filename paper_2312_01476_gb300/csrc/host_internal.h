@@ -69,6 +69,7 @@ struct ejoin_ctx {
     ej::host::Buf cand;
     uint64_t cand_cap = 0;
     ej::host::Buf band;  // candidates near eps for the accurate tier (as many slots as candidates)
+    ej::host::Buf top;   // top-1: per operand row, the pass-0 maximum (u32) and the exact best (u64)
     ej::host::Buf host_in[6];
     ej::host::Buf host_pairs;
     cudaEvent_t ev[ej::host::N_EV] = {};

@@ -128,7 +128,12 @@ struct TileInfo {
     bool diag;  // MODE_SYM: a tile of a diagonal block (keep col >= row only)
 };
 
-enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3, MODE_SYM = 4 };
+enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3, MODE_SYM = 4, MODE_TOPMAX = 5,
+             MODE_TOPCAND = 6 };
+// MODE_TOPMAX / MODE_TOPCAND: the two contraction passes of the top-1 join condition (Sec. VI-E,
+// top-k with k = 1), tiled like MODE_SINGLE.  TOPMAX keeps, per row of A, the largest bulk
+// similarity over the valid columns (no candidates); TOPCAND emits the candidates within a margin
+// of that row maximum.
 
 // MODE_SYM (self-join, R == S): only the block pairs (I, J), I <= J, of
 // 256-row blocks are contracted, each as its two 128-row tiles (2I, J) and
@@ -601,15 +606,25 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             // e4m3: similarity = acc * s_row * s_col.  In the single and self-join modes the rows of a
             // 256-row column tile share one scale (launch_normalize_fp8_grouped), so the two scales fold
             // into a per-lane threshold on the raw accumulator; the other modes scale every element
-            constexpr bool TILE_SCALE = KIND == 1 && (MODE == MODE_SINGLE || MODE == MODE_SYM);
+            constexpr bool TILE_SCALE = KIND == 1 && (MODE == MODE_SINGLE || MODE == MODE_SYM ||
+                                                      MODE == MODE_TOPMAX || MODE == MODE_TOPCAND);
+            float sc_tile = 1.f;  // s_row * s_col of the e4m3 tile (TILE_SCALE)
             float rs = 1.f;
             float thr_lane = thr_t;
             float csc[EPI_CHUNKS];
 #pragma unroll
             for (int c = 0; c < EPI_CHUNKS; ++c) csc[c] = 1.f;
+            float thr_base = thr_t;
+            if constexpr (MODE == MODE_TOPCAND) {
+                // this row's best bulk similarity (pass 0) less the margin
+                thr_base = row_ok ? ord2f(__ldcg(bt.row_best + row)) - bt.top_margin : INFINITY;
+                thr_lane = thr_base;
+            }
+            float lane_max = -INFINITY;  // MODE_TOPMAX
             if constexpr (TILE_SCALE) {
                 const float sc = row_ok ? scaleA[row] * __ldg(scaleB + ti.rowB) : 0.f;
-                thr_lane = sc > 0.f ? __fdiv_rn(thr_t, sc) : (thr_t <= 0.f ? -INFINITY : INFINITY);
+                sc_tile = sc;
+                thr_lane = sc > 0.f ? __fdiv_rn(thr_base, sc) : (thr_base <= 0.f ? -INFINITY : INFINITY);
             } else if constexpr (KIND == 1) {
                 rs = row_ok ? scaleA[row] : 0.f;
 #pragma unroll
@@ -640,6 +655,17 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                     for (int g = 0; g < 4; ++g) a8[g] = fmaxf(u[2 * g], u[2 * g + 1]);
                 }
                 const float mx = fmaxf(fmaxf(a8[0], a8[1]), fmaxf(a8[2], a8[3]));
+                if constexpr (MODE == MODE_TOPMAX) {
+                    // the row maximum over the valid columns only (padding columns hold zeros)
+                    if (left >= 32) {
+                        lane_max = fmaxf(lane_max, mx);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            if (k < left) lane_max = fmaxf(lane_max, f[k]);
+                    }
+                    return;
+                }
                 if (!__any_sync(0xffffffffu, row_ok && mx >= thr_lane)) return;
                 // slow path: per-lane match mask, built only for 8-column groups that hold a match
                 unsigned mask = 0u;
@@ -762,6 +788,10 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                         tmem_wait_ld_regs(vb);
                 }
             }
+            if constexpr (MODE == MODE_TOPMAX) {
+                if (row_ok && lane_max > -INFINITY)
+                    atomicMax(bt.row_best + row, f2ord(TILE_SCALE ? lane_max * sc_tile : lane_max));
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(acc));
@@ -862,6 +892,35 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
                                        count_only, grid, group_m, none, st);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
+                              const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
+                              unsigned *row_best, float margin, uint2 *cand, uint64_t cap,
+                              unsigned long long *cand_count, unsigned *status, uint64_t timeout, int grid,
+                              int group_m, cudaStream_t st)
+{
+    BatchTables bt{};
+    bt.row_best = row_best;
+    bt.top_margin = margin;
+#define EJ_TOP(K, M)                                                                                                  \
+    launch_one<K, M>(tmA, tmB, kp, nA, nB, 0.f, scaleA, scaleB, cand, cap, cand_count, status, timeout, 0, grid,      \
+                     group_m, bt, st)
+    if (pass == 0) {
+        switch (kind) {
+        case 0: return EJ_TOP(0, MODE_TOPMAX);
+        case 1: return EJ_TOP(1, MODE_TOPMAX);
+        case 2: return EJ_TOP(2, MODE_TOPMAX);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (kind) {
+    case 0: return EJ_TOP(0, MODE_TOPCAND);
+    case 1: return EJ_TOP(1, MODE_TOPCAND);
+    case 2: return EJ_TOP(2, MODE_TOPCAND);
+    default: return cudaErrorInvalidValue;
+    }
+#undef EJ_TOP
 }
 
 cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,

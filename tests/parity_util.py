@@ -51,3 +51,36 @@ def compare(R, S, eps, gi, gj, gs, oi, oj, os_, band=1e-5, tol=1e-5, rows=None):
         in_band += len(only_o)
     return {"common": int(len(common)), "max_err": float(err.max()) if err.size else 0.0,
             "band_diffs": int(in_band)}
+
+
+def compare_top1(R, S, gi, gj, gs, oi, oj, os_, tol=1e-5, rows=None):
+    """Check a GPU top-1 result (gi, gj, gs) against the oracle's (oi, oj, os_).
+
+    The rows that get a record must be exactly the oracle's, in ascending order.
+    Per row, the GPU's choice j must be a best pair within ``tol``: its FP64
+    similarity is at least the oracle's maximum less ``tol`` (so where the best
+    and the second best differ by more than ``tol`` it is the oracle's j), and
+    the reported similarity is within ``tol`` of that FP64 value.  ``rows``:
+    the R rows the oracle evaluated (the GPU records of other rows are
+    ignored).  Returns a dict of statistics."""
+    gi = np.asarray(gi, dtype=np.int64)
+    gj = np.asarray(gj, dtype=np.int64)
+    gs = np.asarray(gs, dtype=np.float64)
+    assert np.all(np.diff(gi) > 0), "top-1 records are not in strictly ascending i"
+    if rows is not None:
+        keep = np.isin(gi, np.asarray(rows, dtype=np.int64))
+        gi, gj, gs = gi[keep], gj[keep], gs[keep]
+    oi = np.asarray(oi, dtype=np.int64)
+    assert np.array_equal(gi, oi), f"rows with a record differ: {len(gi)} GPU vs {len(oi)} oracle"
+    if len(gi) == 0:
+        return {"rows": 0, "same_j": 0, "max_gap": 0.0, "max_err": 0.0}
+    assert gj.max() < S.shape[0], "j out of range"
+    s = oracle.sim_pairs(R, S, gi.astype(np.uint32), gj.astype(np.uint32))
+    gap = np.asarray(os_, dtype=np.float64) - s
+    bad = gap > tol
+    assert not bad.any(), f"{bad.sum()} rows chose a j more than {tol} below the best: rows {gi[bad][:5]} " \
+                          f"gap {gap[bad][:5]}"
+    err = np.abs(gs - s)
+    assert err.max() <= tol, f"sim error {err.max():.3g} > {tol}"
+    return {"rows": int(len(gi)), "same_j": int((gj == np.asarray(oj, dtype=np.int64)).sum()),
+            "max_gap": float(max(gap.max(), 0.0)), "max_err": float(err.max())}

@@ -311,10 +311,61 @@ def _pins_pass(mutant: int) -> bool:
         return False
 
 
+def _top1_pins_pass(mutant: int) -> bool:
+    """Top-1: exact argmax (rational arithmetic) on small integer rows, with ties to the smaller j."""
+    try:
+        rng = np.random.default_rng(31)
+        for trial in range(4):
+            R = _rand_rel(rng, 9, 4, "int")
+            S = _rand_rel(rng, 13, 4, "int")
+            S[7] = S[2]  # an exact tie: j = 2 must win over j = 7 wherever S[2] is the best
+            oi, oj, os_ = oracle.top1(R, S, mutant=mutant)
+            for i, j, sv in zip(oi.tolist(), oj.tolist(), os_.tolist()):
+                sims = [exact_sim(R[i], S[k]) for k in range(len(S))]
+                best = max(sims)
+                want = min(k for k, v in enumerate(sims) if v == best)
+                if j != want or abs(Decimal(sv) - best) > Decimal("1e-15"):
+                    return False
+        return True
+    except Exception:
+        return False
+
+
 def test_oracle_passes_pins():
     assert _pins_pass(0)
+    assert _top1_pins_pass(0)
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7])
 def test_mutants_are_caught(mutant):
-    assert not _pins_pass(mutant)
+    assert not (_pins_pass(mutant) and _top1_pins_pass(mutant))
+
+
+def test_top1_is_the_best_pair_of_the_threshold_join():
+    # for each R row, the threshold join at eps just below the top-1 similarity holds the top-1 pair
+    # and no pair of larger similarity (Sec. VI-E: the top-k and range conditions on the same product)
+    rng = np.random.default_rng(41)
+    R, S = _rand_rel(rng, 40, 23), _rand_rel(rng, 60, 23)
+    oi, oj, os_ = oracle.top1(R, S)
+    assert list(oi) == list(range(40))
+    for i, j, sv in zip(oi.tolist(), oj.tolist(), os_.tolist()):
+        eps = float(np.nextafter(np.float32(sv), np.float32(-2)))
+        ji, jj, js = oracle.join(R[i:i + 1], S, eps)
+        assert j in set(jj.tolist()) and js.max() <= sv
+
+
+def test_top1_selection_and_permutation():
+    rng = np.random.default_rng(43)
+    R, S = _rand_rel(rng, 30, 17), _rand_rel(rng, 50, 17)
+    aR, aS = rng.integers(0, 10, 30).astype(np.int32), rng.integers(0, 10, 50).astype(np.int32)
+    oi, oj, os_ = oracle.top1(R, S, oracle.Selection(aR, "<", 6), oracle.Selection(aS, ">=", 3))
+    keepS = np.nonzero(aS >= 3)[0]
+    fi, fj, fs = oracle.top1(R, S[keepS])
+    want = {i: (keepS[j], v) for i, j, v in zip(fi.tolist(), fj.tolist(), fs.tolist()) if aR[i] < 6}
+    assert set(oi.tolist()) == set(want)
+    for i, j, v in zip(oi.tolist(), oj.tolist(), os_.tolist()):
+        assert j == want[i][0] and v == want[i][1]
+    perm = rng.permutation(50)
+    pi, pj, ps = oracle.top1(R, S[perm])
+    base = oracle.top1(R, S)
+    assert np.array_equal(perm[pj], base[1]) and np.array_equal(ps, base[2])
