@@ -82,6 +82,12 @@ def _load(mutant: int = 0):
                                     i32p, ctypes.c_int32, ctypes.c_int32,
                                     i32p, ctypes.c_int32, ctypes.c_int32,
                                     i64p, ctypes.c_int64, u32p, u32p, f64p, ctypes.c_int32]
+        lib.oracle_topk.restype = ctypes.c_int64
+        lib.oracle_topk.argtypes = [f32p, ctypes.c_int64, ctypes.c_int64,
+                                    f32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                    i32p, ctypes.c_int32, ctypes.c_int32,
+                                    i32p, ctypes.c_int32, ctypes.c_int32,
+                                    i64p, ctypes.c_int64, u32p, u32p, f64p, ctypes.c_int32]
         lib.oracle_count_selected.restype = ctypes.c_int64
         lib.oracle_count_selected.argtypes = [i32p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
         _libs[mutant] = lib
@@ -192,6 +198,43 @@ def top1(R: np.ndarray, S: np.ndarray, selR: Optional[Selection] = None, selS: O
                         int(threads))
     if n < 0:
         raise MemoryError("oracle_top1: allocation failed")
+    return oi[:n].copy(), oj[:n].copy(), os_[:n].copy()
+
+
+def topk(R: np.ndarray, S: np.ndarray, k: int, selR: Optional[Selection] = None,
+         selS: Optional[Selection] = None, rows: Optional[Sequence[int]] = None, threads: int = 0,
+         mutant: int = 0):
+    """Top-k join condition (Sec. VI-E): for every kept R row i, the min(k, kept S rows) kept S rows of
+    largest similarity, in descending similarity (ties: the smaller j).  Returns (i, j, sim) arrays with
+    each row's records consecutive, rows in ascending i."""
+    lib = _load(mutant)
+    R = _rows_f32(R)
+    S = _rows_f32(S)
+    if R.shape[1] != S.shape[1]:
+        raise ValueError("R and S must have the same dimension")
+    if k <= 0 or R.shape[0] == 0 or S.shape[0] == 0:
+        return np.zeros(0, np.uint32), np.zeros(0, np.uint32), np.zeros(0, np.float64)
+    rows_arr = None
+    if rows is not None:
+        rows_arr = np.ascontiguousarray(np.sort(np.asarray(rows, dtype=np.int64)))
+    n_eval = R.shape[0] if rows_arr is None else len(rows_arr)
+    args_sel = []
+    for sel in (selR, selS):
+        if sel is None:
+            args_sel += [_ptr(None, ctypes.c_int32), 0, 0]
+        else:
+            args_sel += [_ptr(sel.attr, ctypes.c_int32), sel.op, sel.c]
+    cap = max(n_eval * int(k), 1)
+    oi = np.empty(cap, dtype=np.uint32)
+    oj = np.empty(cap, dtype=np.uint32)
+    os_ = np.empty(cap, dtype=np.float64)
+    n = lib.oracle_topk(_ptr(R, ctypes.c_float), R.shape[0], R.strides[0] // 4,
+                        _ptr(S, ctypes.c_float), S.shape[0], S.strides[0] // 4, R.shape[1], int(k),
+                        *args_sel, _ptr(rows_arr, ctypes.c_int64), 0 if rows_arr is None else len(rows_arr),
+                        _ptr(oi, ctypes.c_uint32), _ptr(oj, ctypes.c_uint32), _ptr(os_, ctypes.c_double),
+                        int(threads))
+    if n < 0:
+        raise MemoryError("oracle_topk: allocation failed")
     return oi[:n].copy(), oj[:n].copy(), os_[:n].copy()
 
 

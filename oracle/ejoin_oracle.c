@@ -340,3 +340,92 @@ int64_t oracle_top1(const float *R, int64_t nR, int64_t ldR,
     free(best_s);
     return n_out;
 }
+
+/*
+ * The top-k join condition (Sec. VI-E, "top-k" join predicate; the paper's
+ * figures use k = 1 and k = 32): for every kept row i of R, the min(k, kept S
+ * rows) kept rows j of S of largest similarity, in descending similarity, ties
+ * broken towards the smaller j.  Same arithmetic as oracle_join.
+ *
+ *   rows/n_rows  optional ascending list of R rows to evaluate (NULL: all rows)
+ *   out_*        room for k records per evaluated row
+ *
+ * Writes the records of each kept R row consecutively, rows in ascending i;
+ * returns the number written, or -1 on allocation failure.  Each row keeps its
+ * list sorted by (sim descending, j ascending): S rows are visited in
+ * ascending j and a new row enters only if its similarity is strictly larger
+ * than that of the list entry it passes, so an earlier j stays ahead on ties.
+ */
+int64_t oracle_topk(const float *R, int64_t nR, int64_t ldR,
+                    const float *S, int64_t nS, int64_t ldS, int32_t d, int32_t k,
+                    const int32_t *attrR, int32_t opR, int32_t cR,
+                    const int32_t *attrS, int32_t opS, int32_t cS,
+                    const int64_t *rows, int64_t n_rows,
+                    uint32_t *out_i, uint32_t *out_j, double *out_sim, int32_t n_threads)
+{
+    const int64_t n_eval = rows ? n_rows : nR;
+    if (n_eval <= 0 || nS <= 0 || k <= 0) return 0;
+    double *ns = (double *)malloc((size_t)nS * sizeof(double));
+    int64_t *list_j = (int64_t *)malloc((size_t)n_eval * k * sizeof(int64_t));
+    double *list_s = (double *)malloc((size_t)n_eval * k * sizeof(double));
+    int64_t *list_n = (int64_t *)malloc((size_t)n_eval * sizeof(int64_t));
+    if (!ns || !list_j || !list_s || !list_n) {
+        free(ns);
+        free(list_j);
+        free(list_s);
+        free(list_n);
+        return -1;
+    }
+    for (int64_t j = 0; j < nS; ++j) ns[j] = oracle_norm(S + j * ldS, d);
+    int nt = 1;
+#ifdef _OPENMP
+    nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 4)
+#endif
+    for (int64_t q = 0; q < n_eval; ++q) {
+        const int64_t i = rows ? rows[q] : q;
+        int64_t *lj = list_j + q * k;
+        double *ls = list_s + q * k;
+        int64_t n = 0;
+        list_n[q] = 0;
+        if (!keep_row(attrR, opR, cR, i)) continue;
+        const float *r = R + i * ldR;
+        const double nr = oracle_norm(r, d);
+        for (int64_t j = 0; j < nS; ++j) {
+            if (!keep_row(attrS, opS, cS, j)) continue;
+            const double sim = cosine_from(oracle_dot(r, S + j * ldS, d), nr, ns[j]);
+            /* position p: the first entry that sim beats */
+            int64_t p = n;
+#if ORACLE_MUTANT == 8
+            while (p > 0 && sim >= ls[p - 1]) --p; /* mutant 8: a tie goes to the larger j */
+#else
+            while (p > 0 && sim > ls[p - 1]) --p;
+#endif
+            if (p >= k) continue;
+            const int64_t last = n < k ? n : k - 1; /* entries p .. last-1 move down by one */
+            for (int64_t t = last; t > p; --t) {
+                lj[t] = lj[t - 1];
+                ls[t] = ls[t - 1];
+            }
+            lj[p] = j;
+            ls[p] = sim;
+            if (n < k) ++n;
+        }
+        list_n[q] = n;
+    }
+    (void)nt;
+    int64_t n_out = 0;
+    for (int64_t q = 0; q < n_eval; ++q) {
+        for (int64_t t = 0; t < list_n[q]; ++t) {
+            out_i[n_out] = (uint32_t)(rows ? rows[q] : q);
+            out_j[n_out] = (uint32_t)list_j[q * k + t];
+            out_sim[n_out] = list_s[q * k + t];
+            ++n_out;
+        }
+    }
+    free(ns);
+    free(list_j);
+    free(list_s);
+    free(list_n);
+    return n_out;
+}

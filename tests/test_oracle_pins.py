@@ -331,14 +331,87 @@ def _top1_pins_pass(mutant: int) -> bool:
         return False
 
 
+def _topk_pins_pass(mutant: int) -> bool:
+    """Top-k: each row's list holds min(k, |S|) distinct rows whose exact (rational) similarities are the
+    k largest, in descending order; a row left out that ties exactly with a listed one has the larger j."""
+    try:
+        rng = np.random.default_rng(37)
+        for trial in range(4):
+            R = _rand_rel(rng, 7, 4, "int")
+            S = _rand_rel(rng, 15, 4, "int")
+            S[9] = S[3]  # exact duplicates: equal similarities in any arithmetic
+            S[12] = S[3]
+            S[14] = S[5]
+            for k in (1, 2, 3, 5, 15, 17):
+                oi, oj, os_ = oracle.topk(R, S, k, mutant=mutant)
+                kk = min(k, len(S))
+                if list(oi) != [i for i in range(len(R)) for _ in range(kk)]:
+                    return False
+                for i in range(len(R)):
+                    js = oj[i * kk:(i + 1) * kk].tolist()
+                    ss = os_[i * kk:(i + 1) * kk].tolist()
+                    ex = [exact_sim(R[i], S[j]) for j in range(len(S))]
+                    top = sorted(ex, reverse=True)[:kk]
+                    if len(set(js)) != kk:
+                        return False
+                    for t, (j, v) in enumerate(zip(js, ss)):
+                        if abs(Decimal(v) - ex[j]) > Decimal("1e-15") or abs(ex[j] - top[t]) > Decimal("1e-15"):
+                            return False
+                        if t and (v > ss[t - 1] or (v == ss[t - 1] and j < js[t - 1])):
+                            return False
+                    for j in set(range(len(S))) - set(js):
+                        if any(np.array_equal(S[j], S[jj]) and jj > j for jj in js):
+                            return False
+        return True
+    except Exception:
+        return False
+
+
 def test_oracle_passes_pins():
     assert _pins_pass(0)
     assert _top1_pins_pass(0)
+    assert _topk_pins_pass(0)
 
 
-@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5, 6, 7, 8])
 def test_mutants_are_caught(mutant):
-    assert not (_pins_pass(mutant) and _top1_pins_pass(mutant))
+    assert not (_pins_pass(mutant) and _top1_pins_pass(mutant) and _topk_pins_pass(mutant))
+
+
+def test_topk_agrees_with_top1_and_the_threshold_join():
+    # k = 1 is the top-1 condition; each row's k records are the threshold join at eps just below its
+    # k-th similarity, whenever the k-th and (k+1)-th similarities differ (Sec. VI-E: the top-k and range
+    # conditions on the same product)
+    rng = np.random.default_rng(47)
+    R, S = _rand_rel(rng, 30, 19), _rand_rel(rng, 70, 19)
+    a, b = oracle.topk(R, S, 1), oracle.top1(R, S)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    k = 6
+    oi, oj, os_ = oracle.topk(R, S, k)
+    assert len(oi) == 30 * k
+    for i in range(30):
+        sims = os_[i * k:(i + 1) * k]
+        eps = float(np.nextafter(np.float32(sims[-1]), np.float32(-2)))
+        ji, jj, js = oracle.join(R[i:i + 1], S, eps)
+        assert set(oj[i * k:(i + 1) * k].tolist()) <= set(jj.tolist())
+        assert len(jj) >= k and np.all(np.diff(sims) <= 0)
+
+
+def test_topk_selection_and_short_relations():
+    rng = np.random.default_rng(53)
+    R, S = _rand_rel(rng, 25, 11), _rand_rel(rng, 40, 11)
+    aR, aS = rng.integers(0, 10, 25).astype(np.int32), rng.integers(0, 10, 40).astype(np.int32)
+    oi, oj, os_ = oracle.topk(R, S, 4, oracle.Selection(aR, ">=", 5), oracle.Selection(aS, "<", 2))
+    keepS = np.nonzero(aS < 2)[0]
+    kk = min(4, len(keepS))
+    fi, fj, fs = oracle.topk(R, S[keepS], 4)
+    want_rows = np.nonzero(aR >= 5)[0]
+    assert np.array_equal(oi, np.repeat(want_rows, kk).astype(np.uint32))
+    sel = np.isin(fi, want_rows)
+    assert np.array_equal(oj, keepS[fj[sel]]) and np.array_equal(os_, fs[sel])
+    # k larger than S: every kept S row, sorted
+    oi, oj, os_ = oracle.topk(R[:3], S[:5], 9)
+    assert len(oi) == 15 and all(sorted(oj[t * 5:(t + 1) * 5].tolist()) == list(range(5)) for t in range(3))
 
 
 def test_top1_is_the_best_pair_of_the_threshold_join():
