@@ -31,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "E-join pair comparisons/sec at exact-set match vs FP64; % of tensor peak"
-METRIC_TOP1 = "top-1 join pair comparisons/sec (argmax within 1e-5 of FP64); % of tensor peak"
+METRIC_TOPK = "top-k join pair comparisons/sec (top k within 1e-5 of FP64); % of tensor peak"
 UNIT = "pairs/s"
 CONTRACT_SOURCES = ["sim_tc.cu", "sim_simt.cu", "ejoin_internal.cuh"]
 
@@ -143,10 +143,10 @@ def make_workload(args, seed_offset=0):
         w = inputs.c3_clustered_selfjoin(threads=os.cpu_count() or 8)
     elif args.workload == "c3-capture":
         w = inputs.c3_clustered_selfjoin(n=200_000, threads=os.cpu_count() or 8)
-    elif args.workload == "top1":
-        w = inputs.top1_clustered_selection(sel_c=args.sel_pct, threads=os.cpu_count() or 8)
-    elif args.workload == "top1-capture":
-        w = inputs.top1_clustered_selection(nS=300_000, sel_c=args.sel_pct, threads=os.cpu_count() or 8)
+    elif args.workload in ("top1", "top32"):
+        w = inputs.topk_clustered_selection(sel_c=args.sel_pct, threads=os.cpu_count() or 8)
+    elif args.workload in ("top1-capture", "top32-capture"):
+        w = inputs.topk_clustered_selection(nS=300_000, sel_c=args.sel_pct, threads=os.cpu_count() or 8)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
     return w
@@ -176,24 +176,28 @@ def cpu_oracle_sample(w, target_s: float, threads: int):
             "seconds": round(dt, 3)}
 
 
-def cpu_oracle_top1_sample(w, target_s: float, threads: int):
-    """Time the FP64 oracle's top-1 on R rows x all kept S rows, about target_s seconds of work."""
+def topk_of(workload: str) -> int:
+    return 32 if workload.startswith("top32") else 1
+
+
+def cpu_oracle_topk_sample(w, k: int, target_s: float, threads: int):
+    """Time the FP64 oracle's top-k on R rows x all kept S rows, about target_s seconds of work."""
     import oracle
     selS = oracle.Selection(w.attrS, w.opS, w.cS) if w.attrS is not None else None
     n_s = int((w.attrS < w.cS).sum()) if w.attrS is not None else w.S.shape[0]
-    k = 16
+    m = 16
     for _ in range(2):
         t = time.perf_counter()
-        oracle.top1(w.R, w.S, None, selS, rows=np.arange(k), threads=threads)
+        oracle.topk(w.R, w.S, k, None, selS, rows=np.arange(m), threads=threads)
         dt = max(time.perf_counter() - t, 1e-3)
-        k = int(min(w.R.shape[0], max(8, 0.9 * target_s / dt * k)))
+        m = int(min(w.R.shape[0], max(8, 0.9 * target_s / dt * m)))
         if dt > 0.2 * target_s:
             break
     t = time.perf_counter()
-    oracle.top1(w.R, w.S, None, selS, rows=np.arange(k), threads=threads)
+    oracle.topk(w.R, w.S, k, None, selS, rows=np.arange(m), threads=threads)
     dt = time.perf_counter() - t
-    return {"value": k * n_s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"top-1 of {k} R rows over all {n_s} kept S rows (FP64, extrapolated pairs/s)",
+    return {"value": m * n_s / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"top-{k} of {m} R rows over all {n_s} kept S rows (FP64, extrapolated pairs/s)",
             "seconds": round(dt, 3)}
 
 
@@ -202,13 +206,14 @@ def run_reference(args):
     if rank != 0:
         return
     w = make_workload(args)
-    if args.workload.startswith("top1"):
+    if args.workload.startswith("top"):
         threads = os.cpu_count() or 1
-        vals = [cpu_oracle_top1_sample(w, args.ref_step_s, threads) for _ in range(args.warmup + args.steps)]
+        k = topk_of(args.workload)
+        vals = [cpu_oracle_topk_sample(w, k, args.ref_step_s, threads) for _ in range(args.warmup + args.steps)]
         vals = vals[args.warmup:]
         v = statistics.median([r["value"] for r in vals])
         pairs = w.R.shape[0] * int((w.attrS < w.cS).sum())
-        out = {"impl": "reference", "metric": METRIC_TOP1, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        out = {"impl": "reference", "metric": METRIC_TOPK, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": pairs / v * 1e3, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                "config": {"workload": w.name, "pairs_per_step": pairs, "d": int(w.R.shape[1])},
@@ -382,14 +387,15 @@ def tensor_peak(prec, contract_ms):
     return 0.5 * base, f"0.5 x bf16 {kind} ({pk['source']}, nominal tf32/bf16 ratio)"
 
 
-def run_top1(args):
-    """Top-1 join condition: 10,000 query rows against 1,000,000 rows under a pushed-down S predicate;
-    one step = one ejoin_top1 call (selection, normalisation, the two contraction passes, the FP32
-    re-score of the candidates, one record per query)."""
+def run_topk(args):
+    """Top-k join condition (k = 1 or 32): 10,000 query rows against 1,000,000 rows under a pushed-down
+    S predicate; one step = one ejoin_topk call (selection, normalisation, the two contraction passes,
+    the FP32 re-score and per-row selection of the candidates, k records per query)."""
     import torch
     import paper_2312_01476_gb300 as pkg
     if args.prec == "f32":
-        raise SystemExit("top-1 runs on the tensor cores only (bf16, fp8, tf32)")
+        raise SystemExit("top-k runs on the tensor cores only (bf16, fp8, tf32)")
+    k = topk_of(args.workload)
     w = make_workload(args)
     d = int(w.R.shape[1])
     R = torch.from_numpy(w.R).cuda()
@@ -399,7 +405,7 @@ def run_top1(args):
     ctx = pkg.Ctx(device=0, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING, group_m=args.group_m)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
-        res = pkg.ejoin_top1(ctx, R, S, None, selS)
+        res = pkg.ejoin_topk(ctx, R, S, k, None, selS)
     torch.cuda.synchronize()
     st0 = pkg.ejoin_last_stats(ctx)
     pairs = int(st0["n_sel_r"]) * int(st0["n_sel_s"])
@@ -407,11 +413,11 @@ def run_top1(args):
     sampler.start()
     step_ms, cms, stage, launches = [], [], {"normalize": [], "rescore": []}, 0
     torch.cuda.synchronize()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
+    for step in range(args.steps):
+        flush.fill_(step & 0xFF)
         a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        res = pkg.ejoin_top1(ctx, R, S, None, selS)
+        res = pkg.ejoin_topk(ctx, R, S, k, None, selS)
         z.record()
         st = pkg.ejoin_last_stats(ctx)
         cms.append(st["ms_contract"])
@@ -437,30 +443,31 @@ def run_top1(args):
     e2e = None
     if not args.no_e2e:
         Rp, Sp, Ap = (torch.from_numpy(a).pin_memory() for a in (w.R, w.S, w.attrS))
-        out = torch.empty((w.R.shape[0], 3), dtype=torch.int32).pin_memory()
+        out = torch.empty((w.R.shape[0] * k, 3), dtype=torch.int32).pin_memory()
         e_ms = []
-        for k in range(2 + max(3, args.steps // 2)):
-            flush.fill_(k & 0xFF)
+        for step in range(2 + max(3, args.steps // 2)):
+            flush.fill_(step & 0xFF)
             a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             Rd, Sd, Ad = Rp.cuda(non_blocking=True), Sp.cuda(non_blocking=True), Ap.cuda(non_blocking=True)
-            r = pkg.ejoin_top1(ctx, Rd, Sd, None, pkg.Sel(Ad, w.opS, w.cS))
+            r = pkg.ejoin_topk(ctx, Rd, Sd, k, None, pkg.Sel(Ad, w.opS, w.cS))
             n = r.count
             out[:n].copy_(torch.stack([r.i, r.j, r.sim.view(torch.int32)], 1), non_blocking=True)
             z.record()
             z.synchronize()
-            if k >= 2:
+            if step >= 2:
                 e_ms.append(a.elapsed_time(z))
             del Rd, Sd, Ad
         em = statistics.mean(e_ms)
         e2e = {"value": pairs / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(w.R.nbytes + w.S.nbytes +
                                                                                       w.attrS.nbytes),
                "d2h_bytes_per_step": int(n * 12 + 8), "ms_per_step": round(em, 3)}
-    cpu = None if args.no_cpu_baseline else cpu_oracle_top1_sample(w, args.cpu_s, os.cpu_count() or 1)
-    out = {"metric": METRIC_TOP1, "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+    cpu = None if args.no_cpu_baseline else cpu_oracle_topk_sample(w, k, args.cpu_s, os.cpu_count() or 1)
+    out = {"metric": METRIC_TOPK, "value": pairs / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-           "config": {"workload": w.name, "pairs_per_step": pairs, "d": d, "n_sel_r": int(st0["n_sel_r"]),
+           "config": {"workload": w.name + f", k={k}", "k": k, "pairs_per_step": pairs, "d": d,
+                      "n_sel_r": int(st0["n_sel_r"]),
                       "n_sel_s": int(st0["n_sel_s"]), "records": int(res.count),
                       "candidates": int(st0["candidates"]), "band": st0["band"],
                       "l2": "256 MB buffer written between timed steps (untimed)",
@@ -646,9 +653,10 @@ def main():
     ap.add_argument("--impl", default="ejoin", choices=["ejoin", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp8", "tf32", "f32"])
     ap.add_argument("--workload", default="c2",
-                    choices=["c2", "c2-capture", "c1", "c3", "c3-capture", "c4", "c5", "top1", "top1-capture"])
+                    choices=["c2", "c2-capture", "c1", "c3", "c3-capture", "c4", "c5", "top1", "top1-capture",
+                             "top32", "top32-capture"])
     ap.add_argument("--sel-pct", type=int, default=100,
-                    help="top-1 workloads: percent of S kept by the predicate attr < sel-pct")
+                    help="top-k workloads: percent of S kept by the predicate attr < sel-pct")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds of oracle work per reference step")
     ap.add_argument("--group-m", type=int, default=0, help="contraction raster group width (0: auto)")
@@ -664,8 +672,8 @@ def main():
         run_batch(args)
     elif args.workload == "c5":
         run_learned(args)
-    elif args.workload.startswith("top1"):
-        run_top1(args)
+    elif args.workload.startswith("top"):
+        run_topk(args)
     else:
         run_ejoin(args)
 

@@ -199,9 +199,9 @@ def c5_learned(n: int = 4_000_000, d: int = 768, n_clusters: int = 20_000, theta
                     X, X, eps, self_join=True, extra={"train": Xtr, "calib": Xcal})
 
 
-def top1_clustered_selection(nR: int = 10_000, nS: int = 1_000_000, d: int = 300, n_clusters: int = 1000,
+def topk_clustered_selection(nR: int = 10_000, nS: int = 1_000_000, d: int = 300, n_clusters: int = 1000,
                              theta: float = 0.3, sel_c: int = 100, threads: int = 8) -> Workload:
-    """Top-1 workload: nR query rows against nS rows (both clustered as in the c2 recipe), an int32
+    """Top-k workload: nR query rows against nS rows (both clustered as in the c2 recipe), an int32
     attribute column attr ~ U[0, 100) on S and the pushed-down predicate attr < sel_c (sel_c percent of
     S kept; 100 keeps every row but still evaluates the predicate)."""
     seed = seed_for(6)
@@ -209,7 +209,7 @@ def top1_clustered_selection(nR: int = 10_000, nS: int = 1_000_000, d: int = 300
     R = clustered(nR, d, centres, theta, seed + 10, threads)
     S = clustered(nS, d, centres, theta, seed + 20, threads)
     attr = uniform_attr(nS, 100, seed + 30)
-    return Workload("top-1 clustered R=%d S=%d d=%d sel=attr_S<%d" % (nR, nS, d, sel_c), R, S, float("nan"),
+    return Workload("top-k clustered R=%d S=%d d=%d sel=attr_S<%d" % (nR, nS, d, sel_c), R, S, float("nan"),
                     attrS=attr, opS="<", cS=sel_c)
 
 

@@ -137,8 +137,8 @@ typedef struct ejoin_pairs {
 
 typedef struct ejoin_ctx ejoin_ctx;
 
-/* Per-call statistics of the last ejoin_threshold / ejoin_threshold_host / ejoin_top1 call
- * (top-1: candidates = pairs kept by the second pass, pairs = records written). */
+/* Per-call statistics of the last ejoin_threshold / ejoin_threshold_host / ejoin_topk call
+ * (top-k: candidates = pairs kept by the second pass, pairs = records written). */
 typedef struct ejoin_stats {
     uint64_t n_sel_r, n_sel_s;  /* rows kept by the selections */
     uint64_t candidates;        /* pairs at or above eps - band in the bulk precision (a symmetric
@@ -195,17 +195,24 @@ ejoin_status ejoin_threshold_host(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, floa
                                   const ejoin_sel *selR, const ejoin_sel *selS,
                                   ejoin_pair *h_pairs, uint64_t capacity, uint64_t *count);
 
-/* The top-1 join condition (Sec. VI-E, the "top-k" vector join predicate with
- * k = 1): for every row i of R kept by selR, the row j of S kept by selS of
- * largest cosine similarity, ties to the smaller j.  Writes one record
- * (i, j, sim) per kept R row, in ascending i, when S keeps a row (none
- * otherwise).  Device pointers as for ejoin_threshold; out->d_pairs NULL: the
- * library allocates one record per kept R row.  Evaluation: two passes of the
- * tensor-core contraction (each row's largest bulk similarity, then the
- * columns within 2 * band of it, which hold the exact argmax) and an FP32
- * re-score of those candidates; the chosen j's similarity is within 1e-5 of
- * the row's FP64 maximum and sim is its FP32 cosine.  ctx must use BF16, e4m3
- * or TF32 (F32: EJOIN_EUNSUPPORTED).  Synchronises.  EOVERFLOW as above. */
+/* The top-k join condition (Sec. VI-E, the "top-k" vector join predicate; the
+ * paper evaluates k = 1 and k = 32), 1 <= k <= 32: for every row i of R kept
+ * by selR, the kk = min(k, kept S rows) rows j of S kept by selS of largest
+ * cosine similarity, in descending similarity, ties to the smaller j.  Writes
+ * kk records (i, j, sim) per kept R row, the rows in ascending i, each row's
+ * records consecutive (record t of the r-th kept row at r * kk + t).  Device
+ * pointers as for ejoin_threshold; out->d_pairs NULL: the library allocates
+ * kk records per kept R row.  Evaluation: two passes of the tensor-core
+ * contraction (per row, a lower bound of its k-th largest bulk similarity,
+ * then every column within 2 * band of it, which holds the exact top k) and
+ * an FP32 re-score of those candidates; the t-th record's FP64 similarity is
+ * within 1e-5 of the row's t-th largest, and sim is its FP32 cosine.  ctx
+ * must use BF16, e4m3 or TF32 (F32: EJOIN_EUNSUPPORTED); k outside [1, 32]:
+ * EJOIN_EINVAL.  Synchronises.  EOVERFLOW as above. */
+ejoin_status ejoin_topk(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, int32_t k, const ejoin_sel *selR,
+                        const ejoin_sel *selS, ejoin_pairs *out);
+
+/* ejoin_topk with k = 1: one record per kept R row. */
 ejoin_status ejoin_top1(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, const ejoin_sel *selR,
                         const ejoin_sel *selS, ejoin_pairs *out);
 

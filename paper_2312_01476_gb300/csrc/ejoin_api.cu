@@ -551,15 +551,18 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     return EJOIN_OK;
 }
 
-// Top-1 join condition (Sec. VI-E, top-k with k = 1) on the tensor cores: pass 0 takes every R row's
-// largest bulk similarity, pass 1 keeps the columns within 2 * band of it (the exact argmax among them,
-// since the bulk error is at most band), and the FP32 re-score picks the best of those per row.
-ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, const ejoin_sel *selR,
+// Top-k join condition (Sec. VI-E) on the tensor cores, 1 <= k <= 32.  Pass 0 takes every R row's
+// largest bulk similarity per column group (one group for k = 1); for k > 1 the k-th largest group
+// maximum, a lower bound of the row's k-th largest bulk similarity, becomes its threshold.  Pass 1
+// keeps the columns within 2 * band of the threshold: the bulk error is at most band, so they hold
+// the exact top k.  The FP32 re-score then picks the best k of those per row.
+ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int k, const ejoin_sel *selR,
                       const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
                       uint64_t *count_out)
 {
     c->stats = ejoin_stats{};
     if (!rel_ok(R) || !rel_ok(S) || R.d != S.d || !sel_ok(selR) || !sel_ok(selS)) return EJOIN_EINVAL;
+    if (k < 1 || k > TOPK_MAX_K) return EJOIN_EINVAL;
     const int prec = c->prec;
     if (prec == EJOIN_F32) return EJOIN_EUNSUPPORTED;
     const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
@@ -582,14 +585,39 @@ ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, cons
     }
     const int64_t rowsA = round_up(std::max<int64_t>(R.n, 1), 256);
     const int64_t rowsB = round_up(std::max<int64_t>(S.n, 1), 256);
-    if ((e = ensure(c->top, (size_t)rowsA * 12)) != cudaSuccess) return from_cuda(e);
+    // column groups of pass 0: 128 columns (an epilogue lane's share of a tile), wider when the
+    // group maxima would exceed TOPK_MAX_GROUPS per row or 4 GiB in all
+    int shift = 62;
+    int64_t ld = 1;
+    if (k > 1) {
+        const int64_t nS = std::max<int64_t>(S.n, 1);
+        for (shift = 7;; ++shift) {
+            ld = ((nS - 1) >> shift) + 1;
+            if (ld <= TOPK_MAX_GROUPS && (double)rowsA * (double)ld * 4.0 <= 4294967296.0) break;
+        }
+    }
+    // per-row scratch: k = 1: best (u64) and the row maximum (u32); k > 1: threshold, count, offset,
+    // fill (u32 each) and the group maxima
+    const size_t top_bytes = k == 1 ? (size_t)rowsA * 12 : (size_t)rowsA * 16 + (size_t)rowsA * ld * 4;
+    if ((e = ensure(c->top, top_bytes)) != cudaSuccess) return from_cuda(e);
     unsigned long long *best = (unsigned long long *)c->top.p;
-    unsigned *row_best = (unsigned *)(best + rowsA);
+    unsigned *row_max = (unsigned *)(best + rowsA);
+    unsigned *thr = (unsigned *)c->top.p;
+    unsigned *row_cnt = thr + rowsA, *row_off = thr + 2 * rowsA, *row_fill = thr + 3 * rowsA;
+    unsigned *gmax = thr + 4 * rowsA;
     if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
     if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
     DevMisc *dm = (DevMisc *)c->misc.p;
     if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), c->stream)) != cudaSuccess) return from_cuda(e);
-    if ((e = cudaMemsetAsync(c->top.p, 0, (size_t)rowsA * 12, c->stream)) != cudaSuccess) return from_cuda(e);
+    if (k == 1) {
+        e = cudaMemsetAsync(c->top.p, 0, top_bytes, c->stream);
+    } else {
+        // counts and fills, and the group maxima (the threshold and offsets are written in full)
+        e = cudaMemsetAsync(row_cnt, 0, (size_t)rowsA * 4, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(row_fill, 0, (size_t)rowsA * 4, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(gmax, 0, (size_t)rowsA * ld * 4, c->stream);
+    }
+    if (e != cudaSuccess) return from_cuda(e);
 
     if (timing) cudaEventRecord(c->ev[0], c->stream);
     Side &sa = c->side[0];
@@ -613,17 +641,24 @@ ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, cons
     const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
     const int gm = c->group_m > 0 ? c->group_m : default_group_m(kp);
     const float margin = 2.f * band;
+    unsigned *pass0_out = k == 1 ? row_max : gmax;
+    unsigned *pass1_thr = k == 1 ? row_max : thr;
     e = launch_sim_tc_top(kind, 0, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p, (const float *)sb.scale.p,
-                          row_best, margin, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status, c->timeout,
-                          c->num_sms, gm, c->stream);
+                          pass0_out, ld, shift, margin, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status,
+                          c->timeout, c->num_sms, gm, c->stream);
     if (e != cudaSuccess) return from_cuda(e);
+    c->stats.launches += 1;
+    if (k > 1) {
+        e = launch_topk_threshold(gmax, ld, shift, nA, rowsA, nB, k, thr, c->num_sms, c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        c->stats.launches += 1;
+    }
     auto pass1 = [&]() -> cudaError_t {
         c->stats.launches += 1;
         return launch_sim_tc_top(kind, 1, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
-                                 (const float *)sb.scale.p, row_best, margin, (uint2 *)c->cand.p, c->cand_cap,
+                                 (const float *)sb.scale.p, pass1_thr, 1, 62, margin, (uint2 *)c->cand.p, c->cand_cap,
                                  &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
     };
-    c->stats.launches += 1;
     if ((e = pass1()) != cudaSuccess) return from_cuda(e);
     if (timing) cudaEventRecord(c->ev[2], c->stream);
     DevMisc hm;
@@ -638,7 +673,7 @@ ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, cons
     if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
     if (hm.status) return EJOIN_ECUDA;
     while (hm.cand_count > c->cand_cap) {
-        // candidate buffer too small: grow it and run pass 1 again (the row maxima stay)
+        // candidate buffer too small: grow it and run pass 1 again (the thresholds stay)
         c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
         if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
         if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
@@ -651,7 +686,9 @@ ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, cons
         c->stats.contract_retries++;
     }
     c->stats.candidates = hm.cand_count;
-    const uint64_t n_out = c->stats.n_sel_s > 0 ? c->stats.n_sel_r : 0;
+    if (k > 1 && hm.cand_count >= (1ull << 32)) return EJOIN_EUNSUPPORTED;  // 32-bit row offsets
+    const uint64_t kk = std::min<uint64_t>((uint64_t)k, c->stats.n_sel_s);
+    const uint64_t n_out = c->stats.n_sel_r * kk;
     if (*pairs_io == nullptr && may_alloc && n_out > 0) {
         void *p = nullptr;
         if ((e = cudaMalloc(&p, n_out * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
@@ -659,19 +696,37 @@ ejoin_status run_top1(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, cons
         *cap_io = n_out;
     }
     if (*pairs_io == nullptr) *cap_io = 0;
-    if (hm.cand_count > 0) {
+    const uint32_t *idsR = selR ? (const uint32_t *)sa.ids.p : nullptr;
+    const uint32_t *idsS = selS ? (const uint32_t *)sb.ids.p : nullptr;
+    if (hm.cand_count > 0 && k == 1) {
         e = launch_top1_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
-                                selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
-                                (const float *)sa.inv.p, (const float *)sb.inv.p, best, c->num_sms, c->stream);
-        if (e != cudaSuccess) return from_cuda(e);
-        e = launch_top1_emit(best, nA, rowsA, selR ? (const uint32_t *)sa.ids.p : nullptr, *pairs_io, *cap_io,
-                             &dm->pair_count, c->num_sms, c->stream);
+                                idsR, idsS, (const float *)sa.inv.p, (const float *)sb.inv.p, best, c->num_sms,
+                                c->stream);
+        if (e == cudaSuccess)
+            e = launch_top1_emit(best, nA, rowsA, idsR, *pairs_io, *cap_io, &dm->pair_count, c->num_sms, c->stream);
         if (e != cudaSuccess) return from_cuda(e);
         c->stats.launches += 2;
+    } else if (hm.cand_count > 0) {
+        // keys beside the candidates, then bucketed by row
+        if ((e = ensure(c->band, c->cand_cap * 8)) != cudaSuccess) return from_cuda(e);
+        if ((e = ensure(c->topseg, c->cand_cap * 8)) != cudaSuccess) return from_cuda(e);
+        unsigned long long *keys = (unsigned long long *)c->band.p, *seg = (unsigned long long *)c->topseg.p;
+        e = launch_topk_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
+                                idsR, idsS, (const float *)sa.inv.p, (const float *)sb.inv.p, keys, row_cnt,
+                                c->num_sms, c->stream);
+        if (e == cudaSuccess) e = launch_sel_scan(row_cnt, rowsA, row_off, (long long *)&dm->pad2[0], c->stream);
+        if (e == cudaSuccess)
+            e = launch_topk_scatter((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, keys, row_off, row_fill,
+                                    seg, c->num_sms, c->stream);
+        if (e == cudaSuccess)
+            e = launch_topk_select(seg, row_off, row_cnt, nA, rowsA, (int)kk, idsR, *pairs_io, *cap_io,
+                                   &dm->pair_count, c->num_sms, c->stream);
+        if (e != cudaSuccess) return from_cuda(e);
+        c->stats.launches += 4;
     }
     if (timing) cudaEventRecord(c->ev[3], c->stream);
     if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
-    if (hm.pair_count) return EJOIN_ECUDA;  // a kept row without a best pair
+    if (hm.pair_count) return EJOIN_ECUDA;  // a kept row with fewer candidates than records
     c->stats.pairs = n_out;
     if (timing) {
         c->stats.ms_normalize = elapsed(c->ev[0], c->ev[1]);
@@ -706,8 +761,8 @@ ejoin_status ejoin_threshold(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float eps, 
     return st;
 }
 
-ejoin_status ejoin_top1(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, const ejoin_sel *selR, const ejoin_sel *selS,
-                        ejoin_pairs *out)
+ejoin_status ejoin_topk(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, int32_t k, const ejoin_sel *selR,
+                        const ejoin_sel *selS, ejoin_pairs *out)
 {
     if (!c || !out) return EJOIN_EINVAL;
     DeviceGuard g(c->device);
@@ -715,7 +770,7 @@ ejoin_status ejoin_top1(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, const ejoin_sel 
     ejoin_pair *p = out->d_pairs;
     uint64_t cap = out->capacity;
     const bool alloc = p == nullptr;
-    ejoin_status st = run_top1(c, R, S, selR, selS, &p, &cap, alloc, &count);
+    ejoin_status st = run_topk(c, R, S, k, selR, selS, &p, &cap, alloc, &count);
     if (alloc && p) {
         out->d_pairs = p;
         out->capacity = cap;
@@ -728,6 +783,12 @@ ejoin_status ejoin_top1(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, const ejoin_sel 
             return EJOIN_ECUDA;
     }
     return st;
+}
+
+ejoin_status ejoin_top1(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, const ejoin_sel *selR, const ejoin_sel *selS,
+                        ejoin_pairs *out)
+{
+    return ejoin_topk(c, R, S, 1, selR, selS, out);
 }
 
 ejoin_status ejoin_threshold_host(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float eps, const ejoin_sel *selR,

@@ -57,9 +57,13 @@ struct BatchTables {
     // tile-list mode of a self-join listing only block pairs on and above the diagonal of 256-row
     // blocks: inside a diagonal block (row tile m, column tile n, m / 2 == n) keep col >= row
     int sym;
-    // top-1 passes: per operand row of A, the largest bulk similarity (order-preserving bits,
-    // f2ord), and the margin below it that the candidate pass keeps
+    // top-k passes.  Pass 0: row_best[r * top_ld + (c >> top_shift)] = the largest bulk similarity
+    // (order-preserving bits, f2ord) of operand row r of A over the column group of c (one group for
+    // top-1).  Pass 1: row_best[r] = a lower bound of row r's k-th largest bulk similarity, and the
+    // margin below it that the candidate pass keeps
     unsigned *row_best;
+    long long top_ld;
+    int top_shift;
     float top_margin;
 };
 
@@ -162,14 +166,15 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
                               float thr, const float *scale, uint2 *cand, uint64_t cap,
                               unsigned long long *cand_count, unsigned *status, uint64_t timeout, int count_only,
                               int grid, int group_m, cudaStream_t st);
-// Top-1 passes of the contraction (single join): pass 0 records in row_best[r] the largest bulk
-// similarity of operand row r of A (atomicMax on f2ord; row_best zeroed by the caller); pass 1
-// emits the candidates (r, c) with bulk similarity >= ord2f(row_best[r]) - margin.
+// Top-k passes of the contraction (single join): pass 0 records in row_best[r * top_ld + (c >> top_shift)]
+// the largest bulk similarity of operand row r of A over the column group of c (atomicMax on f2ord;
+// row_best zeroed by the caller; top_shift >= 7, the 128 columns of an epilogue lane stay in one group);
+// pass 1 emits the candidates (r, c) with bulk similarity >= ord2f(row_best[r]) - margin.
 cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                               const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
-                              unsigned *row_best, float margin, uint2 *cand, uint64_t cap,
-                              unsigned long long *cand_count, unsigned *status, uint64_t timeout, int grid,
-                              int group_m, cudaStream_t st);
+                              unsigned *row_best, long long top_ld, int top_shift, float margin, uint2 *cand,
+                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                              int grid, int group_m, cudaStream_t st);
 // Contraction with the exact re-score fused in (extra warps consume the candidates from a
 // shared-memory ring and write final pairs).  Needs 16-byte aligned rows, ld % 4 == 0 and
 // d % 4 == 0.
@@ -207,9 +212,13 @@ inline int default_group_m(int64_t kp)
     return (int)g;
 }
 size_t sim_tc_smem_bytes();
-// Top-1: best[r] = max over the candidates (r, c) of (f2ord(FP32 sim) << 32 | ~original j) (best
-// zeroed by the caller); then out[r] = (i, j, sim) for every operand row r of A (rows without a
-// best are counted in *missing).
+// Top-k join condition (topk.cu).  Group maxima per row of the first pass: at most this many.
+constexpr int64_t TOPK_MAX_GROUPS = 8192;
+constexpr int TOPK_MAX_K = 32;
+// Every candidate's similarity is the FP32 cosine from the raw rows, as the threshold re-score's.
+// k = 1: best[r] = max over the candidates (r, c) of (f2ord(sim) << 32 | ~original j) (best zeroed
+// by the caller); then out[r] = (i, j, sim) for every operand row r of A (rows without a best are
+// counted in *missing).
 cudaError_t launch_top1_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                                 const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
                                 const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *best,
@@ -217,6 +226,25 @@ cudaError_t launch_top1_rescore(const uint2 *cand, const unsigned long long *can
 cudaError_t launch_top1_emit(const unsigned long long *best, const long long *nA_dev, int64_t nA_max,
                              const uint32_t *idsR, ejoin_pair *out, uint64_t out_cap, unsigned long long *missing,
                              int num_sms, cudaStream_t st);
+// k > 1: thr[r] = the k-th largest of row r's group maxima gmax[r * ld + g], g < ceil(nB / 2^shift)
+// (f2ord(-inf) when there are fewer than k groups), a lower bound of its k-th largest bulk similarity.
+cudaError_t launch_topk_threshold(const unsigned *gmax, int64_t ld, int shift, const long long *nA_dev,
+                                  int64_t nA_max, const long long *nB_dev, int k, unsigned *thr, int num_sms,
+                                  cudaStream_t st);
+// keys[t] = f2ord(sim) << 32 | ~original j of candidate t, and row_cnt[r] += candidates of row r.
+cudaError_t launch_topk_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
+                                const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *keys,
+                                unsigned *row_cnt, int num_sms, cudaStream_t st);
+// seg[row_off[r] + t] = the keys of row r's candidates (row_fill zeroed by the caller).
+cudaError_t launch_topk_scatter(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                const unsigned long long *keys, const unsigned *row_off, unsigned *row_fill,
+                                unsigned long long *seg, int num_sms, cudaStream_t st);
+// out[r * kk + t] = row r's (t+1)-th largest key as (i, j, sim), t < kk (a row with fewer than kk keys
+// is counted in *missing and padded with (i, ~0u, -inf)).
+cudaError_t launch_topk_select(const unsigned long long *seg, const unsigned *row_off, const unsigned *row_cnt,
+                               const long long *nA_dev, int64_t nA_max, int kk, const uint32_t *idsR, ejoin_pair *out,
+                               uint64_t out_cap, unsigned long long *missing, int num_sms, cudaStream_t st);
 // Candidates: cand[0 .. min(*cand_count, cand_cap)).  Candidates whose FP32 similarity
 // lies within fp64_band of eps are listed in band_list (capacity band_cap >= cand_cap,
 // counted in *band_count) and decided by a second kernel, the accurate tier.  mirror: the

@@ -69,7 +69,8 @@ struct ejoin_ctx {
     ej::host::Buf cand;
     uint64_t cand_cap = 0;
     ej::host::Buf band;  // candidates near eps for the accurate tier (as many slots as candidates)
-    ej::host::Buf top;   // top-1: per operand row, the pass-0 maximum (u32) and the exact best (u64)
+    ej::host::Buf top;     // top-k: per operand row scratch (maxima, thresholds, counts, offsets)
+    ej::host::Buf topseg;  // top-k, k > 1: the candidates' keys bucketed by row
     ej::host::Buf host_in[6];
     ej::host::Buf host_pairs;
     cudaEvent_t ev[ej::host::N_EV] = {};

@@ -557,98 +557,3 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
 }
 
 }  // namespace ej
-
-// ---------------------------------------------------------------------------
-// Top-1 join condition (Sec. VI-E, top-k with k = 1): exact choice among the
-// candidates of the top-1 contraction passes.  Every candidate's similarity
-// is recomputed in FP32 from the raw rows (as in the threshold re-score) and
-// the per-row best is kept with a 64-bit atomicMax on
-// (f2ord(sim) << 32 | ~j), so that a tie goes to the smaller original j.
-namespace ej {
-
-__global__ void __launch_bounds__(256) top1_rescore_kernel(
-    const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
-    const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
-    const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
-    const float *__restrict__ invS, unsigned long long *__restrict__ best)
-{
-    const int lane = threadIdx.x & 31;
-    uint64_t n = *cand_count;
-    if (n > cand_cap) n = cand_cap;
-    const bool vec = (d % 4 == 0) && (ldR % 4 == 0) && (ldS % 4 == 0) &&
-                     ((reinterpret_cast<uintptr_t>(R) | reinterpret_cast<uintptr_t>(S)) % 16 == 0);
-    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t k = w0; k < n; k += nw) {
-        const uint2 c = cand[k];
-        const uint32_t i = idsR ? idsR[c.x] : c.x, j = idsS ? idsS[c.y] : c.y;
-        const float *r = R + (int64_t)i * ldR, *s = S + (int64_t)j * ldS;
-        float acc = 0.f;
-        if (vec) {
-            for (int g = lane; g < (d >> 2); g += 32) {
-                const float4 a = __ldg(reinterpret_cast<const float4 *>(r) + g);
-                const float4 b = __ldg(reinterpret_cast<const float4 *>(s) + g);
-                acc = fmaf(a.x, b.x, acc);
-                acc = fmaf(a.y, b.y, acc);
-                acc = fmaf(a.z, b.z, acc);
-                acc = fmaf(a.w, b.w, acc);
-            }
-        } else {
-            for (int kk = lane; kk < d; kk += 32) acc = fmaf(__ldg(r + kk), __ldg(s + kk), acc);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        const float sim = fminf(1.f, fmaxf(-1.f, acc * invR[c.x] * invS[c.y]));
-        if (lane == 0) atomicMax(best + c.x, ((unsigned long long)f2ord(sim) << 32) | (unsigned long long)(~j));
-    }
-}
-
-// One record per kept R row, at its operand row r (so in ascending original i): every row has a
-// best pair once S keeps a row, because pass 1 keeps the column that set the row's pass-0 maximum.
-// A row without one (not expected) is counted in *missing and written as (i, ~0u, -inf).
-__global__ void top1_emit_kernel(const unsigned long long *__restrict__ best, const long long *__restrict__ nA_dev,
-                                 int64_t nA_max, const uint32_t *__restrict__ idsR, ejoin_pair *__restrict__ out,
-                                 uint64_t out_cap, unsigned long long *missing)
-{
-    int64_t n = *nA_dev;
-    if (n > nA_max) n = nA_max;
-    if ((uint64_t)n > out_cap) n = (int64_t)out_cap;
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long b = best[r];
-        ejoin_pair p;
-        p.i = idsR ? idsR[r] : (uint32_t)r;
-        if (b) {
-            p.j = ~(uint32_t)(b & 0xffffffffull);
-            p.sim = ord2f((unsigned)(b >> 32));
-        } else {
-            p.j = ~0u;
-            p.sim = -INFINITY;
-            atomicAdd(missing, 1ull);
-        }
-        out[r] = p;
-    }
-}
-
-cudaError_t launch_top1_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
-                                const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
-                                const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *best,
-                                int num_sms, cudaStream_t st)
-{
-    if (cand_cap == 0) return cudaSuccess;
-    const unsigned g = (unsigned)std::min<uint64_t>((cand_cap + 7) / 8, (uint64_t)num_sms * 8);
-    top1_rescore_kernel<<<g, 256, 0, st>>>(cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS,
-                                           best);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_top1_emit(const unsigned long long *best, const long long *nA_dev, int64_t nA_max,
-                             const uint32_t *idsR, ejoin_pair *out, uint64_t out_cap, unsigned long long *missing,
-                             int num_sms, cudaStream_t st)
-{
-    if (nA_max <= 0 || out_cap == 0) return cudaSuccess;
-    const unsigned g = (unsigned)std::min<int64_t>((nA_max + 255) / 256, (int64_t)num_sms * 8);
-    top1_emit_kernel<<<g, 256, 0, st>>>(best, nA_dev, nA_max, idsR, out, out_cap, missing);
-    return cudaGetLastError();
-}
-
-}  // namespace ej

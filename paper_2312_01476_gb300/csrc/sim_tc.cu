@@ -790,7 +790,8 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             }
             if constexpr (MODE == MODE_TOPMAX) {
                 if (row_ok && lane_max > -INFINITY)
-                    atomicMax(bt.row_best + row, f2ord(TILE_SCALE ? lane_max * sc_tile : lane_max));
+                    atomicMax(bt.row_best + row * bt.top_ld + (colbase >> bt.top_shift),
+                              f2ord(TILE_SCALE ? lane_max * sc_tile : lane_max));
             }
             tc_fence_before();
             __syncwarp();
@@ -896,12 +897,14 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
 
 cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                               const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
-                              unsigned *row_best, float margin, uint2 *cand, uint64_t cap,
-                              unsigned long long *cand_count, unsigned *status, uint64_t timeout, int grid,
-                              int group_m, cudaStream_t st)
+                              unsigned *row_best, long long top_ld, int top_shift, float margin, uint2 *cand,
+                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                              int grid, int group_m, cudaStream_t st)
 {
     BatchTables bt{};
     bt.row_best = row_best;
+    bt.top_ld = top_ld;
+    bt.top_shift = top_shift;
     bt.top_margin = margin;
 #define EJ_TOP(K, M)                                                                                                  \
     launch_one<K, M>(tmA, tmB, kp, nA, nB, 0.f, scaleA, scaleB, cand, cap, cand_count, status, timeout, 0, grid,      \

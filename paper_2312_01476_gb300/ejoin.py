@@ -117,6 +117,9 @@ def load_library(path: str = LIB_PATH):
                                          P(ejoin_sel), ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_uint64)]
     lib.ejoin_top1.restype = ctypes.c_int
     lib.ejoin_top1.argtypes = [ctypes.c_void_p, ejoin_rel, ejoin_rel, P(ejoin_sel), P(ejoin_sel), P(ejoin_pairs)]
+    lib.ejoin_topk.restype = ctypes.c_int
+    lib.ejoin_topk.argtypes = [ctypes.c_void_p, ejoin_rel, ejoin_rel, ctypes.c_int32, P(ejoin_sel), P(ejoin_sel),
+                               P(ejoin_pairs)]
     lib.ejoin_pairs_free.restype = ctypes.c_int
     lib.ejoin_pairs_free.argtypes = [ctypes.c_void_p, P(ejoin_pairs)]
     lib.ejoin_last_stats.restype = ctypes.c_int
@@ -323,22 +326,28 @@ def ejoin_threshold(ctx: Ctx, R, S, eps: float, selR: Optional[Sel] = None, selS
     raise EJoinError(EJOIN_EOVERFLOW, "ejoin_threshold")
 
 
-def ejoin_top1(ctx: Ctx, R, S, selR: Optional[Sel] = None, selS: Optional[Sel] = None) -> Result:
-    """Device top-1 join condition (Sec. VI-E, top-k with k = 1) of CUDA tensors R, S: for every kept
-    R row i, the kept S row j of largest cosine similarity (ties: the smaller j), in ascending i.
-    Returns views of a cached device result buffer (valid until the next call on ctx)."""
+def ejoin_topk(ctx: Ctx, R, S, k: int, selR: Optional[Sel] = None, selS: Optional[Sel] = None) -> Result:
+    """Device top-k join condition (Sec. VI-E), 1 <= k <= 32, of CUDA tensors R, S: for every kept R
+    row i, the min(k, kept S rows) kept S rows of largest cosine similarity in descending similarity
+    (ties: the smaller j); rows in ascending i, each row's records consecutive.  Returns views of a
+    cached device result buffer (valid until the next call on ctx)."""
     import torch
     lib = load_library()
     rR, rS = _dev_rel(R), _dev_rel(S)
     sR, sS = _dev_sel(selR), _dev_sel(selS)
-    cap = max(int(R.shape[0]), 1)
+    cap = max(int(R.shape[0]) * max(int(k), 1), 1)
     if ctx._out is None or ctx._out.shape[0] < cap:
         ctx._out = torch.empty((cap, 3), dtype=torch.int32, device=R.device)
     out = ejoin_pairs(ctypes.c_void_p(ctx._out.data_ptr()), ctx._out.shape[0], None, 0)
-    _check(lib.ejoin_top1(ctx.handle, rR, rS, _sel_ptr(sR), _sel_ptr(sS), ctypes.byref(out)), "ejoin_top1")
+    _check(lib.ejoin_topk(ctx.handle, rR, rS, int(k), _sel_ptr(sR), _sel_ptr(sS), ctypes.byref(out)), "ejoin_topk")
     n = int(out.count)
     v = ctx._out[:n]
     return Result(v[:, 0], v[:, 1], v[:, 2].view(torch.float32), n)
+
+
+def ejoin_top1(ctx: Ctx, R, S, selR: Optional[Sel] = None, selS: Optional[Sel] = None) -> Result:
+    """ejoin_topk with k = 1: one record per kept R row."""
+    return ejoin_topk(ctx, R, S, 1, selR, selS)
 
 
 def _host_arr(a, dtype):

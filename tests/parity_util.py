@@ -84,3 +84,42 @@ def compare_top1(R, S, gi, gj, gs, oi, oj, os_, tol=1e-5, rows=None):
     assert err.max() <= tol, f"sim error {err.max():.3g} > {tol}"
     return {"rows": int(len(gi)), "same_j": int((gj == np.asarray(oj, dtype=np.int64)).sum()),
             "max_gap": float(max(gap.max(), 0.0)), "max_err": float(err.max())}
+
+
+def compare_topk(R, S, k, gi, gj, gs, oi, oj, os_, tol=1e-5, rows=None):
+    """Check a GPU top-k result against the oracle's: the same rows with the same number of records
+    each, in ascending i; per row, distinct columns in non-increasing reported similarity, each
+    reported similarity within ``tol`` of the pair's FP64 value, and the t-th largest FP64
+    similarity of the chosen columns within ``tol`` of the row's true t-th largest (so the chosen
+    set is the oracle's wherever the similarities around the k-th are more than ``tol`` apart).
+    Returns a dict of statistics."""
+    gi = np.asarray(gi, dtype=np.int64)
+    gj = np.asarray(gj, dtype=np.int64)
+    gs = np.asarray(gs, dtype=np.float64)
+    assert np.all(np.diff(gi) >= 0), "top-k records are not in ascending i"
+    if rows is not None:
+        keep = np.isin(gi, np.asarray(rows, dtype=np.int64))
+        gi, gj, gs = gi[keep], gj[keep], gs[keep]
+    oi = np.asarray(oi, dtype=np.int64)
+    assert np.array_equal(gi, oi), f"records per row differ: {len(gi)} GPU vs {len(oi)} oracle"
+    if len(gi) == 0:
+        return {"rows": 0, "same_set": 0, "max_gap": 0.0, "max_err": 0.0}
+    ur, cnt = np.unique(gi, return_counts=True)
+    kk = int(cnt[0])
+    assert np.all(cnt == kk) and kk <= k
+    n = len(ur)
+    J, G = gj.reshape(n, kk), gs.reshape(n, kk)
+    assert J.max() < S.shape[0], "j out of range"
+    assert all(len(set(r.tolist())) == kk for r in J), "a row lists a column twice"
+    assert np.all(np.diff(G, axis=1) <= 0), "records of a row are not in descending similarity"
+    s = oracle.sim_pairs(R, S, gi.astype(np.uint32), gj.astype(np.uint32)).reshape(n, kk)
+    err = np.abs(G - s)
+    assert err.max() <= tol, f"sim error {err.max():.3g} > {tol}"
+    O = np.asarray(os_, dtype=np.float64).reshape(n, kk)
+    gap = np.abs(np.sort(s, axis=1)[:, ::-1] - O)
+    bad = gap.max(axis=1) > tol
+    assert not bad.any(), f"{bad.sum()} rows chose columns outside the top {kk} by more than {tol}: rows " \
+                          f"{ur[bad][:5]}"
+    OJ = np.asarray(oj, dtype=np.int64).reshape(n, kk)
+    same = sum(set(a.tolist()) == set(b.tolist()) for a, b in zip(J, OJ))
+    return {"rows": int(n), "same_set": int(same), "max_gap": float(gap.max()), "max_err": float(err.max())}

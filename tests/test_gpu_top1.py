@@ -158,7 +158,7 @@ def test_top1_candidate_buffer_regrowth():
 @pytest.mark.parametrize("prec", PRECS)
 def test_top1_full_size_sampled_rows(prec):
     # 10,000 queries x 1,000,000 rows, d = 300, the S predicate attr < 10 (10 % of S kept)
-    w = inputs.top1_clustered_selection(sel_c=10, threads=THREADS)
+    w = inputs.topk_clustered_selection(sel_c=10, threads=THREADS)
     R, S, A = dev(w.R), dev(w.S), dev(w.attrS)
     with pkg.Ctx(device=0, prec=prec, flags=pkg.EJOIN_FLAG_TIMING) as ctx:
         res = pkg.ejoin_top1(ctx, R, S, None, pkg.Sel(A, w.opS, w.cS))
