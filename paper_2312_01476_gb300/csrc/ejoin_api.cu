@@ -551,11 +551,12 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     return EJOIN_OK;
 }
 
-// Top-k join condition (Sec. VI-E) on the tensor cores, 1 <= k <= 32.  Pass 0 takes every R row's
-// largest bulk similarity per column group (one group for k = 1); for k > 1 the k-th largest group
-// maximum, a lower bound of the row's k-th largest bulk similarity, becomes its threshold.  Pass 1
-// keeps the columns within 2 * band of the threshold: the bulk error is at most band, so they hold
-// the exact top k.  The FP32 re-score then picks the best k of those per row.
+// Top-k join condition (Sec. VI-E) on the tensor cores, 1 <= k <= 32.  k > 1: pass 0 takes every
+// R row's largest bulk similarity per column group, and the k-th largest group maximum, a lower
+// bound of the row's k-th largest bulk similarity, becomes its threshold; pass 1 keeps the columns
+// within 2 * band of the threshold: the bulk error is at most band, so they hold the exact top k.
+// k = 1: a single pass keeps the columns within 2 * band of the running row maximum.  The FP32
+// re-score then picks the best k of the candidates per row.
 ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int k, const ejoin_sel *selR,
                       const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
                       uint64_t *count_out)
@@ -585,13 +586,13 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     }
     const int64_t rowsA = round_up(std::max<int64_t>(R.n, 1), 256);
     const int64_t rowsB = round_up(std::max<int64_t>(S.n, 1), 256);
-    // column groups of pass 0: 128 columns (an epilogue lane's share of a tile), wider when the
-    // group maxima would exceed TOPK_MAX_GROUPS per row or 4 GiB in all
+    // column groups of pass 0: 256 columns (one column tile), wider when the group maxima would
+    // exceed TOPK_MAX_GROUPS per row or 4 GiB in all
     int shift = 62;
     int64_t ld = 1;
     if (k > 1) {
         const int64_t nS = std::max<int64_t>(S.n, 1);
-        for (shift = 7;; ++shift) {
+        for (shift = 8;; ++shift) {
             ld = ((nS - 1) >> shift) + 1;
             if (ld <= TOPK_MAX_GROUPS && (double)rowsA * (double)ld * 4.0 <= 4294967296.0) break;
         }
@@ -643,19 +644,19 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     const float margin = 2.f * band;
     unsigned *pass0_out = k == 1 ? row_max : gmax;
     unsigned *pass1_thr = k == 1 ? row_max : thr;
-    e = launch_sim_tc_top(kind, 0, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p, (const float *)sb.scale.p,
-                          pass0_out, ld, shift, margin, (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status,
-                          c->timeout, c->num_sms, gm, c->stream);
-    if (e != cudaSuccess) return from_cuda(e);
-    c->stats.launches += 1;
     if (k > 1) {
-        e = launch_topk_threshold(gmax, ld, shift, nA, rowsA, nB, k, thr, c->num_sms, c->stream);
+        e = launch_sim_tc_top(kind, 0, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
+                              (const float *)sb.scale.p, pass0_out, ld, shift, margin, (uint2 *)c->cand.p, c->cand_cap,
+                              &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
+        if (e == cudaSuccess) e = launch_topk_threshold(gmax, ld, shift, nA, rowsA, nB, k, thr, c->num_sms, c->stream);
         if (e != cudaSuccess) return from_cuda(e);
-        c->stats.launches += 1;
+        c->stats.launches += 2;
     }
+    // k = 1: one pass on the running row maximum (a repeat after a candidate overflow starts from the
+    // final maxima and keeps only the columns within the margin of them)
     auto pass1 = [&]() -> cudaError_t {
         c->stats.launches += 1;
-        return launch_sim_tc_top(kind, 1, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
+        return launch_sim_tc_top(kind, k == 1 ? 2 : 1, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
                                  (const float *)sb.scale.p, pass1_thr, 1, 62, margin, (uint2 *)c->cand.p, c->cand_cap,
                                  &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
     };

@@ -169,7 +169,9 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
 // Top-k passes of the contraction (single join): pass 0 records in row_best[r * top_ld + (c >> top_shift)]
 // the largest bulk similarity of operand row r of A over the column group of c (atomicMax on f2ord;
 // row_best zeroed by the caller; top_shift >= 7, the 128 columns of an epilogue lane stay in one group);
-// pass 1 emits the candidates (r, c) with bulk similarity >= ord2f(row_best[r]) - margin.
+// pass 1 emits the candidates (r, c) with bulk similarity >= ord2f(row_best[r]) - margin; pass 2 is
+// top-1 in one pass: per tile, row_best[r] is raised to the row's tile maximum and the columns
+// within margin of the raised value are emitted (row_best zeroed by the caller).
 cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                               const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
                               unsigned *row_best, long long top_ld, int top_shift, float margin, uint2 *cand,

@@ -129,11 +129,15 @@ struct TileInfo {
 };
 
 enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3, MODE_SYM = 4, MODE_TOPMAX = 5,
-             MODE_TOPCAND = 6 };
-// MODE_TOPMAX / MODE_TOPCAND: the two contraction passes of the top-1 join condition (Sec. VI-E,
-// top-k with k = 1), tiled like MODE_SINGLE.  TOPMAX keeps, per row of A, the largest bulk
-// similarity over the valid columns (no candidates); TOPCAND emits the candidates within a margin
-// of that row maximum.
+             MODE_TOPCAND = 6, MODE_TOP1 = 7 };
+// MODE_TOPMAX / MODE_TOPCAND: the two contraction passes of the top-k join condition (Sec. VI-E),
+// tiled like MODE_SINGLE.  TOPMAX keeps, per row of A and column group, the largest bulk similarity
+// over the valid columns (no candidates); TOPCAND emits the candidates within a margin of a per-row
+// threshold.  MODE_TOP1: top-1 in one pass.  Each lane emits a 32-column chunk's columns within the
+// margin of its row's running maximum (read at the tile start) merged with the row's maximum over
+// the tile's chunks so far, this chunk included, and raises the running maximum at the tile end
+// (atomicMax).  Every such threshold is at most the final row maximum less the margin, so the
+// column of the exact maximum, within the margin of the final one, is always emitted.
 
 // MODE_SYM (self-join, R == S): only the block pairs (I, J), I <= J, of
 // 256-row blocks are contracted, each as its two 128-row tiles (2I, J) and
@@ -590,6 +594,12 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
             const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
             const float thr_t = ti.thr;
+            // top-k modes: the row's threshold / running maximum, loaded before the accumulator wait so
+            // that its latency hides behind the MMAs
+            unsigned pre_best = 0u;
+            if constexpr (MODE == MODE_TOPCAND || MODE == MODE_TOP1) {
+                if (q * 32 + lane < ti.limA) pre_best = __ldcg(bt.row_best + ti.rowA + q * 32 + lane);
+            }
             int ok = 0;
             if (lane == 0) ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, timeout, abort_flag, status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -607,7 +617,8 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             // 256-row column tile share one scale (launch_normalize_fp8_grouped), so the two scales fold
             // into a per-lane threshold on the raw accumulator; the other modes scale every element
             constexpr bool TILE_SCALE = KIND == 1 && (MODE == MODE_SINGLE || MODE == MODE_SYM ||
-                                                      MODE == MODE_TOPMAX || MODE == MODE_TOPCAND);
+                                                      MODE == MODE_TOPMAX || MODE == MODE_TOPCAND ||
+                                                      MODE == MODE_TOP1);
             float sc_tile = 1.f;  // s_row * s_col of the e4m3 tile (TILE_SCALE)
             float rs = 1.f;
             float thr_lane = thr_t;
@@ -617,10 +628,13 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             float thr_base = thr_t;
             if constexpr (MODE == MODE_TOPCAND) {
                 // this row's best bulk similarity (pass 0) less the margin
-                thr_base = row_ok ? ord2f(__ldcg(bt.row_best + row)) - bt.top_margin : INFINITY;
+                thr_base = row_ok ? ord2f(pre_best) - bt.top_margin : INFINITY;
                 thr_lane = thr_base;
             }
-            float lane_max = -INFINITY;  // MODE_TOPMAX
+            float lane_max = -INFINITY;  // MODE_TOPMAX, MODE_TOP1 (raw accumulator units)
+            // MODE_TOP1: the row's running maximum as loaded at the tile start (it only grows, so a stale
+            // value is a lower bound of the final one)
+            const float best0 = pre_best ? ord2f(pre_best) : -INFINITY;
             if constexpr (TILE_SCALE) {
                 const float sc = row_ok ? scaleA[row] * __ldg(scaleB + ti.rowB) : 0.f;
                 sc_tile = sc;
@@ -655,7 +669,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                     for (int g = 0; g < 4; ++g) a8[g] = fmaxf(u[2 * g], u[2 * g + 1]);
                 }
                 const float mx = fmaxf(fmaxf(a8[0], a8[1]), fmaxf(a8[2], a8[3]));
-                if constexpr (MODE == MODE_TOPMAX) {
+                if constexpr (MODE == MODE_TOPMAX || MODE == MODE_TOP1) {
                     // the row maximum over the valid columns only (padding columns hold zeros)
                     if (left >= 32) {
                         lane_max = fmaxf(lane_max, mx);
@@ -664,7 +678,19 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                         for (int k = 0; k < 32; ++k)
                             if (k < left) lane_max = fmaxf(lane_max, f[k]);
                     }
-                    return;
+                }
+                if constexpr (MODE == MODE_TOPMAX) return;
+                if constexpr (MODE == MODE_TOP1) {
+                    // threshold: the running maximum merged with this row's maximum over the chunks seen so
+                    // far in this tile (this chunk included), less the margin
+                    thr_lane = INFINITY;
+                    if (row_ok && lane_max > -INFINITY) {
+                        const float tb = fmaxf(best0, TILE_SCALE ? lane_max * sc_tile : lane_max) - bt.top_margin;
+                        if constexpr (TILE_SCALE)
+                            thr_lane = sc_tile > 0.f ? __fdiv_rn(tb, sc_tile) : (tb <= 0.f ? -INFINITY : INFINITY);
+                        else
+                            thr_lane = tb;
+                    }
                 }
                 if (!__any_sync(0xffffffffu, row_ok && mx >= thr_lane)) return;
                 // slow path: per-lane match mask, built only for 8-column groups that hold a match
@@ -765,8 +791,8 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                 __syncwarp();
             };
 
-            // software pipeline: the load of chunk c+1 is in flight while chunk c is scanned
             uint32_t va[32], vb[32];
+            // software pipeline: the load of chunk c+1 is in flight while chunk c is scanned
             tmem_ld_32cols(tbase, va);
             tmem_wait_ld_regs(va);
 #pragma unroll
@@ -792,6 +818,13 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                 if (row_ok && lane_max > -INFINITY)
                     atomicMax(bt.row_best + row * bt.top_ld + (colbase >> bt.top_shift),
                               f2ord(TILE_SCALE ? lane_max * sc_tile : lane_max));
+            }
+            if constexpr (MODE == MODE_TOP1) {
+                // raise the running maximum (no reply awaited)
+                if (row_ok && lane_max > -INFINITY) {
+                    const unsigned o = f2ord(TILE_SCALE ? lane_max * sc_tile : lane_max);
+                    if (o > pre_best) atomicMax(bt.row_best + row, o);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -914,6 +947,14 @@ cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const 
         case 0: return EJ_TOP(0, MODE_TOPMAX);
         case 1: return EJ_TOP(1, MODE_TOPMAX);
         case 2: return EJ_TOP(2, MODE_TOPMAX);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (pass == 2) {
+        switch (kind) {
+        case 0: return EJ_TOP(0, MODE_TOP1);
+        case 1: return EJ_TOP(1, MODE_TOP1);
+        case 2: return EJ_TOP(2, MODE_TOP1);
         default: return cudaErrorInvalidValue;
         }
     }

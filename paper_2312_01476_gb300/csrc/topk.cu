@@ -23,35 +23,6 @@ namespace ej {
 
 namespace {
 
-// FP32 cosine of R row i and S row j (one warp; the same lane-strided FMA order as the threshold
-// re-score's FP32 tier), clamped to [-1, 1].
-__device__ __forceinline__ float warp_cosine(const float *__restrict__ r, const float *__restrict__ s, int d,
-                                             bool vec, float inv_r, float inv_s, int lane)
-{
-    float acc = 0.f;
-    if (vec) {
-        for (int g = lane; g < (d >> 2); g += 32) {
-            const float4 a = __ldg(reinterpret_cast<const float4 *>(r) + g);
-            const float4 b = __ldg(reinterpret_cast<const float4 *>(s) + g);
-            acc = fmaf(a.x, b.x, acc);
-            acc = fmaf(a.y, b.y, acc);
-            acc = fmaf(a.z, b.z, acc);
-            acc = fmaf(a.w, b.w, acc);
-        }
-    } else {
-        for (int k = lane; k < d; k += 32) acc = fmaf(__ldg(r + k), __ldg(s + k), acc);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    return fminf(1.f, fmaxf(-1.f, acc * inv_r * inv_s));
-}
-
-__device__ __forceinline__ bool rows_vec_ok(const float *R, int64_t ldR, const float *S, int64_t ldS, int d)
-{
-    return (d % 4 == 0) && (ldR % 4 == 0) && (ldS % 4 == 0) &&
-           ((reinterpret_cast<uintptr_t>(R) | reinterpret_cast<uintptr_t>(S)) % 16 == 0);
-}
-
 __device__ __forceinline__ unsigned long long pack_key(float sim, uint32_t j)
 {
     return ((unsigned long long)f2ord(sim) << 32) | (unsigned long long)(~j);
@@ -103,23 +74,102 @@ __device__ __forceinline__ unsigned long long warp_merge_desc(unsigned long long
     return x;
 }
 
-__global__ void __launch_bounds__(256) top1_rescore_kernel(
+// FP32 re-score of the candidates, one warp per 32 candidates: lane t fetches candidate t, then the
+// warp gathers the rows of C candidates at once (V float4 per lane per row, every load issued before
+// the first FMA: 2 * C * V independent loads in flight per lane) for rows of d <= 128 * V floats,
+// 16-byte aligned; V = 0 is the general fallback (one candidate at a time, scalar loads).  Each
+// lane ends with its candidate's key.  TOP1: atomicMax of the key into best[r]; otherwise the key
+// is stored beside the candidate and row_cnt[r] counts it.
+constexpr int RK_WARPS = 8;
+
+template <int V, int C, bool TOP1>
+__global__ void __launch_bounds__(RK_WARPS * 32) topk_rescore_kernel(
     const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
     const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
     const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
-    const float *__restrict__ invS, unsigned long long *__restrict__ best)
+    const float *__restrict__ invS, unsigned long long *__restrict__ out_keys, unsigned *__restrict__ row_cnt)
 {
     const int lane = threadIdx.x & 31;
     uint64_t n = *cand_count;
     if (n > cand_cap) n = cand_cap;
-    const bool vec = rows_vec_ok(R, ldR, S, ldS, d);
+    const int d4 = d >> 2;
     const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t t = w0; t < n; t += nw) {
-        const uint2 c = cand[t];
-        const uint32_t i = idsR ? idsR[c.x] : c.x, j = idsS ? idsS[c.y] : c.y;
-        const float sim = warp_cosine(R + (int64_t)i * ldR, S + (int64_t)j * ldS, d, vec, invR[c.x], invS[c.y], lane);
-        if (lane == 0) atomicMax(best + c.x, pack_key(sim, j));
+    for (uint64_t base = w0 * 32; base < n; base += nw * 32) {
+        const bool valid = base + lane < n;
+        uint32_t cr = 0, gi = 0, gj = 0;
+        float sc = 0.f;
+        if (valid) {
+            const uint2 c = cand[base + lane];
+            cr = c.x;
+            gi = idsR ? idsR[c.x] : c.x;
+            gj = idsS ? idsS[c.y] : c.y;
+            sc = invR[c.x] * invS[c.y];
+        }
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        float my_acc = 0.f;
+        if constexpr (V > 0) {
+#pragma unroll 1
+            for (int q0 = 0; q0 < 32; q0 += C) {
+                if (!((vmask >> q0) & 1u)) break;  // warp-uniform
+                float4 a[C][V], b[C][V];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t ii = __shfl_sync(0xffffffffu, gi, q0 + c);
+                    const uint32_t jj = __shfl_sync(0xffffffffu, gj, q0 + c);
+                    const bool ok = (vmask >> (q0 + c)) & 1u;
+                    const float4 *r = reinterpret_cast<const float4 *>(R + (int64_t)ii * ldR);
+                    const float4 *s = reinterpret_cast<const float4 *>(S + (int64_t)jj * ldS);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int g = lane + 32 * v;
+                        const bool in = ok && g < d4;
+                        a[c][v] = in ? __ldg(r + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[c][v] = in ? __ldg(s + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                float acc[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    acc[c] = 0.f;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        acc[c] = fmaf(a[c][v].x, b[c][v].x, acc[c]);
+                        acc[c] = fmaf(a[c][v].y, b[c][v].y, acc[c]);
+                        acc[c] = fmaf(a[c][v].z, b[c][v].z, acc[c]);
+                        acc[c] = fmaf(a[c][v].w, b[c][v].w, acc[c]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+#pragma unroll
+                for (int c = 0; c < C; ++c)
+                    if (lane == q0 + c) my_acc = acc[c];
+            }
+        } else {
+            for (int q = 0; q < 32; ++q) {
+                if (!((vmask >> q) & 1u)) break;
+                const uint32_t ii = __shfl_sync(0xffffffffu, gi, q);
+                const uint32_t jj = __shfl_sync(0xffffffffu, gj, q);
+                const float *r = R + (int64_t)ii * ldR, *s = S + (int64_t)jj * ldS;
+                float acc = 0.f;
+                for (int kk = lane; kk < d; kk += 32) acc = fmaf(__ldg(r + kk), __ldg(s + kk), acc);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == q) my_acc = acc;
+            }
+        }
+        if (valid) {
+            const unsigned long long key = pack_key(fminf(1.f, fmaxf(-1.f, my_acc * sc)), gj);
+            if constexpr (TOP1) {
+                atomicMax(out_keys + cr, key);
+            } else {
+                out_keys[base + lane] = key;
+                atomicAdd(row_cnt + cr, 1u);
+            }
+        }
     }
 }
 
@@ -145,7 +195,10 @@ __global__ void top1_emit_kernel(const unsigned long long *__restrict__ best, co
 }
 
 // Block per row: the k-th largest of the row's valid group maxima, found bit by bit from the top
-// (the largest T with at least k values >= T is the k-th largest value).
+// (the largest T with at least k values >= T is the k-th largest value).  Only the leading
+// THR_BITS bits are searched: the result, with its low bits zero, is at most the k-th largest
+// (a lower bound is all the candidate pass needs) and below it by less than 2^-11 relative.
+constexpr int THR_BITS = 20;
 constexpr int THR_THREADS = 256;
 
 __global__ void __launch_bounds__(THR_THREADS) topk_threshold_kernel(const unsigned *__restrict__ gmax, int64_t ld,
@@ -170,7 +223,7 @@ __global__ void __launch_bounds__(THR_THREADS) topk_threshold_kernel(const unsig
         for (int64_t g = threadIdx.x; g < G; g += THR_THREADS) sv[g] = gmax[r * ld + g];
         __syncthreads();
         unsigned res = 0u;
-        for (int b = 31; b >= 0; --b) {
+        for (int b = 31; b > 31 - THR_BITS; --b) {
             const unsigned cand = res | (1u << b);
             unsigned c = 0;
             for (int64_t g = threadIdx.x; g < G; g += THR_THREADS) c += sv[g] >= cand ? 1u : 0u;
@@ -184,29 +237,6 @@ __global__ void __launch_bounds__(THR_THREADS) topk_threshold_kernel(const unsig
         }
         if (threadIdx.x == 0) thr[r] = res;
         __syncthreads();  // sv is refilled for the next row
-    }
-}
-
-__global__ void __launch_bounds__(256) topk_rescore_kernel(
-    const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
-    const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
-    const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
-    const float *__restrict__ invS, unsigned long long *__restrict__ keys, unsigned *__restrict__ row_cnt)
-{
-    const int lane = threadIdx.x & 31;
-    uint64_t n = *cand_count;
-    if (n > cand_cap) n = cand_cap;
-    const bool vec = rows_vec_ok(R, ldR, S, ldS, d);
-    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t t = w0; t < n; t += nw) {
-        const uint2 c = cand[t];
-        const uint32_t i = idsR ? idsR[c.x] : c.x, j = idsS ? idsS[c.y] : c.y;
-        const float sim = warp_cosine(R + (int64_t)i * ldR, S + (int64_t)j * ldS, d, vec, invR[c.x], invS[c.y], lane);
-        if (lane == 0) {
-            keys[t] = pack_key(sim, j);
-            atomicAdd(row_cnt + c.x, 1u);
-        }
     }
 }
 
@@ -272,15 +302,40 @@ unsigned grid_for(uint64_t work_items, uint64_t per_block, int num_sms, int bloc
 
 }  // namespace
 
+namespace {
+
+template <bool TOP1>
+cudaError_t launch_rescore_keys(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
+                                const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *keys,
+                                unsigned *row_cnt, int num_sms, cudaStream_t st)
+{
+    if (cand_cap == 0) return cudaSuccess;
+    const unsigned g = grid_for(cand_cap, RK_WARPS * 32, num_sms, 8);
+    const int T = RK_WARPS * 32;
+    const bool aligned = (d % 4 == 0) && (ldR % 4 == 0) && (ldS % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(R) % 16 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
+#define EJ_RK_ARGS cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, keys, row_cnt
+    if (aligned && d <= 128) topk_rescore_kernel<1, 4, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+    else if (aligned && d <= 256) topk_rescore_kernel<2, 4, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+    else if (aligned && d <= 384) topk_rescore_kernel<3, 4, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+    else if (aligned && d <= 512) topk_rescore_kernel<4, 2, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+    else if (aligned && d <= 768) topk_rescore_kernel<6, 2, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+    else if (aligned && d <= 1024) topk_rescore_kernel<8, 2, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+    else topk_rescore_kernel<0, 1, TOP1><<<g, T, 0, st>>>(EJ_RK_ARGS);
+#undef EJ_RK_ARGS
+    return cudaGetLastError();
+}
+
+}  // namespace
+
 cudaError_t launch_top1_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                                 const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
                                 const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *best,
                                 int num_sms, cudaStream_t st)
 {
-    if (cand_cap == 0) return cudaSuccess;
-    top1_rescore_kernel<<<grid_for(cand_cap, 8, num_sms, 8), 256, 0, st>>>(cand, cand_count, cand_cap, R, ldR, S, ldS,
-                                                                         d, idsR, idsS, invR, invS, best);
-    return cudaGetLastError();
+    return launch_rescore_keys<true>(cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, best,
+                                     nullptr, num_sms, st);
 }
 
 cudaError_t launch_top1_emit(const unsigned long long *best, const long long *nA_dev, int64_t nA_max,
@@ -315,10 +370,8 @@ cudaError_t launch_topk_rescore(const uint2 *cand, const unsigned long long *can
                                 const uint32_t *idsS, const float *invR, const float *invS, unsigned long long *keys,
                                 unsigned *row_cnt, int num_sms, cudaStream_t st)
 {
-    if (cand_cap == 0) return cudaSuccess;
-    topk_rescore_kernel<<<grid_for(cand_cap, 8, num_sms, 8), 256, 0, st>>>(cand, cand_count, cand_cap, R, ldR, S, ldS,
-                                                                         d, idsR, idsS, invR, invS, keys, row_cnt);
-    return cudaGetLastError();
+    return launch_rescore_keys<false>(cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, keys,
+                                      row_cnt, num_sms, st);
 }
 
 cudaError_t launch_topk_scatter(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,

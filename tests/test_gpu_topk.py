@@ -44,7 +44,7 @@ def topk(prec, R, S, k, selR=None, selS=None, **kw):
 @pytest.mark.parametrize("shape,k", [((300, 5000, 37), 2), ((129, 9000, 128), 7), ((1000, 6000, 300), 32),
                                      ((37, 4100, 64), 32), ((64, 300, 96), 32)])
 def test_topk_ragged(prec, shape, k):
-    # (64, 300): three column groups for k = 32, so every column is a candidate
+    # (64, 300): two column groups for k = 32, so every column is a candidate
     nR, nS, d = shape
     rng = np.random.default_rng(nR + nS + d + k)
     R = rng.standard_normal((nR, d)).astype(np.float32)
@@ -103,11 +103,11 @@ def test_topk_exact_ties_at_the_boundary(prec):
 
 
 def test_topk_wide_column_groups():
-    # 1,100,000 S rows: more than 8192 groups of 128 columns, so pass 0 widens the groups to 256
+    # 2,200,000 S rows: more than 8192 groups of 256 columns, so pass 0 widens the groups to 512
     rng = np.random.default_rng(191)
     d = 32
     R = rng.standard_normal((300, d)).astype(np.float32)
-    S = rng.standard_normal((1_100_000, d)).astype(np.float32)
+    S = rng.standard_normal((2_200_000, d)).astype(np.float32)
     gi, gj, gs, st = topk("bf16", R, S, 32)
     rows = np.sort(rng.choice(300, 24, replace=False))
     oi, oj, os_ = oracle.topk(R, S, 32, rows=rows, threads=THREADS)
