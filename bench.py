@@ -430,17 +430,22 @@ def run_topk(args):
     clocks = sampler.stop()
     ms = statistics.mean(step_ms)
     c_ms = statistics.mean(cms)
-    # k = 1 evaluates every kept pair once (one contraction pass), k > 1 twice (passes 0 and 1):
-    # 2 d FLOPs per pair per pass
+    # executed FLOPs, 2 d per evaluated pair: k = 1 evaluates every kept pair once (one pass); k > 1
+    # adds the first pass over every stride-th 256-column tile (stride 8 while at least 4k tiles remain)
     passes = 1 if k == 1 else 2
-    flop = 2.0 * d * pairs * passes
+    flop = 2.0 * d * pairs
+    if k > 1:
+        n_s = int(st0["n_sel_s"])
+        tiles = -(-n_s // 256)
+        stride = max(1, min(8, tiles // (4 * k)))
+        flop += 2.0 * d * int(st0["n_sel_r"]) * min(n_s, -(-tiles // stride) * 256)
     peak, note = tensor_peak(args.prec, c_ms / passes)
     achieved = flop / (c_ms * 1e-3) / 1e12
     kernel_key = f"sim_tc_top_{args.prec}_{args.workload}"
     roofline = {"kernel": kernel_key + (" (single pass)" if k == 1 else " (passes 0 + 1)"), "bound": "tensor",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "peak_note": note, "traffic": recorded_traffic(kernel_key), "flop_per_launch": flop / passes,
-                "ms_per_launch": round(c_ms / passes, 4)}
+                "peak_note": note + ("" if k == 1 else "; both passes and the threshold kernel between them"),
+                "traffic": recorded_traffic(kernel_key), "flop_per_step": flop, "ms_contract": round(c_ms, 4)}
     # end to end through the public API: pinned host inputs copied in, the records copied out
     e2e = None
     if not args.no_e2e:

@@ -645,9 +645,12 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     unsigned *pass0_out = k == 1 ? row_max : gmax;
     unsigned *pass1_thr = k == 1 ? row_max : thr;
     if (k > 1) {
+        // pass 0 on every 8th column tile (at least 4k of them): the k-th largest maximum over any set
+        // of column groups bounds the k-th largest similarity from below, the sample only loosens it
         e = launch_sim_tc_top(kind, 0, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
-                              (const float *)sb.scale.p, pass0_out, ld, shift, margin, (uint2 *)c->cand.p, c->cand_cap,
-                              &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
+                              (const float *)sb.scale.p, pass0_out, ld, shift, TOPK_SAMPLE_STRIDE, 4 * k, margin,
+                              (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status, c->timeout, c->num_sms,
+                              gm, c->stream);
         if (e == cudaSuccess) e = launch_topk_threshold(gmax, ld, shift, nA, rowsA, nB, k, thr, c->num_sms, c->stream);
         if (e != cudaSuccess) return from_cuda(e);
         c->stats.launches += 2;
@@ -657,7 +660,8 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     auto pass1 = [&]() -> cudaError_t {
         c->stats.launches += 1;
         return launch_sim_tc_top(kind, k == 1 ? 2 : 1, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
-                                 (const float *)sb.scale.p, pass1_thr, 1, 62, margin, (uint2 *)c->cand.p, c->cand_cap,
+                                 (const float *)sb.scale.p, pass1_thr, 1, 62, 1, 1, margin, (uint2 *)c->cand.p,
+                                 c->cand_cap,
                                  &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
     };
     if ((e = pass1()) != cudaSuccess) return from_cuda(e);

@@ -64,6 +64,8 @@ struct BatchTables {
     unsigned *row_best;
     long long top_ld;
     int top_shift;
+    // pass 0 may sample every top_stride-th column tile while that leaves at least top_min_tiles
+    int top_stride, top_min_tiles;
     float top_margin;
 };
 
@@ -168,15 +170,17 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
                               int grid, int group_m, cudaStream_t st);
 // Top-k passes of the contraction (single join): pass 0 records in row_best[r * top_ld + (c >> top_shift)]
 // the largest bulk similarity of operand row r of A over the column group of c (atomicMax on f2ord;
-// row_best zeroed by the caller; top_shift >= 7, the 128 columns of an epilogue lane stay in one group);
+// row_best zeroed by the caller; top_shift >= 7, the 128 columns of an epilogue lane stay in one group),
+// over every top_stride-th 256-column tile only while at least top_min_tiles tiles remain (groups
+// without a sampled tile stay 0);
 // pass 1 emits the candidates (r, c) with bulk similarity >= ord2f(row_best[r]) - margin; pass 2 is
 // top-1 in one pass: per tile, row_best[r] is raised to the row's tile maximum and the columns
 // within margin of the raised value are emitted (row_best zeroed by the caller).
 cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                               const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
-                              unsigned *row_best, long long top_ld, int top_shift, float margin, uint2 *cand,
-                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                              int grid, int group_m, cudaStream_t st);
+                              unsigned *row_best, long long top_ld, int top_shift, int top_stride, int top_min_tiles,
+                              float margin, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
+                              unsigned *status, uint64_t timeout, int grid, int group_m, cudaStream_t st);
 // Contraction with the exact re-score fused in (extra warps consume the candidates from a
 // shared-memory ring and write final pairs).  Needs 16-byte aligned rows, ld % 4 == 0 and
 // d % 4 == 0.
@@ -217,6 +221,7 @@ size_t sim_tc_smem_bytes();
 // Top-k join condition (topk.cu).  Group maxima per row of the first pass: at most this many.
 constexpr int64_t TOPK_MAX_GROUPS = 8192;
 constexpr int TOPK_MAX_K = 32;
+constexpr int TOPK_SAMPLE_STRIDE = 8;  // column-tile stride of the first top-k pass
 // Every candidate's similarity is the FP32 cosine from the raw rows, as the threshold re-score's.
 // k = 1: best[r] = max over the candidates (r, c) of (f2ord(sim) << 32 | ~original j) (best zeroed
 // by the caller); then out[r] = (i, j, sim) for every operand row r of A (rows without a best are

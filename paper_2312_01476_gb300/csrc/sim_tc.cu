@@ -351,7 +351,8 @@ __device__ __forceinline__ void rescore_role(uint8_t *smem, const FuseArgs &fa, 
 
 template <int MODE>
 __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &bt, long long tiles_m,
-                                                long long tiles_n, long long nA, long long nB, float thr, int group_m)
+                                                long long tiles_n, long long nA, long long nB, float thr, int group_m,
+                                                long long col_stride = 1)
 {
     TileInfo ti;
     ti.diag = false;
@@ -390,6 +391,7 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
         ti.thr = __ldg(bt.thr + lo);
     } else {
         tile_coords(t, tiles_m, tiles_n, group_m, m, n);
+        n *= col_stride;
         ti.rowA = m * BM;
         ti.rowB = n * BN;
         ti.limA = (int)min((long long)BM, nA - m * BM);
@@ -434,7 +436,14 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long nA = MODE == MODE_BATCH ? 0 : *nA_ptr, nB = MODE == MODE_BATCH ? 0 : *nB_ptr;
-    const long long tiles_m = (nA + BM - 1) / BM, tiles_n = (nB + BN - 1) / BN;
+    const long long tiles_m = (nA + BM - 1) / BM;
+    // MODE_TOPMAX may sample every col_stride-th column tile, keeping at least top_min_tiles of them
+    long long col_stride = 1;
+    if (MODE == MODE_TOPMAX && bt.top_stride > 1) {
+        const long long tn = (nB + BN - 1) / BN;
+        col_stride = max(1ll, min((long long)bt.top_stride, tn / max(1ll, (long long)bt.top_min_tiles)));
+    }
+    const long long tiles_n = ((nB + BN - 1) / BN + col_stride - 1) / col_stride;
     long long total = tiles_m * tiles_n;
     if (MODE == MODE_BATCH) total = __ldg(bt.tile_off + bt.n_jobs);
     if (MODE == MODE_SYM) total = sym_total(SymRaster{(nA + 2 * BM - 1) / (2 * BM), 1});
@@ -485,7 +494,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             uint64_t issued = 0;
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
+                const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m, col_stride);
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, timeout, abort_flag, status)) {
                         ok = false;
@@ -592,7 +601,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
         };
 
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-            const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m);
+            const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m, col_stride);
             const float thr_t = ti.thr;
             // top-k modes: the row's threshold / running maximum, loaded before the accumulator wait so
             // that its latency hides behind the MMAs
@@ -930,14 +939,16 @@ cudaError_t launch_sim_tc_sym(int kind, const CUtensorMap *tmA, const CUtensorMa
 
 cudaError_t launch_sim_tc_top(int kind, int pass, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp,
                               const long long *nA, const long long *nB, const float *scaleA, const float *scaleB,
-                              unsigned *row_best, long long top_ld, int top_shift, float margin, uint2 *cand,
-                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                              int grid, int group_m, cudaStream_t st)
+                              unsigned *row_best, long long top_ld, int top_shift, int top_stride, int top_min_tiles,
+                              float margin, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
+                              unsigned *status, uint64_t timeout, int grid, int group_m, cudaStream_t st)
 {
     BatchTables bt{};
     bt.row_best = row_best;
     bt.top_ld = top_ld;
     bt.top_shift = top_shift;
+    bt.top_stride = top_stride;
+    bt.top_min_tiles = top_min_tiles;
     bt.top_margin = margin;
 #define EJ_TOP(K, M)                                                                                                  \
     launch_one<K, M>(tmA, tmB, kp, nA, nB, 0.f, scaleA, scaleB, cand, cap, cand_count, status, timeout, 0, grid,      \

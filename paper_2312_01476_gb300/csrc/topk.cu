@@ -235,7 +235,8 @@ __global__ void __launch_bounds__(THR_THREADS) topk_threshold_kernel(const unsig
             for (int w = 0; w < THR_THREADS / 32; ++w) tot += wsum[b & 1][w];
             if (tot >= (unsigned)k) res = cand;
         }
-        if (threadIdx.x == 0) thr[r] = res;
+        // res == 0: fewer than k groups hold a value (a sampled first pass): no bound
+        if (threadIdx.x == 0) thr[r] = res ? res : f2ord(-INFINITY);
         __syncthreads();  // sv is refilled for the next row
     }
 }

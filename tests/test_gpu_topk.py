@@ -114,6 +114,25 @@ def test_topk_wide_column_groups():
     compare_topk(R, S, 32, gi, gj, gs, oi, oj, os_, rows=rows)
 
 
+@pytest.mark.parametrize("order", ["shuffled", "sorted_by_cluster"])
+def test_topk_sampled_first_pass(order):
+    # 300,000 S rows = 1172 column tiles: the first pass samples every 8th tile (k = 32 needs >= 128);
+    # with S sorted by cluster a row's neighbours sit in a few consecutive tiles the sample may miss,
+    # which loosens the threshold but must not change the result
+    d = 64
+    centres = inputs.sphere_centres(300, d, 201)
+    R = inputs.clustered(200, d, centres, 0.3, 202)
+    S, cid = inputs.clustered(300_000, d, centres, 0.3, 203, with_ids=True)
+    if order == "sorted_by_cluster":
+        S = np.ascontiguousarray(S[np.argsort(cid, kind="stable")])
+    for prec in PRECS:
+        gi, gj, gs, st = topk(prec, R, S, 32)
+        rows = np.arange(0, 200, 5)
+        oi, oj, os_ = oracle.topk(R, S, 32, rows=rows, threads=THREADS)
+        compare_topk(R, S, 32, gi, gj, gs, oi, oj, os_, rows=rows)
+        assert st["pairs"] == 200 * 32
+
+
 def test_topk_regrowth_and_invalid_k():
     rng = np.random.default_rng(199)
     R = rng.standard_normal((200, 64)).astype(np.float32)
