@@ -232,3 +232,21 @@ def clustered_torch(n: int, d: int, centres, theta: float, seed: int, device="cu
     x.mul_(math.tan(theta) / math.sqrt(d)).add_(centres[cid])
     x.div_(torch.linalg.vector_norm(x, dim=1, keepdim=True))
     return x
+
+
+def eselect_workload(n: int = 10_000_000, d: int = 768, m: int = 32, n_clusters: int = 20_000,
+                     theta: float = THETA_768, eps: float = 0.9, device="cuda"):
+    """ℰ-selection workload, generated on the device: n rows clustered as in c3 (20,000 centres on
+    S^(d-1), spread THETA_768) in chunks of 2^20 rows (chunk c seeded (seed + 10) * 1000 + c), and m
+    query rows around the same centres (seed + 20), so that each query keeps about n / 20,000 rows at
+    eps = 0.9.  Returns (R, Q, eps) as CUDA tensors and a float."""
+    import torch
+    seed = seed_for(7)
+    centres = torch.from_numpy(sphere_centres(n_clusters, d, seed)).to(device)
+    R = torch.empty((n, d), dtype=torch.float32, device=device)
+    step = 1 << 20
+    for c, lo in enumerate(range(0, n, step)):
+        hi = min(n, lo + step)
+        R[lo:hi] = clustered_torch(hi - lo, d, centres, theta, (seed + 10) * 1000 + c, device)
+    Q = clustered_torch(m, d, centres, theta, seed + 20, device)
+    return R, Q, eps

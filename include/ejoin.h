@@ -216,6 +216,24 @@ ejoin_status ejoin_topk(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, int32_t k, con
 ejoin_status ejoin_top1(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, const ejoin_sel *selR,
                         const ejoin_sel *selS, ejoin_pairs *out);
 
+/* ℰ-selection of R against a batch of query vectors (Sec. III-C, Eq.
+ * (ℰ-Selection), with a cosine predicate per query; cost one scan of R,
+ * Sec. IV-A, Eq. (ℰ-Selection Cost)): every pair (i, q) with selR(i) and
+ * cos(R_i, Q_q) >= eps, written as {i, q, sim} (j is the query's row in Q).
+ * R.x, Q.x, the selection's arrays and out as for ejoin_threshold (device
+ * pointers; out->d_pairs NULL: the library allocates).  Q may hold any number
+ * of rows (processed 64 at a time).  The scan is a TF32 tensor-core product
+ * of R's FP32 rows with the normalised queries, the row norms taken from the
+ * same tiles; the guard band of TF32 (or the context's band) selects the
+ * candidates, which the FP32 re-score (and its accurate tier near eps)
+ * decides, so the result obeys the same rule as ejoin_threshold: exact
+ * outside |sim - eps| < 1e-5, sims within 1e-5.  The context's precision is
+ * not used.  Without selR, with R.x 16-byte aligned and R.ld % 4 == 0, R is
+ * read in place once; otherwise the kept rows are compacted and normalised
+ * first.  Synchronises; EOVERFLOW as for ejoin_threshold. */
+ejoin_status ejoin_eselect(ejoin_ctx *ctx, ejoin_rel R, const ejoin_sel *selR, ejoin_rel Q, float eps,
+                           ejoin_pairs *out);
+
 /* Release a result buffer that the library allocated. */
 ejoin_status ejoin_pairs_free(ejoin_ctx *ctx, ejoin_pairs *pairs);
 

@@ -102,6 +102,23 @@ bool make_tmap(CUtensorMap *m, const void *base, int fmt, int64_t kp, int64_t ro
 
 
 
+// FP32 rows of a caller's matrix read in place: d columns (the K extent; the box's columns past d read
+// as zeros), `rows` rows ld floats apart, a (32-float x box_rows) box, 128-byte swizzle.  Needs a
+// 16-byte aligned base and ld % 4 == 0.
+bool make_tmap_rows_f32(CUtensorMap *m, const float *base, int64_t d, int64_t ld, int64_t rows, uint32_t box_rows)
+{
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+    cuuint32_t box[2] = {32u, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 float default_band(int prec, int64_t kp)
 {
     const double g = (double)kp * std::ldexp(1.0, -24);  // FP32 accumulation over kp terms
@@ -744,6 +761,138 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     return EJOIN_OK;
 }
 
+// ℰ-selection (Sec. III-C, Eq. (ℰ-Selection)) of R against a batch of queries Q: the pairs (i, q) with
+// selR(i) and cos(R_i, Q_q) >= eps.  Without a selection, and for rows that meet the TMA alignment, the
+// scan reads R in place once (esel.cu); otherwise (or when a row's sum of squares leaves the FP32
+// range) the kept rows are first compacted and normalised.  The candidates of every 64-query chunk
+// go to one list, which the threshold join's re-score decides exactly.
+ejoin_status run_eselect(ejoin_ctx *c, const ejoin_rel &R, const ejoin_sel *selR, const ejoin_rel &Q, float eps,
+                         ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc, uint64_t *count_out)
+{
+    c->stats = ejoin_stats{};
+    if (!rel_ok(R) || !rel_ok(Q) || R.d != Q.d || !sel_ok(selR) || std::isnan(eps)) return EJOIN_EINVAL;
+    const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
+    const bool count_only = (c->flags & EJOIN_FLAG_COUNT_ONLY) != 0;
+    const int64_t kp = ejoin_padded_dim(EJOIN_TF32, R.d);
+    const float band = c->band_cfg >= 0.f ? c->band_cfg : default_band(EJOIN_TF32, kp);
+    c->stats.band = band;
+    const int64_t m = Q.n;
+    const int64_t n_chunks = (m + 63) / 64;
+    cudaError_t e;
+    Side &sa = c->side[0];
+    Side &sq = c->side[1];
+    const int64_t qrows = std::max<int64_t>(n_chunks, 1) * 64;
+    const int64_t rows = round_up(std::max<int64_t>(R.n, 1), 128);
+    if ((e = ensure(sq.norm, (size_t)qrows * kp * 4)) != cudaSuccess) return from_cuda(e);
+    if ((e = ensure(sq.inv, (size_t)qrows * 4)) != cudaSuccess) return from_cuda(e);
+    if ((e = ensure(sa.inv, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+    if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
+    if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    bool direct = !selR && R.n > 0 && R.ld % 4 == 0 && (reinterpret_cast<uintptr_t>(R.x) & 15) == 0;
+
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        c->stats.launches = 0;
+        if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), c->stream)) != cudaSuccess) return from_cuda(e);
+        if (timing) cudaEventRecord(c->ev[0], c->stream);
+        ejoin_status st = prepare_side(c, 1, Q, nullptr, FMT_F32, kp, sq.norm.p, kp, (float *)sq.inv.p, nullptr,
+                                       nullptr, &dm->n_sel[1], &dm->status, false);
+        if (st != EJOIN_OK) return st;
+        CUtensorMap tmR;
+        if (direct) {
+            if ((e = launch_set_count(&dm->n_sel[0], (long long)R.n, c->stream)) != cudaSuccess) return from_cuda(e);
+            c->stats.launches += 1;
+            if (!make_tmap_rows_f32(&tmR, R.x, R.d, R.ld, R.n, 128)) return EJOIN_ECUDA;
+        } else {
+            if ((e = ensure(sa.norm, (size_t)rows * kp * 4)) != cudaSuccess) return from_cuda(e);
+            if (selR && (e = ensure(sa.ids, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
+            st = prepare_side(c, 0, R, selR, FMT_F32, kp, sa.norm.p, kp, (float *)sa.inv.p, nullptr,
+                              (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false);
+            if (st != EJOIN_OK) return st;
+            if (!make_tmap(&tmR, sa.norm.p, FMT_F32, kp, rows, 128)) return EJOIN_ECUDA;
+        }
+        if (timing) cudaEventRecord(c->ev[1], c->stream);
+        auto scan = [&]() -> cudaError_t {
+            for (int64_t ch = 0; ch < n_chunks; ++ch) {
+                CUtensorMap tmQ;
+                if (!make_tmap(&tmQ, (const char *)sq.norm.p + (size_t)ch * 64 * kp * 4, FMT_F32, kp, 64, 64))
+                    return cudaErrorInvalidValue;
+                const int mc = (int)std::min<int64_t>(64, m - ch * 64);
+                cudaError_t ee = launch_esel(&tmR, &tmQ, (int)(kp / 32), &dm->n_sel[0], mc, (int)(ch * 64),
+                                             eps - band, (direct && ch == 0) ? (float *)sa.inv.p : nullptr,
+                                             (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status,
+                                             c->timeout, c->num_sms, c->stream);
+                if (ee != cudaSuccess) return ee;
+                c->stats.launches += 1;
+            }
+            return cudaSuccess;
+        };
+        if (m > 0 && R.n > 0 && (e = scan()) != cudaSuccess) return from_cuda(e);
+        if (timing) cudaEventRecord(c->ev[2], c->stream);
+        DevMisc hm;
+        auto read_misc = [&]() -> cudaError_t {
+            cudaError_t ee = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream);
+            return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
+        };
+        if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+        if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
+        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        if ((hm.status & ERR_RANGE) && direct) {
+            direct = false;  // a row needs the rescaling normalisation pass
+            continue;
+        }
+        if (hm.status) return EJOIN_ECUDA;
+        c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
+        c->stats.n_sel_s = (uint64_t)m;
+        while (hm.cand_count > c->cand_cap) {
+            c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+            if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+            if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+                return from_cuda(e);
+            if ((e = scan()) != cudaSuccess) return from_cuda(e);
+            if (timing) cudaEventRecord(c->ev[2], c->stream);
+            if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+            if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+            if (hm.status) return EJOIN_ECUDA;
+            c->stats.contract_retries++;
+        }
+        c->stats.candidates = hm.cand_count;
+        if (*pairs_io == nullptr && may_alloc && !count_only) {
+            const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
+            void *p = nullptr;
+            if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
+            *pairs_io = (ejoin_pair *)p;
+            *cap_io = cap;
+        }
+        if (*pairs_io == nullptr && !count_only) *cap_io = 0;
+        if ((e = ensure(c->band, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+        if (hm.cand_count) {
+            e = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, Q.x, Q.ld, R.d,
+                               (!direct && selR) ? (const uint32_t *)sa.ids.p : nullptr, nullptr,
+                               (const float *)sa.inv.p, (const float *)sq.inv.p, eps, c->fp64_band, *pairs_io,
+                               count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0,
+                               c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap, 0);
+            if (e != cudaSuccess) return from_cuda(e);
+            c->stats.launches += c->fp64_band > 0.f ? 2 : 1;
+        }
+        if (timing) cudaEventRecord(c->ev[3], c->stream);
+        if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+        c->stats.pairs = hm.pair_count;
+        c->stats.fp64_rescored = hm.band_count;
+        if (timing) {
+            c->stats.ms_normalize = elapsed(c->ev[0], c->ev[1]);
+            c->stats.ms_contract = elapsed(c->ev[1], c->ev[2]);
+            c->stats.ms_rescore = elapsed(c->ev[2], c->ev[3]);
+            c->stats.ms_total = elapsed(c->ev[0], c->ev[3]);
+        }
+        c->stats.fused = direct ? 1 : 0;
+        *count_out = hm.pair_count;
+        if (!count_only && hm.pair_count > *cap_io) return EJOIN_EOVERFLOW;
+        return EJOIN_OK;
+    }
+    return EJOIN_ECUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -776,6 +925,30 @@ ejoin_status ejoin_topk(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, int32_t k, const
     uint64_t cap = out->capacity;
     const bool alloc = p == nullptr;
     ejoin_status st = run_topk(c, R, S, k, selR, selS, &p, &cap, alloc, &count);
+    if (alloc && p) {
+        out->d_pairs = p;
+        out->capacity = cap;
+    }
+    out->count = count;
+    if (out->d_count && (st == EJOIN_OK || st == EJOIN_EOVERFLOW)) {
+        const uint64_t cnt = count;
+        if (cudaMemcpyAsync(out->d_count, &cnt, sizeof(uint64_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return EJOIN_ECUDA;
+    }
+    return st;
+}
+
+ejoin_status ejoin_eselect(ejoin_ctx *c, ejoin_rel R, const ejoin_sel *selR, ejoin_rel Q, float eps,
+                           ejoin_pairs *out)
+{
+    if (!c || !out) return EJOIN_EINVAL;
+    DeviceGuard g(c->device);
+    uint64_t count = 0;
+    ejoin_pair *p = out->d_pairs;
+    uint64_t cap = out->capacity;
+    const bool alloc = p == nullptr;
+    ejoin_status st = run_eselect(c, R, selR, Q, eps, &p, &cap, alloc, &count);
     if (alloc && p) {
         out->d_pairs = p;
         out->capacity = cap;

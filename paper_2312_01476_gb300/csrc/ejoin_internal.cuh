@@ -14,7 +14,9 @@
 namespace ej {
 
 // Bits of the device error word (DevMisc::status).
-enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+// ERR_RANGE: a row's FP32 sum of squares overflowed or underflowed in a kernel that does not rescale
+// (the host repeats the work through the rescaling normalisation pass)
+enum : unsigned { ERR_NONFINITE = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u, ERR_RANGE = 8u };
 
 // Storage format of normalised rows.
 enum Fmt : int { FMT_F32 = 0, FMT_BF16 = 1, FMT_FP8 = 2 };
@@ -218,6 +220,13 @@ inline int default_group_m(int64_t kp)
     return (int)g;
 }
 size_t sim_tc_smem_bytes();
+// ℰ-selection scan (esel.cu): candidates (row of R, col_base + c) for the queries c < m with
+// acc >= thr_rel * ||row||, acc the TF32 product of the FP32 rows (tmR: box 32 x 128, 128-byte swizzle)
+// with up to 64 normalised queries (tmQ: box 32 x 64); writes 1/||row|| to inv_out when given.
+// nR: device row count.  ERR_RANGE in *status: a row's sum of squares left the FP32 range.
+cudaError_t launch_esel(const CUtensorMap *tmR, const CUtensorMap *tmQ, int num_kb, const long long *nR, int m,
+                        int col_base, float thr_rel, float *inv_out, uint2 *cand, uint64_t cap,
+                        unsigned long long *cand_count, unsigned *status, uint64_t timeout, int grid, cudaStream_t st);
 // Top-k join condition (topk.cu).  Group maxima per row of the first pass: at most this many.
 constexpr int64_t TOPK_MAX_GROUPS = 8192;
 constexpr int TOPK_MAX_K = 32;

@@ -117,6 +117,9 @@ def load_library(path: str = LIB_PATH):
                                          P(ejoin_sel), ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_uint64)]
     lib.ejoin_top1.restype = ctypes.c_int
     lib.ejoin_top1.argtypes = [ctypes.c_void_p, ejoin_rel, ejoin_rel, P(ejoin_sel), P(ejoin_sel), P(ejoin_pairs)]
+    lib.ejoin_eselect.restype = ctypes.c_int
+    lib.ejoin_eselect.argtypes = [ctypes.c_void_p, ejoin_rel, P(ejoin_sel), ejoin_rel, ctypes.c_float,
+                                  P(ejoin_pairs)]
     lib.ejoin_topk.restype = ctypes.c_int
     lib.ejoin_topk.argtypes = [ctypes.c_void_p, ejoin_rel, ejoin_rel, ctypes.c_int32, P(ejoin_sel), P(ejoin_sel),
                                P(ejoin_pairs)]
@@ -324,6 +327,30 @@ def ejoin_threshold(ctx: Ctx, R, S, eps: float, selR: Optional[Sel] = None, selS
         v = ctx._out[:n]
         return Result(v[:, 0], v[:, 1], v[:, 2].view(torch.float32), n)
     raise EJoinError(EJOIN_EOVERFLOW, "ejoin_threshold")
+
+
+def ejoin_eselect(ctx: Ctx, R, Q, eps: float, selR: Optional[Sel] = None, capacity: Optional[int] = None) -> Result:
+    """Device ℰ-selection (Sec. III-C, Eq. (ℰ-Selection)) of the rows of CUDA tensor R against the query
+    rows of CUDA tensor Q: every (i, q) with selR(i) and cos(R_i, Q_q) >= eps, as (i, j = q, sim).
+    Returns views of a cached device result buffer (valid until the next call on ctx)."""
+    import torch
+    lib = load_library()
+    rR, rQ = _dev_rel(R), _dev_rel(Q)
+    sR = _dev_sel(selR)
+    cap = capacity or (ctx._out.shape[0] if ctx._out is not None else 1 << 16)
+    for _ in range(3):
+        if ctx._out is None or ctx._out.shape[0] < cap:
+            ctx._out = torch.empty((cap, 3), dtype=torch.int32, device=R.device)
+        out = ejoin_pairs(ctypes.c_void_p(ctx._out.data_ptr()), ctx._out.shape[0], None, 0)
+        st = lib.ejoin_eselect(ctx.handle, rR, _sel_ptr(sR), rQ, ctypes.c_float(eps), ctypes.byref(out))
+        if st == EJOIN_EOVERFLOW:
+            cap = int(out.count) + 1024
+            continue
+        _check(st, "ejoin_eselect")
+        n = int(out.count)
+        v = ctx._out[:n]
+        return Result(v[:, 0], v[:, 1], v[:, 2].view(torch.float32), n)
+    raise EJoinError(EJOIN_EOVERFLOW, "ejoin_eselect")
 
 
 def ejoin_topk(ctx: Ctx, R, S, k: int, selR: Optional[Sel] = None, selS: Optional[Sel] = None) -> Result:
