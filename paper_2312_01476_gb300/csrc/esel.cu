@@ -201,13 +201,14 @@ __global__ void __launch_bounds__(E_THREADS, 1)
                     ok = false;
                     break;
                 }
-                // the row's 128 bytes of this stage (16-byte chunks permuted by the swizzle: the sum of
-                // squares does not depend on their order)
+                // the row's 128 bytes of this stage, 16-byte chunk j ^ (lane & 7) at step j: the rows of a
+                // quarter-warp start on the same bank, so this order puts their chunks on distinct banks
+                // (and the sum of squares does not depend on the order)
                 const float4 *row = reinterpret_cast<const float4 *>(smem + E_OFF_A + stage * E_A_STAGE + r * 128);
                 float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float4 v = row[j];
+                    const float4 v = row[j ^ (lane & 7)];
                     p0 = fmaf(v.x, v.x, p0);
                     p1 = fmaf(v.y, v.y, p1);
                     p2 = fmaf(v.z, v.z, p2);
