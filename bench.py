@@ -57,23 +57,27 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def contract_source_sha():
+ESEL_SOURCES = ["esel.cu", "ejoin_internal.cuh"]
+
+
+def contract_source_sha(sources=None):
     h = hashlib.sha256()
-    for f in CONTRACT_SOURCES:
+    for f in sources or CONTRACT_SOURCES:
         with open(os.path.join(ROOT, "paper_2312_01476_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel_key: str):
-    """DRAM bytes per launch from a committed ncu summary, if its source hash still matches."""
+def recorded_traffic(kernel_key: str, sources=None):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's sources still hash to the
+    recorded value."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         t = json.load(f)
     e = t.get(kernel_key)
-    if not e or e.get("source_sha") != contract_source_sha():
+    if not e or e.get("source_sha") != contract_source_sha(sources):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -526,7 +530,7 @@ def run_eselect(args):
     achieved = algo_bytes / (s_ms * 1e-3) / 1e9
     roofline = {"kernel": "esel_kernel", "bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                "peak_note": f"STREAM-style copy, {pk['source']}", "traffic": recorded_traffic("esel_kernel_esel"),
+                "peak_note": f"STREAM-style copy, {pk['source']}", "traffic": recorded_traffic("esel_kernel_esel", ESEL_SOURCES),
                 "bytes_per_launch": algo_bytes, "ms_per_launch": round(s_ms, 4)}
     e2e = None
     if not args.no_e2e:
