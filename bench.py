@@ -205,9 +205,66 @@ def cpu_oracle_topk_sample(w, k: int, target_s: float, threads: int):
             "seconds": round(dt, 3)}
 
 
+def reference_sampled(args, threads):
+    """The oracle on a bounded sample of the batched (c4), learned (c5) and E-selection workloads, whose
+    full inputs are generated on the device: same recipes, a few rows of R against a block of S (or the
+    queries), pairs/s extrapolated to the full step."""
+    import oracle
+    import ejoin_inputs as inputs
+    if args.workload == "esel":
+        d, m, eps, seed = 768, 32, 0.9, inputs.seed_for(7)
+        centres = inputs.sphere_centres(20_000, d, seed)
+        R = inputs.clustered(20_000, d, centres, inputs.THETA_768, seed + 10, threads)
+        S = inputs.clustered(m, d, centres, inputs.THETA_768, seed + 20, threads)
+        full, metric = 10_000_000 * m, METRIC_ESEL
+        name = "E-selection: R = 10000000 x 768 clustered rows (20,000 centres), 32 queries, eps=0.9"
+        sample = "20,000 rows x 32 queries (FP64)"
+    elif args.workload == "c4":
+        d, eps, seed = 384, 0.875, inputs.seed_for(4)
+        centres = inputs.sphere_centres(1000, d, seed)
+        R = inputs.clustered(64, d, centres, 0.3, seed + 1, threads)
+        S = inputs.clustered(20_000, d, centres, 0.3, seed + 2, threads)
+        sizes, _ = inputs.c4_batch_sizes()
+        full, metric = int((sizes[:, 0] * sizes[:, 1]).sum()), METRIC
+        name = "batched joins: 512 jobs, lognormal sizes (median 20,000), d=384"
+        sample = "64 rows x 20,000 rows of a median-size job (FP64)"
+    else:  # c5
+        d, eps, seed = 768, 0.9, inputs.seed_for(5)
+        centres = inputs.sphere_centres(20_000, d, seed)
+        S = inputs.clustered(200_000, d, centres, inputs.THETA_768, seed + 10, threads)
+        R = S[:8]
+        full, metric = 4_000_000 ** 2, METRIC
+        name = "clustered self-join n=4000000 d=768 eps=0.90"
+        sample = "8 rows x 200,000 rows of the same recipe (FP64)"
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        n_calls = 0
+        while True:
+            oracle.join(R, S, eps, threads=threads)
+            n_calls += 1
+            if time.perf_counter() - t >= min(args.ref_step_s, 5.0):
+                break
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            vals.append(n_calls * R.shape[0] * S.shape[0] / dt)
+    return name, metric, full, statistics.median(vals), sample
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
+        return
+    if args.workload in ("c4", "c5", "esel"):
+        threads = os.cpu_count() or 1
+        name, metric, full, v, sample = reference_sampled(args, threads)
+        out = {"impl": "reference", "metric": metric, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": full / v * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": name, "pairs_per_step": full},
+               "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+               "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
         return
     w = make_workload(args)
     if args.workload.startswith("top"):
