@@ -812,6 +812,42 @@ def run_learned(args):
     ctx.close()
 
 
+def measure_library_peaks():
+    """cuBLAS dense throughput on this GPU for the three tensor-core input types of the contraction
+    (8192^3 products, 50 timed iterations after 5 warm-up ones): context for the nominal FP8/BF16 and
+    TF32/BF16 ratios the rooflines use."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = True
+    n = 8192
+
+    def timeit(fn, iters=50):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(iters):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / iters
+
+    out = {}
+    A = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    B = torch.randn(n, n, device="cuda", dtype=torch.bfloat16)
+    out["bf16_tflops"] = 2 * n ** 3 / timeit(lambda: A @ B) / 1e9
+    A32, B32 = A.float(), B.float()
+    out["tf32_tflops"] = 2 * n ** 3 / timeit(lambda: A32 @ B32) / 1e9
+    A8 = A.to(torch.float8_e4m3fn)
+    B8 = B.to(torch.float8_e4m3fn).t().contiguous().t()
+    one = torch.ones((), device="cuda")
+    out["fp8_e4m3_tflops"] = 2 * n ** 3 / timeit(
+        lambda: torch._scaled_mm(A8, B8, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)) / 1e9
+    out["tf32_over_bf16"] = out["tf32_tflops"] / out["bf16_tflops"]
+    out["fp8_over_bf16"] = out["fp8_e4m3_tflops"] / out["bf16_tflops"]
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -823,6 +859,7 @@ def main():
                     choices=["c2", "c2-capture", "c1", "c3", "c3-capture", "c4", "c5", "top1", "top1-capture",
                              "top32", "top32-capture", "esel"])
     ap.add_argument("--esel-rows", type=int, default=10_000_000, help="rows of R for --workload esel")
+    ap.add_argument("--peaks", action="store_true", help="print cuBLAS BF16 / TF32 / FP8 throughput and exit")
     ap.add_argument("--sel-pct", type=int, default=100,
                     help="top-k workloads: percent of S kept by the predicate attr < sel-pct")
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
@@ -832,6 +869,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true", help="accepted for compatibility; parity lives in tests/")
     args = ap.parse_args()
+    if args.peaks:
+        measure_library_peaks()
+        return
     if args.warmup < 3 and args.impl == "ejoin":
         log("warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
