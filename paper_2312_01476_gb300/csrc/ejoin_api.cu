@@ -359,6 +359,27 @@ float elapsed(cudaEvent_t a, cudaEvent_t b)
     return ms;
 }
 
+// The device error word as a status: non-finite input first, then an expired wait, then anything else.
+ejoin_status status_of(unsigned err)
+{
+    if (err & ERR_NONFINITE) return EJOIN_ENONFINITE;
+    if (err & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+    return err ? EJOIN_ECUDA : EJOIN_OK;
+}
+
+// Workspace of one operand side: n rows (rounded up to whole 256-row tiles) of kp elements in format fmt,
+// their inverse norms, e4m3 scales, and the kept-row ids when a selection is given.
+cudaError_t ensure_operand(Side &sd, int64_t n, int64_t kp, int fmt, bool with_ids)
+{
+    const int64_t rows = round_up(std::max<int64_t>(n, 1), 256);
+    cudaError_t e;
+    if ((e = ensure(sd.norm, (size_t)rows * kp * fmt_bytes(fmt))) != cudaSuccess) return e;
+    if ((e = ensure(sd.inv, (size_t)rows * 4)) != cudaSuccess) return e;
+    if (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4)) != cudaSuccess) return e;
+    if (with_ids && (e = ensure(sd.ids, (size_t)rows * 4)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 // Device pipeline shared by ejoin_threshold and ejoin_threshold_host.
 ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, float eps, const ejoin_sel *selR,
                            const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
@@ -372,7 +393,6 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     const int prec = c->prec;
     const int fmt = fmt_of(prec);
     const int64_t kp = ejoin_padded_dim(prec, R.d);
-    const size_t eb = fmt_bytes(fmt);
     const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld && same_sel(selR, selS);
     const float band = c->band_cfg >= 0.f ? c->band_cfg : default_band(prec, kp);
     c->stats.band = band;
@@ -381,14 +401,9 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     // workspace
     const ejoin_rel *rels[2] = {&R, &S};
     const ejoin_sel *sels[2] = {selR, selS};
-    for (int w = 0; w < (self ? 1 : 2); ++w) {
-        const int64_t rows = round_up(std::max<int64_t>(rels[w]->n, 1), 256);
-        Side &sd = c->side[w];
-        if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) != cudaSuccess) return from_cuda(e);
-        if ((e = ensure(sd.inv, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
-        if (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
-        if (sels[w] && (e = ensure(sd.ids, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
-    }
+    for (int w = 0; w < (self ? 1 : 2); ++w)
+        if ((e = ensure_operand(c->side[w], rels[w]->n, kp, fmt, sels[w] != nullptr)) != cudaSuccess)
+            return from_cuda(e);
     if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
     if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
     DevMisc *dm = (DevMisc *)c->misc.p;
@@ -461,9 +476,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
         c->stats.n_sel_r = (uint64_t)hf.n_sel[0];
         c->stats.n_sel_s = (uint64_t)(self ? hf.n_sel[0] : hf.n_sel[1]);
-        if (hf.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
-        if (hf.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
-        if (hf.status) return EJOIN_ECUDA;
+        if (hf.status) return status_of(hf.status);
         c->stats.candidates = hf.cand_count;
         c->stats.pairs = hf.pair_count;
         c->stats.fp64_rescored = hf.band_count;
@@ -510,9 +523,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
     c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
     c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
-    if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
-    if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
-    if (hm.status) return EJOIN_ECUDA;
+    if (hm.status) return status_of(hm.status);
     while (hm.cand_count > c->cand_cap) {
         // candidate buffer too small: grow and run the contraction again
         c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
@@ -522,7 +533,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         if ((st = contract()) != EJOIN_OK) return st;
         if (timing) cudaEventRecord(c->ev[2], c->stream);
         if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
-        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
+        if (hm.status) return status_of(hm.status);
         c->stats.contract_retries++;
     }
     c->stats.candidates = hm.cand_count;
@@ -586,21 +597,15 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
     const int fmt = fmt_of(prec);
     const int64_t kp = ejoin_padded_dim(prec, R.d);
-    const size_t eb = fmt_bytes(fmt);
     const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld && same_sel(selR, selS);
     const float band = c->band_cfg >= 0.f ? c->band_cfg : default_band(prec, kp);
     c->stats.band = band;
     cudaError_t e;
     const ejoin_rel *rels[2] = {&R, &S};
     const ejoin_sel *sels[2] = {selR, selS};
-    for (int w = 0; w < (self ? 1 : 2); ++w) {
-        const int64_t rows = round_up(std::max<int64_t>(rels[w]->n, 1), 256);
-        Side &sd = c->side[w];
-        if ((e = ensure(sd.norm, (size_t)rows * kp * eb)) != cudaSuccess) return from_cuda(e);
-        if ((e = ensure(sd.inv, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
-        if (fmt == FMT_FP8 && (e = ensure(sd.scale, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
-        if (sels[w] && (e = ensure(sd.ids, (size_t)rows * 4)) != cudaSuccess) return from_cuda(e);
-    }
+    for (int w = 0; w < (self ? 1 : 2); ++w)
+        if ((e = ensure_operand(c->side[w], rels[w]->n, kp, fmt, sels[w] != nullptr)) != cudaSuccess)
+            return from_cuda(e);
     const int64_t rowsA = round_up(std::max<int64_t>(R.n, 1), 256);
     const int64_t rowsB = round_up(std::max<int64_t>(S.n, 1), 256);
     // column groups of pass 0: 256 columns (one column tile), wider when the group maxima would
@@ -691,9 +696,7 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
     c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
     c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
-    if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
-    if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
-    if (hm.status) return EJOIN_ECUDA;
+    if (hm.status) return status_of(hm.status);
     while (hm.cand_count > c->cand_cap) {
         // candidate buffer too small: grow it and run pass 1 again (the thresholds stay)
         c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
@@ -703,8 +706,7 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
         if ((e = pass1()) != cudaSuccess) return from_cuda(e);
         if (timing) cudaEventRecord(c->ev[2], c->stream);
         if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
-        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
-        if (hm.status) return EJOIN_ECUDA;
+        if (hm.status) return status_of(hm.status);
         c->stats.contract_retries++;
     }
     c->stats.candidates = hm.cand_count;
@@ -835,13 +837,11 @@ ejoin_status run_eselect(ejoin_ctx *c, const ejoin_rel &R, const ejoin_sel *selR
             return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
         };
         if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
-        if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
-        if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
-        if ((hm.status & ERR_RANGE) && direct) {
+        if ((hm.status & ERR_RANGE) && !(hm.status & (ERR_NONFINITE | ERR_TIMEOUT)) && direct) {
             direct = false;  // a row needs the rescaling normalisation pass
             continue;
         }
-        if (hm.status) return EJOIN_ECUDA;
+        if (hm.status) return status_of(hm.status);
         c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
         c->stats.n_sel_s = (uint64_t)m;
         while (hm.cand_count > c->cand_cap) {
@@ -852,8 +852,7 @@ ejoin_status run_eselect(ejoin_ctx *c, const ejoin_rel &R, const ejoin_sel *selR
             if ((e = scan()) != cudaSuccess) return from_cuda(e);
             if (timing) cudaEventRecord(c->ev[2], c->stream);
             if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
-            if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
-            if (hm.status) return EJOIN_ECUDA;
+            if (hm.status) return status_of(hm.status);
             c->stats.contract_retries++;
         }
         c->stats.candidates = hm.cand_count;
