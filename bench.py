@@ -501,11 +501,13 @@ def run_topk(args):
     clocks = sampler.stop()
     ms = statistics.mean(step_ms)
     c_ms = statistics.mean(cms)
-    # executed FLOPs, 2 d per evaluated pair: k = 1 evaluates every kept pair once (one pass); k > 1
-    # adds the first pass over every stride-th 256-column tile (stride 8 while at least 4k tiles remain)
-    passes = 1 if k == 1 else 2
+    # executed FLOPs, 2 d per evaluated pair: BF16/TF32 top-1 evaluates every kept pair once (one pass);
+    # k > 1 and e4m3 add the first pass over every stride-th 256-column tile (stride 8 while at least 4k
+    # tiles remain)
+    two_pass = k > 1 or args.prec == "fp8"
+    passes = 2 if two_pass else 1
     flop = 2.0 * d * pairs
-    if k > 1:
+    if two_pass:
         n_s = int(st0["n_sel_s"])
         tiles = -(-n_s // 256)
         stride = max(1, min(8, tiles // (4 * k)))
@@ -513,9 +515,9 @@ def run_topk(args):
     peak, note = tensor_peak(args.prec, c_ms / passes)
     achieved = flop / (c_ms * 1e-3) / 1e12
     kernel_key = f"sim_tc_top_{args.prec}_{args.workload}"
-    roofline = {"kernel": kernel_key + (" (single pass)" if k == 1 else " (passes 0 + 1)"), "bound": "tensor",
+    roofline = {"kernel": kernel_key + (" (passes 0 + 1)" if two_pass else " (single pass)"), "bound": "tensor",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "peak_note": note + ("" if k == 1 else "; both passes and the threshold kernel between them"),
+                "peak_note": note + ("; both passes and the threshold kernel between them" if two_pass else ""),
                 "traffic": recorded_traffic(kernel_key), "flop_per_step": flop, "ms_contract": round(c_ms, 4)}
     # end to end through the public API: pinned host inputs copied in, the records copied out
     e2e = None

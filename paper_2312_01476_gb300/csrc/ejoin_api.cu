@@ -579,12 +579,12 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     return EJOIN_OK;
 }
 
-// Top-k join condition (Sec. VI-E) on the tensor cores, 1 <= k <= 32.  k > 1: pass 0 takes every
-// R row's largest bulk similarity per column group, and the k-th largest group maximum, a lower
+// Top-k join condition (Sec. VI-E) on the tensor cores, 1 <= k <= 32.  k > 1 (and e4m3): pass 0 takes
+// every R row's largest bulk similarity per column group, and the k-th largest group maximum, a lower
 // bound of the row's k-th largest bulk similarity, becomes its threshold; pass 1 keeps the columns
 // within 2 * band of the threshold: the bulk error is at most band, so they hold the exact top k.
-// k = 1: a single pass keeps the columns within 2 * band of the running row maximum.  The FP32
-// re-score then picks the best k of the candidates per row.
+// k = 1 otherwise: a single pass keeps the columns within 2 * band of the running row maximum.  The
+// FP32 re-score then picks the best k of the candidates per row.
 ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int k, const ejoin_sel *selR,
                       const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
                       uint64_t *count_out)
@@ -608,39 +608,33 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
             return from_cuda(e);
     const int64_t rowsA = round_up(std::max<int64_t>(R.n, 1), 256);
     const int64_t rowsB = round_up(std::max<int64_t>(S.n, 1), 256);
+    // k > 1, and e4m3 at any k (whose wide band makes the early running maximum of one pass a poor
+    // threshold): a sampled first pass and a threshold kernel before the candidate pass
+    const bool two_pass = k > 1 || fmt == FMT_FP8;
     // column groups of pass 0: 256 columns (one column tile), wider when the group maxima would
     // exceed TOPK_MAX_GROUPS per row or 4 GiB in all
     int shift = 62;
     int64_t ld = 1;
-    if (k > 1) {
+    if (two_pass) {
         const int64_t nS = std::max<int64_t>(S.n, 1);
         for (shift = 8;; ++shift) {
             ld = ((nS - 1) >> shift) + 1;
             if (ld <= TOPK_MAX_GROUPS && (double)rowsA * (double)ld * 4.0 <= 4294967296.0) break;
         }
     }
-    // per-row scratch: k = 1: best (u64) and the row maximum (u32); k > 1: threshold, count, offset,
-    // fill (u32 each) and the group maxima
-    const size_t top_bytes = k == 1 ? (size_t)rowsA * 12 : (size_t)rowsA * 16 + (size_t)rowsA * ld * 4;
+    // per-row scratch, zeroed: the best key (u64, k = 1); the threshold or running maximum, count,
+    // offset and fill (u32 each); the group maxima of pass 0
+    const size_t top_bytes = (size_t)rowsA * 24 + (two_pass ? (size_t)rowsA * ld * 4 : 0);
     if ((e = ensure(c->top, top_bytes)) != cudaSuccess) return from_cuda(e);
     unsigned long long *best = (unsigned long long *)c->top.p;
-    unsigned *row_max = (unsigned *)(best + rowsA);
-    unsigned *thr = (unsigned *)c->top.p;
+    unsigned *thr = (unsigned *)(best + rowsA);
     unsigned *row_cnt = thr + rowsA, *row_off = thr + 2 * rowsA, *row_fill = thr + 3 * rowsA;
     unsigned *gmax = thr + 4 * rowsA;
     if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
     if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
     DevMisc *dm = (DevMisc *)c->misc.p;
     if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), c->stream)) != cudaSuccess) return from_cuda(e);
-    if (k == 1) {
-        e = cudaMemsetAsync(c->top.p, 0, top_bytes, c->stream);
-    } else {
-        // counts and fills, and the group maxima (the threshold and offsets are written in full)
-        e = cudaMemsetAsync(row_cnt, 0, (size_t)rowsA * 4, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(row_fill, 0, (size_t)rowsA * 4, c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(gmax, 0, (size_t)rowsA * ld * 4, c->stream);
-    }
-    if (e != cudaSuccess) return from_cuda(e);
+    if ((e = cudaMemsetAsync(c->top.p, 0, top_bytes, c->stream)) != cudaSuccess) return from_cuda(e);
 
     if (timing) cudaEventRecord(c->ev[0], c->stream);
     Side &sa = c->side[0];
@@ -664,25 +658,23 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     const int kind = prec == EJOIN_BF16 ? 0 : (prec == EJOIN_FP8_E4M3 ? 1 : 2);
     const int gm = c->group_m > 0 ? c->group_m : default_group_m(kp);
     const float margin = 2.f * band;
-    unsigned *pass0_out = k == 1 ? row_max : gmax;
-    unsigned *pass1_thr = k == 1 ? row_max : thr;
-    if (k > 1) {
+    if (two_pass) {
         // pass 0 on every 8th column tile (at least 4k of them): the k-th largest maximum over any set
         // of column groups bounds the k-th largest similarity from below, the sample only loosens it
         e = launch_sim_tc_top(kind, 0, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
-                              (const float *)sb.scale.p, pass0_out, ld, shift, TOPK_SAMPLE_STRIDE, 4 * k, margin,
+                              (const float *)sb.scale.p, gmax, ld, shift, TOPK_SAMPLE_STRIDE, 4 * k, margin,
                               (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status, c->timeout, c->num_sms,
                               gm, c->stream);
         if (e == cudaSuccess) e = launch_topk_threshold(gmax, ld, shift, nA, rowsA, nB, k, thr, c->num_sms, c->stream);
         if (e != cudaSuccess) return from_cuda(e);
         c->stats.launches += 2;
     }
-    // k = 1: one pass on the running row maximum (a repeat after a candidate overflow starts from the
-    // final maxima and keeps only the columns within the margin of them)
+    // one pass (k = 1, not e4m3): on the running row maximum in thr (a repeat after a candidate overflow
+    // starts from the final maxima and keeps only the columns within the margin of them)
     auto pass1 = [&]() -> cudaError_t {
         c->stats.launches += 1;
-        return launch_sim_tc_top(kind, k == 1 ? 2 : 1, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
-                                 (const float *)sb.scale.p, pass1_thr, 1, 62, 1, 1, margin, (uint2 *)c->cand.p,
+        return launch_sim_tc_top(kind, two_pass ? 1 : 2, &tmA, &tmB, (int)kp, nA, nB, (const float *)sa.scale.p,
+                                 (const float *)sb.scale.p, thr, 1, 62, 1, 1, margin, (uint2 *)c->cand.p,
                                  c->cand_cap,
                                  &dm->cand_count, &dm->status, c->timeout, c->num_sms, gm, c->stream);
     };
