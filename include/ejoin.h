@@ -229,8 +229,10 @@ ejoin_status ejoin_top1(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, const ejoin_se
  * decides, so the result obeys the same rule as ejoin_threshold: exact
  * outside |sim - eps| < 1e-5, sims within 1e-5.  The context's precision is
  * not used.  Without selR, with R.x 16-byte aligned and R.ld % 4 == 0, R is
- * read in place once; otherwise the kept rows are compacted and normalised
- * first.  Synchronises; EOVERFLOW as for ejoin_threshold. */
+ * read in place once per 64 queries; otherwise the kept rows are compacted
+ * and normalised first.  For batches of hundreds of queries or more,
+ * ejoin_threshold(R, Q, eps, selR, NULL) reads R once for all of them and is
+ * the faster call.  Synchronises; EOVERFLOW as for ejoin_threshold. */
 ejoin_status ejoin_eselect(ejoin_ctx *ctx, ejoin_rel R, const ejoin_sel *selR, ejoin_rel Q, float eps,
                            ejoin_pairs *out);
 
