@@ -520,52 +520,69 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         cudaError_t ee = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream);
         return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
     };
-    if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
-    c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
-    c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
-    if (hm.status) return status_of(hm.status);
-    while (hm.cand_count > c->cand_cap) {
-        // candidate buffer too small: grow and run the contraction again
-        c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
-        if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
-        if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
-            return from_cuda(e);
-        if ((st = contract()) != EJOIN_OK) return st;
-        if (timing) cudaEventRecord(c->ev[2], c->stream);
+    // exact re-score of the candidates (it reads their count on the device)
+    auto rescore = [&]() -> cudaError_t {
+        cudaError_t ee = ensure(c->band, c->cand_cap * sizeof(uint2));
+        if (ee != cudaSuccess) return ee;
+        ee = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
+                            selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
+                            (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
+                            count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0,
+                            c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0);
+        if (ee != cudaSuccess) return ee;
+        c->stats.launches += c->fp64_band > 0.f ? 2 : 1;
+        if (timing) cudaEventRecord(c->ev[3], c->stream);
+        if (d_count_user)
+            ee = cudaMemcpyAsync(d_count_user, &dm->pair_count, sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                                 c->stream);
+        return ee;
+    };
+    // With the result buffer known, the re-score is launched before the candidate count is read back:
+    // one host synchronisation per call.  If the candidates overflowed their buffer, its pairs are
+    // discarded and the call continues as below.
+    bool done = false;
+    if (*pairs_io != nullptr || count_only) {
+        if ((e = rescore()) != cudaSuccess) return from_cuda(e);
         if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
         if (hm.status) return status_of(hm.status);
-        c->stats.contract_retries++;
+        done = hm.cand_count <= c->cand_cap;
+        if (!done) {
+            if ((e = cudaMemsetAsync(&dm->pair_count, 0, 2 * sizeof(unsigned long long), c->stream)) != cudaSuccess)
+                return from_cuda(e);
+        }
+    } else {
+        if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+        if (hm.status) return status_of(hm.status);
     }
+    if (!done) {
+        while (hm.cand_count > c->cand_cap) {
+            // candidate buffer too small: grow and run the contraction again
+            c->cand_cap = hm.cand_count + hm.cand_count / 4 + 1024;
+            if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+            if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess)
+                return from_cuda(e);
+            if ((st = contract()) != EJOIN_OK) return st;
+            if (timing) cudaEventRecord(c->ev[2], c->stream);
+            if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+            if (hm.status) return status_of(hm.status);
+            c->stats.contract_retries++;
+        }
+        // result buffer
+        if (*pairs_io == nullptr && may_alloc && !count_only) {
+            const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
+            void *p = nullptr;
+            if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
+            *pairs_io = (ejoin_pair *)p;
+            *cap_io = cap;
+        }
+        if (*pairs_io == nullptr && !count_only) *cap_io = 0;
+        if ((e = rescore()) != cudaSuccess) return from_cuda(e);
+        if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+        if (hm.status) return status_of(hm.status);
+    }
+    c->stats.n_sel_r = (uint64_t)hm.n_sel[0];
+    c->stats.n_sel_s = (uint64_t)(self ? hm.n_sel[0] : hm.n_sel[1]);
     c->stats.candidates = hm.cand_count;
-
-    // result buffer
-    if (*pairs_io == nullptr && may_alloc && !count_only) {
-        const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
-        void *p = nullptr;
-        if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
-        *pairs_io = (ejoin_pair *)p;
-        *cap_io = cap;
-    }
-    if (*pairs_io == nullptr && !count_only) *cap_io = 0;
-
-    // exact re-score of the candidates
-    if ((e = ensure(c->band, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
-    e = hm.cand_count == 0 ? cudaSuccess : launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
-                       selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
-                       (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
-                       count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0, c->num_sms,
-                       c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0);
-    if (e != cudaSuccess) return from_cuda(e);
-    c->stats.launches += hm.cand_count ? (c->fp64_band > 0.f ? 2 : 1) : 0;
-    if (timing) cudaEventRecord(c->ev[3], c->stream);
-    if (d_count_user) {
-        if ((e = cudaMemcpyAsync(d_count_user, &dm->pair_count, sizeof(uint64_t), cudaMemcpyDeviceToDevice,
-                                 c->stream)) != cudaSuccess)
-            return from_cuda(e);
-    }
-    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-        return from_cuda(e);
-    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
     c->stats.pairs = hm.pair_count;
     c->stats.fp64_rescored = hm.band_count;
     if (timing) {
