@@ -730,7 +730,7 @@ def run_batch(args):
 
 
 def run_learned(args):
-    """4M-row self-join with learned tile pruning vs the plain BF16 join (the judge)."""
+    """4M-row self-join with learned tile pruning against the plain BF16 join, which checks its result."""
     import torch
     import ejoin_inputs as inputs
     import paper_2312_01476_gb300 as pkg
