@@ -414,10 +414,13 @@ def run_ejoin(args):
             e_ms.append(a.elapsed_time(b))
             h2d_ms.append(pkg.ejoin_last_stats(ctx)["ms_h2d"])
         em = statistics.mean(e_ms)
-        h2d = w.R.nbytes + (0 if w.self_join else w.S.nbytes) + (w.attrR.nbytes if w.attrR is not None else 0)
-        e2e = {"value": world * pairs_per_step / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        hst = pkg.ejoin_last_stats(ctx)
+        # bytes that crossed the host link: with pinned inputs the kernels read only the predicate columns and
+        # the kept rows in place; otherwise the inputs are copied whole
+        e2e = {"value": world * pairs_per_step / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(hst["h2d_bytes"]),
                "d2h_bytes_per_step": int(cnt * 12 + 8), "ms_per_step": round(em, 3),
-               "ms_h2d": round(statistics.mean(h2d_ms), 3)}
+               "inputs_read_in_place": bool(hst["host_in_place"]),
+               "ms_h2d_copies": round(statistics.mean(h2d_ms), 3)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -77,6 +77,8 @@ typedef enum ejoin_prec {
                                       self-join on the tensor cores contracts only the 256-row block
                                       pairs on and above the diagonal and writes every pair (i, j),
                                       i != j, in both orders; the result is the same set */
+#define EJOIN_FLAG_HOST_COPY  0x10u /* ejoin_threshold_host: copy the inputs to the device whole even when
+                                       the kernels could read them in place (see there) */
 
 typedef struct ejoin_config {
     int32_t device;          /* CUDA device ordinal */
@@ -152,6 +154,10 @@ typedef struct ejoin_stats {
     float ms_h2d, ms_d2h;       /* ejoin_threshold_host only, FLAG_TIMING only */
     int32_t contract_retries;   /* candidate-buffer regrowths */
     int32_t fused;              /* 1 if the re-score ran fused into the contraction */
+    uint64_t h2d_bytes;         /* ejoin_threshold_host only: bytes read from host memory (copied, or read
+                                   in place by the kernels) */
+    int32_t host_in_place;      /* ejoin_threshold_host only: 1 if the kernels read the host buffers in place */
+    int32_t reserved;
 } ejoin_stats;
 
 /* Create a context on cfg->device (made current for the call).  cfg may be
@@ -188,9 +194,15 @@ ejoin_status ejoin_threshold(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, float eps
                              const ejoin_sel *selR, const ejoin_sel *selS, ejoin_pairs *out);
 
 /* Same operator with HOST inputs and a HOST result buffer: R.x, S.x, the
- * selections' arrays and h_pairs are host pointers (pinned memory gives full
- * copy bandwidth).  The inputs are copied to the device, joined, and the
- * pairs copied back; *count receives the total (EOVERFLOW as above). */
+ * selections' arrays and h_pairs are host pointers; *count receives the total
+ * (EOVERFLOW as above).  When every input buffer is device-accessible host
+ * memory (pinned, e.g. cudaHostAlloc or cudaHostRegister), the selection
+ * kernels read the attribute columns in place and the normalisation pass reads
+ * only the kept rows in place, copying them to the device for the re-score: the
+ * relational predicate is pushed below the host-to-device transfer (Sec. VI-E
+ * pre-filter), and only the kept rows cross the link.  Otherwise (pageable
+ * memory, or EJOIN_FLAG_HOST_COPY) the inputs are copied whole first.  The
+ * pairs are copied back to h_pairs in either case. */
 ejoin_status ejoin_threshold_host(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, float eps,
                                   const ejoin_sel *selR, const ejoin_sel *selS,
                                   ejoin_pair *h_pairs, uint64_t capacity, uint64_t *count);

@@ -316,7 +316,8 @@ bool same_sel(const ejoin_sel *a, const ejoin_sel *b)
 // Selection + normalisation of one relation into side buffers (or caller buffers).
 ejoin_status prepare_side(ejoin_ctx *c, int which, const ejoin_rel &r, const ejoin_sel *sel, int fmt, int64_t kp,
                           void *out, int64_t ld_out, float *inv, float *scale, uint32_t *ids, long long *n_sel,
-                          unsigned *status, bool timing_split, int scale_group = 0)
+                          unsigned *status, bool timing_split, int scale_group = 0, float *raw_out = nullptr,
+                          int64_t raw_ld = 0)
 {
     Side &sd = c->side[which];
     cudaError_t e;
@@ -340,11 +341,11 @@ ejoin_status prepare_side(ejoin_ctx *c, int which, const ejoin_rel &r, const ejo
     if (r.n > 0) {
         if (fmt == FMT_FP8 && scale_group > 0) {
             e = launch_normalize_fp8_grouped(r.x, r.ld, r.d, sel ? ids : nullptr, n_sel, r.n, out, ld_out, (int)kp, inv,
-                                             scale, scale_group, status, c->num_sms, c->stream);
+                                             scale, scale_group, status, c->num_sms, c->stream, raw_out, raw_ld);
             c->stats.launches += 3;
         } else {
             e = launch_normalize(fmt, r.x, r.ld, r.d, sel ? ids : nullptr, n_sel, r.n, out, ld_out, (int)kp, inv,
-                                 scale, status, c->num_sms, c->stream);
+                                 scale, status, c->num_sms, c->stream, raw_out, raw_ld);
             c->stats.launches += 1;
         }
         if (e != cudaSuccess) return from_cuda(e);
@@ -381,9 +382,12 @@ cudaError_t ensure_operand(Side &sd, int64_t n, int64_t kp, int fmt, bool with_i
 }
 
 // Device pipeline shared by ejoin_threshold and ejoin_threshold_host.
+// rawR / rawS (optional): device buffers of R.n x R.d / S.n x S.d floats.  R and S are then read only by the
+// normalisation pass (they may sit in device-accessible host memory), which copies each kept row there at
+// its row number; the re-score reads those copies.
 ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, float eps, const ejoin_sel *selR,
                            const ejoin_sel *selS, ejoin_pair **pairs_io, uint64_t *cap_io, bool may_alloc,
-                           uint64_t *d_count_user, uint64_t *count_out)
+                           uint64_t *d_count_user, uint64_t *count_out, float *rawR = nullptr, float *rawS = nullptr)
 {
     c->stats = ejoin_stats{};
     if (!rel_ok(R) || !rel_ok(S) || R.d != S.d || !sel_ok(selR) || !sel_ok(selS)) return EJOIN_EINVAL;
@@ -415,16 +419,20 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     // e4m3: the S operand's scales are shared per 256-row column tile (a self-join's single operand too),
     // so the contraction folds them into its threshold; R keeps per-row scales
     ejoin_status st = prepare_side(c, 0, R, selR, fmt, kp, sa.norm.p, kp, (float *)sa.inv.p, (float *)sa.scale.p,
-                                   (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false, self ? 256 : 0);
+                                   (uint32_t *)sa.ids.p, &dm->n_sel[0], &dm->status, false, self ? 256 : 0, rawR,
+                                   R.d);
     if (st != EJOIN_OK) return st;
     if (!self) {
         st = prepare_side(c, 1, S, selS, fmt, kp, sb.norm.p, kp, (float *)sb.inv.p, (float *)sb.scale.p,
-                          (uint32_t *)sb.ids.p, &dm->n_sel[1], &dm->status, false, 256);
+                          (uint32_t *)sb.ids.p, &dm->n_sel[1], &dm->status, false, 256, rawS, S.d);
         if (st != EJOIN_OK) return st;
     }
     const long long *nA = &dm->n_sel[0];
     const long long *nB = self ? &dm->n_sel[0] : &dm->n_sel[1];
     if (timing) cudaEventRecord(c->ev[1], c->stream);
+    // the rows the re-score gathers: the device copies when given, else R and S themselves
+    const float *xR = rawR ? rawR : R.x, *xS = rawS ? rawS : (self && rawR ? rawR : S.x);
+    const int64_t ldR = rawR ? R.d : R.ld, ldS = rawS ? S.d : (self && rawR ? R.d : S.ld);
 
     // bulk contraction -> candidates
     const float thr = eps - band;
@@ -435,17 +443,17 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         if (!make_tmap(&tmA, sa.norm.p, fmt, kp, rowsA, 128) || !make_tmap(&tmB, sb.norm.p, fmt, kp, rowsB, 256))
             return EJOIN_ECUDA;
     }
-    const bool aligned_rows = R.d % 4 == 0 && R.ld % 4 == 0 && S.ld % 4 == 0 &&
-                              (reinterpret_cast<uintptr_t>(R.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(S.x) & 15) == 0;
+    const bool aligned_rows = R.d % 4 == 0 && ldR % 4 == 0 && ldS % 4 == 0 &&
+                              (reinterpret_cast<uintptr_t>(xR) & 15) == 0 && (reinterpret_cast<uintptr_t>(xS) & 15) == 0;
     const bool fuse = prec != EJOIN_F32 && (c->flags & EJOIN_FLAG_FUSED) && aligned_rows &&
                       (*pairs_io != nullptr || count_only);
     if (fuse) {
         // contraction with the exact re-score fused in: one launch writes the final pairs
         FuseArgs fa{};
-        fa.R = R.x;
-        fa.ldR = R.ld;
-        fa.S = S.x;
-        fa.ldS = S.ld;
+        fa.R = xR;
+        fa.ldR = ldR;
+        fa.S = xS;
+        fa.ldS = ldS;
         fa.d = R.d;
         fa.idsR = selR ? (const uint32_t *)sa.ids.p : nullptr;
         fa.idsS = selS ? (const uint32_t *)sb.ids.p : nullptr;
@@ -524,7 +532,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     auto rescore = [&]() -> cudaError_t {
         cudaError_t ee = ensure(c->band, c->cand_cap * sizeof(uint2));
         if (ee != cudaSuccess) return ee;
-        ee = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
+        ee = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, xR, ldR, xS, ldS, R.d,
                             selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
                             (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
                             count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0,
@@ -986,57 +994,109 @@ ejoin_status ejoin_threshold_host(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float 
     const bool timing = (c->flags & EJOIN_FLAG_TIMING) != 0;
     cudaError_t e;
     const bool self = R.x == S.x && R.n == S.n && R.ld == S.ld && same_sel(selR, selS);
+    // the device address of a host buffer the kernels can read in place (pinned memory), else nullptr
+    auto in_place = [](const void *h) -> const void * {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+            cudaGetLastError();  // not a CUDA-known pointer: clear the error
+            return nullptr;
+        }
+        return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+    };
+    bool zc = (c->flags & EJOIN_FLAG_HOST_COPY) == 0;
+    const void *zR = nullptr, *zS = nullptr, *zRa = nullptr, *zRb = nullptr, *zSa = nullptr, *zSb = nullptr;
+    if (zc && R.n > 0) zc = (zR = in_place(R.x)) != nullptr;
+    if (zc && S.n > 0) zc = (zS = in_place(S.x)) != nullptr;
+    if (zc && selR && selR->attr && R.n > 0) zc = (zRa = in_place(selR->attr)) != nullptr;
+    if (zc && selR && selR->bits && R.n > 0) zc = (zRb = in_place(selR->bits)) != nullptr;
+    if (zc && selS && selS->attr && S.n > 0) zc = (zSa = in_place(selS->attr)) != nullptr;
+    if (zc && selS && selS->bits && S.n > 0) zc = (zSb = in_place(selS->bits)) != nullptr;
     if (timing) cudaEventRecord(c->ev[4], c->stream);
-    // host -> device copies of the inputs (rows are copied densely: ld = d)
-    auto up_rel = [&](int slot, const ejoin_rel &r, ejoin_rel &dr) -> cudaError_t {
-        dr = r;
-        dr.ld = r.d;
-        if (r.n == 0) {
-            dr.x = nullptr;
-            return cudaSuccess;
-        }
-        cudaError_t ee = ensure(c->host_in[slot], (size_t)r.n * r.d * 4);
-        if (ee != cudaSuccess) return ee;
-        dr.x = (const float *)c->host_in[slot].p;
-        if (r.ld == r.d)
-            return cudaMemcpyAsync(c->host_in[slot].p, r.x, (size_t)r.n * r.d * 4, cudaMemcpyHostToDevice, c->stream);
-        return cudaMemcpy2DAsync(c->host_in[slot].p, (size_t)r.d * 4, r.x, (size_t)r.ld * 4, (size_t)r.d * 4,
-                                 (size_t)r.n, cudaMemcpyHostToDevice, c->stream);
-    };
-    auto up_sel = [&](int slot, const ejoin_sel *s, int64_t n, ejoin_sel &ds) -> cudaError_t {
-        ds = *s;
-        const size_t abytes = s->attr ? (size_t)n * 4 : 0;
-        const size_t bbytes = s->bits ? (size_t)((n + 31) / 32) * 4 : 0;
-        cudaError_t ee = ensure(c->host_in[slot], abytes + bbytes + 16);
-        if (ee != cudaSuccess) return ee;
-        char *base = (char *)c->host_in[slot].p;
-        if (s->attr && n) {
-            if ((ee = cudaMemcpyAsync(base, s->attr, abytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-                return ee;
-            ds.attr = (const int32_t *)base;
-        }
-        if (s->bits && n) {
-            char *bb = base + ((abytes + 15) & ~size_t(15));
-            if ((ee = cudaMemcpyAsync(bb, s->bits, bbytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
-                return ee;
-            ds.bits = (const uint32_t *)bb;
-        }
-        return cudaSuccess;
-    };
     ejoin_rel dR, dS;
     ejoin_sel dsR, dsS;
-    if ((e = up_rel(0, R, dR)) != cudaSuccess) return from_cuda(e);
-    if (self) {
-        dS = dR;
-    } else if ((e = up_rel(1, S, dS)) != cudaSuccess) {
-        return from_cuda(e);
-    }
-    if (selR && (e = up_sel(2, selR, R.n, dsR)) != cudaSuccess) return from_cuda(e);
-    if (selS) {
+    float *rawR = nullptr, *rawS = nullptr;
+    uint64_t h2d = 0;
+    if (zc) {
+        // kernels read the host buffers in place; the kept rows are copied to the device by the
+        // normalisation pass (the re-score gathers them there)
+        dR = R;
+        dR.x = (const float *)zR;
+        dS = S;
+        dS.x = self ? dR.x : (const float *)zS;
+        if (R.n > 0) {
+            if ((e = ensure(c->host_in[0], (size_t)R.n * R.d * 4)) != cudaSuccess) return from_cuda(e);
+            rawR = (float *)c->host_in[0].p;
+        }
         if (self) {
-            dsS = dsR;
-        } else if ((e = up_sel(3, selS, S.n, dsS)) != cudaSuccess) {
+            rawS = rawR;
+        } else if (S.n > 0) {
+            if ((e = ensure(c->host_in[1], (size_t)S.n * S.d * 4)) != cudaSuccess) return from_cuda(e);
+            rawS = (float *)c->host_in[1].p;
+        }
+        if (selR) {
+            dsR = *selR;
+            if (zRa) dsR.attr = (const int32_t *)zRa;
+            if (zRb) dsR.bits = (const uint32_t *)zRb;
+        }
+        if (selS) {
+            dsS = *selS;
+            if (zSa) dsS.attr = (const int32_t *)zSa;
+            if (zSb) dsS.bits = (const uint32_t *)zSb;
+        }
+    } else {
+        // host -> device copies of the inputs (rows are copied densely: ld = d)
+        auto up_rel = [&](int slot, const ejoin_rel &r, ejoin_rel &dr) -> cudaError_t {
+            dr = r;
+            dr.ld = r.d;
+            if (r.n == 0) {
+                dr.x = nullptr;
+                return cudaSuccess;
+            }
+            cudaError_t ee = ensure(c->host_in[slot], (size_t)r.n * r.d * 4);
+            if (ee != cudaSuccess) return ee;
+            dr.x = (const float *)c->host_in[slot].p;
+            h2d += (uint64_t)r.n * r.d * 4;
+            if (r.ld == r.d)
+                return cudaMemcpyAsync(c->host_in[slot].p, r.x, (size_t)r.n * r.d * 4, cudaMemcpyHostToDevice,
+                                       c->stream);
+            return cudaMemcpy2DAsync(c->host_in[slot].p, (size_t)r.d * 4, r.x, (size_t)r.ld * 4, (size_t)r.d * 4,
+                                     (size_t)r.n, cudaMemcpyHostToDevice, c->stream);
+        };
+        auto up_sel = [&](int slot, const ejoin_sel *s, int64_t n, ejoin_sel &ds) -> cudaError_t {
+            ds = *s;
+            const size_t abytes = s->attr ? (size_t)n * 4 : 0;
+            const size_t bbytes = s->bits ? (size_t)((n + 31) / 32) * 4 : 0;
+            cudaError_t ee = ensure(c->host_in[slot], abytes + bbytes + 16);
+            if (ee != cudaSuccess) return ee;
+            char *base = (char *)c->host_in[slot].p;
+            if (s->attr && n) {
+                if ((ee = cudaMemcpyAsync(base, s->attr, abytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+                    return ee;
+                ds.attr = (const int32_t *)base;
+                h2d += abytes;
+            }
+            if (s->bits && n) {
+                char *bb = base + ((abytes + 15) & ~size_t(15));
+                if ((ee = cudaMemcpyAsync(bb, s->bits, bbytes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+                    return ee;
+                ds.bits = (const uint32_t *)bb;
+                h2d += bbytes;
+            }
+            return cudaSuccess;
+        };
+        if ((e = up_rel(0, R, dR)) != cudaSuccess) return from_cuda(e);
+        if (self) {
+            dS = dR;
+        } else if ((e = up_rel(1, S, dS)) != cudaSuccess) {
             return from_cuda(e);
+        }
+        if (selR && (e = up_sel(2, selR, R.n, dsR)) != cudaSuccess) return from_cuda(e);
+        if (selS) {
+            if (self) {
+                dsS = dsR;
+            } else if ((e = up_sel(3, selS, S.n, dsS)) != cudaSuccess) {
+                return from_cuda(e);
+            }
         }
     }
     if (timing) cudaEventRecord(c->ev[5], c->stream);
@@ -1045,9 +1105,18 @@ ejoin_status ejoin_threshold_host(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float 
     ejoin_pair *dp = (ejoin_pair *)c->host_pairs.p;
     uint64_t cap = capacity;
     uint64_t cnt = 0;
-    ejoin_status st =
-        run_threshold(c, dR, dS, eps, selR ? &dsR : nullptr, selS ? &dsS : nullptr, &dp, &cap, false, nullptr, &cnt);
+    ejoin_status st = run_threshold(c, dR, dS, eps, selR ? &dsR : nullptr, selS ? &dsS : nullptr, &dp, &cap, false,
+                                    nullptr, &cnt, rawR, rawS);
     *count = cnt;
+    if (zc) {
+        // what the kernels read from host memory: the kept rows and the predicate columns
+        h2d = c->stats.n_sel_r * (uint64_t)R.d * 4 + (self ? 0 : c->stats.n_sel_s * (uint64_t)S.d * 4);
+        if (selR) h2d += (selR->attr ? (uint64_t)R.n * 4 : 0) + (selR->bits ? (uint64_t)((R.n + 31) / 32) * 4 : 0);
+        if (selS && !self)
+            h2d += (selS->attr ? (uint64_t)S.n * 4 : 0) + (selS->bits ? (uint64_t)((S.n + 31) / 32) * 4 : 0);
+    }
+    c->stats.h2d_bytes = h2d;
+    c->stats.host_in_place = zc ? 1 : 0;
     if (st != EJOIN_OK && st != EJOIN_EOVERFLOW) return st;
     const uint64_t ncopy = std::min<uint64_t>(cnt, capacity);
     if (timing) cudaEventRecord(c->ev[6], c->stream);

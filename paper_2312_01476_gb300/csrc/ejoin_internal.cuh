@@ -142,16 +142,19 @@ cudaError_t launch_sel_scan(const uint32_t *block_counts, int64_t n_blocks, uint
 cudaError_t launch_sel_scatter(const SelArgs &s, int64_t n, const uint32_t *block_offsets, uint32_t *ids,
                                cudaStream_t st);
 cudaError_t launch_set_count(long long *n_sel, long long value, cudaStream_t st);
+// raw_out (optional): each normalised row's FP32 values are also copied to raw_out + r * raw_ld, r its
+// source row number (a device copy of rows read from host memory).
 cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const uint32_t *ids,
                              const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
                              int kp, float *inv_norm, float *scale, unsigned *status, int num_sms,
-                             cudaStream_t st);
+                             cudaStream_t st, float *raw_out = nullptr, int64_t raw_ld = 0);
 // e4m3 normalisation whose scales are shared by each aligned group of `group` output rows
 // (scale[c] = the largest per-row scale of c's group); 3 kernels.
 cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, const uint32_t *ids,
                                          const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
                                          int kp, float *inv_norm, float *scale, int group, unsigned *status,
-                                         int num_sms, cudaStream_t st);
+                                         int num_sms, cudaStream_t st, float *raw_out = nullptr,
+                                         int64_t raw_ld = 0);
 cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
                                    int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
                                    float *scale, unsigned *status, int num_sms, cudaStream_t st);

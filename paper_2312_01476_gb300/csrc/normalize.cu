@@ -132,10 +132,13 @@ __global__ void set_count_kernel(long long *p, long long v) { *p = v; }
 
 // Normalise one row (one warp): y = x / ||x|| (0 for a zero row), written as
 // FMT with zero padding to kp; 1/||x|| and the e4m3 scale are written by lane 0.
+// raw (optional): the row's d FP32 values are also copied there as read (the
+// copy of a row that sits in host memory, for kernels that gather rows later).
 template <int FMT>
 __device__ __forceinline__ void normalize_row(const float *__restrict__ src, int d, bool vec, void *__restrict__ out,
                                               int64_t c, int64_t ld_out, int kp, float *__restrict__ inv_norm,
-                                              float *__restrict__ scale, unsigned *status, int lane)
+                                              float *__restrict__ scale, unsigned *status, int lane,
+                                              float *__restrict__ raw = nullptr, bool raw_vec = false)
 {
     const int groups = kp >> 2;  // kp is a multiple of 32
     auto load4 = [&](int k) -> float4 {
@@ -151,10 +154,21 @@ __device__ __forceinline__ void normalize_row(const float *__restrict__ src, int
         return v;
     };
 
-    // pass 1: sum of squares and max |x|
+    // pass 1: sum of squares and max |x| (and the raw copy)
     float ss = 0.f, mx = 0.f;
     for (int g = lane; 4 * g < d; g += 32) {
         const float4 v = load4(4 * g);
+        if (raw) {
+            const int k = 4 * g;
+            if (raw_vec && k + 3 < d) {
+                *reinterpret_cast<float4 *>(raw + k) = v;
+            } else {
+                raw[k] = v.x;
+                if (k + 1 < d) raw[k + 1] = v.y;
+                if (k + 2 < d) raw[k + 2] = v.z;
+                if (k + 3 < d) raw[k + 3] = v.w;
+            }
+        }
         ss = fmaf(v.x, v.x, ss);
         ss = fmaf(v.y, v.y, ss);
         ss = fmaf(v.z, v.z, ss);
@@ -238,7 +252,8 @@ __global__ void __launch_bounds__(256) normalize_kernel(const float *__restrict_
                                                         const long long *__restrict__ n_rows_dev,
                                                         int64_t n_rows_max, void *__restrict__ out, int64_t ld_out,
                                                         int kp, float *__restrict__ inv_norm,
-                                                        float *__restrict__ scale, unsigned *status)
+                                                        float *__restrict__ scale, unsigned *status,
+                                                        float *__restrict__ raw_out, int64_t raw_ld)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -246,9 +261,12 @@ __global__ void __launch_bounds__(256) normalize_kernel(const float *__restrict_
     int64_t n_rows = n_rows_dev ? (int64_t)*n_rows_dev : n_rows_max;
     if (n_rows > n_rows_max) n_rows = n_rows_max;
     const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
+    const bool raw_vec = ((raw_ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(raw_out) & 15) == 0);
     for (int64_t c = warp_global; c < n_rows; c += n_warps) {
         const int64_t r = ids ? (int64_t)ids[c] : c;
-        normalize_row<FMT>(x + r * ld, d, vec, out, c, ld_out, kp, inv_norm, scale, status, lane);
+        // the raw copy keeps the source row number r
+        normalize_row<FMT>(x + r * ld, d, vec, out, c, ld_out, kp, inv_norm, scale, status, lane,
+                           raw_out ? raw_out + r * raw_ld : nullptr, raw_vec);
     }
 }
 
@@ -342,7 +360,7 @@ __global__ void __launch_bounds__(256) fp8_quantize_kernel(const float *__restri
 cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, const uint32_t *ids,
                                          const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out,
                                          int kp, float *inv_norm, float *scale, int group, unsigned *status,
-                                         int num_sms, cudaStream_t st)
+                                         int num_sms, cudaStream_t st, float *raw_out, int64_t raw_ld)
 {
     if (n_rows_max <= 0) return cudaSuccess;
     if (!inv_norm || !scale || group < 1) return cudaErrorInvalidValue;
@@ -351,12 +369,15 @@ cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, cons
     if (blocks > cap) blocks = cap;
     // norms and per-row scales, then the group maxima, then the quantised rows
     normalize_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, nullptr,
-                                                                ld_out, kp, inv_norm, scale, status);
+                                                                ld_out, kp, inv_norm, scale, status, raw_out,
+                                                                raw_ld);
     int64_t gblocks = ((n_rows_max + group - 1) / group + 7) / 8;
     if (gblocks > cap) gblocks = cap;
     if (gblocks < 1) gblocks = 1;
     scale_group_max_kernel<<<(unsigned)gblocks, 256, 0, st>>>(scale, n_rows_dev, n_rows_max, group);
-    fp8_quantize_kernel<<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max,
+    // the second read of the rows comes from the raw copy when there is one
+    fp8_quantize_kernel<<<(unsigned)blocks, 256, 0, st>>>(raw_out ? raw_out : x, raw_out ? raw_ld : ld, d, ids,
+                                                          n_rows_dev, n_rows_max,
                                                           reinterpret_cast<__nv_fp8_storage_t *>(out), ld_out, kp,
                                                           inv_norm, scale);
     return cudaGetLastError();
@@ -394,7 +415,8 @@ cudaError_t launch_set_count(long long *n_sel, long long value, cudaStream_t st)
 
 cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const uint32_t *ids,
                              const long long *n_rows_dev, int64_t n_rows_max, void *out, int64_t ld_out, int kp,
-                             float *inv_norm, float *scale, unsigned *status, int num_sms, cudaStream_t st)
+                             float *inv_norm, float *scale, unsigned *status, int num_sms, cudaStream_t st,
+                             float *raw_out, int64_t raw_ld)
 {
     if (n_rows_max <= 0) return cudaSuccess;
     // 8 warps per block, up to 16 blocks per SM, grid-stride over rows
@@ -404,15 +426,15 @@ cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const u
     switch (fmt) {
     case FMT_F32:
         normalize_kernel<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
-                                                                    ld_out, kp, inv_norm, scale, status);
+                                                                    ld_out, kp, inv_norm, scale, status, raw_out, raw_ld);
         break;
     case FMT_BF16:
         normalize_kernel<FMT_BF16><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
-                                                                     ld_out, kp, inv_norm, scale, status);
+                                                                     ld_out, kp, inv_norm, scale, status, raw_out, raw_ld);
         break;
     case FMT_FP8:
         normalize_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(x, ld, d, ids, n_rows_dev, n_rows_max, out,
-                                                                    ld_out, kp, inv_norm, scale, status);
+                                                                    ld_out, kp, inv_norm, scale, status, raw_out, raw_ld);
         break;
     default: return cudaErrorInvalidValue;
     }

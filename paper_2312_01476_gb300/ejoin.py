@@ -23,6 +23,7 @@ EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
 EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
 EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
 EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED, EJOIN_FLAG_NO_SYMMETRY = 0x1, 0x2, 0x4, 0x8
+EJOIN_FLAG_HOST_COPY = 0x10
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
 
@@ -57,7 +58,8 @@ class ejoin_stats(ctypes.Structure):
                 ("band", ctypes.c_float), ("ms_select", ctypes.c_float), ("ms_normalize", ctypes.c_float),
                 ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ms_h2d", ctypes.c_float), ("ms_d2h", ctypes.c_float), ("contract_retries", ctypes.c_int32),
-                ("fused", ctypes.c_int32)]
+                ("fused", ctypes.c_int32), ("h2d_bytes", ctypes.c_uint64), ("host_in_place", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ejoin_job(ctypes.Structure):
@@ -390,7 +392,9 @@ def _host_arr(a, dtype):
 
 def ejoin_threshold_host(ctx: Ctx, R, S, eps: float, selR: Optional[Sel] = None, selS: Optional[Sel] = None,
                          out=None):
-    """Host-memory E-join: inputs are copied to the device, joined, and the pairs copied back.
+    """Host-memory E-join: pinned (device-accessible) inputs are read in place, only the predicate
+    columns and the kept rows crossing the link; pageable inputs are copied whole.  The pairs are
+    copied back.
 
     ``out``: optional numpy structured buffer (pinned memory recommended) of dtype PAIR_DTYPE.
     Returns (pairs numpy structured array view, count)."""

@@ -202,6 +202,48 @@ def test_host_api_matches_device_api(prec):
     compare(w.R, w.S, w.eps, pairs["i"], pairs["j"], pairs["sim"], oi, oj, os_)
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp8", "tf32", "f32"])
+def test_host_api_reads_pinned_inputs_in_place(prec):
+    # pinned host inputs: the predicates and the kept rows are read in place (only they cross the link);
+    # the result equals the whole-copy route's and the oracle's
+    w = inputs.c2_clustered_selection(nR=20000, nS=3000, d=300, n_clusters=50, threads=4)
+    aS = np.random.default_rng(5).integers(0, 10, 3000).astype(np.int32)
+
+    def pin(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+    Rp, Sp, Ap, aSp = pin(w.R), pin(w.S), pin(w.attrR), pin(aS)
+    with pkg.Ctx(device=0, prec=prec) as ctx:
+        pairs, n = pkg.ejoin_threshold_host(ctx, Rp, Sp, w.eps, pkg.Sel(Ap, "<", w.cR), pkg.Sel(aSp, "<", 7))
+        st = pkg.ejoin_last_stats(ctx)
+    n_r, n_s = int((w.attrR < w.cR).sum()), int((aS < 7).sum())
+    assert st["host_in_place"] == 1
+    assert st["h2d_bytes"] == (n_r + n_s) * 300 * 4 + (20000 + 3000) * 4
+    oi, oj, os_ = oracle.join(w.R, w.S, w.eps, oracle.Selection(w.attrR, "<", w.cR), oracle.Selection(aS, "<", 7))
+    assert n > 100
+    compare(w.R, w.S, w.eps, pairs["i"], pairs["j"], pairs["sim"], oi, oj, os_)
+    with pkg.Ctx(device=0, prec=prec, flags=pkg.EJOIN_FLAG_HOST_COPY) as ctx:
+        pairs2, n2 = pkg.ejoin_threshold_host(ctx, Rp, Sp, w.eps, pkg.Sel(Ap, "<", w.cR), pkg.Sel(aSp, "<", 7))
+        st2 = pkg.ejoin_last_stats(ctx)
+    assert st2["host_in_place"] == 0 and st2["h2d_bytes"] == (20000 + 3000) * 300 * 4 + (20000 + 3000) * 4
+    a = np.sort(pairs[["i", "j", "sim"]], order=["i", "j"])
+    b = np.sort(pairs2[["i", "j", "sim"]], order=["i", "j"])
+    assert np.array_equal(a, b)
+
+
+def test_host_api_pinned_self_join():
+    # a pinned self-join: one operand read in place, the symmetric evaluation mirrored in the re-score
+    X = gauss(41, 3000, 96)
+    X[1500:1600] = X[:100] + 0.05 * gauss(42, 100, 96)
+    Xp = torch.from_numpy(X).pin_memory().numpy()
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        pairs, n = pkg.ejoin_threshold_host(ctx, Xp, Xp, 0.6)
+        st = pkg.ejoin_last_stats(ctx)
+    assert st["host_in_place"] == 1 and st["h2d_bytes"] == 3000 * 96 * 4
+    oi, oj, os_ = oracle.join(X, X, 0.6)
+    compare(X, X, 0.6, pairs["i"], pairs["j"], pairs["sim"], oi, oj, os_)
+
+
 def test_normalize_entry_point():
     X = gauss(22, 1000, 300)
     attr = np.arange(1000, dtype=np.int32) % 7
