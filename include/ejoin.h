@@ -201,8 +201,9 @@ ejoin_status ejoin_threshold(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, float eps
  * only the kept rows in place, copying them to the device for the re-score: the
  * relational predicate is pushed below the host-to-device transfer (Sec. VI-E
  * pre-filter), and only the kept rows cross the link.  Otherwise (pageable
- * memory, or EJOIN_FLAG_HOST_COPY) the inputs are copied whole first.  The
- * pairs are copied back to h_pairs in either case. */
+ * memory, or EJOIN_FLAG_HOST_COPY) the inputs are copied whole first.  On
+ * the in-place route a device-accessible h_pairs is written by the re-score
+ * directly; otherwise the pairs are copied back to it. */
 ejoin_status ejoin_threshold_host(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, float eps,
                                   const ejoin_sel *selR, const ejoin_sel *selS,
                                   ejoin_pair *h_pairs, uint64_t capacity, uint64_t *count);

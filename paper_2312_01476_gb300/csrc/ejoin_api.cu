@@ -1100,9 +1100,15 @@ ejoin_status ejoin_threshold_host(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float 
         }
     }
     if (timing) cudaEventRecord(c->ev[5], c->stream);
-    if ((e = ensure(c->host_pairs, std::max<uint64_t>(capacity, 1) * sizeof(ejoin_pair))) != cudaSuccess)
-        return from_cuda(e);
-    ejoin_pair *dp = (ejoin_pair *)c->host_pairs.p;
+    // a pinned result buffer is written by the re-score in place; otherwise through a device buffer
+    ejoin_pair *dp = nullptr;
+    if (zc && capacity) dp = (ejoin_pair *)in_place(h_pairs);
+    const bool out_in_place = dp != nullptr;
+    if (!out_in_place) {
+        if ((e = ensure(c->host_pairs, std::max<uint64_t>(capacity, 1) * sizeof(ejoin_pair))) != cudaSuccess)
+            return from_cuda(e);
+        dp = (ejoin_pair *)c->host_pairs.p;
+    }
     uint64_t cap = capacity;
     uint64_t cnt = 0;
     ejoin_status st = run_threshold(c, dR, dS, eps, selR ? &dsR : nullptr, selS ? &dsS : nullptr, &dp, &cap, false,
@@ -1120,7 +1126,7 @@ ejoin_status ejoin_threshold_host(ejoin_ctx *c, ejoin_rel R, ejoin_rel S, float 
     if (st != EJOIN_OK && st != EJOIN_EOVERFLOW) return st;
     const uint64_t ncopy = std::min<uint64_t>(cnt, capacity);
     if (timing) cudaEventRecord(c->ev[6], c->stream);
-    if (ncopy && (c->flags & EJOIN_FLAG_COUNT_ONLY) == 0) {
+    if (ncopy && !out_in_place && (c->flags & EJOIN_FLAG_COUNT_ONLY) == 0) {
         if ((e = cudaMemcpyAsync(h_pairs, dp, ncopy * sizeof(ejoin_pair), cudaMemcpyDeviceToHost, c->stream)) !=
             cudaSuccess)
             return from_cuda(e);

@@ -213,8 +213,11 @@ def test_host_api_reads_pinned_inputs_in_place(prec):
         return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
 
     Rp, Sp, Ap, aSp = pin(w.R), pin(w.S), pin(w.attrR), pin(aS)
+    outp = torch.empty(12 * 400000, dtype=torch.uint8).pin_memory().numpy().view(pkg.PAIR_DTYPE)
     with pkg.Ctx(device=0, prec=prec) as ctx:
-        pairs, n = pkg.ejoin_threshold_host(ctx, Rp, Sp, w.eps, pkg.Sel(Ap, "<", w.cR), pkg.Sel(aSp, "<", 7))
+        # a pinned result buffer too: the re-score writes the pairs into it directly
+        pairs, n = pkg.ejoin_threshold_host(ctx, Rp, Sp, w.eps, pkg.Sel(Ap, "<", w.cR), pkg.Sel(aSp, "<", 7),
+                                            out=outp)
         st = pkg.ejoin_last_stats(ctx)
     n_r, n_s = int((w.attrR < w.cR).sum()), int((aS < 7).sum())
     assert st["host_in_place"] == 1
