@@ -141,3 +141,19 @@ def test_eselect_full_size_sampled_rows():
     compare(Rs, Qh, eps, li, gj[keep], gs[keep], oi, oj, os_)
     del R, Q, res
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("d", [4, 33, 1030])
+def test_eselect_dimensions_off_the_k_slice(d):
+    # the scan reads R in place with the caller's row stride (here d rounded up to 4 floats); columns past d in
+    # the last 32-float K-slice read as zeros
+    R, Q = clustered_pair(900, 12, d, 6, 350 + d, theta=0.2)
+    ld = (d + 3) // 4 * 4
+    Rw = torch.zeros((900, ld), dtype=torch.float32, device="cuda")
+    Rw[:, :d] = dev(R)
+    Rw[:, d:] = 7.0  # padding columns must not enter the similarity
+    eps = 0.8
+    gi, gj, gs, st = esel(Rw[:, :d], dev(Q), eps)
+    oi, oj, os_ = oracle.join(R, Q, eps, threads=THREADS)
+    compare(R, Q, eps, gi, gj, gs, oi, oj, os_)
+    assert st["fused"] == 1

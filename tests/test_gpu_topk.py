@@ -165,3 +165,14 @@ def test_topk_full_size_sampled_rows(prec):
     assert np.all(w.attrS[gj] < w.cS)
     del R, S, A, res
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("d", [4, 1030])
+def test_topk_small_and_large_dimensions(prec, d):
+    rng = np.random.default_rng(211 + d)
+    R = rng.standard_normal((200, d)).astype(np.float32)
+    S = rng.standard_normal((2500, d)).astype(np.float32)
+    gi, gj, gs, st = topk(prec, R, S, 8)
+    oi, oj, os_ = oracle.topk(R, S, 8, threads=THREADS)
+    compare_topk(R, S, 8, gi, gj, gs, oi, oj, os_)
