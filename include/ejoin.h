@@ -375,6 +375,10 @@ typedef struct ejoin_prune_stats {
     float ball_radius_mean_a, ball_radius_mean_b;
     float wide_ball_frac_a, wide_ball_frac_b;
     uint64_t anchors_a, max_group_rows_a;
+    /* the part of ms_prepare spent on R: normalisation and sketches, covering anchors, and anchor
+       assignment with the reorder and gathers */
+    float ms_sketch_a, ms_cover_a, ms_assign_a;
+    int32_t reserved;
 } ejoin_prune_stats;
 
 /* Threshold join of R and S (device, no selection) that contracts only the

@@ -63,11 +63,12 @@ cudaError_t launch_gather_rows(const void *in, int64_t row_bytes, const uint32_t
 cudaError_t launch_gather_u32(const uint32_t *in, const uint32_t *perm, int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_gather_f32(const float *in, const uint32_t *perm, int64_t n, float *out, cudaStream_t st);
 // Covering anchors: drop[a] = 1 when an earlier candidate b < a has sketch cosine >= tau with
-// candidate a (rows cand[] of S), and covered[i] |= (some anchor has cosine >= tau with row rows[i]).
+// candidate a (rows cand[] of S).
 cudaError_t launch_cover_drop(const float *S, const uint32_t *cand, int nc, float tau, unsigned char *drop,
                               cudaStream_t st);
-cudaError_t launch_cover_update(const float *S, const uint32_t *rows, int64_t m, const float *anchors, int n_anchor,
-                                float tau, unsigned char *covered, cudaStream_t st);
+// covered[r] = 1 for each candidate (r, c) in cand[0 .. min(*count, cap)).
+cudaError_t launch_cover_mark(const uint2 *cand, const unsigned long long *count, uint64_t cap,
+                              unsigned char *covered, int num_sms, cudaStream_t st);
 // Assignment of rows to covering anchors from the candidates (row, anchor) of a threshold
 // contraction of the sketches against the anchors: best[r] = max over r's candidates of
 // (cosine bits << 32 | anchor) (best zeroed by the caller); key[r] = its anchor, or n_anchor

@@ -150,52 +150,53 @@ __global__ void gather_f32_kernel(const float *__restrict__ in, const uint32_t *
 __global__ void cover_drop_kernel(const float *__restrict__ S, const uint32_t *__restrict__ cand, int nc, float tau,
                                   unsigned char *__restrict__ drop)
 {
+    // one warp per candidate a; its lanes test 32 earlier candidates at a time, each lane a full 64-term dot
     const int lane = threadIdx.x & 31;
     const int a = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     if (a >= nc) return;
-    const float2 x = __ldg(reinterpret_cast<const float2 *>(S + (int64_t)cand[a] * SK) + lane);
-    bool hit = false;
-    for (int b = 0; b < a && !hit; ++b) {
-        const float2 y = __ldg(reinterpret_cast<const float2 *>(S + (int64_t)cand[b] * SK) + lane);
-        float dot = fmaf(x.x, y.x, x.y * y.y);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        hit = dot >= tau;  // warp-uniform
-    }
-    if (lane == 0) drop[a] = hit ? 1 : 0;
-}
-
-// covered[i] |= max over the anchors of <S[rows[i]], anchor> >= tau (one thread per row).
-__global__ void cover_update_kernel(const float *__restrict__ S, const uint32_t *__restrict__ rows, int64_t m,
-                                    const float *__restrict__ anchors, int n_anchor, float tau,
-                                    unsigned char *__restrict__ covered)
-{
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m || covered[i]) return;
     float x[SK];
+    const float4 *xa = reinterpret_cast<const float4 *>(S + (int64_t)cand[a] * SK);
 #pragma unroll
     for (int q = 0; q < SK / 4; ++q) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(S + (int64_t)rows[i] * SK) + q);
+        const float4 v = __ldg(xa + q);
         x[4 * q] = v.x;
         x[4 * q + 1] = v.y;
         x[4 * q + 2] = v.z;
         x[4 * q + 3] = v.w;
     }
-    for (int a = 0; a < n_anchor; ++a) {
-        float dot = 0.f;
+    bool hit = false;
+    for (int b0 = 0; b0 < a; b0 += 32) {
+        const int b = b0 + lane;
+        if (b < a) {
+            const float4 *yb = reinterpret_cast<const float4 *>(S + (int64_t)cand[b] * SK);
+            float dot = 0.f;
 #pragma unroll
-        for (int q = 0; q < SK / 4; ++q) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(anchors + (int64_t)a * SK) + q);
-            dot = fmaf(x[4 * q], v.x, dot);
-            dot = fmaf(x[4 * q + 1], v.y, dot);
-            dot = fmaf(x[4 * q + 2], v.z, dot);
-            dot = fmaf(x[4 * q + 3], v.w, dot);
+            for (int q = 0; q < SK / 4; ++q) {
+                const float4 v = __ldg(yb + q);
+                dot = fmaf(x[4 * q], v.x, dot);
+                dot = fmaf(x[4 * q + 1], v.y, dot);
+                dot = fmaf(x[4 * q + 2], v.z, dot);
+                dot = fmaf(x[4 * q + 3], v.w, dot);
+            }
+            hit = dot >= tau;
         }
-        if (dot >= tau) {
-            covered[i] = 1;
-            return;
+        if (__any_sync(0xffffffffu, hit)) {
+            hit = true;
+            break;
         }
     }
+    if (lane == 0) drop[a] = hit ? 1 : 0;
+}
+
+// covered[r] = 1 for every candidate (r, anchor) of a threshold contraction of the sample rows against
+// the round's anchors.
+__global__ void cover_mark_kernel(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ count,
+                                  uint64_t cap, unsigned char *__restrict__ covered)
+{
+    uint64_t n = *count;
+    if (n > cap) n = cap;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x)
+        covered[cand[t].x] = 1;
 }
 
 // One block (256 threads) per tile of tile_rows (<= 256) consecutive sketch
@@ -467,11 +468,12 @@ cudaError_t launch_cover_drop(const float *S, const uint32_t *cand, int nc, floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_cover_update(const float *S, const uint32_t *rows, int64_t m, const float *anchors, int n_anchor,
-                                float tau, unsigned char *covered, cudaStream_t st)
+cudaError_t launch_cover_mark(const uint2 *cand, const unsigned long long *count, uint64_t cap,
+                              unsigned char *covered, int num_sms, cudaStream_t st)
 {
-    if (m <= 0 || n_anchor <= 0) return cudaSuccess;
-    cover_update_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(S, rows, m, anchors, n_anchor, tau, covered);
+    if (cap == 0) return cudaSuccess;
+    const uint64_t want = (cap + 255) / 256, lim = (uint64_t)num_sms * 8;
+    cover_mark_kernel<<<(unsigned)(want < lim ? (want ? want : 1) : lim), 256, 0, st>>>(cand, count, cap, covered);
     return cudaGetLastError();
 }
 

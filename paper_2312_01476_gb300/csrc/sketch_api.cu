@@ -43,6 +43,7 @@ struct ejoin_sketch {
     struct Side {
         Buf S, key1, perm1, perm, hist, a_idx, anchors2, norm, inv, scale, sS, maxdot, cent, rad;
         Buf skb, anb, tinv, best, cnt;  // assignment contraction: BF16 sketches and anchors, argmax
+        Buf smpb, rab;                  // covering rounds: BF16 sketches of the sample and of a round's anchors
         int n_anchor = 0;               // covering anchors of the last reorder
     } pw[2];
     Buf list, list_count;
@@ -271,7 +272,8 @@ void ejoin_sketch_destroy(ejoin_sketch *sk)
             release(*b);
         for (auto &w : sk->pw)
             for (Buf *b : {&w.S, &w.key1, &w.perm1, &w.perm, &w.hist, &w.a_idx, &w.anchors2, &w.norm, &w.inv,
-                           &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad, &w.skb, &w.anb, &w.tinv, &w.best, &w.cnt})
+                           &w.scale, &w.sS, &w.maxdot, &w.cent, &w.rad, &w.skb, &w.anb, &w.tinv, &w.best, &w.cnt,
+                           &w.smpb, &w.rab})
                 release(*b);
     }
     delete sk;
@@ -471,6 +473,7 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
         return from_cuda(e);
     if ((e = sketch_forward(sk, r.x, n, r.ld, (const float *)sd.inv.p, (float *)pw.S.p, st)) != cudaSuccess)
         return from_cuda(e);
+    if (w == 0) cudaEventRecord(c->ev[5], st);
 
     // covering anchors over a strided sample of m rows, candidates taken in a fixed pseudo-random order
     const float *S = (const float *)pw.S.p;
@@ -493,6 +496,23 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
     if ((e = cudaMemcpyAsync(samp, aidx.data(), m * 4, cudaMemcpyHostToDevice, st)) ||
         (e = cudaMemsetAsync(cov_dev, 0, (size_t)std::max<int64_t>(m, 1), st)))
         return from_cuda(e);
+    // the sample's sketches in BF16 for the coverage contraction of each round (coverage only steers the
+    // reorder, so the BF16 rounding of the test is harmless)
+    const int64_t rows_m = round_up(std::max<int64_t>(m, 1), 256);
+    if ((e = ensure(pw.cnt, 16)) || (e = ensure(pw.smpb, (size_t)rows_m * SKW * 2)) ||
+        (e = ensure(pw.rab, (size_t)COVER_ROUND * SKW * 2)))
+        return from_cuda(e);
+    long long *ccnt = (long long *)pw.cnt.p;
+    if ((e = launch_set_count(ccnt, m, st)) ||
+        (e = launch_normalize(FMT_BF16, S, SKW, SKW, samp, ccnt, m, pw.smpb.p, SKW, SKW, nullptr, nullptr, &dm->status,
+                              c->num_sms, st)))
+        return from_cuda(e);
+    CUtensorMap tmSmp, tmRnd;
+    if (!make_tmap(&tmSmp, pw.smpb.p, FMT_BF16, SKW, rows_m, 128) ||
+        !make_tmap(&tmRnd, pw.rab.p, FMT_BF16, SKW, COVER_ROUND, 256))
+        return EJOIN_ECUDA;
+    if (c->cand_cap == 0) c->cand_cap = c->cap_hint;
+    if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
     int n_anchor = 0;
     while (n_anchor < COVER_MAX_ANCHORS) {
         cand.clear();
@@ -509,15 +529,34 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
         for (int a = 0; a < nc && n_anchor + (int)kept.size() < COVER_MAX_ANCHORS; ++a)
             if (!drop[a]) kept.push_back(cand[a]);
         const int nk = (int)kept.size();
+        // the round's anchors, then the sample rows they cover: a BF16 threshold contraction of the sample
+        // sketches against them on the tensor cores marks every row with cosine >= COVER_TAU to one of them
         if ((e = cudaMemcpyAsync(cand_dev, kept.data(), nk * 4, cudaMemcpyHostToDevice, st)) ||
             (e = launch_gather_rows(pw.S.p, SKW * 4, cand_dev, nk, anchors + (int64_t)n_anchor * SKW, st)) ||
-            (e = launch_cover_update(S, samp, m, anchors + (int64_t)n_anchor * SKW, nk, COVER_TAU, cov_dev, st)) ||
-            (e = cudaMemcpyAsync(cov.data(), cov_dev, m, cudaMemcpyDeviceToHost, st)) ||
-            (e = cudaStreamSynchronize(st)))  // kept and cov are host vectors
+            (e = launch_set_count(ccnt + 1, nk, st)) ||
+            (e = launch_normalize(FMT_BF16, anchors + (int64_t)n_anchor * SKW, SKW, SKW, nullptr, ccnt + 1, nk,
+                                  pw.rab.p, SKW, SKW, nullptr, nullptr, &dm->status, c->num_sms, st)))
             return from_cuda(e);
+        for (int attempt = 0;; ++attempt) {
+            unsigned long long n_cand = 0;
+            if ((e = cudaMemsetAsync(&dm->cand_count, 0, 8, st)) ||
+                (e = launch_sim_tc(0, &tmSmp, &tmRnd, SKW, ccnt, ccnt + 1, COVER_TAU, nullptr, nullptr,
+                                   (uint2 *)c->cand.p, c->cand_cap, &dm->cand_count, &dm->status, c->timeout, 0,
+                                   c->num_sms, default_group_m(SKW), st)) ||
+                (e = launch_cover_mark((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, cov_dev, c->num_sms,
+                                       st)) ||
+                (e = cudaMemcpyAsync(cov.data(), cov_dev, m, cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaMemcpyAsync(&n_cand, &dm->cand_count, 8, cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaStreamSynchronize(st)))  // kept and cov are host vectors
+                return from_cuda(e);
+            if (n_cand <= c->cand_cap || attempt == 2) break;
+            c->cand_cap = n_cand + n_cand / 4 + 1024;
+            if ((e = ensure(c->cand, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
+        }
         n_anchor += nk;
     }
     pw.n_anchor = n_anchor;
+    if (w == 0) cudaEventRecord(c->ev[6], st);
 
     // every row joins its most similar anchor: a BF16 threshold contraction of the sketches against
     // the anchors on the tensor cores finds, for each row, the anchors within sketch cosine 0.6, and an
@@ -605,6 +644,7 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     cudaEvent_t *ev = c->ev;
     cudaEventRecord(ev[0], st);
     if ((s = prune_side(sk, 0, R, fmt, kp)) != EJOIN_OK) return s;
+    cudaEventRecord(ev[7], st);
     if (!self && (s = prune_side(sk, 1, S, fmt, kp)) != EJOIN_OK) return s;
     auto &pa = sk->pw[0];
     auto &pb = self ? sk->pw[0] : sk->pw[1];
@@ -749,6 +789,9 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     P_.ms_contract = ms(2, 3);
     P_.ms_rescore = ms(3, 4);
     P_.ms_total = ms(0, 4);
+    P_.ms_sketch_a = ms(0, 5);
+    P_.ms_cover_a = ms(5, 6);
+    P_.ms_assign_a = ms(6, 7);
     c->stats.candidates = hm.cand_count;
     c->stats.pairs = hm.pair_count;
     c->stats.fp64_rescored = hm.band_count;

@@ -82,7 +82,9 @@ class ejoin_prune_stats(ctypes.Structure):
                 ("ms_contract", ctypes.c_float), ("ms_rescore", ctypes.c_float), ("ms_total", ctypes.c_float),
                 ("ball_radius_mean_a", ctypes.c_float), ("ball_radius_mean_b", ctypes.c_float),
                 ("wide_ball_frac_a", ctypes.c_float), ("wide_ball_frac_b", ctypes.c_float),
-                ("anchors_a", ctypes.c_uint64), ("max_group_rows_a", ctypes.c_uint64)]
+                ("anchors_a", ctypes.c_uint64), ("max_group_rows_a", ctypes.c_uint64),
+                ("ms_sketch_a", ctypes.c_float), ("ms_cover_a", ctypes.c_float), ("ms_assign_a", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
 _lib = None
 
