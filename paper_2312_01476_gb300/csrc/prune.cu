@@ -321,10 +321,15 @@ __global__ void __launch_bounds__(256) tile_stats_kernel(const float *__restrict
         centroid[(int64_t)blockIdx.x * NB * SK + e] = c[e / SK][e % SK];
 }
 
-// TP x TP tile pairs per block (256 threads, 4 pairs each).  A tile pair is
-// kept when some ball pair (a, b) has cos(max(0, angle(c_a, c_b) - r_a - r_b))
-// >= cos_keep; kept pairs are appended with one atomic per warp.
+// TP x TP tile pairs per block (256 threads, 2 x 2 pairs each).  A tile pair is kept when some ball pair
+// (a, b) has cos(max(0, angle(c_a, c_b) - r_a - r_b)) >= cos_keep, i.e. angle(c_a, c_b) <= r_a + r_b + alpha
+// with alpha = acos(cos_keep): always when r_a + alpha + r_b >= pi, else when
+// c_a . c_b >= cos(r_a + alpha) cos(r_b) - sin(r_a + alpha) sin(r_b) (= cos(r_a + alpha + r_b)), tested with
+// a margin of 1e-6 towards keeping.  The 64-term dots of a thread's 8 x 8 ball pairs are register-tiled;
+// the balls sit in shared memory ball-major ([ball][tile]), so a warp's loads fall on distinct banks.
+// Kept pairs are appended with one atomic per warp.
 constexpr int TP = 32;
+constexpr float PI_F = 3.14159265358979f;
 __global__ void __launch_bounds__(256) tile_pairs_kernel(const float *__restrict__ cA, const float *__restrict__ rA,
                                                          int64_t tA, const float *__restrict__ cB,
                                                          const float *__restrict__ rB, int64_t tB, float cos_keep,
@@ -332,48 +337,83 @@ __global__ void __launch_bounds__(256) tile_pairs_kernel(const float *__restrict
                                                          unsigned long long *count, int sym)
 {
     extern __shared__ float sm[];
-    float *sa = sm;                          // [TP * NB][SK + 1]
-    float *sb = sa + TP * NB * (SK + 1);     // [TP * NB][SK + 1]
-    float *ra = sb + TP * NB * (SK + 1);     // [TP * NB]
-    float *rb = ra + TP * NB;                // [TP * NB]
+    float *sa = sm;                       // [NB][TP][SK + 1]: ball x of tile t at row x * TP + t
+    float *sb = sa + NB * TP * (SK + 1);  // [NB][TP][SK + 1]
+    float *pa = sb + NB * TP * (SK + 1);  // [NB * TP][3]: r, cos(r + alpha), sin(r + alpha)
+    float *pb = pa + NB * TP * 3;         // [NB * TP][3]: r, cos r, sin r
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t a0 = (int64_t)blockIdx.y * TP, b0 = (int64_t)blockIdx.x * TP;
+    const float alpha = cos_keep >= 1.f ? 0.f : (cos_keep <= -1.f ? PI_F : acosf(cos_keep));
     for (int e = tid; e < TP * NB * SK; e += 256) {
-        const int tb = e / SK, q = e % SK;  // tb = tile * NB + ball
-        const int64_t ga = a0 * NB + tb, gb = b0 * NB + tb;
-        sa[tb * (SK + 1) + q] = ga < tA * NB ? cA[ga * SK + q] : 0.f;
-        sb[tb * (SK + 1) + q] = gb < tB * NB ? cB[gb * SK + q] : 0.f;
+        const int tb = e / SK, q = e % SK;  // tb = tile * NB + ball in the global order
+        const int t = tb / NB, x = tb % NB;
+        sa[(x * TP + t) * (SK + 1) + q] = a0 + t < tA ? cA[((a0 + t) * NB + x) * SK + q] : 0.f;
+        sb[(x * TP + t) * (SK + 1) + q] = b0 + t < tB ? cB[((b0 + t) * NB + x) * SK + q] : 0.f;
     }
     for (int e = tid; e < TP * NB; e += 256) {
-        ra[e] = a0 * NB + e < tA * NB ? rA[a0 * NB + e] : -1.f;
-        rb[e] = b0 * NB + e < tB * NB ? rB[b0 * NB + e] : -1.f;
+        const int t = e / NB, x = e % NB, k = x * TP + t;
+        const float ra = a0 + t < tA ? rA[(a0 + t) * NB + x] : -1.f;
+        const float rb = b0 + t < tB ? rB[(b0 + t) * NB + x] : -1.f;
+        pa[3 * k] = ra;
+        pa[3 * k + 1] = cosf(ra + alpha);
+        pa[3 * k + 2] = sinf(ra + alpha);
+        pb[3 * k] = rb;
+        pb[3 * k + 1] = cosf(rb);
+        pb[3 * k + 2] = sinf(rb);
     }
     __syncthreads();
-    // thread -> 2 x 2 tile pairs: rows (ty*2 + i), cols (tx*2 + j), ty, tx in 0..15
+    // thread -> 2 x 2 tile pairs: rows 2 ty + i, cols 2 tx + j (ty, tx in 0..15), i.e. 8 x 8 ball pairs
     const int ty = tid >> 4, tx = tid & 15;
+    float acc[2][NB][2][NB];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int x = 0; x < NB; ++x)
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+#pragma unroll
+                for (int y = 0; y < NB; ++y) acc[i][x][j][y] = 0.f;
+#pragma unroll 4
+    for (int q = 0; q < SK; ++q) {
+        float av[2][NB], bv[2][NB];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int x = 0; x < NB; ++x) av[i][x] = sa[(x * TP + 2 * ty + i) * (SK + 1) + q];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int y = 0; y < NB; ++y) bv[j][y] = sb[(y * TP + 2 * tx + j) * (SK + 1) + q];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int x = 0; x < NB; ++x)
+#pragma unroll
+                for (int j = 0; j < 2; ++j)
+#pragma unroll
+                    for (int y = 0; y < NB; ++y) acc[i][x][j][y] = fmaf(av[i][x], bv[j][y], acc[i][x][j][y]);
+    }
     unsigned mask = 0u;
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const int ta = ty * 2 + i;
+        const int ta = 2 * ty + i;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            const int tb = tx * 2 + j;
+            const int tb = 2 * tx + j;
             if (a0 + ta >= tA || b0 + tb >= tB) continue;
             if (sym && ((a0 + ta) >> 1) > b0 + tb) continue;  // self-join: block pairs on or above the diagonal
             bool keep = false;
-            for (int x = 0; x < NB && !keep; ++x) {
-                const float rx = ra[ta * NB + x];
-                if (rx < 0.f) continue;
-                const float *ca = sa + (ta * NB + x) * (SK + 1);
-                for (int y = 0; y < NB && !keep; ++y) {
-                    const float ry = rb[tb * NB + y];
-                    if (ry < 0.f) continue;
-                    const float *cb = sb + (tb * NB + y) * (SK + 1);
-                    float dot = 0.f;
-#pragma unroll 16
-                    for (int q = 0; q < SK; ++q) dot = fmaf(ca[q], cb[q], dot);
-                    const float gap = acosf(fmaxf(-1.f, fminf(1.f, dot))) - rx - ry;
-                    keep = gap <= 0.f || cosf(gap) >= cos_keep;
+#pragma unroll
+            for (int x = 0; x < NB; ++x) {
+                const float *qa = pa + 3 * (x * TP + ta);
+#pragma unroll
+                for (int y = 0; y < NB; ++y) {
+                    const float *qb = pb + 3 * (y * TP + tb);
+                    if (qa[0] < 0.f || qb[0] < 0.f) continue;  // unused ball
+                    if (qa[0] + alpha + qb[0] >= PI_F)
+                        keep = true;
+                    else
+                        keep |= acc[i][x][j][y] >= qa[1] * qb[1] - qa[2] * qb[2] - 1e-6f;
                 }
             }
             if (keep) mask |= 1u << (i * 2 + j);
@@ -493,7 +533,7 @@ cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, cons
 {
     if (k != SK) return cudaErrorInvalidValue;
     if (tA <= 0 || tB <= 0) return cudaSuccess;
-    const int smem = (2 * TP * NB * (SK + 1) + 2 * TP * NB) * 4;
+    const int smem = (2 * TP * NB * (SK + 1) + 2 * TP * NB * 3) * 4;
     cudaError_t e = cudaFuncSetAttribute(tile_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((tB + TP - 1) / TP), (unsigned)((tA + TP - 1) / TP));
