@@ -104,6 +104,109 @@ __global__ void __launch_bounds__(GNT) gemm_f32_kernel(const GemmArgs g)
     }
 }
 
+// Inference form of the layer product: C[i][j] = act(rowscale[i] * sum_k A[i][k] W[j][k] + bias[j]) with A
+// (M x K) and W (N x K) both contiguous along k, K % 16 == 0, lda, ldw % 4 == 0 and 16-byte aligned rows.
+// 128 x 128 output tile per block, 8 x 8 outputs per thread (two LDS.128 of A and two of W per k feed 64
+// FMAs), float4 global loads along k into k-major shared memory, and the next 16-wide K slice prefetched
+// into registers during the current one.
+constexpr int NT_T = 128, NT_K = 16;
+
+__global__ void __launch_bounds__(256) gemm_nt_f32_kernel(const float *__restrict__ A, int64_t lda,
+                                                          const float *__restrict__ W, int64_t ldw,
+                                                          const float *__restrict__ bias,
+                                                          const float *__restrict__ rowscale, int act,
+                                                          float *__restrict__ C, int64_t ldc, int64_t M, int N,
+                                                          int K)
+{
+    __shared__ __align__(16) float As[NT_K][NT_T + 4];
+    __shared__ __align__(16) float Ws[NT_K][NT_T + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.y * NT_T;
+    const int n0 = blockIdx.x * NT_T;
+    // loader: thread -> rows lr and lr + 64 of the tile, k quad lq (4 floats) of the slice
+    const int lr = tid >> 2, lq = (tid & 3) * 4;
+    auto load = [&](int k0, float4 (&a)[2], float4 (&w)[2]) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t gi = m0 + lr + 64 * h;
+            const int gj = n0 + lr + 64 * h;
+            a[h] = gi < M ? __ldg(reinterpret_cast<const float4 *>(A + gi * lda + k0 + lq))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            w[h] = gj < N ? __ldg(reinterpret_cast<const float4 *>(W + (int64_t)gj * ldw + k0 + lq))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    float acc[8][8] = {};
+    float4 ra[2], rw[2];
+    load(0, ra, rw);
+    for (int k0 = 0; k0 < K; k0 += NT_K) {
+        __syncthreads();  // the previous slice has been consumed
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = lr + 64 * h;
+            As[lq + 0][r] = ra[h].x;
+            As[lq + 1][r] = ra[h].y;
+            As[lq + 2][r] = ra[h].z;
+            As[lq + 3][r] = ra[h].w;
+            Ws[lq + 0][r] = rw[h].x;
+            Ws[lq + 1][r] = rw[h].y;
+            Ws[lq + 2][r] = rw[h].z;
+            Ws[lq + 3][r] = rw[h].w;
+        }
+        __syncthreads();
+        if (k0 + NT_K < K) load(k0 + NT_K, ra, rw);
+#pragma unroll
+        for (int kk = 0; kk < NT_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[kk][64 + ty * 4]);
+            const float4 w0 = *reinterpret_cast<const float4 *>(&Ws[kk][tx * 4]);
+            const float4 w1 = *reinterpret_cast<const float4 *>(&Ws[kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], wv[j], acc[i][j]);
+        }
+    }
+    // outputs: rows ty*4 + {0..3} and 64 + ty*4 + {0..3}, columns tx*4 + {0..3} and 64 + tx*4 + {0..3}
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int64_t row = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (row >= M) continue;
+        const float rs = rowscale ? rowscale[row] : 1.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int col = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (col >= N) continue;
+            float v = acc[i][j] * rs;
+            if (bias) v += bias[col];
+            if (act == ACT_GELU) v = gelu_f(v);
+            C[row * ldc + col] = v;
+        }
+    }
+}
+
+cudaError_t launch_gemm_nt_f32(const float *A, int64_t lda, const float *W, int64_t ldw, const float *bias,
+                               const float *rowscale, int act, float *C, int64_t ldc, int64_t M, int N, int K,
+                               cudaStream_t st)
+{
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (K % NT_K || lda % 4 || ldw % 4 || (reinterpret_cast<uintptr_t>(A) & 15) ||
+        (reinterpret_cast<uintptr_t>(W) & 15))
+        return cudaErrorInvalidValue;
+    const int64_t max_rows = (int64_t)65535 * NT_T;
+    for (int64_t r0 = 0; r0 < M; r0 += max_rows) {
+        const int64_t m = std::min<int64_t>(max_rows, M - r0);
+        dim3 grid((unsigned)((N + NT_T - 1) / NT_T), (unsigned)((m + NT_T - 1) / NT_T));
+        gemm_nt_f32_kernel<<<grid, 256, 0, st>>>(A + r0 * lda, lda, W, ldw, bias, rowscale ? rowscale + r0 : nullptr,
+                                                 act, C + r0 * ldc, ldc, m, N, K);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_gemm_f32(const GemmArgs &g, int num_sms, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;

@@ -35,6 +35,11 @@ struct GemmArgs {
 };
 
 cudaError_t launch_gemm_f32(const GemmArgs &g, int num_sms, cudaStream_t st);
+// C = act(rowscale[i] * A W^T + bias) with A (M x K) and W (N x K) contiguous along k (the inference form of a
+// layer); needs K % 16 == 0, lda and ldw multiples of 4 and 16-byte aligned A and W (else cudaErrorInvalidValue).
+cudaError_t launch_gemm_nt_f32(const float *A, int64_t lda, const float *W, int64_t ldw, const float *bias,
+                               const float *rowscale, int act, float *C, int64_t ldc, int64_t M, int N, int K,
+                               cudaStream_t st);
 cudaError_t launch_rownorm(const float *z, int64_t n, int k, float *s, float *nz, int num_sms, cudaStream_t st);
 // wsum: device pointer to the sum of the pair weights.
 cudaError_t launch_pair_grad(const float *s, int64_t B, int k, const float *t, const float *w, const float *wsum,

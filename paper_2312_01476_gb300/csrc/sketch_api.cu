@@ -70,36 +70,49 @@ cudaError_t sketch_forward(ejoin_sketch *sk, const float *x, int64_t n, int64_t 
     float *W = P(sk->params);
     for (int64_t r0 = 0; r0 < n; r0 += chunk) {
         const int64_t m = std::min<int64_t>(chunk, n - r0);
-        GemmArgs g1;
-        g1.A = x + r0 * ld;
-        g1.a_rs = ld;
-        g1.a_cs = 1;
-        g1.B = W + sk->oW1;
-        g1.b_rs = 1;
-        g1.b_cs = sk->d;
-        g1.C = P(sk->fH);
-        g1.ldc = sk->hid;
-        g1.bias = W + sk->ob1;
-        g1.rowscale = inv + r0;
-        g1.M = m;
-        g1.N = sk->hid;
-        g1.K = sk->d;
-        g1.act = ACT_GELU;
-        if ((e = launch_gemm_f32(g1, c->num_sms, st)) != cudaSuccess) return e;
-        GemmArgs g2;
-        g2.A = P(sk->fH);
-        g2.a_rs = sk->hid;
-        g2.a_cs = 1;
-        g2.B = W + sk->oW2;
-        g2.b_rs = 1;
-        g2.b_cs = sk->hid;
-        g2.C = P(sk->fZ);
-        g2.ldc = sk->out;
-        g2.bias = W + sk->ob2;
-        g2.M = m;
-        g2.N = sk->out;
-        g2.K = sk->hid;
-        if ((e = launch_gemm_f32(g2, c->num_sms, st)) != cudaSuccess) return e;
+        // the inference-form GEMM where the layout allows it, else the generic one
+        e = launch_gemm_nt_f32(x + r0 * ld, ld, W + sk->oW1, sk->d, W + sk->ob1, inv + r0, ACT_GELU, P(sk->fH),
+                               sk->hid, m, sk->hid, sk->d, st);
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            GemmArgs g1;
+            g1.A = x + r0 * ld;
+            g1.a_rs = ld;
+            g1.a_cs = 1;
+            g1.B = W + sk->oW1;
+            g1.b_rs = 1;
+            g1.b_cs = sk->d;
+            g1.C = P(sk->fH);
+            g1.ldc = sk->hid;
+            g1.bias = W + sk->ob1;
+            g1.rowscale = inv + r0;
+            g1.M = m;
+            g1.N = sk->hid;
+            g1.K = sk->d;
+            g1.act = ACT_GELU;
+            e = launch_gemm_f32(g1, c->num_sms, st);
+        }
+        if (e != cudaSuccess) return e;
+        e = launch_gemm_nt_f32(P(sk->fH), sk->hid, W + sk->oW2, sk->hid, W + sk->ob2, nullptr, ACT_NONE, P(sk->fZ),
+                               sk->out, m, sk->out, sk->hid, st);
+        if (e == cudaErrorInvalidValue) {
+            cudaGetLastError();
+            GemmArgs g2;
+            g2.A = P(sk->fH);
+            g2.a_rs = sk->hid;
+            g2.a_cs = 1;
+            g2.B = W + sk->oW2;
+            g2.b_rs = 1;
+            g2.b_cs = sk->hid;
+            g2.C = P(sk->fZ);
+            g2.ldc = sk->out;
+            g2.bias = W + sk->ob2;
+            g2.M = m;
+            g2.N = sk->out;
+            g2.K = sk->hid;
+            e = launch_gemm_f32(g2, c->num_sms, st);
+        }
+        if (e != cudaSuccess) return e;
         if ((e = launch_rownorm(P(sk->fZ), m, sk->out, S_out + r0 * sk->out, nullptr, c->num_sms, st)) !=
             cudaSuccess)
             return e;
