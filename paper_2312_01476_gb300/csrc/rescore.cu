@@ -208,6 +208,14 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
             valid = true;
         }
         const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        // symmetric self-joins (dense tiles): the R row of the previous candidate, kept in registers, since
+        // consecutive candidates often share it (a lane of the contraction epilogue emits its row's matches
+        // of a chunk together).  Sparse candidate lists gain nothing and would pay the registers.
+        constexpr bool REUSE = MIRROR;
+        uint32_t prev_i = 0xffffffffu;
+        float4 a_prev[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) a_prev[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
         for (int q0 = 0; q0 < RS_PER_WARP; q0 += C) {
             if (!((vmask >> q0) & 1u)) break;  // warp-uniform
@@ -218,15 +226,24 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_mlp_kernel(
                 ii[c] = __shfl_sync(0xffffffffu, gi, q0 + c);
                 jj[c] = __shfl_sync(0xffffffffu, gj, q0 + c);
                 const bool ok = (vmask >> (q0 + c)) & 1u;
+                const bool same = REUSE && ok && ii[c] == (c == 0 ? prev_i : ii[c - 1]);  // warp-uniform
                 const float4 *r = reinterpret_cast<const float4 *>(R + (int64_t)ii[c] * ldR);
                 const float4 *s = reinterpret_cast<const float4 *>(S + (int64_t)jj[c] * ldS);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const int g = lane + 32 * v;
                     const bool in = ok && g < d4;
-                    a[c][v] = in ? __ldg(r + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (same)
+                        a[c][v] = c == 0 ? a_prev[v] : a[c > 0 ? c - 1 : 0][v];
+                    else
+                        a[c][v] = in ? __ldg(r + g) : make_float4(0.f, 0.f, 0.f, 0.f);
                     b[c][v] = in ? __ldg(s + g) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+            }
+            if constexpr (REUSE) {
+                prev_i = ((vmask >> (q0 + C - 1)) & 1u) ? ii[C - 1] : 0xffffffffu;
+#pragma unroll
+                for (int v = 0; v < V; ++v) a_prev[v] = a[C - 1][v];
             }
             float acc[C];
 #pragma unroll
