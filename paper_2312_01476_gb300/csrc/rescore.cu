@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(256) rescore_band_kernel(const uint2 *__restri
 // V > 0: rows gathered as V float4 per lane (16-byte aligned inputs, d % 4 == 0,
 // d <= 128 V); V == 0: scalar loop for any d and alignment.
 template <int V>
-__global__ void __launch_bounds__(RS_WARPS * 32) rescore_batch_kernel(
+__global__ void __launch_bounds__(RS_WARPS * 32, 2) rescore_batch_kernel(
     const uint2 *__restrict__ cand, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
     const BatchRows br, int d, const float *__restrict__ invA, const float *__restrict__ invB, float fp64_band,
     BatchPair *__restrict__ out, uint64_t out_cap, unsigned long long *out_count, unsigned long long *band_count)
@@ -392,52 +392,78 @@ __global__ void __launch_bounds__(RS_WARPS * 32) rescore_batch_kernel(
             valid = true;
         }
         const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        // C candidates per step: their rows are gathered together (2 C V loads in flight per lane), then
+        // summed and decided one by one
+        constexpr int C = V == 0 ? 1 : (V <= 3 ? 4 : 2);
+        static_assert(RS_PER_WARP % C == 0, "candidates per warp step");
 #pragma unroll 1
-        for (int q = 0; q < RS_PER_WARP; ++q) {
-            if (!((vmask >> q) & 1u)) break;  // warp-uniform
-            const uint32_t jb = __shfl_sync(0xffffffffu, job, q);
-            const uint32_t ii = __shfl_sync(0xffffffffu, gi, q);
-            const uint32_t jj = __shfl_sync(0xffffffffu, gj, q);
-            const float eps = __shfl_sync(0xffffffffu, ej, q);
-            const float *r = br.R[jb] + (int64_t)ii * br.ldR[jb];
-            const float *s = br.S[jb] + (int64_t)jj * br.ldS[jb];
-            float acc = 0.f;
+        for (int q0 = 0; q0 < RS_PER_WARP; q0 += C) {
+            if (!((vmask >> q0) & 1u)) break;  // warp-uniform
+            uint32_t jb[C], ii[C], jj[C];
+            const float *rp[C], *sp[C];
+            float acc[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const bool ok = (vmask >> (q0 + c)) & 1u;
+                jb[c] = __shfl_sync(0xffffffffu, job, q0 + c);
+                ii[c] = __shfl_sync(0xffffffffu, gi, q0 + c);
+                jj[c] = __shfl_sync(0xffffffffu, gj, q0 + c);
+                rp[c] = ok ? br.R[jb[c]] + (int64_t)ii[c] * br.ldR[jb[c]] : nullptr;
+                sp[c] = ok ? br.S[jb[c]] + (int64_t)jj[c] * br.ldS[jb[c]] : nullptr;
+                acc[c] = 0.f;
+            }
             if constexpr (V > 0) {
-                float4 a[V], b[V];
+                float4 a[C][V], b[C][V];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const int g = lane + 32 * v;
-                    a[v] = g < d4 ? __ldg(reinterpret_cast<const float4 *>(r) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
-                    b[v] = g < d4 ? __ldg(reinterpret_cast<const float4 *>(s) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int c = 0; c < C; ++c) {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int g = lane + 32 * v;
+                        const bool in = rp[c] != nullptr && g < d4;
+                        a[c][v] = in ? __ldg(reinterpret_cast<const float4 *>(rp[c]) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        b[c][v] = in ? __ldg(reinterpret_cast<const float4 *>(sp[c]) + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    acc = fmaf(a[v].x, b[v].x, acc);
-                    acc = fmaf(a[v].y, b[v].y, acc);
-                    acc = fmaf(a[v].z, b[v].z, acc);
-                    acc = fmaf(a[v].w, b[v].w, acc);
-                }
+                for (int c = 0; c < C; ++c)
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        acc[c] = fmaf(a[c][v].x, b[c][v].x, acc[c]);
+                        acc[c] = fmaf(a[c][v].y, b[c][v].y, acc[c]);
+                        acc[c] = fmaf(a[c][v].z, b[c][v].z, acc[c]);
+                        acc[c] = fmaf(a[c][v].w, b[c][v].w, acc[c]);
+                    }
             } else {
-                for (int kk = lane; kk < d; kk += 32) acc = fmaf(__ldg(r + kk), __ldg(s + kk), acc);
+                if (rp[0])
+                    for (int kk = lane; kk < d; kk += 32) acc[0] = fmaf(__ldg(rp[0] + kk), __ldg(sp[0] + kk), acc[0]);
             }
-            acc = warp_sum_f(acc);
-            float sim = fminf(1.f, fmaxf(-1.f, acc * __shfl_sync(0xffffffffu, sc, q)));
-            bool emit = sim >= eps;
-            int band = 0;
-            if (fabsf(sim - eps) < fp64_band) {
-                // accurate tier: compensated dot product and norms, finished in FP64
-                const double s64 = accurate_cosine(r, s, d, lane);
-                emit = s64 >= (double)eps;
-                sim = (float)s64;
-                band = 1;
-            }
-            if (lane == q) {
-                my_emit = emit;
-                my.job = jb;
-                my.i = ii;
-                my.j = jj;
-                my.sim = sim;
-                my_band = band;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < C; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int q = q0 + c;
+                if (!((vmask >> q) & 1u)) break;  // warp-uniform
+                const float eps = __shfl_sync(0xffffffffu, ej, q);
+                float sim = fminf(1.f, fmaxf(-1.f, acc[c] * __shfl_sync(0xffffffffu, sc, q)));
+                bool emit = sim >= eps;
+                int band = 0;
+                if (fabsf(sim - eps) < fp64_band) {
+                    // accurate tier: compensated dot product and norms, finished in FP64
+                    const double s64 = accurate_cosine(rp[c], sp[c], d, lane);
+                    emit = s64 >= (double)eps;
+                    sim = (float)s64;
+                    band = 1;
+                }
+                if (lane == q) {
+                    my_emit = emit;
+                    my.job = jb[c];
+                    my.i = ii[c];
+                    my.j = jj[c];
+                    my.sim = sim;
+                    my_band = band;
+                }
             }
         }
         const unsigned m = __ballot_sync(0xffffffffu, my_emit);
