@@ -20,7 +20,7 @@
 
 #include <mutex>
 
-#include "ejoin_internal.cuh"
+#include "host_internal.h"
 
 using namespace ej;
 
@@ -78,34 +78,7 @@ ejoin_status device_setup(int dev, DeviceState **out)
     return EJOIN_OK;
 }
 
-bool encode_bf16_tmap(CUtensorMap *m, const void *base, int64_t kp, int64_t rows, uint32_t box_rows)
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return false;
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(kp * 2)};
-    cuuint32_t box[2] = {64, box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
 
-int64_t rup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
-
-ejoin_status st_of(cudaError_t e)
-{
-    if (e == cudaSuccess) return EJOIN_OK;
-    return e == cudaErrorMemoryAllocation ? EJOIN_ENOMEM : EJOIN_ECUDA;
-}
 
 }  // namespace
 
@@ -117,8 +90,8 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
     if (R.d != S.d || R.d < 1 || R.d > 4096 || R.n < 0 || S.n < 0 || R.ld < R.d || S.ld < S.d) return EJOIN_EINVAL;
     if ((R.n && !R.x) || (S.n && !S.x) || (capacity && !d_pairs) || eps != eps) return EJOIN_EINVAL;
     // size limits of the fixed scratch array
-    const int64_t kp = rup(R.d, 64);
-    const int64_t rowsA = rup(R.n > 0 ? R.n : 1, 256), rowsB = rup(S.n > 0 ? S.n : 1, 256);
+    const int64_t kp = host::round_up(R.d, 64);
+    const int64_t rowsA = host::round_up(R.n > 0 ? R.n : 1, 256), rowsB = host::round_up(S.n > 0 ? S.n : 1, 256);
     if (R.n > EJOIN_STATIC_MAX_ROWS || S.n > EJOIN_STATIC_MAX_ROWS ||
         (rowsA + rowsB) * kp > (int64_t)EJOIN_STATIC_MAX_OPERAND_ELEMS)
         return EJOIN_EINVAL;
@@ -147,28 +120,30 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
     }();
 
     cudaError_t e;
-    if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), s)) != cudaSuccess) return st_of(e);
-    if ((e = launch_set_count(&dm->n_sel[0], R.n, s)) != cudaSuccess) return st_of(e);
-    if ((e = launch_set_count(&dm->n_sel[1], S.n, s)) != cudaSuccess) return st_of(e);
+    if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), s)) != cudaSuccess) return host::from_cuda(e);
+    if ((e = launch_set_count(&dm->n_sel[0], R.n, s)) != cudaSuccess) return host::from_cuda(e);
+    if ((e = launch_set_count(&dm->n_sel[1], S.n, s)) != cudaSuccess) return host::from_cuda(e);
     if ((e = launch_normalize(FMT_BF16, R.x, R.ld, R.d, nullptr, &dm->n_sel[0], R.n, A, kp, (int)kp, invA, nullptr,
                               &dm->status, ds->num_sms, s)) != cudaSuccess)
-        return st_of(e);
+        return host::from_cuda(e);
     if ((e = launch_normalize(FMT_BF16, S.x, S.ld, S.d, nullptr, &dm->n_sel[1], S.n, B, kp, (int)kp, invB, nullptr,
                               &dm->status, ds->num_sms, s)) != cudaSuccess)
-        return st_of(e);
+        return host::from_cuda(e);
     CUtensorMap tmA, tmB;
-    if (!encode_bf16_tmap(&tmA, A, kp, rowsA, 128) || !encode_bf16_tmap(&tmB, B, kp, rowsB, 256)) return EJOIN_ECUDA;
+    if (!host::make_tmap(&tmA, A, FMT_BF16, kp, rowsA, 128) || !host::make_tmap(&tmB, B, FMT_BF16, kp, rowsB, 256))
+        return EJOIN_ECUDA;
     if ((e = launch_sim_tc(0, &tmA, &tmB, (int)kp, &dm->n_sel[0], &dm->n_sel[1], eps - band, nullptr, nullptr, cand,
                            EJOIN_STATIC_MAX_CANDIDATES, &dm->cand_count, &dm->status, 1ull << 31, 0, ds->num_sms,
                            default_group_m(kp), s)) != cudaSuccess)
-        return st_of(e);
+        return host::from_cuda(e);
     if ((e = launch_rescore(cand, &dm->cand_count, EJOIN_STATIC_MAX_CANDIDATES, R.x, R.ld, S.x, S.ld, R.d, nullptr,
                             nullptr, invA, invB, eps, 2e-5f, d_pairs, capacity, &dm->pair_count, &dm->band_count, 0,
                             ds->num_sms, s, band_list, EJOIN_STATIC_MAX_CANDIDATES)) != cudaSuccess)
-        return st_of(e);
+        return host::from_cuda(e);
     DevMisc hm;
-    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return st_of(e);
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return st_of(e);
+    if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return host::from_cuda(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return host::from_cuda(e);
     if (hm.status & ERR_NONFINITE) return EJOIN_ENONFINITE;
     if (hm.status & ERR_TIMEOUT) return EJOIN_ETIMEOUT;
     if (hm.status) return EJOIN_ECUDA;
