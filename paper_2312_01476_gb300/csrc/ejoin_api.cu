@@ -769,6 +769,7 @@ ejoin_status run_topk(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S, int 
     }
     if (timing) cudaEventRecord(c->ev[3], c->stream);
     if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+    if (hm.status) return status_of(hm.status);
     if (hm.pair_count) return EJOIN_ECUDA;  // a kept row with fewer candidates than records
     c->stats.pairs = n_out;
     if (timing) {
@@ -895,6 +896,7 @@ ejoin_status run_eselect(ejoin_ctx *c, const ejoin_rel &R, const ejoin_sel *selR
         }
         if (timing) cudaEventRecord(c->ev[3], c->stream);
         if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
+        if (hm.status) return status_of(hm.status);
         c->stats.pairs = hm.pair_count;
         c->stats.fp64_rescored = hm.band_count;
         if (timing) {
