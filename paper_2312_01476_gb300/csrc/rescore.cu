@@ -571,25 +571,21 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
 #define EJ_RESCORE_ARGS                                                                                              \
     cand, cand_count, cand_cap, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap, out_count, \
         band_count, count_only, band_list, band_cap
+    // fenced gathers, C chosen so that at most 12 float4 of row data per lane are in flight
+#define EJ_DISPATCH(M)                                                                                              \
+    if (aligned && d <= 128) rescore_mlp_kernel<1, 4, M, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);                 \
+    else if (aligned && d <= 256) rescore_mlp_kernel<2, 2, M, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);            \
+    else if (aligned && d <= 384) rescore_mlp_kernel<3, 2, M, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);            \
+    else if (aligned && d <= 512) rescore_mlp_kernel<4, 1, M, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);            \
+    else if (aligned && d <= 768) rescore_mlp_kernel<6, 1, M, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);            \
+    else if (aligned && d <= 1024) rescore_mlp_kernel<8, 1, M, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);           \
+    else rescore_kernel<M><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
     if (mirror) {
-        // symmetric self-joins: R-row reuse across consecutive candidates, no fence
-        if (aligned && d <= 128) rescore_mlp_kernel<1, 4, true, false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 256) rescore_mlp_kernel<2, 4, true, false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 384) rescore_mlp_kernel<3, 4, true, false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 512) rescore_mlp_kernel<4, 2, true, false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 768) rescore_mlp_kernel<6, 2, true, false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 1024) rescore_mlp_kernel<8, 2, true, false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else rescore_kernel<true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+        EJ_DISPATCH(true)
     } else {
-        // fenced gathers, C chosen so that at most 12 float4 of row data per lane are in flight
-        if (aligned && d <= 128) rescore_mlp_kernel<1, 4, false, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 256) rescore_mlp_kernel<2, 2, false, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 384) rescore_mlp_kernel<3, 2, false, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 512) rescore_mlp_kernel<4, 1, false, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 768) rescore_mlp_kernel<6, 1, false, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else if (aligned && d <= 1024) rescore_mlp_kernel<8, 1, false, true><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
-        else rescore_kernel<false><<<g, T, 0, st>>>(EJ_RESCORE_ARGS);
+        EJ_DISPATCH(false)
     }
+#undef EJ_DISPATCH
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || fp64_band <= 0.f) return e;
     // the accurate tier over the candidates listed near eps (stream order: after the FP32 tier)
