@@ -501,12 +501,13 @@ class Batch:
         _check(load_library().ejoin_batch_result(self.handle, ctypes.byref(p), ctypes.byref(cap)),
                "ejoin_batch_result")
         n = min(int(count), int(cap.value))
+        dev = f"cuda:{self.ctx.device}"
         if n == 0:
-            z = torch.zeros(0, dtype=torch.int32, device="cuda")
+            z = torch.zeros(0, dtype=torch.int32, device=dev)
             return z, z, z, z.view(torch.float32)
         # wrap the device buffer without copying it: 4 x 32-bit words per record
         buf = _DevBuf(p.value, n * 16)
-        t = torch.as_tensor(buf, device="cuda").view(torch.int32).view(n, 4)
+        t = torch.as_tensor(buf, device=dev).view(torch.int32).view(n, 4)
         return t[:, 0], t[:, 1], t[:, 2], t[:, 3].view(torch.float32)
 
     def info(self) -> dict:
@@ -577,7 +578,8 @@ class Sketch:
 
     def set_params(self, flat: np.ndarray):
         flat = np.ascontiguousarray(flat, dtype=np.float32)
-        assert flat.size == self.n_params
+        if flat.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters, got {flat.size}")
         _check(load_library().ejoin_sketch_set_params(self.handle, flat.ctypes.data), "ejoin_sketch_set_params")
 
     def get_params(self) -> np.ndarray:
