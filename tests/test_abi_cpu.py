@@ -11,7 +11,8 @@ HEADER = os.path.join(ROOT, "include", "ejoin.h")
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    with open(HEADER) as f:
+        src = f.read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(ejoin_[a-z_0-9]+)\s*\(", src)))
 

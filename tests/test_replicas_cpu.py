@@ -41,7 +41,7 @@ def _rank_main(rank, world, port, out):
 
 def test_step_time_is_the_maximum_over_two_gloo_ranks():
     port = free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of this multi-threaded process
         out = m.dict()
         mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
         assert dict(out) == {0: 11.0, 1: 11.0}
