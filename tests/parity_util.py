@@ -123,3 +123,27 @@ def compare_topk(R, S, k, gi, gj, gs, oi, oj, os_, tol=1e-5, rows=None):
     OJ = np.asarray(oj, dtype=np.int64).reshape(n, kk)
     same = sum(set(a.tolist()) == set(b.tolist()) for a, b in zip(J, OJ))
     return {"rows": int(n), "same_set": int(same), "max_gap": float(gap.max()), "max_err": float(err.max())}
+
+
+def check_every_pair(R, S, eps, gi, gj, gs, keep_r=None, keep_s=None, sample=20000, seed=0, tol=1e-5):
+    """Properties every GPU record must have, checked over the WHOLE result (at any size): ids in range
+    and kept by the selections (boolean masks keep_r / keep_s), no duplicate pair, a reported similarity
+    of at least eps - tol, and, on a seeded sample of the records drawn from the whole list, the FP64
+    similarity within tol of the reported one and at least eps - tol."""
+    gi = np.asarray(gi, dtype=np.int64)
+    gj = np.asarray(gj, dtype=np.int64)
+    gs = np.asarray(gs, dtype=np.float64)
+    assert gi.size == 0 or (gi.min() >= 0 and gi.max() < R.shape[0]), "R id out of range"
+    assert gj.size == 0 or (gj.min() >= 0 and gj.max() < S.shape[0]), "S id out of range"
+    if keep_r is not None:
+        assert np.asarray(keep_r)[gi].all(), "a pair of an R row the selection drops"
+    if keep_s is not None:
+        assert np.asarray(keep_s)[gj].all(), "a pair of an S row the selection drops"
+    keys = to_keys(gi, gj, S.shape[0])
+    assert len(np.unique(keys)) == len(keys), "duplicate pairs in the GPU result"
+    assert gs.size == 0 or gs.min() >= float(np.float32(eps)) - tol, "a reported similarity below eps"
+    if gi.size:
+        idx = np.random.default_rng(seed).choice(gi.size, size=min(sample, gi.size), replace=False)
+        want = oracle.sim_pairs(R, S, gi[idx].astype(np.uint32), gj[idx].astype(np.uint32))
+        assert np.abs(want - gs[idx]).max() <= tol, "sampled record: reported similarity off"
+        assert want.min() >= float(np.float32(eps)) - tol, "sampled record below eps in FP64"

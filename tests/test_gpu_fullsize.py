@@ -14,7 +14,7 @@ import pytest
 
 import ejoin_inputs as inputs
 import oracle
-from parity_util import compare
+from parity_util import check_every_pair, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -51,9 +51,10 @@ def test_c2_full_size_sampled_rows(c2, prec):
     oi, oj, os_ = oracle.join(w.R, w.S, w.eps, oracle.Selection(w.attrR, w.opR, w.cR), rows=rows, threads=THREADS)
     assert len(oi) > 1000
     gi, gj = res.i.cpu().numpy().view(np.uint32), res.j.cpu().numpy().view(np.uint32)
-    compare(w.R, w.S, w.eps, gi, gj, res.sim.cpu().numpy(), oi, oj, os_, rows=rows)
-    # no pair of an unselected R row
-    assert not np.isin(gi[:100_000].astype(np.int64), np.nonzero(w.attrR >= w.cR)[0]).any()
+    gs = res.sim.cpu().numpy()
+    compare(w.R, w.S, w.eps, gi, gj, gs, oi, oj, os_, rows=rows)
+    # the whole result: ids kept by the selection, no duplicates, sims >= eps, sampled records exact
+    check_every_pair(w.R, w.S, w.eps, gi, gj, gs, keep_r=w.attrR < w.cR, seed=7)
 
 
 @pytest.mark.parametrize("prec", ["bf16", "fp8"])
@@ -70,7 +71,12 @@ def test_c3_full_size_sampled_rows(prec):
     rows = sampled_rows(np.arange(n), 12, 3)
     oi, oj, os_ = oracle.join(w.R, w.R, w.eps, rows=rows, threads=THREADS)
     gi, gj = res.i.cpu().numpy().view(np.uint32), res.j.cpu().numpy().view(np.uint32)
-    compare(w.R, w.R, w.eps, gi, gj, res.sim.cpu().numpy(), oi, oj, os_, rows=rows)
+    gs = res.sim.cpu().numpy()
+    compare(w.R, w.R, w.eps, gi, gj, gs, oi, oj, os_, rows=rows)
+    check_every_pair(w.R, w.R, w.eps, gi, gj, gs, seed=8)
+    # the mirrored self-join: (j, i) present for every (i, j)
+    keys = gi.astype(np.int64) * n + gj
+    assert np.isin(gj.astype(np.int64) * n + gi, keys).all()
     del X, res
     torch.cuda.empty_cache()
 
