@@ -337,8 +337,8 @@ def run_ejoin(args):
     attr = torch.from_numpy(w.attrR).cuda() if w.attrR is not None else None
     selR = pkg.Sel(attr, w.opR, w.cR) if attr is not None else None
     fp64_band = 2e-3 if args.workload.startswith("c3") else -1.0
-    ctx = pkg.Ctx(device=local, prec=args.prec, flags=pkg.EJOIN_FLAG_TIMING, group_m=args.group_m,
-                  fp64_band=fp64_band)
+    flags = pkg.EJOIN_FLAG_TIMING | (pkg.EJOIN_FLAG_GATHER_RESCORE if args.gather_rescore else 0)
+    ctx = pkg.Ctx(device=local, prec=args.prec, flags=flags, group_m=args.group_m, fp64_band=fp64_band)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
 
     for _ in range(args.warmup):
@@ -870,6 +870,8 @@ def main():
     ap.add_argument("--cpu-s", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--ref-step-s", type=float, default=4.0, help="seconds of oracle work per reference step")
     ap.add_argument("--group-m", type=int, default=0, help="contraction raster group width (0: auto)")
+    ap.add_argument("--gather-rescore", action="store_true",
+                    help="re-score in emission order (EJOIN_FLAG_GATHER_RESCORE) instead of by panels of R rows")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true", help="accepted for compatibility; parity lives in tests/")

@@ -83,13 +83,21 @@ typedef enum ejoin_prec {
                                       i != j, in both orders; the result is the same set */
 #define EJOIN_FLAG_HOST_COPY  0x10u /* ejoin_threshold_host: copy the inputs to the device whole even when
                                        the kernels could read them in place (see there) */
+#define EJOIN_FLAG_GATHER_RESCORE 0x20u /* re-score the candidates in emission order, gathering both FP32 rows of
+                                           each from global memory.  By default, for d % 4 == 0, d <= 1024 and
+                                           16-byte aligned rows, the candidates are first bucketed by panels of
+                                           consecutive R rows and each panel's rows are staged in shared memory
+                                           once; both give the same pairs and similarities */
 
 typedef struct ejoin_config {
     int32_t device;          /* CUDA device ordinal */
     void *stream;            /* cudaStream_t for all work; NULL = the legacy default stream */
     int32_t prec;            /* ejoin_prec */
     float band;              /* guard band around eps for re-scoring; < 0: the rigorous default
-                                for prec and d (see DESIGN notes of each precision) */
+                                1.25 (2u + u^2 + 2 g + 8 * 2^-24) for prec and d, with g = kp 2^-24
+                                (FP32 accumulation over the kp padded columns) and u = 2^-8 (BF16),
+                                2^-10 (TF32) or, for e4m3, 2^-4 + 2^-10 sqrt(kp) / 448 (u = 0 for
+                                the FP32 CUDA-core path) */
     float fp64_band;         /* candidates with |sim32 - eps| < fp64_band are re-scored in FP64;
                                 < 0: default 2e-5 */
     uint64_t capacity_hint;  /* initial candidate-buffer size in pairs (0: 1 << 20); grows on demand */
@@ -401,6 +409,15 @@ typedef struct ejoin_prune_stats {
 ejoin_status ejoin_threshold_pruned(ejoin_ctx *ctx, ejoin_sketch *sk, ejoin_rel R, ejoin_rel S, float eps,
                                     float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *stats);
 
+/* Bound on every device-side wait of later calls on ctx, in SM clock cycles
+ * (0: 2^31, about one second), as ejoin_config.timeout_cycles.  A wait that
+ * runs out makes the call return EJOIN_ETIMEOUT with no valid result; its
+ * kernel first lets the copies and MMAs it has issued complete (a fixed bound
+ * of its own, about 8 s), frees its tensor memory and returns, so the context
+ * stays usable.  No counterpart in the paper (failure detection of the GPU
+ * path). */
+ejoin_status ejoin_set_timeout(ejoin_ctx *ctx, uint64_t timeout_cycles);
+
 /* Statistics of the last call on ctx. */
 ejoin_status ejoin_last_stats(const ejoin_ctx *ctx, ejoin_stats *out);
 
@@ -433,11 +450,12 @@ const char *ejoin_version(void);
  * Limits (EJOIN_EINVAL beyond them): R.n, S.n <= EJOIN_STATIC_MAX_ROWS and
  * (ceil(R.n/256) + ceil(S.n/256)) * 256 * ceil(d/64) * 64 <=
  * EJOIN_STATIC_MAX_OPERAND_ELEMS.  Every GPU that loads the library holds the
- * EJOIN_STATIC_SCRATCH_BYTES array until the process exits.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls share the array
- * and it keeps the last call's contents; counters are cleared at the start of
- * each call, and calls that overlap on the GPU race on the array.
+ * EJOIN_STATIC_SCRATCH_BYTES array until the process exits.  Every call looks
+ * up the array's device address (cudaGetSymbolAddress) with the current device
+ * and reads the counts back, synchronising `stream`: do not call it while that
+ * stream is being captured into a CUDA graph.  All calls share the array and
+ * it keeps the last call's contents; counters are cleared at the start of each
+ * call, and calls that overlap on the GPU race on the array.
  * ------------------------------------------------------------------------- */
 #define EJOIN_STATIC_MAX_ROWS 65536
 #define EJOIN_STATIC_MAX_OPERAND_ELEMS (1u << 24)

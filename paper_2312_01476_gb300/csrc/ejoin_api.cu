@@ -194,7 +194,7 @@ ejoin_status ejoin_create(ejoin_ctx **out, const ejoin_config *cfg)
         c->stream = reinterpret_cast<cudaStream_t>(cfg->stream);
         c->prec = cfg->prec;
         c->band_cfg = cfg->band;
-        c->fp64_band = cfg->fp64_band < 0.f ? 2e-5f : cfg->fp64_band;
+        c->fp64_band = cfg->fp64_band < 0.f ? DEFAULT_FP64_BAND : cfg->fp64_band;
         c->cap_hint = cfg->capacity_hint ? cfg->capacity_hint : (1u << 20);
         c->flags = cfg->flags;
         c->timeout = cfg->timeout_cycles ? cfg->timeout_cycles : (1ull << 31);
@@ -259,12 +259,23 @@ void ejoin_destroy(ejoin_ctx *c)
         release(c->misc);
         release(c->cand);
         release(c->band);
+        release(c->psorted);
+        release(c->pbuf);
+        release(c->top);
+        release(c->topseg);
         for (auto &b : c->host_in) release(b);
         release(c->host_pairs);
         if (c->events)
             for (auto &ev : c->ev) cudaEventDestroy(ev);
     }
     delete c;
+}
+
+ejoin_status ejoin_set_timeout(ejoin_ctx *c, uint64_t timeout_cycles)
+{
+    if (!c) return EJOIN_EINVAL;
+    c->timeout = timeout_cycles ? timeout_cycles : (1ull << 31);
+    return EJOIN_OK;
 }
 
 ejoin_status ejoin_last_stats(const ejoin_ctx *c, ejoin_stats *out)
@@ -530,17 +541,33 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         cudaError_t ee = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, c->stream);
         return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
     };
-    // exact re-score of the candidates (it reads their count on the device)
+    // exact re-score of the candidates (it reads their count on the device): panel-ordered where the rows
+    // allow it (R rows staged in shared memory per panel), else plain gathers in emission order
+    const bool panels = aligned_rows && R.d <= 1024 && !(c->flags & EJOIN_FLAG_GATHER_RESCORE);
     auto rescore = [&]() -> cudaError_t {
         cudaError_t ee = ensure(c->band, c->cand_cap * sizeof(uint2));
         if (ee != cudaSuccess) return ee;
-        ee = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, xR, ldR, xS, ldS, R.d,
-                            selR ? (const uint32_t *)sa.ids.p : nullptr, selS ? (const uint32_t *)sb.ids.p : nullptr,
-                            (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
-                            count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0,
-                            c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0);
-        if (ee != cudaSuccess) return ee;
-        c->stats.launches += c->fp64_band > 0.f ? 2 : 1;
+        const uint32_t *idsA = selR ? (const uint32_t *)sa.ids.p : nullptr;
+        const uint32_t *idsB = selS ? (const uint32_t *)sb.ids.p : nullptr;
+        if (panels) {
+            if ((ee = ensure(c->psorted, c->cand_cap * sizeof(uint2))) != cudaSuccess) return ee;
+            if ((ee = ensure(c->pbuf, rescore_panel_buf_bytes(R.n, S.n, R.d))) != cudaSuccess) return ee;
+            ee = launch_rescore_panels((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, (uint2 *)c->psorted.p,
+                                       c->pbuf.p, R.n, S.n, nA, xR, ldR, xS, ldS, R.d, idsA, idsB, (const float *)sa.inv.p,
+                                       (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
+                                       count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count,
+                                       count_only ? 1 : 0, c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap,
+                                       sym ? 1 : 0);
+            if (ee != cudaSuccess) return ee;
+            c->stats.launches += c->fp64_band > 0.f ? 7 : 6;
+        } else {
+            ee = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, xR, ldR, xS, ldS, R.d, idsA,
+                                idsB, (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
+                                count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0,
+                                c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0);
+            if (ee != cudaSuccess) return ee;
+            c->stats.launches += c->fp64_band > 0.f ? 2 : 1;
+        }
         if (timing) cudaEventRecord(c->ev[3], c->stream);
         if (d_count_user)
             ee = cudaMemcpyAsync(d_count_user, &dm->pair_count, sizeof(uint64_t), cudaMemcpyDeviceToDevice,

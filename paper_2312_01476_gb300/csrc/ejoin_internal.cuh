@@ -276,6 +276,23 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
                            unsigned long long *out_count, unsigned long long *band_count, int count_only,
                            int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror = 0);
 
+// Panel-ordered re-score (same decisions and similarities as launch_rescore, bit for bit): the candidates
+// are bucketed into `sorted` (cand_cap entries) by (block of S rows sized for L2, panel of
+// rescore_panel_rows(d) consecutive operand rows of R), and each panel's FP32 R rows are staged in shared
+// memory once, so only the S rows are gathered per candidate.  Needs d % 4 == 0, d <= 1024,
+// ldR % 4 == 0, ldS % 4 == 0 and 16-byte aligned R and S (cudaErrorInvalidValue otherwise); panel_buf
+// holds rescore_panel_buf_bytes(n_rows, n_rows_s, d) bytes, n_rows and n_rows_s upper bounds of the
+// operand rows of R (*nA_dev at run time) and of S.
+int rescore_panel_rows(int d);
+size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d);
+cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                  uint2 *sorted, void *panel_buf, int64_t n_rows, int64_t n_rows_s,
+                                  const long long *nA_dev, const float *R, int64_t ldR, const float *S, int64_t ldS,
+                                  int d, const uint32_t *idsR, const uint32_t *idsS, const float *invR,
+                                  const float *invS, float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
+                                  unsigned long long *out_count, unsigned long long *band_count, int count_only,
+                                  int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror);
+
 // ------------------------------------------------------- device PTX helpers
 #if defined(__CUDACC__)
 
@@ -334,6 +351,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
             *abort_flag = 1;
             atomicOr(status, ERR_TIMEOUT);
             return false;
+        }
+    }
+}
+
+// Wait for asynchronous work this CTA has already issued (TMA copies landing in its shared memory, MMAs
+// writing its TMEM) before it frees TMEM or exits.  Issued copies and MMAs always complete, in
+// microseconds, so this wait does not use the caller's timeout, which may be set short enough to expire
+// while they are in flight: it has a fixed bound of its own (DRAIN_CYCLES, about 8 s at 2 GHz), after
+// which it records ERR_TIMEOUT and returns.
+constexpr uint64_t DRAIN_CYCLES = 1ull << 34;
+__device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity, unsigned *status)
+{
+    if (mbar_try_wait(bar, parity)) return;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((uint64_t)(clock64() - t0) > DRAIN_CYCLES) {
+            atomicOr(status, ERR_TIMEOUT);
+            return;
         }
     }
 }

@@ -49,16 +49,6 @@ __device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t adesc, uint6
         "l"(adesc), "l"(bdesc), "r"(E_IDESC), "r"(accum));
 }
 
-__device__ __forceinline__ void esel_drain_wait(uint32_t bar, uint32_t parity, uint64_t timeout, unsigned *status)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if ((uint64_t)(clock64() - t0) > timeout) {
-            atomicOr(status, ERR_TIMEOUT);
-            return;
-        }
-    }
-}
 
 __global__ void __launch_bounds__(E_THREADS, 1)
     esel_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmQ, int num_kb,
@@ -136,7 +126,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
             for (int s = 0; s < E_STAGES; ++s) {
                 if ((uint64_t)s < issued) {
                     const uint64_t last = (uint64_t)s + (uint64_t)E_STAGES * ((issued - 1 - (uint64_t)s) / E_STAGES);
-                    esel_drain_wait(full_bar(s), (uint32_t)((last / E_STAGES) & 1u), timeout, status);
+                    mbar_drain_wait(full_bar(s), (uint32_t)((last / E_STAGES) & 1u), status);
                 }
             }
         }
@@ -179,7 +169,7 @@ __global__ void __launch_bounds__(E_THREADS, 1)
                 }
             }
             tc_commit(drain_bar);
-            esel_drain_wait(drain_bar, 0u, timeout, status);
+            mbar_drain_wait(drain_bar, 0u, status);
         }
         __syncwarp();
     } else if (warp < 6) {

@@ -28,6 +28,9 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 bool make_tmap(CUtensorMap *m, const void *base, int fmt, int64_t kp, int64_t rows, uint32_t box_rows);
 // Rigorous default guard band of a precision at padded dimension kp.
 float default_band(int prec, int64_t kp);
+// Default half-width around eps inside which the accurate tier (compensated dot products finished in
+// FP64) decides a candidate instead of the FP32 re-score.
+constexpr float DEFAULT_FP64_BAND = 2e-5f;
 
 struct DeviceGuard {
     int prev = -1;
@@ -69,6 +72,8 @@ struct ejoin_ctx {
     ej::host::Buf cand;
     uint64_t cand_cap = 0;
     ej::host::Buf band;  // candidates near eps for the accurate tier (as many slots as candidates)
+    ej::host::Buf psorted;  // panel-ordered re-score: the candidates bucketed by panel of R rows
+    ej::host::Buf pbuf;     // panel-ordered re-score: per-panel counts, offsets and chunk offsets
     ej::host::Buf top;     // top-k: per operand row scratch (maxima, thresholds, counts, offsets)
     ej::host::Buf topseg;  // top-k, k > 1: the candidates' keys bucketed by row
     ej::host::Buf host_in[6];

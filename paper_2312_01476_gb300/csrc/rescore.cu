@@ -551,6 +551,28 @@ cudaError_t launch_score_pairs(const float *R, int64_t ldR, const float *S, int6
     return cudaGetLastError();
 }
 
+// The accurate tier over the candidates that the FP32 tier listed near eps (stream order: after it).
+static cudaError_t launch_band_tier(const uint2 *band_list, const unsigned long long *band_count, uint64_t band_cap,
+                                    const float *R, int64_t ldR, const float *S, int64_t ldS, int d, float eps,
+                                    ejoin_pair *out, uint64_t out_cap, unsigned long long *out_count, int count_only,
+                                    bool aligned, bool mirror, int num_sms, cudaStream_t st)
+{
+    const unsigned gb = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((band_cap + 255) / 256, (uint64_t)num_sms * 8));
+#define EJ_BAND(M, V)                                                                                               \
+    rescore_band_kernel<M, V><<<gb, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, \
+                                                  out_count, count_only)
+    if (mirror) {
+        if (aligned) EJ_BAND(true, true);
+        else EJ_BAND(true, false);
+    } else {
+        if (aligned) EJ_BAND(false, true);
+        else EJ_BAND(false, false);
+    }
+#undef EJ_BAND
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap, const float *R,
                            int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *idsR,
                            const uint32_t *idsS, const float *invR, const float *invS, float eps, float fp64_band,
@@ -587,22 +609,611 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
     }
 #undef EJ_DISPATCH
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || fp64_band <= 0.f) return e;
-    // the accurate tier over the candidates listed near eps (stream order: after the FP32 tier)
-    const unsigned gb = (unsigned)std::min<uint64_t>((band_cap + 255) / 256, (uint64_t)num_sms * 8);
-#define EJ_BAND(M, V)                                                                                               \
-    rescore_band_kernel<M, V><<<gb, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, \
-                                                  out_count, count_only)
-    if (mirror) {
-        if (aligned) EJ_BAND(true, true);
-        else EJ_BAND(true, false);
-    } else {
-        if (aligned) EJ_BAND(false, true);
-        else EJ_BAND(false, false);
-    }
-#undef EJ_BAND
 #undef EJ_RESCORE_ARGS
+    if (e != cudaSuccess || fp64_band <= 0.f) return e;
+    return launch_band_tier(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, out_count,
+                            count_only, aligned, mirror != 0, num_sms, st);
+}
+
+// ---------------------------------------------------------------------------
+// Panel-ordered re-score.
+//
+// The candidates of a clustered join reuse each row about as often as the row
+// has matches (c2: ~100), but the plain re-score gathers both FP32 rows of
+// every candidate from L2 (2 * 4d bytes per candidate), which makes it bound
+// by L2 -> SM traffic.  Here the candidates are first bucketed (counting
+// sort: histogram, scan, scatter) by (S block, R panel): a panel is P
+// consecutive operand rows of R, an S block about PANEL_SBLOCK_BYTES of
+// consecutive FP32 rows of S, and the buckets are processed S-block-major.  A
+// CTA stages its panel's FP32 R rows in shared memory once (cp.async, 16-byte
+// pieces) and gathers only the S row of each candidate from global memory, so
+// the L2 -> SM bytes per candidate halve, while the CTAs running together
+// work inside one S block that stays resident in L2.  Per candidate the FP32
+// arithmetic, its order and the decision are those of rescore_mlp_kernel, so
+// the similarities are bit-identical; only the order of the records differs.
+// Buckets are cut into chunks of at most PANEL_CHUNK candidates so that one
+// dense bucket does not serialise on one CTA.
+namespace {
+constexpr int PANEL_CHUNK = 2048;
+constexpr int PANEL_SMEM_MAX = 49152;  // staged R rows per CTA (three CTAs per SM with the sorted chunk and staging)
+constexpr int PANEL_MAX_ROWS = 128;
+constexpr int PANEL_CTAS = 3;
+constexpr int64_t PANEL_SBLOCK_BYTES = 32ll << 20;
+constexpr int64_t PANEL_MAX_BUCKETS = 1ll << 22;
+constexpr int SCAN_THREADS = 1024;
+
+// Bucket geometry: bucket(c) = (c.y / sb) * np + (c.x >> shift), nb = nsb * np buckets.
+struct PanelGeom {
+    int shift;    // log2 of the panel height P
+    int64_t np;   // panels over the operand rows of R
+    int64_t sb;   // operand rows of S per S block
+    int64_t nsb;  // S blocks
+    int64_t nb;   // buckets
+};
+}  // namespace
+
+int rescore_panel_rows(int d)
+{
+    const int row_bytes = ((d + 3) / 4) * 16;
+    int p = PANEL_MAX_ROWS;
+    while (p > 8 && p * row_bytes > PANEL_SMEM_MAX) p >>= 1;
+    return p * row_bytes <= PANEL_SMEM_MAX ? p : 0;
+}
+
+static PanelGeom panel_geom(int64_t n_rows, int64_t n_rows_s, int d)
+{
+    PanelGeom g{};
+    const int P = rescore_panel_rows(d);
+    while ((1 << g.shift) < P) ++g.shift;
+    g.np = std::max<int64_t>(1, (n_rows + P - 1) / P);
+    const int64_t row_bytes = (int64_t)((d + 3) / 4) * 16;
+    const int64_t ns = std::max<int64_t>(1, n_rows_s);
+    int64_t nsb = std::max<int64_t>(1, (ns * row_bytes + PANEL_SBLOCK_BYTES - 1) / PANEL_SBLOCK_BYTES);
+    nsb = std::min<int64_t>(nsb, std::max<int64_t>(1, PANEL_MAX_BUCKETS / g.np));
+    g.sb = (ns + nsb - 1) / nsb;
+    g.nsb = (ns + g.sb - 1) / g.sb;
+    g.nb = g.nsb * g.np;
+    return g;
+}
+
+__device__ __forceinline__ unsigned panel_bucket(uint2 c, int shift, int64_t np, int64_t sb)
+{
+    return (unsigned)((int64_t)(c.y / (uint64_t)sb) * np + (int64_t)(c.x >> shift));
+}
+
+// cnt[bucket(c)] += 1 for every candidate (one atomic per group of lanes sharing a bucket)
+__global__ void __launch_bounds__(256) panel_hist_kernel(const uint2 *__restrict__ cand,
+                                                         const unsigned long long *__restrict__ cand_count,
+                                                         uint64_t cand_cap, PanelGeom g, unsigned long long *cnt)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t n = *cand_count;
+    if (n > cand_cap) n = cand_cap;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = w0 * 32; base < n; base += nw * 32) {
+        const uint64_t k = base + lane;
+        const bool ok = k < n;
+        const unsigned p = ok ? panel_bucket(cand[k], g.shift, g.np, g.sb) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, p);
+        if (ok && lane == __ffs(peers) - 1) atomicAdd(cnt + p, (unsigned long long)__popc(peers));
+    }
+}
+
+// Scan of the bucket counts in three phases (SCAN_ITEMS buckets per block): per-block totals of cnt and of
+// the chunk counts ceil(cnt / PANEL_CHUNK); one block scans those totals; each block then writes
+// off[b] = sum of cnt[< b], cursor[b] = off[b] and choff[b] = sum of the chunk counts of the buckets < b
+// (off[nb] = candidates, choff[nb] = chunks).
+constexpr int SCAN_ITEMS = SCAN_THREADS * 8;
+
+// Block-wide inclusive scan of two values per thread (x, y); returns the block totals through tx, ty.
+__device__ __forceinline__ void block_scan2(unsigned long long &x, unsigned long long &y, unsigned long long &tx,
+                                            unsigned long long &ty)
+{
+    __shared__ unsigned long long wa[32], wb[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long ya = __shfl_up_sync(0xffffffffu, x, o);
+        const unsigned long long yb = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) {
+            x += ya;
+            y += yb;
+        }
+    }
+    if (lane == 31) {
+        wa[warp] = x;
+        wb[warp] = y;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long a = lane < (int)(blockDim.x >> 5) ? wa[lane] : 0ull;
+        unsigned long long b = lane < (int)(blockDim.x >> 5) ? wb[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long ya = __shfl_up_sync(0xffffffffu, a, o);
+            const unsigned long long yb = __shfl_up_sync(0xffffffffu, b, o);
+            if (lane >= o) {
+                a += ya;
+                b += yb;
+            }
+        }
+        wa[lane] = a;
+        wb[lane] = b;
+    }
+    __syncthreads();
+    if (warp) {
+        x += wa[warp - 1];
+        y += wb[warp - 1];
+    }
+    tx = wa[(blockDim.x >> 5) - 1];
+    ty = wb[(blockDim.x >> 5) - 1];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) panel_scan_reduce_kernel(const unsigned long long *__restrict__ cnt,
+                                                                         int64_t nb, unsigned long long *tot)
+{
+    const int64_t b0 = (int64_t)blockIdx.x * SCAN_ITEMS;
+    unsigned long long a = 0, c = 0;
+    for (int k = threadIdx.x; k < SCAN_ITEMS; k += SCAN_THREADS) {
+        const int64_t i = b0 + k;
+        const unsigned long long v = i < nb ? cnt[i] : 0ull;
+        a += v;
+        c += (v + PANEL_CHUNK - 1) / PANEL_CHUNK;
+    }
+    unsigned long long ta, tc;
+    block_scan2(a, c, ta, tc);
+    if (threadIdx.x == 0) {
+        tot[2 * blockIdx.x] = ta;
+        tot[2 * blockIdx.x + 1] = tc;
+    }
+}
+
+// one block: exclusive scan of the per-block totals in place (tot[2 * blocks], tot[2 * blocks + 1] = totals)
+__global__ void __launch_bounds__(SCAN_THREADS) panel_scan_top_kernel(unsigned long long *tot, int blocks)
+{
+    __shared__ unsigned long long carry_a, carry_c;
+    if (threadIdx.x == 0) carry_a = carry_c = 0ull;
+    __syncthreads();
+    for (int base = 0; base < blocks; base += SCAN_THREADS) {
+        const int i = base + threadIdx.x;
+        const unsigned long long va = i < blocks ? tot[2 * i] : 0ull, vc = i < blocks ? tot[2 * i + 1] : 0ull;
+        unsigned long long a = va, c = vc, ta, tc;
+        block_scan2(a, c, ta, tc);
+        if (i < blocks) {
+            tot[2 * i] = carry_a + a - va;
+            tot[2 * i + 1] = carry_c + c - vc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_a += ta;
+            carry_c += tc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        tot[2 * blocks] = carry_a;
+        tot[2 * blocks + 1] = carry_c;
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) panel_scan_down_kernel(const unsigned long long *__restrict__ cnt,
+                                                                       int64_t nb, const unsigned long long *tot,
+                                                                       unsigned long long *off,
+                                                                       unsigned long long *cursor,
+                                                                       unsigned long long *choff)
+{
+    // each thread scans 8 consecutive buckets of the block's SCAN_ITEMS
+    constexpr int PER = SCAN_ITEMS / SCAN_THREADS;
+    const int64_t i0 = (int64_t)blockIdx.x * SCAN_ITEMS + (int64_t)threadIdx.x * PER;
+    unsigned long long v[PER], a = 0, c = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        v[k] = i0 + k < nb ? cnt[i0 + k] : 0ull;
+        a += v[k];
+        c += (v[k] + PANEL_CHUNK - 1) / PANEL_CHUNK;
+    }
+    unsigned long long ta, tc;
+    const unsigned long long a_in = a, c_in = c;
+    block_scan2(a, c, ta, tc);
+    unsigned long long ea = tot[2 * blockIdx.x] + a - a_in, ec = tot[2 * blockIdx.x + 1] + c - c_in;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (i0 + k < nb) {
+            off[i0 + k] = ea;
+            cursor[i0 + k] = ea;
+            choff[i0 + k] = ec;
+        }
+        ea += v[k];
+        ec += (v[k] + PANEL_CHUNK - 1) / PANEL_CHUNK;
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        off[nb] = tot[2 * gridDim.x];
+        choff[nb] = tot[2 * gridDim.x + 1];
+    }
+}
+
+// sorted[cursor[b]++] = candidate, b its bucket (one atomic per group of lanes sharing a bucket)
+__global__ void __launch_bounds__(256) panel_scatter_kernel(const uint2 *__restrict__ cand,
+                                                            const unsigned long long *__restrict__ cand_count,
+                                                            uint64_t cand_cap, PanelGeom g, unsigned long long *cursor,
+                                                            uint2 *__restrict__ sorted)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t n = *cand_count;
+    if (n > cand_cap) n = cand_cap;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = w0 * 32; base < n; base += nw * 32) {
+        const uint64_t k = base + lane;
+        const bool ok = k < n;
+        const uint2 c = ok ? cand[k] : make_uint2(0u, 0u);
+        const unsigned p = ok ? panel_bucket(c, g.shift, g.np, g.sb) : 0xffffffffu;
+        const unsigned peers = __match_any_sync(0xffffffffu, p);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long pos = 0;
+        if (ok && lane == leader) pos = atomicAdd(cursor + p, (unsigned long long)__popc(peers));
+        pos = __shfl_sync(0xffffffffu, pos, leader);
+        if (ok) sorted[pos + __popc(peers & ((1u << lane) - 1u))] = c;
+    }
+}
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Sum over the 32 lanes of C values per lane at once (transposed butterfly): at each of the first
+// log2(C) levels a lane keeps half of its values, hands the other half to its partner and adds the
+// partner's half of its own; the remaining levels are the plain butterfly on the one value left.  Every
+// value is combined over the same lane pairs (lane, lane ^ o), o = 16, 8, 4, 2, 1, as in
+// `v += __shfl_xor_sync(v, o)`, so each total is bit-identical to that butterfly, for
+// log2(C) + 5 - ... shuffles in place of 5 C.  On return lane c * (32 / C) holds the total of value c.
+template <int C>
+__device__ __forceinline__ float transpose_sum(float (&p)[C], int lane)
+{
+    float v[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) v[k] = p[k];
+    int n = C;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (n > 1) {
+            const bool hi = lane & o;
+            const int h = n >> 1;
+#pragma unroll
+            for (int k = 0; k < C / 2; ++k) {
+                if (k < h) {
+                    const float send = hi ? v[k] : v[k + h];
+                    const float keep = hi ? v[k + h] : v[k];
+                    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            n = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
+    return v[0];
+}
+
+// Per-warp staged emission of re-score results: each warp collects its records in a shared-memory
+// staging area of PANEL_STG records and claims global space with one atomic per flush, so no block-wide
+// barrier is needed per step.  mirror: a pair (i, j), i != j, is written as (i, j) and (j, i).
+constexpr int PANEL_STG = 96;
+template <bool MIRROR>
+__device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, float sim, ejoin_pair *stg, int &stg_n,
+                                          unsigned long long *out_count, ejoin_pair *__restrict__ out,
+                                          uint64_t out_cap, int count_only, int lane, bool final_flush)
+{
+    const int mine = emit ? ((MIRROR && i != j) ? 2 : 1) : 0;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    if (stg_n + tot > PANEL_STG || (final_flush && stg_n + tot > 0)) {
+        // flush what is staged, then this step's records go straight to global memory
+        const int n_all = stg_n + tot;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(out_count, (unsigned long long)n_all);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (!count_only) {
+            __syncwarp();
+            for (int x = lane; x < stg_n; x += 32)
+                if (base + (unsigned long long)x < out_cap) out[base + x] = stg[x];
+            if (mine) {
+                const unsigned long long pos = base + (unsigned long long)(stg_n + incl - mine);
+                if (pos < out_cap) out[pos] = ejoin_pair{i, j, sim};
+                if (mine == 2 && pos + 1 < out_cap) out[pos + 1] = ejoin_pair{j, i, sim};
+            }
+        }
+        stg_n = 0;
+        __syncwarp();
+        return;
+    }
+    if (mine && !count_only) {
+        const int pos = stg_n + incl - mine;
+        stg[pos] = ejoin_pair{i, j, sim};
+        if (mine == 2) stg[pos + 1] = ejoin_pair{j, i, sim};
+    }
+    stg_n += tot;
+    __syncwarp();
+}
+
+// Re-score of bucket-sorted candidates (d % 4 == 0, 16-byte aligned rows, d <= 128 V).  Per chunk (at
+// most PANEL_CHUNK candidates of one bucket): the panel's R rows are staged in shared memory (cp.async)
+// while the chunk's candidates are counting-sorted by R row in shared memory.  Each warp then takes 16
+// consecutive candidates per block step: the S rows of C of them are gathered at once (fenced, as in
+// rescore_mlp_kernel), the R row is read from shared memory into registers only when it changes (the
+// chunk is sorted by row), and the C per-lane partial sums are reduced together (transpose_sum).
+// Per candidate the lane partials and their reduction tree are those of rescore_mlp_kernel.
+template <int V, int C, bool MIRROR, int CTAS>
+__global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
+    const uint2 *__restrict__ sorted, const unsigned long long *__restrict__ off,
+    const unsigned long long *__restrict__ choff, PanelGeom pg, const long long *__restrict__ nA_dev,
+    const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
+    const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
+    const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
+    unsigned long long *out_count, unsigned long long *band_count, int count_only, uint2 *__restrict__ band_list,
+    uint64_t band_cap)
+{
+    static_assert(RS_PER_WARP % C == 0 && (C & (C - 1)) == 0, "candidates per warp step");
+    extern __shared__ float4 dyn[];
+    __shared__ int rcnt[PANEL_MAX_ROWS];
+    __shared__ ejoin_pair stg_all[RS_WARPS][PANEL_STG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ejoin_pair *stg = stg_all[warp];
+    int stg_n = 0;
+    const int d4 = d >> 2;
+    const int shift = pg.shift;
+    const int P = 1 << shift;
+    float4 *panel = dyn;                                                // P x d4
+    uint2 *cs = reinterpret_cast<uint2 *>(dyn + (size_t)P * (size_t)d4);  // the chunk, sorted by row
+    const long long nA = *nA_dev;
+    const unsigned long long n_chunks = choff[pg.nb];
+    for (unsigned long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+        // the chunk's bucket: the last b with choff[b] <= ch (it holds at least one chunk)
+        int64_t lo = 0, hi = pg.nb;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(choff + mid) <= ch) lo = mid;
+            else hi = mid;
+        }
+        const unsigned long long k0 = __ldg(off + lo) + (ch - __ldg(choff + lo)) * (unsigned long long)PANEL_CHUNK;
+        const int len = (int)min((unsigned long long)PANEL_CHUNK, __ldg(off + lo + 1) - k0);
+        const long long row0 = (long long)(lo % pg.np) << shift;  // the bucket's R panel
+        const int rows = (int)min((long long)P, nA - row0);
+        __syncthreads();  // the previous chunk is done with the panel, the sorted chunk and the counts
+        for (int r = warp; r < rows; r += RS_WARPS) {
+            const long long o = row0 + r;
+            const uint32_t src = idsR ? idsR[o] : (uint32_t)o;
+            const float4 *g = reinterpret_cast<const float4 *>(R + (int64_t)src * ldR);
+            for (int x = lane; x < d4; x += 32) cp_async16(panel + r * d4 + x, g + x);
+        }
+        // counting sort of the chunk by R row (while the panel copies are in flight)
+        for (int r = threadIdx.x; r < P; r += blockDim.x) rcnt[r] = 0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < len; k += blockDim.x) atomicAdd(&rcnt[sorted[k0 + k].x - row0], 1);
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive scan of the P <= 128 counts, 4 per lane
+            int v[PANEL_MAX_ROWS / 32], s = 0;
+#pragma unroll
+            for (int t = 0; t < PANEL_MAX_ROWS / 32; ++t) {
+                const int r = lane * (PANEL_MAX_ROWS / 32) + t;
+                v[t] = r < P ? rcnt[r] : 0;
+                s += v[t];
+            }
+            int incl = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int run = incl - s;
+#pragma unroll
+            for (int t = 0; t < PANEL_MAX_ROWS / 32; ++t) {
+                const int r = lane * (PANEL_MAX_ROWS / 32) + t;
+                if (r < P) rcnt[r] = run;
+                run += v[t];
+            }
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < len; k += blockDim.x) {
+            const uint2 c = sorted[k0 + k];
+            cs[atomicAdd(&rcnt[c.x - row0], 1)] = c;
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        // warps take the chunk's candidates 16 at a time, with no block-wide step
+        for (int gbase = warp * RS_PER_WARP; gbase < len; gbase += RS_PER_BLOCK) {
+            bool my_emit = false;
+            uint32_t my_i = 0, my_j = 0;
+            float my_sim = 0.f;
+            // lanes 0..15 fetch the warp's 16 candidates, their original ids, scales and panel rows
+            uint32_t gi = 0, gj = 0, lr = 0;
+            float sc = 0.f;
+            bool valid = false;
+            if (lane < RS_PER_WARP && gbase + lane < len) {
+                const uint2 c = cs[gbase + lane];
+                gi = idsR ? idsR[c.x] : c.x;
+                gj = idsS ? idsS[c.y] : c.y;
+                lr = (uint32_t)((long long)c.x - row0);
+                sc = invR[c.x] * invS[c.y];
+                valid = true;
+            }
+            const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+            if (vmask) {  // warp-uniform
+                float4 a[V];
+                uint32_t cur = 0xffffffffu;  // panel row held in a[]
+#pragma unroll
+                for (int v = 0; v < V; ++v) a[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+                for (int q0 = 0; q0 < RS_PER_WARP; q0 += C) {
+                    if (!((vmask >> q0) & 1u)) break;  // warp-uniform
+                    float4 b[C][V];
+                    uint32_t rr[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const uint32_t jj = __shfl_sync(0xffffffffu, gj, q0 + c);
+                        rr[c] = __shfl_sync(0xffffffffu, lr, q0 + c);
+                        const bool ok = (vmask >> (q0 + c)) & 1u;
+                        const float4 *srow = reinterpret_cast<const float4 *>(S + (int64_t)jj * ldS);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const int g = lane + 32 * v;
+                            b[c][v] = ok && g < d4 ? __ldg(srow + g) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+                    // all C * V gathers in flight together (see rescore_mlp_kernel)
+                    asm volatile("membar.cta;" ::: "memory");
+                    float part[C];
+#pragma unroll
+                    for (int c = 0; c < C; ++c) {
+                        const bool ok = (vmask >> (q0 + c)) & 1u;
+                        if (ok && rr[c] != cur) {  // warp-uniform; rare, the chunk is sorted by row
+                            cur = rr[c];
+#pragma unroll
+                            for (int v = 0; v < V; ++v) {
+                                const int g = lane + 32 * v;
+                                a[v] = g < d4 ? panel[cur * (uint32_t)d4 + g] : make_float4(0.f, 0.f, 0.f, 0.f);
+                            }
+                        }
+                        float acc = 0.f;
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            acc = fmaf(a[v].x, b[c][v].x, acc);
+                            acc = fmaf(a[v].y, b[c][v].y, acc);
+                            acc = fmaf(a[v].z, b[c][v].z, acc);
+                            acc = fmaf(a[v].w, b[c][v].w, acc);
+                        }
+                        part[c] = acc;
+                    }
+                    const float tot = transpose_sum<C>(part, lane);
+                    // lane q0 + c takes candidate c's dot product from lane c * (32 / C) and decides it
+                    const float mine = __shfl_sync(0xffffffffu, tot, ((lane - q0) & (C - 1)) * (32 / C));
+                    if (lane >= q0 && lane < q0 + C && ((vmask >> lane) & 1u)) {
+                        float sim = mine * sc;
+                        sim = fminf(1.f, fmaxf(-1.f, sim));
+                        bool emit = sim >= eps;
+                        if (fabsf(sim - eps) < fp64_band) {
+                            // near eps: decided by the accurate tier (rescore_band_kernel)
+                            const unsigned long long p = atomicAdd(band_count, 1ull);
+                            if (p < band_cap) band_list[p] = make_uint2(gi, gj);
+                            emit = false;
+                        }
+                        my_emit = emit;
+                        my_i = gi;
+                        my_j = gj;
+                        my_sim = sim;
+                    }
+                }
+            }
+            warp_emit<MIRROR>(my_emit, my_i, my_j, my_sim, stg, stg_n, out_count, out, out_cap, count_only, lane,
+                              false);
+        }
+    }
+    warp_emit<MIRROR>(false, 0u, 0u, 0.f, stg, stg_n, out_count, out, out_cap, count_only, lane, true);
+}
+
+size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d)
+{
+    if (rescore_panel_rows(d) == 0) return 0;
+    const PanelGeom g = panel_geom(n_rows, n_rows_s, d);
+    const int64_t scan_blocks = (g.nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    return (size_t)(4 * g.nb + 2 + 2 * scan_blocks + 2) * sizeof(unsigned long long);
+}
+
+template <int V, int C, bool M, int CTAS = PANEL_CTAS>
+static cudaError_t launch_panel_kernel(unsigned grid, size_t smem, cudaStream_t st, const uint2 *sorted,
+                                       const unsigned long long *off, const unsigned long long *choff,
+                                       const PanelGeom &pg, const long long *nA_dev, const float *R, int64_t ldR,
+                                       const float *S, int64_t ldS, int d, const uint32_t *idsR,
+                                       const uint32_t *idsS, const float *invR, const float *invS, float eps,
+                                       float fp64_band, ejoin_pair *out, uint64_t out_cap,
+                                       unsigned long long *out_count, unsigned long long *band_count, int count_only,
+                                       uint2 *band_list, uint64_t band_cap)
+{
+    // the shared-memory opt-in, once per device and instantiation
+    static unsigned long long configured = 0ull;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!((configured >> dev) & 1ull)) {
+        e = cudaFuncSetAttribute(rescore_panel_kernel<V, C, M, CTAS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 PANEL_SMEM_MAX + PANEL_CHUNK * (int)sizeof(uint2));
+        if (e != cudaSuccess) return e;
+        configured |= 1ull << dev;
+    }
+    rescore_panel_kernel<V, C, M, CTAS><<<grid, RS_WARPS * 32, smem, st>>>(
+        sorted, off, choff, pg, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap,
+        out_count, band_count, count_only, band_list, band_cap);
     return cudaGetLastError();
+}
+
+cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                  uint2 *sorted, void *panel_buf, int64_t n_rows, int64_t n_rows_s,
+                                  const long long *nA_dev, const float *R, int64_t ldR, const float *S, int64_t ldS,
+                                  int d, const uint32_t *idsR, const uint32_t *idsS, const float *invR,
+                                  const float *invS, float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
+                                  unsigned long long *out_count, unsigned long long *band_count, int count_only,
+                                  int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror)
+{
+    if (cand_cap == 0) return cudaSuccess;
+    if (fp64_band > 0.f && (!band_list || band_cap < cand_cap)) return cudaErrorInvalidValue;
+    const bool aligned = (d % 4 == 0) && (ldR % 4 == 0) && (ldS % 4 == 0) &&
+                         (reinterpret_cast<uintptr_t>(R) % 16 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
+    const int P = rescore_panel_rows(d);
+    if (!aligned || d > 1024 || P == 0 || !sorted || !panel_buf) return cudaErrorInvalidValue;
+    const PanelGeom g = panel_geom(n_rows, n_rows_s, d);
+    if (g.nb >= (int64_t)0xffffffffll) return cudaErrorInvalidValue;
+    unsigned long long *cnt = static_cast<unsigned long long *>(panel_buf);
+    unsigned long long *off = cnt + g.nb;        // nb + 1
+    unsigned long long *cursor = off + g.nb + 1;  // nb
+    unsigned long long *choff = cursor + g.nb;    // nb + 1
+    unsigned long long *tot = choff + g.nb + 1;    // 2 * scan_blocks + 2
+    const int64_t scan_blocks = (g.nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)g.nb * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    const unsigned gs = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((cand_cap + 255) / 256, (uint64_t)num_sms * 8));
+    panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cnt);
+    panel_scan_reduce_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot);
+    panel_scan_top_kernel<<<1, SCAN_THREADS, 0, st>>>(tot, (int)scan_blocks);
+    panel_scan_down_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot, off, cursor, choff);
+    panel_scatter_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cursor, sorted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const uint64_t max_chunks = (uint64_t)g.nb + cand_cap / PANEL_CHUNK + 1;
+    const unsigned grid =
+        (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(max_chunks, (uint64_t)num_sms * PANEL_CTAS));
+    const size_t smem = (size_t)P * (size_t)(d / 4) * 16 + PANEL_CHUNK * sizeof(uint2);
+#define EJ_PANEL_ARGS                                                                                            \
+    grid, smem, st, sorted, off, choff, g, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, \
+        out_cap, out_count, band_count, count_only, band_list, band_cap
+#define EJ_PANEL(M)                                                                            \
+    if (d <= 128) e = launch_panel_kernel<1, 8, M>(EJ_PANEL_ARGS);                             \
+    else if (d <= 256) e = launch_panel_kernel<2, 4, M>(EJ_PANEL_ARGS);                        \
+    else if (d <= 384) e = launch_panel_kernel<3, 4, M>(EJ_PANEL_ARGS);                        \
+    else if (d <= 512) e = launch_panel_kernel<4, 2, M>(EJ_PANEL_ARGS);                        \
+    else if (d <= 768) e = launch_panel_kernel<6, 2, M, 2>(EJ_PANEL_ARGS);                     \
+    else e = launch_panel_kernel<8, 1, M, 2>(EJ_PANEL_ARGS);
+    if (mirror) {
+        EJ_PANEL(true)
+    } else {
+        EJ_PANEL(false)
+    }
+#undef EJ_PANEL
+#undef EJ_PANEL_ARGS
+    if (e != cudaSuccess || fp64_band <= 0.f) return e;
+    return launch_band_tier(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, out_count,
+                            count_only, true, mirror != 0, num_sms, st);
 }
 
 }  // namespace ej

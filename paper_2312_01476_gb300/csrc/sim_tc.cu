@@ -20,7 +20,8 @@
 //               masks, warp prefix sums, staging in shared memory, one global
 //               atomic per flush of up to 512 candidates.
 // Every wait is bounded by `timeout` SM cycles; on expiry the CTA raises an
-// abort flag, records ERR_TIMEOUT, drains its in-flight copies and MMAs,
+// abort flag, records ERR_TIMEOUT, drains its in-flight copies and MMAs (with
+// a fixed bound of its own, not `timeout`: issued work always completes),
 // frees TMEM and exits.
 #include "ejoin_internal.cuh"
 
@@ -401,17 +402,6 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
     return ti;
 }
 
-// Wait without the abort shortcut (used only to drain in-flight work at exit).
-__device__ __forceinline__ void mbar_drain_wait(uint32_t bar, uint32_t parity, uint64_t timeout, unsigned *status)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if ((uint64_t)(clock64() - t0) > timeout) {
-            atomicOr(status, ERR_TIMEOUT);
-            return;
-        }
-    }
-}
 }  // namespace
 
 template <int KIND, int MODE>
@@ -516,7 +506,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             for (int s = 0; s < STAGES; ++s) {
                 if ((uint64_t)s < issued) {
                     const uint64_t last = (uint64_t)s + (uint64_t)STAGES * ((issued - 1 - (uint64_t)s) / STAGES);
-                    mbar_drain_wait(full_bar(s), (uint32_t)((last / STAGES) & 1u), timeout, status);
+                    mbar_drain_wait(full_bar(s), (uint32_t)((last / STAGES) & 1u), status);
                 }
             }
         }
@@ -561,7 +551,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             }
             // drain: all issued MMAs complete before TMEM is released
             tc_commit(drain_bar);
-            mbar_drain_wait(drain_bar, 0u, timeout, status);
+            mbar_drain_wait(drain_bar, 0u, status);
         }
         __syncwarp();
     } else if (warp >= 2 + EPI_WARPS) {

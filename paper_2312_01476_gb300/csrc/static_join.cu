@@ -42,43 +42,46 @@ static_assert(OFF_OPER % 1024 == 0, "operand area alignment for TMA");
 static_assert(sizeof(DevMisc) <= MISC_BYTES, "counter block");
 
 // The scratch array.  Host code must not use its name as a device address:
-// the address comes from cudaGetSymbolAddress in device_setup().
+// the address comes from cudaGetSymbolAddress in device_setup(), on every call.
 static __device__ __align__(256) unsigned char g_static_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-struct DeviceState {
+// Per-device attributes that outlive any context (SM count, architecture).  The scratch array's address
+// is not cached: a module can be reloaded into a new primary context (after cudaDeviceReset) at another
+// address, so every call looks it up again with the device current.
+struct DeviceInfo {
     bool ready = false;
-    unsigned char *scratch = nullptr;
     int num_sms = 0;
     bool sm103 = false;
 };
-DeviceState g_dev[MAX_DEVICES];
+DeviceInfo g_dev[MAX_DEVICES];
 std::mutex g_mu;
 
-ejoin_status device_setup(int dev, DeviceState **out)
+ejoin_status device_setup(int dev, int *num_sms, bool *sm103, unsigned char **scratch)
 {
     if (dev < 0 || dev >= MAX_DEVICES) return EJOIN_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_mu);
-    DeviceState &s = g_dev[dev];
-    if (!s.ready) {
-        void *p = nullptr;
-        // `dev` is the current device here (the caller's)
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return EJOIN_ECUDA;
-        int sms = 0, major = 0, minor = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
-            return EJOIN_ECUDA;
-        s.scratch = static_cast<unsigned char *>(p);
-        s.num_sms = sms;
-        s.sm103 = major == 10 && minor == 3;
-        s.ready = true;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DeviceInfo &s = g_dev[dev];
+        if (!s.ready) {
+            int sms = 0, major = 0, minor = 0;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+                return EJOIN_ECUDA;
+            s.num_sms = sms;
+            s.sm103 = major == 10 && minor == 3;
+            s.ready = true;
+        }
+        *num_sms = s.num_sms;
+        *sm103 = s.sm103;
     }
-    *out = &s;
+    // `dev` is the current device here (the caller's)
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || p == nullptr) return EJOIN_ECUDA;
+    *scratch = static_cast<unsigned char *>(p);
     return EJOIN_OK;
 }
-
-
 
 }  // namespace
 
@@ -99,13 +102,14 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return EJOIN_ECUDA;
-    DeviceState *ds = nullptr;
-    ejoin_status st = device_setup(dev, &ds);
+    int num_sms = 0;
+    bool sm103 = false;
+    unsigned char *base = nullptr;
+    ejoin_status st = device_setup(dev, &num_sms, &sm103, &base);
     if (st != EJOIN_OK) return st;
-    if (!ds->sm103) return EJOIN_EUNSUPPORTED;
+    if (!sm103) return EJOIN_EUNSUPPORTED;
 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    unsigned char *base = ds->scratch;
     DevMisc *dm = reinterpret_cast<DevMisc *>(base + OFF_MISC);
     float *invA = reinterpret_cast<float *>(base + OFF_INV_A);
     float *invB = reinterpret_cast<float *>(base + OFF_INV_B);
@@ -113,32 +117,28 @@ extern "C" ejoin_status ejoin_threshold_static(ejoin_rel R, ejoin_rel S, float e
     uint2 *band_list = reinterpret_cast<uint2 *>(base + OFF_BAND);
     void *A = base + OFF_OPER;
     void *B = base + OFF_OPER + (size_t)rowsA * kp * 2;
-    const float band = [&] {
-        // rigorous BF16 band (same expression as the context path's default)
-        const double u = 1.0 / 256.0, g = (double)kp / 16777216.0, small = 8.0 / 16777216.0;
-        return (float)(1.25 * (2 * u + u * u + 2 * g + small));
-    }();
+    const float band = host::default_band(EJOIN_BF16, kp);  // the context path's rigorous default
 
     cudaError_t e;
     if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), s)) != cudaSuccess) return host::from_cuda(e);
     if ((e = launch_set_count(&dm->n_sel[0], R.n, s)) != cudaSuccess) return host::from_cuda(e);
     if ((e = launch_set_count(&dm->n_sel[1], S.n, s)) != cudaSuccess) return host::from_cuda(e);
     if ((e = launch_normalize(FMT_BF16, R.x, R.ld, R.d, nullptr, &dm->n_sel[0], R.n, A, kp, (int)kp, invA, nullptr,
-                              &dm->status, ds->num_sms, s)) != cudaSuccess)
+                              &dm->status, num_sms, s)) != cudaSuccess)
         return host::from_cuda(e);
     if ((e = launch_normalize(FMT_BF16, S.x, S.ld, S.d, nullptr, &dm->n_sel[1], S.n, B, kp, (int)kp, invB, nullptr,
-                              &dm->status, ds->num_sms, s)) != cudaSuccess)
+                              &dm->status, num_sms, s)) != cudaSuccess)
         return host::from_cuda(e);
     CUtensorMap tmA, tmB;
     if (!host::make_tmap(&tmA, A, FMT_BF16, kp, rowsA, 128) || !host::make_tmap(&tmB, B, FMT_BF16, kp, rowsB, 256))
         return EJOIN_ECUDA;
     if ((e = launch_sim_tc(0, &tmA, &tmB, (int)kp, &dm->n_sel[0], &dm->n_sel[1], eps - band, nullptr, nullptr, cand,
-                           EJOIN_STATIC_MAX_CANDIDATES, &dm->cand_count, &dm->status, 1ull << 31, 0, ds->num_sms,
+                           EJOIN_STATIC_MAX_CANDIDATES, &dm->cand_count, &dm->status, 1ull << 31, 0, num_sms,
                            default_group_m(kp), s)) != cudaSuccess)
         return host::from_cuda(e);
     if ((e = launch_rescore(cand, &dm->cand_count, EJOIN_STATIC_MAX_CANDIDATES, R.x, R.ld, S.x, S.ld, R.d, nullptr,
-                            nullptr, invA, invB, eps, 2e-5f, d_pairs, capacity, &dm->pair_count, &dm->band_count, 0,
-                            ds->num_sms, s, band_list, EJOIN_STATIC_MAX_CANDIDATES)) != cudaSuccess)
+                            nullptr, invA, invB, eps, host::DEFAULT_FP64_BAND, d_pairs, capacity, &dm->pair_count,
+                            &dm->band_count, 0, num_sms, s, band_list, EJOIN_STATIC_MAX_CANDIDATES)) != cudaSuccess)
         return host::from_cuda(e);
     DevMisc hm;
     if ((e = cudaMemcpyAsync(&hm, dm, sizeof(DevMisc), cudaMemcpyDeviceToHost, s)) != cudaSuccess)

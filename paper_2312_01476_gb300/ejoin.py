@@ -23,7 +23,7 @@ EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
 EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
 EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
 EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED, EJOIN_FLAG_NO_SYMMETRY = 0x1, 0x2, 0x4, 0x8
-EJOIN_FLAG_HOST_COPY = 0x10
+EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE = 0x10, 0x20
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
 
@@ -107,6 +107,8 @@ def load_library(path: str = LIB_PATH):
     lib.ejoin_create.argtypes = [P(ctypes.c_void_p), P(ejoin_config)]
     lib.ejoin_destroy.restype = None
     lib.ejoin_destroy.argtypes = [ctypes.c_void_p]
+    lib.ejoin_set_timeout.restype = ctypes.c_int
+    lib.ejoin_set_timeout.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
     lib.ejoin_normalize.restype = ctypes.c_int
     lib.ejoin_normalize.argtypes = [ctypes.c_void_p, ejoin_rel, P(ejoin_sel), ctypes.c_int32, ctypes.c_void_p,
                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -270,6 +272,11 @@ def ejoin_create(**kw) -> Ctx:
 
 def ejoin_destroy(ctx: Ctx):
     ctx.close()
+
+
+def ejoin_set_timeout(ctx: Ctx, timeout_cycles: int):
+    """Bound (SM cycles, 0 = default) on the device-side waits of later calls on ctx."""
+    _check(load_library().ejoin_set_timeout(ctx.handle, int(timeout_cycles)), "ejoin_set_timeout")
 
 
 def _dev_rel(x) -> ejoin_rel:
