@@ -9,13 +9,14 @@
 // partition offsets m0, n0).  D never leaves the chip (Sec. V-B: the
 // "buffer" of a partition pair is a TMEM accumulator here).
 //
-// Structure (one persistent CTA per SM, 320 threads):
+// Structure (one persistent CTA per SM, 320 threads; 576 for e4m3):
 //   warp 0      TMA producer: 128-byte-swizzled K-slices of the R tile
 //               (128 rows) and S tile (256 rows) into a 4-stage smem ring.
 //   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma per stage into one
 //               of two 128 x 256 FP32 accumulators (512 TMEM columns).
-//   warps 2..9  epilogue, two warps per TMEM lane quarter, each on 128 of the
-//               256 accumulator columns: software-pipelined tcgen05.ld of 32
+//   warps 2..    epilogue, two (e4m3: four) warps per TMEM lane quarter, each
+//               on 128 (64) of the 256 accumulator columns: software-pipelined
+//               tcgen05.ld of 32
 //               columns, tree max-reduce for a fast reject, per-lane match
 //               masks, warp prefix sums, staging in shared memory, one global
 //               atomic per flush of up to 512 candidates.
@@ -33,27 +34,28 @@ constexpr int STAGES = 4;
 constexpr int ROW_BYTES = 128;  // K bytes of one stage row = one 128-byte swizzle atom
 constexpr int A_STAGE = BM * ROW_BYTES;
 constexpr int B_STAGE = BN * ROW_BYTES;
-constexpr int STAGING = 512;  // candidate slots per epilogue warp
 constexpr int FLUSH_TILES = 16;  // tiles between candidate flushes of an epilogue warp (or when staging is full)
-constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, 128 accumulator columns each
-constexpr int EPI_CHUNKS = BN / 2 / 32;  // 32-column chunks per epilogue warp
-constexpr int THREADS = (2 + EPI_WARPS) * 32;
-// fused re-score: warps 2 + EPI_WARPS .. consume candidates from a shared-memory ring that
+// Epilogue warps: the same number per TMEM lane quarter, each on a slice of the accumulator columns.  e4m3
+// tiles take half the MMA time of BF16 tiles, so their epilogue is split over 16 warps (64 columns each);
+// BF16 and TF32 use 8 (128 columns each), which leaves the MMA warp's scheduler less crowded.
+constexpr int epi_warps(int kind) { return kind == 1 ? 16 : 8; }
+constexpr int EPI_WARPS_MAX = 16;
+constexpr int STAGING_BYTES = 32768;  // candidate staging of all epilogue warps
+// fused re-score: warps 2 + epi_warps(kind) .. consume candidates from a shared-memory ring that
 // replaces the epilogue staging: QN cells of 8 data bytes, QN 32-bit cell sequence numbers,
 // then RS_STG staged result records per re-score warp
 constexpr int RS_WARPS_F = 4;
 constexpr int QN = 2048;
 constexpr int RS_STG = 128;
-constexpr int THREADS_FUSED = (2 + EPI_WARPS + RS_WARPS_F) * 32;
 constexpr uint32_t TMEM_COLS = 512;
 
 constexpr int OFF_A = 0;
 constexpr int OFF_B = OFF_A + STAGES * A_STAGE;
 constexpr int OFF_STG = OFF_B + STAGES * B_STAGE;
-constexpr int OFF_CTR = OFF_STG + EPI_WARPS * STAGING * 8;
-constexpr int OFF_BAR = OFF_CTR + EPI_WARPS * 4;
-static_assert(QN * 12 + RS_WARPS_F * RS_STG * 12 <= EPI_WARPS * STAGING * 8, "fused ring fits the staging area");
-static_assert(EPI_WARPS * 4 >= 12, "fused ring counters");
+constexpr int OFF_CTR = OFF_STG + STAGING_BYTES;
+constexpr int OFF_BAR = OFF_CTR + EPI_WARPS_MAX * 4;
+static_assert(QN * 12 + RS_WARPS_F * RS_STG * 12 <= STAGING_BYTES, "fused ring fits the staging area");
+static_assert(EPI_WARPS_MAX * 4 >= 12, "fused ring counters");
 constexpr int N_BARS = 2 * STAGES + 2 + 2 + 1;
 constexpr int OFF_MISC = OFF_BAR + N_BARS * 8;
 constexpr int SMEM_USED = OFF_MISC + 16;
@@ -110,6 +112,19 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
 __device__ __forceinline__ void tile_coords(long long t, long long tiles_m, long long tiles_n, int group_m,
                                             long long &m, long long &n)
 {
+    if (tiles_m * tiles_n < 0x7fffffffll && (long long)group_m * tiles_n < 0x7fffffffll) {
+        // 32-bit arithmetic (a 64-bit division is a long software sequence, paid per tile by every role)
+        const uint32_t tt = (uint32_t)t, tm = (uint32_t)tiles_m;
+        const uint32_t per_group = (uint32_t)group_m * (uint32_t)tiles_n;
+        const uint32_t g = tt / per_group;
+        const uint32_t first = g * (uint32_t)group_m;
+        const uint32_t gsz = min(tm - first, (uint32_t)group_m);
+        const uint32_t u = tt - g * per_group;
+        const uint32_t nn = u / gsz;
+        m = first + (u - nn * gsz);
+        n = nn;
+        return;
+    }
     const long long per_group = (long long)group_m * tiles_n;
     const long long g = t / per_group;
     const long long first = g * group_m;
@@ -183,8 +198,9 @@ __device__ __forceinline__ void sym_coords(long long t, const SymRaster &sr, lon
     const long long tri = tri_cols * (tri_cols + 1) / 2;
     long long x, y;
     if (b < tri) {
-        // column x holds x + 1 block rows: largest x with x (x + 1) / 2 <= b
-        x = (long long)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+        // column x holds x + 1 block rows: largest x with x (x + 1) / 2 <= b (b < G (G + 1) / 2 is small:
+        // the single-precision root is within one of x, and the loops below correct it)
+        x = (long long)((sqrtf(8.0f * (float)b + 1.0f) - 1.0f) * 0.5f);
         while (x * (x + 1) / 2 > b) --x;
         while ((x + 1) * (x + 2) / 2 <= b) ++x;
         y = b - x * (x + 1) / 2;
@@ -198,7 +214,10 @@ __device__ __forceinline__ void sym_coords(long long t, const SymRaster &sr, lon
     diag = x == y;
 }
 
-constexpr int threads_for(int mode) { return mode == MODE_FUSED ? THREADS_FUSED : THREADS; }
+constexpr int threads_for(int kind, int mode)
+{
+    return (2 + epi_warps(kind) + (mode == MODE_FUSED ? RS_WARPS_F : 0)) * 32;
+}
 
 // Re-score role of the fused kernel: take 8 queue slots at a time, gather the
 // FP32 rows of up to 8 candidates at once, FP32 dot (FP64 tier inside the
@@ -206,7 +225,7 @@ constexpr int threads_for(int mode) { return mode == MODE_FUSED ? THREADS_FUSED 
 // output.  Exits when every epilogue warp is done and the queue is drained.
 __device__ __forceinline__ void rescore_role(uint8_t *smem, const FuseArgs &fa, volatile int *abort_flag,
                                              unsigned *status, uint64_t timeout, int rw, int lane,
-                                             unsigned long long *band_count_total)
+                                             unsigned long long *band_count_total, int n_epi)
 {
     // bounded multi-producer / multi-consumer ring with per-cell sequence numbers: the producer
     // of position p waits for seq == p, writes, sets seq = p + 1; the consumer of p waits for
@@ -255,7 +274,7 @@ __device__ __forceinline__ void rescore_role(uint8_t *smem, const FuseArgs &fa, 
                     valid = true;
                     break;
                 }
-                if (vctr[2] == (uint32_t)EPI_WARPS && sl >= vctr[0]) {
+                if (vctr[2] == (uint32_t)n_epi && sl >= vctr[0]) {
                     ended = true;  // every candidate has been queued, and none at this position
                     break;
                 }
@@ -350,6 +369,14 @@ __device__ __forceinline__ void rescore_role(uint8_t *smem, const FuseArgs &fa, 
     if (lane == 0 && n_band) atomicAdd(band_count_total, n_band);
 }
 
+// max(a, b, c) in one instruction (three-input max.f32, sm_100 and later); the operands are finite
+__device__ __forceinline__ float fmax3(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 template <int MODE>
 __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &bt, long long tiles_m,
                                                 long long tiles_n, long long nA, long long nB, float thr, int group_m,
@@ -405,7 +432,7 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
 }  // namespace
 
 template <int KIND, int MODE>
-__global__ void __launch_bounds__(threads_for(MODE), 1)
+__global__ void __launch_bounds__(threads_for(KIND, MODE), 1)
     sim_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kp,
                   const long long *__restrict__ nA_ptr, const long long *__restrict__ nB_ptr, float thr,
                   const float *__restrict__ scaleA, const float *__restrict__ scaleB, uint2 *__restrict__ cand,
@@ -424,6 +451,10 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_MISC + 4);
 
+    constexpr int EPI_WARPS = epi_warps(KIND);
+    constexpr int SLICE_COLS = BN / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
+    constexpr int EPI_CHUNKS = SLICE_COLS / 32;       // 32-column chunks per epilogue warp
+    constexpr int STAGING = STAGING_BYTES / 8 / EPI_WARPS;  // candidate slots per epilogue warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long nA = MODE == MODE_BATCH ? 0 : *nA_ptr, nB = MODE == MODE_BATCH ? 0 : *nB_ptr;
     const long long tiles_m = (nA + BM - 1) / BM;
@@ -557,12 +588,13 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
     } else if (warp >= 2 + EPI_WARPS) {
         // ------------------------------------------------- fused re-score role
         if constexpr (MODE == MODE_FUSED)
-            rescore_role(smem, fa, abort_flag, status, timeout, warp - 2 - EPI_WARPS, lane, fa.band_count);
+            rescore_role(smem, fa, abort_flag, status, timeout, warp - 2 - EPI_WARPS, lane, fa.band_count,
+                         EPI_WARPS);
     } else {
         // ------------------------------------------------------------ epilogue
         const int e = warp - 2;      // 0 .. EPI_WARPS-1
         const int q = warp & 3;      // TMEM lane quarter this warp may access
-        const int half = e >> 2;     // which 128 accumulator columns
+        const int slice = e >> 2;    // which SLICE_COLS accumulator columns
         uint2 *stg = reinterpret_cast<uint2 *>(smem + OFF_STG) + e * STAGING;
         int *stg_ctr = reinterpret_cast<int *>(smem + OFF_CTR) + e;  // mirrors stg_cnt for slot claims
         // (in the fused mode these words hold the queue counters, set once at kernel start)
@@ -599,6 +631,16 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             if constexpr (MODE == MODE_TOPCAND || MODE == MODE_TOP1) {
                 if (q * 32 + lane < ti.limA) pre_best = __ldcg(bt.row_best + ti.rowA + q * 32 + lane);
             }
+            // e4m3 with tile-shared column scales: the row's and the tile's scales, loaded before the
+            // accumulator wait for the same reason
+            float pre_sa = 0.f, pre_sb = 0.f;
+            if constexpr (KIND == 1 && (MODE == MODE_SINGLE || MODE == MODE_SYM || MODE == MODE_TOPMAX ||
+                                        MODE == MODE_TOPCAND || MODE == MODE_TOP1)) {
+                if (q * 32 + lane < ti.limA) {
+                    pre_sa = scaleA[ti.rowA + q * 32 + lane];
+                    pre_sb = __ldg(scaleB + ti.rowB);
+                }
+            }
             int ok = 0;
             if (lane == 0) ok = mbar_wait_bounded(tfull_bar(acc), acc_phase, timeout, abort_flag, status) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -608,10 +650,10 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             const int row_local = q * 32 + lane;
             const bool row_ok = row_local < ti.limA;
             const long long row = ti.rowA + row_local;  // emitted operand row
-            const int colbase_local = half * (BN / 2);
+            const int colbase_local = slice * SLICE_COLS;
             const long long colbase = ti.rowB + colbase_local;
             const uint32_t tbase =
-                tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN) + (uint32_t)(half * (BN / 2));
+                tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN) + (uint32_t)(slice * SLICE_COLS);
             // e4m3: similarity = acc * s_row * s_col.  In the single and self-join modes the rows of a
             // 256-row column tile share one scale (launch_normalize_fp8_grouped), so the two scales fold
             // into a per-lane threshold on the raw accumulator; the other modes scale every element
@@ -635,7 +677,7 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
             // value is a lower bound of the final one)
             const float best0 = pre_best ? ord2f(pre_best) : -INFINITY;
             if constexpr (TILE_SCALE) {
-                const float sc = row_ok ? scaleA[row] * __ldg(scaleB + ti.rowB) : 0.f;
+                const float sc = row_ok ? pre_sa * pre_sb : 0.f;
                 sc_tile = sc;
                 thr_lane = sc > 0.f ? __fdiv_rn(thr_base, sc) : (thr_base <= 0.f ? -INFINITY : INFINITY);
             } else if constexpr (KIND == 1) {
@@ -656,18 +698,14 @@ __global__ void __launch_bounds__(threads_for(MODE), 1)
                     f[k] = __uint_as_float(v[k]);
                     if (KIND == 1 && !TILE_SCALE) f[k] *= rs * __shfl_sync(0xffffffffu, csc[c], k);
                 }
-                // max tree: a8[g] = max of f[8g .. 8g+7]
+                // max tree of three-input maxima: a8[g] = max of f[8g .. 8g+7]
                 float a8[4];
-                {
-                    float t[16], u[8];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) t[k] = fmaxf(f[2 * k], f[2 * k + 1]);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) u[k] = fmaxf(t[2 * k], t[2 * k + 1]);
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) a8[g] = fmaxf(u[2 * g], u[2 * g + 1]);
+                for (int g = 0; g < 4; ++g) {
+                    const float* h = f + 8 * g;
+                    a8[g] = fmax3(fmax3(h[0], h[1], h[2]), fmax3(h[3], h[4], h[5]), fmaxf(h[6], h[7]));
                 }
-                const float mx = fmaxf(fmaxf(a8[0], a8[1]), fmaxf(a8[2], a8[3]));
+                const float mx = fmax3(a8[0], a8[1], fmaxf(a8[2], a8[3]));
                 if constexpr (MODE == MODE_TOPMAX || MODE == MODE_TOP1) {
                     // the row maximum over the valid columns only (padding columns hold zeros)
                     if (left >= 32) {
@@ -881,7 +919,7 @@ static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, in
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
-    sim_tc_kernel<KIND, MODE><<<grid, threads_for(MODE), SMEM_BYTES, st>>>(
+    sim_tc_kernel<KIND, MODE><<<grid, threads_for(KIND, MODE), SMEM_BYTES, st>>>(
         *tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout, count_only,
         group_m < 1 ? 1 : group_m, bt, fa);
     return cudaGetLastError();
