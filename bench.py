@@ -738,7 +738,6 @@ def run_learned(args):
     import ejoin_inputs as inputs
     import paper_2312_01476_gb300 as pkg
     from paper_2312_01476_gb300 import ejoin as E
-    from paper_2312_01476_gb300 import learned as L
     w = inputs.c5_learned(threads=os.cpu_count() or 8)
     d = int(w.R.shape[1])
     X = torch.from_numpy(w.R).cuda()
@@ -746,16 +745,10 @@ def run_learned(args):
     Xcal = torch.from_numpy(w.extra["calib"]).cuda()
     ctx = pkg.Ctx(device=0, prec="bf16", flags=pkg.EJOIN_FLAG_TIMING)
     sk = E.Sketch(ctx, d, 256, 64)
-    sk.set_params(L.init_params(d, 256, 64, inputs.seed_for(5)))
-    t0 = time.perf_counter()
-    p, q, t, wt = L.labelled_pairs(ctx, Xtr, w.eps, 10_000_000, seed=inputs.seed_for(5))
-    t_label = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    hist = L.train(sk, Xtr, p, q, t, wt, epochs=3, batch=65536, lr=2e-3, log_every=50)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    eps_sk = L.calibrate(sk, ctx, Xcal, w.eps, recall=0.999)
-    del p, q, t, wt
+    # training and calibration in the library: labels from the exact join of a held-out sample, 10M pairs,
+    # 3 epochs, eps_sketch for recall 0.999 on a second held-out sample
+    eps_sk, train_rep = E.ejoin_sketch_train(sk, Xtr, Xcal, w.eps, n_pairs=10_000_000, epochs=3, batch=65536,
+                                             lr=2e-3, recall=0.999, seed=inputs.seed_for(5), init=True)
 
     def timed(fn, steps, warm):
         for _ in range(warm):
@@ -779,6 +772,11 @@ def run_learned(args):
     keep = np.isin(gi, rows)
     pruned_sample = set(zip(gi[keep].tolist(), gj[keep].tolist()))
     del res_p
+    # the library's sampled recall estimate (an extra call, outside the timed region)
+    _, st_est = E.ejoin_threshold_pruned(ctx, sk, X, X, w.eps, eps_sk, recall_est=True)
+    st_p["recall_est"] = st_est["recall_est"]
+    st_p["recall_sample_rows"] = st_est["recall_sample_rows"]
+    st_p["recall_sample_matches"] = st_est["recall_sample_matches"]
     res_f, ms_plain = timed(lambda: pkg.ejoin_threshold(ctx, X, X, w.eps), 1, 1)
     n_plain = res_f.count
     st_f = pkg.ejoin_last_stats(ctx)
@@ -804,8 +802,7 @@ def run_learned(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
            "config": {"workload": w.name + ", learned tile pruning (768-256-64 GELU sketch)",
                       "pairs_per_step": logical, "eps_sketch": eps_sk, "train_pairs": 10_000_000,
-                      "train_seconds": round(t_train, 2), "label_seconds": round(t_label, 2),
-                      "loss_history": [round(x, 5) for x in hist]},
+                      "training": train_rep},
            "pruned": st_p, "plain_bf16": {"ms_per_step": round(ms_plain, 2), "pairs": int(n_plain),
                                           "ms_contract": st_f["ms_contract"], "ms_rescore": st_f["ms_rescore"]},
            "recall": n_pruned / max(1, n_plain), "speedup_vs_plain_bf16": ms_plain / ms_pruned,

@@ -123,6 +123,15 @@ def clustered(n: int, d: int, centres: np.ndarray, theta: float, seed: int,
     return (out, ids) if with_ids else out
 
 
+def sketch_init_params(d: int, hidden: int, out: int, seed: int) -> np.ndarray:
+    """Seeded starting parameters of the sketch network (flat layout W1, b1, W2, b2): W1 and W2 scaled
+    Gaussian (1/sqrt of the fan-in), biases zero."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((hidden, d)) / math.sqrt(d)
+    W2 = rng.standard_normal((out, hidden)) / math.sqrt(hidden)
+    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(out)]).astype(np.float32)
+
+
 def uniform_attr(n: int, hi: int, seed: int) -> np.ndarray:
     rng = np.random.default_rng([seed, 0xA77])
     return rng.integers(0, hi, size=n, dtype=np.int32)

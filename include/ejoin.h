@@ -88,6 +88,10 @@ typedef enum ejoin_prec {
                                            16-byte aligned rows, the candidates are first bucketed by panels of
                                            consecutive R rows and each panel's rows are staged in shared memory
                                            once; both give the same pairs and similarities */
+#define EJOIN_FLAG_SORT       0x40u /* ejoin_threshold, ejoin_threshold_host, ejoin_eselect and
+                                       ejoin_threshold_pruned return their records sorted by (i, j)
+                                       ascending (a device radix sort after the join; the call
+                                       synchronises once more) instead of in no particular order */
 
 typedef struct ejoin_config {
     int32_t device;          /* CUDA device ordinal */
@@ -374,6 +378,51 @@ ejoin_status ejoin_row_inv_norm(ejoin_ctx *ctx, ejoin_rel X, float *d_inv);
 ejoin_status ejoin_score_pairs(ejoin_ctx *ctx, ejoin_rel R, ejoin_rel S, const uint32_t *d_i, const uint32_t *d_j,
                                int64_t n_pairs, float *d_sim);
 
+/* Training of the sketch network on the GPU, with its labelled set and its calibration.  X_train and
+ * X_cal are two held-out device samples of the rows the pruned join will see (raw FP32 rows, at least two
+ * each).  Steps, all in the library's kernels:
+ *   1. labels: the exact self-join of X_train at eps - label_margin (ejoin_threshold; matches and near
+ *      misses, each with its exact FP32 similarity as target, weight w_join), of which a seeded draw keeps
+ *      about n_pairs / 2 pairs (i != j), then uniform random row pairs of X_train scored exactly (weight 1)
+ *      up to n_pairs in all;
+ *   2. epochs: Adam steps (ejoin_sketch_train_step) over batches of the labelled pairs, each epoch in a
+ *      seeded order (a keyed bijection of the pair indices);
+ *   3. calibration: eps_sketch = the (1 - recall) quantile (linear interpolation between order statistics)
+ *      of the sketch cosine over the exact matches of X_cal at eps, less cal_margin.
+ * Every draw depends on cfg->seed only.  With init nonzero the parameters are first set to a seeded
+ * scaled Gaussian (W1 ~ N(0, 1/d), W2 ~ N(0, 1/hidden), biases 0) and the Adam state is reset; otherwise
+ * training continues from the current parameters.  *eps_sketch receives the calibrated threshold for
+ * ejoin_threshold_pruned (-1 when X_cal has no match), report (optional) the figures below.  Uses the
+ * context's stream and workspace (its statistics then describe the calibration join) and allocates its
+ * temporaries; synchronises.  The paper has no learned component. */
+typedef struct ejoin_sketch_train_cfg {
+    float eps;            /* the join threshold the sketch will prune for */
+    float label_margin;   /* labelling join at eps - label_margin (<= 0: 0.2) */
+    float w_join;         /* weight of the pairs from the labelling join (<= 0: 8) */
+    int64_t n_pairs;      /* labelled pairs (<= 0: 10,000,000; at most 2^31) */
+    int32_t epochs;       /* passes over the labelled pairs (<= 0: 3) */
+    int32_t batch;        /* pairs per Adam step (<= 0: 65,536) */
+    float lr;             /* Adam learning rate (<= 0: 0.002) */
+    float recall;         /* target recall of the calibration, in (0, 1] (else 0.999) */
+    float cal_margin;     /* subtracted from the calibrated quantile (< 0: 0.01) */
+    uint64_t seed;
+    int32_t init;         /* nonzero: seeded initialisation of the parameters first */
+} ejoin_sketch_train_cfg;
+
+typedef struct ejoin_sketch_train_report {
+    uint64_t label_join_pairs;     /* pairs of the labelling join, (i, i) included */
+    uint64_t labelled_join;        /* labelled pairs drawn from it */
+    uint64_t labelled_random;      /* random labelled pairs */
+    float loss_first, loss_last;   /* weighted loss of the first and of the last Adam step's batch */
+    uint64_t calibration_matches;  /* exact matches of X_cal at eps */
+    float eps_sketch;
+    float ms_label, ms_train, ms_calibrate;
+} ejoin_sketch_train_report;
+
+ejoin_status ejoin_sketch_train(ejoin_sketch *sk, ejoin_rel X_train, ejoin_rel X_cal,
+                                const ejoin_sketch_train_cfg *cfg, float *eps_sketch,
+                                ejoin_sketch_train_report *report);
+
 typedef struct ejoin_prune_stats {
     uint64_t tiles_total;  /* 128 x 256 tile pairs of the full join */
     uint64_t tiles_kept;   /* tile pairs whose sketch bound reaches eps_sketch */
@@ -390,7 +439,10 @@ typedef struct ejoin_prune_stats {
     /* the part of ms_prepare spent on R: normalisation and sketches, covering anchors, and anchor
        assignment with the reorder and gathers */
     float ms_sketch_a, ms_cover_a, ms_assign_a;
-    int32_t reserved;
+    /* recall estimate (filled when recall_est is given): the share of the exact matches of the sampled R
+       rows that the pruned join returns, the rows sampled and their exact matches */
+    float recall_est;
+    uint64_t recall_sample_rows, recall_sample_matches;
 } ejoin_prune_stats;
 
 /* Threshold join of R and S (device, no selection) that contracts only the
@@ -405,9 +457,14 @@ typedef struct ejoin_prune_stats {
  * on the sketch cosine of every row pair the two balls hold.  Every candidate is re-scored exactly, so the result is a subset of
  * ejoin_threshold's (equal up to the pairs whose sketch cosine is below
  * eps_sketch).  ctx must use BF16, e4m3 or TF32; out as for ejoin_threshold;
- * stats optional.  Synchronises. */
+ * stats optional.  recall_est (optional): the recall of the returned set
+ * against the plain join, estimated on up to 2048 evenly spaced rows of R:
+ * their exact join with S runs through the plain path, and a match counts as
+ * returned iff its tile pair was kept (that is exactly when the pruned join
+ * returns it); the estimate costs that sampled join.  Synchronises. */
 ejoin_status ejoin_threshold_pruned(ejoin_ctx *ctx, ejoin_sketch *sk, ejoin_rel R, ejoin_rel S, float eps,
-                                    float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *stats);
+                                    float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *stats,
+                                    float *recall_est);
 
 /* Bound on every device-side wait of later calls on ctx, in SM clock cycles
  * (0: 2^31, about one second), as ejoin_config.timeout_cycles.  A wait that

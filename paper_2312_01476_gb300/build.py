@@ -22,7 +22,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libejoin.so")
 
 SOURCES = ["ejoin_api.cu", "normalize.cu", "sim_simt.cu", "sim_tc.cu", "rescore.cu", "static_join.cu", "batch_api.cu",
-           "mlp.cu", "prune.cu", "sketch_api.cu", "topk.cu", "esel.cu"]
+           "mlp.cu", "prune.cu", "sketch_api.cu", "topk.cu", "esel.cu", "sort.cu", "train.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -153,6 +153,25 @@ float default_band(int prec, int64_t kp)
 
 using namespace ej::host;
 
+namespace ej {
+namespace host {
+ejoin_status sort_result(ejoin_ctx *c, ejoin_pair *pairs, uint64_t n, uint64_t n_i, uint64_t n_j)
+{
+    if (n <= 1) return EJOIN_OK;
+    if (n > 0xffffffffull) return EJOIN_EUNSUPPORTED;
+    cudaError_t e;
+    if ((e = ensure(c->sort_tmp, n * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
+    if ((e = ensure(c->sort_scratch, sort_pairs_scratch_bytes(n))) != cudaSuccess) return from_cuda(e);
+    if ((e = launch_sort_pairs(pairs, (ejoin_pair *)c->sort_tmp.p, n, n_i, n_j, c->sort_scratch.p, c->stream)) !=
+        cudaSuccess)
+        return from_cuda(e);
+    c->stats.launches += 1;
+    if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return from_cuda(e);
+    return EJOIN_OK;
+}
+}  // namespace host
+}  // namespace ej
+
 extern "C" {
 
 const char *ejoin_version(void) { return "ejoin-gb300 0.1 (sm_103a)"; }
@@ -261,6 +280,8 @@ void ejoin_destroy(ejoin_ctx *c)
         release(c->band);
         release(c->psorted);
         release(c->pbuf);
+        release(c->sort_tmp);
+        release(c->sort_scratch);
         release(c->top);
         release(c->topseg);
         for (auto &b : c->host_in) release(b);
@@ -509,6 +530,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         }
         *count_out = hf.pair_count;
         if (!count_only && hf.pair_count > *cap_io) return EJOIN_EOVERFLOW;
+        if ((c->flags & EJOIN_FLAG_SORT) && !count_only) return sort_result(c, *pairs_io, hf.pair_count, R.n, S.n);
         return EJOIN_OK;
     }
     // a self-join on the tensor cores contracts the upper triangle only (mirrored in the re-score)
@@ -606,7 +628,8 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         }
         // result buffer
         if (*pairs_io == nullptr && may_alloc && !count_only) {
-            const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
+            // a symmetric self-join writes each off-diagonal candidate in both orders
+            const uint64_t cap = std::max<uint64_t>(sym ? 2 * hm.cand_count : hm.cand_count, 1);
             void *p = nullptr;
             if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
             *pairs_io = (ejoin_pair *)p;
@@ -630,6 +653,7 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     }
     *count_out = hm.pair_count;
     if (!count_only && hm.pair_count > *cap_io) return EJOIN_EOVERFLOW;
+    if ((c->flags & EJOIN_FLAG_SORT) && !count_only) return sort_result(c, *pairs_io, hm.pair_count, R.n, S.n);
     return EJOIN_OK;
 }
 
@@ -935,6 +959,7 @@ ejoin_status run_eselect(ejoin_ctx *c, const ejoin_rel &R, const ejoin_sel *selR
         c->stats.fused = direct ? 1 : 0;
         *count_out = hm.pair_count;
         if (!count_only && hm.pair_count > *cap_io) return EJOIN_EOVERFLOW;
+        if ((c->flags & EJOIN_FLAG_SORT) && !count_only) return sort_result(c, *pairs_io, hm.pair_count, R.n, Q.n);
         return EJOIN_OK;
     }
     return EJOIN_ECUDA;

@@ -293,6 +293,13 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
                                   unsigned long long *out_count, unsigned long long *band_count, int count_only,
                                   int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror);
 
+// Sort of n result records by (i, j) ascending (sort.cu), i < n_i and j < n_j: LSD radix sort over the
+// significant bits of j, then of i, ping-ponging between data and tmp (n records); the result ends in
+// data.  scratch holds sort_pairs_scratch_bytes(n) bytes; n < 2^32.
+size_t sort_pairs_scratch_bytes(uint64_t n);
+cudaError_t launch_sort_pairs(ejoin_pair *data, ejoin_pair *tmp, uint64_t n, uint64_t n_i, uint64_t n_j,
+                              void *scratch, cudaStream_t st);
+
 // ------------------------------------------------------- device PTX helpers
 #if defined(__CUDACC__)
 

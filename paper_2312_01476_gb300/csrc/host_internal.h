@@ -55,6 +55,15 @@ constexpr int N_EV = 8;
 }  // namespace host
 }  // namespace ej
 
+struct ejoin_ctx;
+namespace ej {
+namespace host {
+// EJOIN_FLAG_SORT: sort the n records at `pairs` (device-accessible) by (i, j), i < n_i, j < n_j, on the
+// context's stream, and synchronise.
+ejoin_status sort_result(ejoin_ctx *c, ejoin_pair *pairs, uint64_t n, uint64_t n_i, uint64_t n_j);
+}  // namespace host
+}  // namespace ej
+
 struct ejoin_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -74,6 +83,7 @@ struct ejoin_ctx {
     ej::host::Buf band;  // candidates near eps for the accurate tier (as many slots as candidates)
     ej::host::Buf psorted;  // panel-ordered re-score: the candidates bucketed by panel of R rows
     ej::host::Buf pbuf;     // panel-ordered re-score: per-panel counts, offsets and chunk offsets
+    ej::host::Buf sort_tmp, sort_scratch;  // EJOIN_FLAG_SORT: second record buffer and digit counts
     ej::host::Buf top;     // top-k: per operand row scratch (maxima, thresholds, counts, offsets)
     ej::host::Buf topseg;  // top-k, k > 1: the candidates' keys bucketed by row
     ej::host::Buf host_in[6];

@@ -53,6 +53,34 @@ cudaError_t launch_colsum(const float *x, int64_t n, int k, float *out, int num_
 cudaError_t launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2,
                         float eps, int step, int num_sms, cudaStream_t st);
 
+// ---- training set-up (train.cu); draws are functions of (seed, index) only
+// params = [W1 (hid x d) ~ N(0, 1/d), b1 = 0, W2 (out x hid) ~ N(0, 1/hid), b2 = 0]
+cudaError_t launch_init_params(float *params, int d, int hid, int out, uint64_t seed, int num_sms, cudaStream_t st);
+// The join pairs (i, j), i != j, whose draw falls below keep / 2^32, in input order, as labelled pairs
+// (p, q, target = the pair's similarity, weight w_join), the first cap of them written; *d_total = their
+// number.  scratch holds label_scratch_bytes(n) bytes (a multiple of 16).
+size_t label_scratch_bytes(uint64_t n_join);
+cudaError_t launch_label_join_pairs(const ejoin_pair *pairs, uint64_t n, uint64_t seed, uint32_t keep, float w_join,
+                                    void *scratch, unsigned long long *d_total, uint64_t cap, uint32_t *p, uint32_t *q,
+                                    float *t, float *w, cudaStream_t st);
+// n_pairs uniform random row pairs of [0, n_rows)^2 with weight 1 (targets are scored separately).
+cudaError_t launch_random_pairs(uint32_t *p, uint32_t *q, float *w, int64_t n_pairs, uint32_t n_rows, uint64_t seed,
+                                int num_sms, cudaStream_t st);
+// Batch [b0, b0 + m) of epoch `epoch`'s order of the n labelled pairs (a seeded bijection of [0, n)).
+cudaError_t launch_gather_batch(const uint32_t *p, const uint32_t *q, const float *t, const float *w, uint64_t n,
+                                uint64_t seed, int epoch, uint64_t b0, int64_t m, uint32_t *bp, uint32_t *bq,
+                                float *bt, float *bw, int num_sms, cudaStream_t st);
+// rec[k] = {f2ord(v[k]), k, v[k]}: sorted by (i, j) they list the values in ascending order.
+cudaError_t launch_value_records(const float *v, int64_t n, ejoin_pair *rec, int num_sms, cudaStream_t st);
+// Recall probe of a pruned join: *found = the exact matches (i', j) in `pairs` (rows i' * stride of R) whose
+// tile pair (position of i in A / 128, position of j in B / 256; either orientation when sym) is in the
+// kept list.  permA / permB: position -> original row.  scratch holds recall_probe_scratch_bytes bytes (a
+// multiple of 16).
+size_t recall_probe_scratch_bytes(int64_t nA, int64_t nB, int64_t tA, int64_t tB);
+cudaError_t launch_recall_probe(const uint32_t *permA, int64_t nA, const uint32_t *permB, int64_t nB,
+                                const uint2 *list, const unsigned long long *list_count, uint64_t list_cap,
+                                int64_t tA, int64_t tB, const ejoin_pair *pairs, uint64_t n_pairs, uint32_t stride,
+                                int sym, void *scratch, unsigned long long *found, int num_sms, cudaStream_t st);
 // ---- pruning (prune.cu)
 // key[r] = base[r] * n_anchor + argmax_a <S[r], anchors[group(r) * n_anchor + a]>, where group(r) =
 // grp ? grp[r] : 0 (anchors of group g are rows g * n_anchor .. of `anchors`).

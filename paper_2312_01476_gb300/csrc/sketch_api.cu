@@ -450,6 +450,7 @@ ejoin_status ejoin_sketch_pair_sims(ejoin_sketch *sk, ejoin_rel X, const float *
 namespace {
 
 constexpr int SKW = 64;
+constexpr int64_t PRUNE_RECALL_ROWS = 2048;  // sampled rows of R for the recall estimate
 // covering anchors (see prune.cu): sample size, candidates per round, anchor limit, coverage cosine
 constexpr int64_t COVER_SAMPLE = 262144;
 constexpr int COVER_ROUND = 4096;
@@ -630,7 +631,7 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
 extern "C" {
 
 ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R, ejoin_rel S, float eps,
-                                    float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *ps)
+                                    float eps_sketch, ejoin_pairs *out, ejoin_prune_stats *ps, float *recall_est)
 {
     if (!c || !sk || !out || sk->ctx != c) return EJOIN_EINVAL;
     if (R.d != S.d || R.d != sk->d || R.n < 0 || S.n < 0 || R.ld < R.d || S.ld < S.d || (R.n && !R.x) ||
@@ -770,7 +771,8 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     // result buffer and exact re-score (sorted rows map back to original ids through the permutations)
     if (out->d_pairs == nullptr) {
         void *p = nullptr;
-        const uint64_t cap = std::max<uint64_t>(hm.cand_count, 1);
+        // a self-join writes each off-diagonal candidate in both orders
+        const uint64_t cap = std::max<uint64_t>(self ? 2 * hm.cand_count : hm.cand_count, 1);
         if ((e = cudaMalloc(&p, cap * sizeof(ejoin_pair))) != cudaSuccess) return from_cuda(e);
         out->d_pairs = (ejoin_pair *)p;
         out->capacity = cap;
@@ -826,7 +828,239 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     c->stats.fp64_rescored = hm.band_count;
     c->stats.band = band;
     out->count = hm.pair_count;
-    return hm.pair_count > out->capacity ? EJOIN_EOVERFLOW : EJOIN_OK;
+    if (recall_est) {
+        // recall estimate: the exact join of every stride-th row of R with S (the plain path), and the share
+        // of its matches whose tile pair the pruned join kept (each such match is found: its bulk
+        // similarity is within the band, and the re-score decides it as the plain join does)
+        const ejoin_stats pruned_stats = c->stats;
+        const int64_t m = std::min<int64_t>(R.n, PRUNE_RECALL_ROWS);
+        const int64_t stride = R.n / m;
+        const ejoin_rel Rs{R.x, m, R.d, R.ld * stride};
+        const uint32_t flags0 = c->flags;
+        c->flags &= ~(EJOIN_FLAG_SORT | EJOIN_FLAG_COUNT_ONLY | EJOIN_FLAG_FUSED);
+        ejoin_pairs sp{nullptr, 0, nullptr, 0};
+        s = ejoin_threshold(c, Rs, S, eps, nullptr, nullptr, &sp);
+        c->flags = flags0;
+        c->stats = pruned_stats;
+        Buf scr;
+        const size_t sb = recall_probe_scratch_bytes(R.n, S.n, tA, tB);
+        unsigned long long found = 0;
+        if (s == EJOIN_OK) {
+            if ((e = ensure(scr, sb + 8)) ||
+                (e = launch_recall_probe((const uint32_t *)pa.perm.p, R.n, (const uint32_t *)pb.perm.p, S.n,
+                                         (const uint2 *)sk->list.p, (const unsigned long long *)sk->list_count.p,
+                                         sk->list_cap, tA, tB, sp.d_pairs, sp.count, (uint32_t)stride, self ? 1 : 0,
+                                         scr.p, (unsigned long long *)((char *)scr.p + sb), c->num_sms, st)) ||
+                (e = cudaMemcpyAsync(&found, (char *)scr.p + sb, 8, cudaMemcpyDeviceToHost, st)) ||
+                (e = cudaStreamSynchronize(st)))
+                s = from_cuda(e);
+        }
+        release(scr);
+        const uint64_t total = sp.count;
+        ejoin_pairs_free(c, &sp);
+        if (s != EJOIN_OK) return s;
+        P_.recall_est = total ? (float)((double)found / (double)total) : 1.f;
+        P_.recall_sample_rows = (uint64_t)m;
+        P_.recall_sample_matches = total;
+        *recall_est = P_.recall_est;
+    }
+    if (hm.pair_count > out->capacity) return EJOIN_EOVERFLOW;
+    if (c->flags & EJOIN_FLAG_SORT) return sort_result(c, out->d_pairs, hm.pair_count, R.n, S.n);
+    return EJOIN_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------------------
+// Training of the sketch network with its labelled set and calibration (ejoin_sketch_train).
+namespace {
+
+// Records of a sorted join as separate row arrays: p[k] = pairs[k].i, q[k] = pairs[k].j.
+cudaError_t split_pairs(const ejoin_pair *pairs, uint64_t n, uint32_t *p, uint32_t *q, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemcpy2DAsync(p, 4, &pairs[0].i, sizeof(ejoin_pair), 4, n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(q, 4, &pairs[0].j, sizeof(ejoin_pair), 4, n, cudaMemcpyDeviceToDevice, st);
+    return e;
+}
+
+// The exact self-join of X at eps, sorted by (i, j), into a library-allocated buffer (caller frees it).
+ejoin_status sorted_self_join(ejoin_ctx *c, const ejoin_rel &X, float eps, ejoin_pairs *out)
+{
+    const uint32_t flags0 = c->flags;
+    c->flags = (flags0 | EJOIN_FLAG_SORT) & ~(EJOIN_FLAG_COUNT_ONLY | EJOIN_FLAG_FUSED);
+    *out = ejoin_pairs{nullptr, 0, nullptr, 0};
+    const ejoin_status s = ejoin_threshold(c, X, X, eps, nullptr, nullptr, out);
+    c->flags = flags0;
+    return s;
+}
+
+bool rel_valid(const ejoin_rel &X, int d) { return X.x && X.d == d && X.ld >= X.d && X.n >= 2 && X.n < (1ll << 31); }
+
+}  // namespace
+
+extern "C" {
+
+ejoin_status ejoin_sketch_train(ejoin_sketch *sk, ejoin_rel X_train, ejoin_rel X_cal,
+                                const ejoin_sketch_train_cfg *cfg_in, float *eps_sketch,
+                                ejoin_sketch_train_report *report)
+{
+    if (!sk || !cfg_in || !eps_sketch || !rel_valid(X_train, sk->d) || !rel_valid(X_cal, sk->d)) return EJOIN_EINVAL;
+    ejoin_sketch_train_cfg cfg = *cfg_in;
+    if (!(cfg.eps == cfg.eps)) return EJOIN_EINVAL;
+    if (cfg.label_margin <= 0.f) cfg.label_margin = 0.2f;
+    if (cfg.w_join <= 0.f) cfg.w_join = 8.f;
+    if (cfg.n_pairs <= 0) cfg.n_pairs = 10000000;
+    if (cfg.epochs <= 0) cfg.epochs = 3;
+    if (cfg.batch <= 0) cfg.batch = 65536;
+    if (cfg.lr <= 0.f) cfg.lr = 2e-3f;
+    if (cfg.recall <= 0.f || cfg.recall > 1.f) cfg.recall = 0.999f;
+    if (cfg.cal_margin < 0.f) cfg.cal_margin = 0.01f;
+    if (cfg.n_pairs > (1ll << 31) || cfg.batch > (1 << 24)) return EJOIN_EINVAL;
+    ejoin_ctx *c = sk->ctx;
+    DeviceGuard g(c->device);
+    cudaStream_t st = c->stream;
+    ejoin_sketch_train_report rep{};
+    cudaError_t e = cudaSuccess;
+    ejoin_status s = EJOIN_OK;
+    Buf lab, scratch, inv, batch, cal, rec;
+    ejoin_pairs jp{nullptr, 0, nullptr, 0};
+    cudaEvent_t ev[4] = {};
+    auto done = [&](ejoin_status r) {
+        if (jp.d_pairs) ejoin_pairs_free(c, &jp);
+        cudaStreamSynchronize(st);
+        for (Buf *b : {&lab, &scratch, &inv, &batch, &cal, &rec}) release(*b);
+        for (auto &x : ev)
+            if (x) cudaEventDestroy(x);
+        return r;
+    };
+    for (auto &x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) return done(EJOIN_ECUDA);
+    const uint64_t seed = cfg.seed;
+    cudaEventRecord(ev[0], st);
+    if (cfg.init) {
+        const size_t bytes = (size_t)sk->n_params * 4;
+        if ((e = launch_init_params(P(sk->params), sk->d, sk->hid, sk->out, seed, c->num_sms, st)) ||
+            (e = cudaMemsetAsync(sk->m.p, 0, bytes, st)) || (e = cudaMemsetAsync(sk->v.p, 0, bytes, st)))
+            return done(from_cuda(e));
+        sk->step = 0;
+    }
+
+    // 1. labelled set: the exact self-join of the training sample at eps - label_margin (matches and near
+    //    misses, each with its exact similarity as target), subsampled to about half of n_pairs, then
+    //    uniform random pairs scored exactly
+    if ((s = sorted_self_join(c, X_train, cfg.eps - cfg.label_margin, &jp)) != EJOIN_OK) return done(s);
+    rep.label_join_pairs = jp.count;
+    const int64_t n_pairs = cfg.n_pairs;
+    const uint64_t off_diag = jp.count > (uint64_t)X_train.n ? jp.count - (uint64_t)X_train.n : 1;
+    const double frac = std::min(1.0, (double)(n_pairs / 2) / (double)off_diag);
+    const uint32_t keep = frac >= 1.0 ? 0xffffffffu : (uint32_t)(frac * 4294967296.0);
+    const uint64_t cap = (uint64_t)n_pairs;  // join pairs first, random pairs fill the rest
+    uint32_t *lp, *lq;
+    float *lt, *lw;
+    if ((e = ensure(lab, (size_t)cap * 16)) ||
+        (e = ensure(scratch, label_scratch_bytes(jp.count) + 64)) ||
+        (e = ensure(inv, (size_t)X_train.n * 4)))
+        return done(from_cuda(e));
+    lp = (uint32_t *)lab.p;
+    lq = lp + cap;
+    lt = (float *)(lq + cap);
+    lw = lt + cap;
+    unsigned long long *d_total = (unsigned long long *)((char *)scratch.p + label_scratch_bytes(jp.count));
+    // the draw keeps about n_pairs / 2 of the join pairs (at most cap are written)
+    if ((e = launch_label_join_pairs(jp.d_pairs, jp.count, seed, keep, cfg.w_join, scratch.p, d_total, cap, lp, lq,
+                                     lt, lw, st)))
+        return done(from_cuda(e));
+    unsigned long long kept = 0;
+    if ((e = cudaMemcpyAsync(&kept, d_total, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+        return done(from_cuda(e));
+    ejoin_pairs_free(c, &jp);
+    jp = ejoin_pairs{nullptr, 0, nullptr, 0};
+    kept = std::min<unsigned long long>(kept, (unsigned long long)n_pairs);
+    const int64_t n_rand = n_pairs - (int64_t)kept;
+    if ((e = launch_row_inv_norm(X_train.x, X_train.n, X_train.d, X_train.ld, (float *)inv.p, c->num_sms, st)) ||
+        (e = launch_random_pairs(lp + kept, lq + kept, lw + kept, n_rand, (uint32_t)X_train.n, seed, c->num_sms,
+                                 st)) ||
+        (e = launch_score_pairs(X_train.x, X_train.ld, X_train.x, X_train.ld, X_train.d, lp + kept, lq + kept,
+                                (const float *)inv.p, (const float *)inv.p, n_rand, lt + kept, c->num_sms, st)))
+        return done(from_cuda(e));
+    rep.labelled_join = kept;
+    rep.labelled_random = (uint64_t)n_rand;
+    cudaEventRecord(ev[1], st);
+
+    // 2. epochs of Adam steps over the labelled set, in a seeded order per epoch
+    const int64_t n_lab = (int64_t)kept + n_rand;
+    const int64_t bsz = std::min<int64_t>(cfg.batch, n_lab);
+    if ((e = ensure(batch, (size_t)bsz * 16))) return done(from_cuda(e));
+    uint32_t *bp = (uint32_t *)batch.p, *bq = bp + bsz;
+    float *bt = (float *)(bq + bsz), *bw = bt + bsz;
+    bool first = true;
+    for (int ep = 0; ep < cfg.epochs; ++ep) {
+        for (int64_t b0 = 0; b0 < n_lab; b0 += bsz) {
+            const int64_t m = std::min<int64_t>(bsz, n_lab - b0);
+            if ((e = launch_gather_batch(lp, lq, lt, lw, (uint64_t)n_lab, seed, ep, (uint64_t)b0, m, bp, bq, bt, bw,
+                                         c->num_sms, st)) ||
+                (e = sketch_grad(sk, X_train.x, X_train.ld, (const float *)inv.p, bp, bq, bt, bw, m, st)))
+                return done(from_cuda(e));
+            sk->step += 1;
+            if ((e = launch_adam(P(sk->params), P(sk->grads), P(sk->m), P(sk->v), sk->n_params, cfg.lr, 0.9f, 0.999f,
+                                 1e-8f, sk->step, c->num_sms, st)))
+                return done(from_cuda(e));
+            const bool last = ep == cfg.epochs - 1 && b0 + bsz >= n_lab;
+            if (first || last) {
+                float loss = 0.f;  // the loss of this step's batch, before its update
+                if ((e = cudaMemcpyAsync(&loss, sk->scal.p, 4, cudaMemcpyDeviceToHost, st)) ||
+                    (e = cudaStreamSynchronize(st)))
+                    return done(from_cuda(e));
+                if (first) rep.loss_first = loss;
+                if (last) rep.loss_last = loss;
+                first = false;
+            }
+        }
+    }
+    cudaEventRecord(ev[2], st);
+
+    // 3. calibration: eps_sketch is the (1 - recall) quantile of the sketch cosine over the exact matches
+    //    of the calibration sample (linear interpolation between order statistics), less cal_margin
+    if ((s = sorted_self_join(c, X_cal, cfg.eps, &jp)) != EJOIN_OK) return done(s);
+    const uint64_t nm = jp.count;
+    rep.calibration_matches = nm;
+    float eps_sk = -1.f;
+    if (nm > 0) {
+        if ((e = ensure(cal, (size_t)nm * 12 + (size_t)X_cal.n * 4)) ||
+            (e = ensure(rec, (size_t)nm * 2 * sizeof(ejoin_pair) + sort_pairs_scratch_bytes(nm))))
+            return done(from_cuda(e));
+        uint32_t *cp = (uint32_t *)cal.p, *cq = cp + nm;
+        float *cs = (float *)(cq + nm), *cinv = cs + nm;
+        ejoin_pair *r0 = (ejoin_pair *)rec.p, *r1 = r0 + nm;
+        void *sscr = r1 + nm;
+        if ((e = split_pairs(jp.d_pairs, nm, cp, cq, st)) ||
+            (e = launch_row_inv_norm(X_cal.x, X_cal.n, X_cal.d, X_cal.ld, cinv, c->num_sms, st)))
+            return done(from_cuda(e));
+        if ((s = ejoin_sketch_pair_sims(sk, X_cal, cinv, cp, cq, (int64_t)nm, cs)) != EJOIN_OK) return done(s);
+        if ((e = launch_value_records(cs, (int64_t)nm, r0, c->num_sms, st)) ||
+            (e = launch_sort_pairs(r0, r1, nm, 1ull << 32, nm, sscr, st)))
+            return done(from_cuda(e));
+        const double pos = (1.0 - (double)cfg.recall) * (double)(nm - 1);
+        const uint64_t lo = (uint64_t)pos;
+        const uint64_t hi = std::min<uint64_t>(lo + 1, nm - 1);
+        ejoin_pair a{}, b{};
+        if ((e = cudaMemcpyAsync(&a, r0 + lo, sizeof a, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(&b, r0 + hi, sizeof b, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+            return done(from_cuda(e));
+        const double q = (double)a.sim + ((double)b.sim - (double)a.sim) * (pos - (double)lo);
+        eps_sk = (float)(q - (double)cfg.cal_margin);
+    }
+    cudaEventRecord(ev[3], st);
+    if ((e = cudaStreamSynchronize(st))) return done(from_cuda(e));
+    cudaEventElapsedTime(&rep.ms_label, ev[0], ev[1]);
+    cudaEventElapsedTime(&rep.ms_train, ev[1], ev[2]);
+    cudaEventElapsedTime(&rep.ms_calibrate, ev[2], ev[3]);
+    rep.eps_sketch = eps_sk;
+    *eps_sketch = eps_sk;
+    if (report) *report = rep;
+    return done(EJOIN_OK);
 }
 
 }  // extern "C"

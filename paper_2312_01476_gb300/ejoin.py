@@ -23,7 +23,7 @@ EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
 EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
 EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
 EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED, EJOIN_FLAG_NO_SYMMETRY = 0x1, 0x2, 0x4, 0x8
-EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE = 0x10, 0x20
+EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE, EJOIN_FLAG_SORT = 0x10, 0x20, 0x40
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
 
@@ -84,7 +84,22 @@ class ejoin_prune_stats(ctypes.Structure):
                 ("wide_ball_frac_a", ctypes.c_float), ("wide_ball_frac_b", ctypes.c_float),
                 ("anchors_a", ctypes.c_uint64), ("max_group_rows_a", ctypes.c_uint64),
                 ("ms_sketch_a", ctypes.c_float), ("ms_cover_a", ctypes.c_float), ("ms_assign_a", ctypes.c_float),
-                ("reserved", ctypes.c_int32)]
+                ("recall_est", ctypes.c_float), ("recall_sample_rows", ctypes.c_uint64),
+                ("recall_sample_matches", ctypes.c_uint64)]
+
+
+class ejoin_sketch_train_cfg(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("label_margin", ctypes.c_float), ("w_join", ctypes.c_float),
+                ("n_pairs", ctypes.c_int64), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("lr", ctypes.c_float), ("recall", ctypes.c_float), ("cal_margin", ctypes.c_float),
+                ("seed", ctypes.c_uint64), ("init", ctypes.c_int32)]
+
+
+class ejoin_sketch_train_report(ctypes.Structure):
+    _fields_ = [("label_join_pairs", ctypes.c_uint64), ("labelled_join", ctypes.c_uint64),
+                ("labelled_random", ctypes.c_uint64), ("loss_first", ctypes.c_float), ("loss_last", ctypes.c_float),
+                ("calibration_matches", ctypes.c_uint64), ("eps_sketch", ctypes.c_float),
+                ("ms_label", ctypes.c_float), ("ms_train", ctypes.c_float), ("ms_calibrate", ctypes.c_float)]
 
 _lib = None
 
@@ -176,7 +191,10 @@ def load_library(path: str = LIB_PATH):
     lib.ejoin_score_pairs.argtypes = [vp, ejoin_rel, ejoin_rel, vp, vp, ctypes.c_int64, vp]
     lib.ejoin_threshold_pruned.restype = ctypes.c_int
     lib.ejoin_threshold_pruned.argtypes = [vp, vp, ejoin_rel, ejoin_rel, ctypes.c_float, ctypes.c_float,
-                                           P(ejoin_pairs), P(ejoin_prune_stats)]
+                                           P(ejoin_pairs), P(ejoin_prune_stats), P(ctypes.c_float)]
+    lib.ejoin_sketch_train.restype = ctypes.c_int
+    lib.ejoin_sketch_train.argtypes = [vp, ejoin_rel, ejoin_rel, P(ejoin_sketch_train_cfg), P(ctypes.c_float),
+                                       P(ejoin_sketch_train_report)]
     if path == LIB_PATH:
         _lib = lib
     return lib
@@ -648,8 +666,24 @@ class Sketch:
             pass
 
 
-def ejoin_threshold_pruned(ctx: Ctx, sk: Sketch, R, S, eps: float, eps_sketch: float, capacity=None):
-    """Pruned device join; returns (Result, stats dict)."""
+def ejoin_sketch_train(sk: Sketch, X_train, X_cal, eps: float, label_margin: float = 0.2, w_join: float = 8.0,
+                       n_pairs: int = 10_000_000, epochs: int = 3, batch: int = 65536, lr: float = 2e-3,
+                       recall: float = 0.999, cal_margin: float = 0.01, seed: int = 0, init: bool = True):
+    """Train the sketch network in the library (labelled set from the exact join of X_train, seeded epochs,
+    calibration on X_cal) and return (eps_sketch, report dict)."""
+    cfg = ejoin_sketch_train_cfg(float(eps), float(label_margin), float(w_join), int(n_pairs), int(epochs),
+                                 int(batch), float(lr), float(recall), float(cal_margin), int(seed), int(bool(init)))
+    eps_sk = ctypes.c_float(0)
+    rep = ejoin_sketch_train_report()
+    _check(load_library().ejoin_sketch_train(sk.handle, _dev_rel(X_train), _dev_rel(X_cal), ctypes.byref(cfg),
+                                             ctypes.byref(eps_sk), ctypes.byref(rep)), "ejoin_sketch_train")
+    return float(eps_sk.value), {name: getattr(rep, name) for name, _ in ejoin_sketch_train_report._fields_}
+
+
+def ejoin_threshold_pruned(ctx: Ctx, sk: Sketch, R, S, eps: float, eps_sketch: float, capacity=None,
+                           recall_est: bool = False):
+    """Pruned device join; returns (Result, stats dict).  recall_est: also estimate the recall against the
+    plain join on sampled rows (stats["recall_est"])."""
     import torch
     lib = load_library()
     rR, rS = _dev_rel(R), _dev_rel(S)
@@ -659,8 +693,10 @@ def ejoin_threshold_pruned(ctx: Ctx, sk: Sketch, R, S, eps: float, eps_sketch: f
             ctx._out = torch.empty((cap, 3), dtype=torch.int32, device=R.device)
         out = ejoin_pairs(ctypes.c_void_p(ctx._out.data_ptr()), ctx._out.shape[0], None, 0)
         st = ejoin_prune_stats()
+        rec = ctypes.c_float(0)
         status = lib.ejoin_threshold_pruned(ctx.handle, sk.handle, rR, rS, ctypes.c_float(eps),
-                                            ctypes.c_float(eps_sketch), ctypes.byref(out), ctypes.byref(st))
+                                            ctypes.c_float(eps_sketch), ctypes.byref(out), ctypes.byref(st),
+                                            ctypes.byref(rec) if recall_est else None)
         if status == EJOIN_EOVERFLOW:
             cap = int(out.count) + 1024
             continue

@@ -129,7 +129,8 @@ def check_every_pair(R, S, eps, gi, gj, gs, keep_r=None, keep_s=None, sample=200
     """Properties every GPU record must have, checked over the WHOLE result (at any size): ids in range
     and kept by the selections (boolean masks keep_r / keep_s), no duplicate pair, a reported similarity
     of at least eps - tol, and, on a seeded sample of the records drawn from the whole list, the FP64
-    similarity within tol of the reported one and at least eps - tol."""
+    similarity within tol of the reported one and at least eps - tol.  Returns the sorted pair keys
+    i * |S| + j."""
     gi = np.asarray(gi, dtype=np.int64)
     gj = np.asarray(gj, dtype=np.int64)
     gs = np.asarray(gs, dtype=np.float64)
@@ -139,11 +140,12 @@ def check_every_pair(R, S, eps, gi, gj, gs, keep_r=None, keep_s=None, sample=200
         assert np.asarray(keep_r)[gi].all(), "a pair of an R row the selection drops"
     if keep_s is not None:
         assert np.asarray(keep_s)[gj].all(), "a pair of an S row the selection drops"
-    keys = to_keys(gi, gj, S.shape[0])
-    assert len(np.unique(keys)) == len(keys), "duplicate pairs in the GPU result"
+    keys = np.sort(to_keys(gi, gj, S.shape[0]))
+    assert keys.size < 2 or np.all(np.diff(keys) > 0), "duplicate pairs in the GPU result"
     assert gs.size == 0 or gs.min() >= float(np.float32(eps)) - tol, "a reported similarity below eps"
     if gi.size:
         idx = np.random.default_rng(seed).choice(gi.size, size=min(sample, gi.size), replace=False)
         want = oracle.sim_pairs(R, S, gi[idx].astype(np.uint32), gj[idx].astype(np.uint32))
         assert np.abs(want - gs[idx]).max() <= tol, "sampled record: reported similarity off"
         assert want.min() >= float(np.float32(eps)) - tol, "sampled record below eps in FP64"
+    return keys

@@ -1,34 +1,23 @@
-"""Training and calibration of the learned sketch for tile pruning.
+"""Test-only orchestration of the sketch training from the primitive C-ABI calls.
 
-Orchestration only: labels come from the exact join on the GPU
-(ejoin_threshold on a held-out sample, and ejoin_score_pairs for random
-pairs), every forward, backward and Adam step runs in the library's kernels
-(ejoin_sketch_train_step), and calibration reads sketch cosines computed by
-ejoin_sketch_pair_sims.
+The library trains the sketch itself (ejoin_sketch_train: labelled set,
+seeded epochs and calibration on the GPU).  This module does the same steps
+from Python over the lower-level entry points (ejoin_threshold for labels,
+ejoin_score_pairs, ejoin_sketch_train_step, ejoin_sketch_pair_sims), with
+numpy's generator for the draws and numpy's quantile, as an independent
+second route whose recall the library's must match.
 
 Recipe: the held-out sample is joined with itself at eps - label_margin; every
 pair found (matches and near misses, with their exact similarity) is a
-labelled pair with weight `w_join`, and random pairs (mostly far apart) fill
-the set with weight 1.  Targets are the exact cosines, so the sketch cosine
-learns to track the true cosine.  eps_sketch is then the (1 - recall)
-quantile of the sketch cosine over true matches of a second held-out sample,
-minus a small margin.
+labelled pair with weight `w_join`, and random pairs fill the set with
+weight 1.  eps_sketch is the (1 - recall) quantile of the sketch cosine over
+the true matches of a second held-out sample, minus a small margin.
 """
 from __future__ import annotations
 
-import math
-
 import numpy as np
 
-from . import ejoin as E
-
-
-def init_params(d: int, hidden: int, out: int, seed: int) -> np.ndarray:
-    """Flat parameters with a scaled Gaussian initialisation."""
-    rng = np.random.default_rng(seed)
-    W1 = rng.standard_normal((hidden, d)) / math.sqrt(d)
-    W2 = rng.standard_normal((out, hidden)) / math.sqrt(hidden)
-    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(out)]).astype(np.float32)
+from paper_2312_01476_gb300 import ejoin as E
 
 
 def labelled_pairs(ctx: E.Ctx, X, eps: float, n_pairs: int, seed: int, label_margin: float = 0.2,

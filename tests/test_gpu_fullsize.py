@@ -73,10 +73,10 @@ def test_c3_full_size_sampled_rows(prec):
     gi, gj = res.i.cpu().numpy().view(np.uint32), res.j.cpu().numpy().view(np.uint32)
     gs = res.sim.cpu().numpy()
     compare(w.R, w.R, w.eps, gi, gj, gs, oi, oj, os_, rows=rows)
-    check_every_pair(w.R, w.R, w.eps, gi, gj, gs, seed=8)
-    # the mirrored self-join: (j, i) present for every (i, j)
-    keys = gi.astype(np.int64) * n + gj
-    assert np.isin(gj.astype(np.int64) * n + gi, keys).all()
+    keys = check_every_pair(w.R, w.R, w.eps, gi, gj, gs, seed=8)
+    # the mirrored self-join: (j, i) present for every (i, j) (the sorted keys of the swapped pairs are
+    # the same sorted keys)
+    assert np.array_equal(np.sort(gj.astype(np.int64) * n + gi), keys)
     del X, res
     torch.cuda.empty_cache()
 

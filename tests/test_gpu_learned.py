@@ -5,10 +5,13 @@
 * training lowers the loss;
 * with pruning disabled (eps_sketch = -2) the pruned join returns exactly the
   plain join's result;
-* on clustered data, the trained sketch keeps recall >= 0.995 of the exact
-  join (calibrated for 0.999 on held-out rows), never emits a pair the exact
-  join does not, and keeps under 8 % of the tile pairs, under a quarter of
-  what the same pipeline keeps with the untrained network.
+* on clustered data, the sketch trained and calibrated in the library
+  (ejoin_sketch_train, through the C ABI alone) keeps recall >= 0.995 of the
+  exact join (calibrated for 0.999 on held-out rows), as does the same recipe
+  orchestrated from Python over the primitive calls, within 0.005 of it; it
+  never emits a pair the exact join does not, keeps under 8 % of the tile
+  pairs, under a quarter of what the untrained network keeps, and the
+  library's sampled recall estimate is within 0.02 of the recall.
 """
 import numpy as np
 import pytest
@@ -26,13 +29,13 @@ if not torch.cuda.is_available():
 
 import paper_2312_01476_gb300 as pkg  # noqa: E402
 from paper_2312_01476_gb300 import ejoin as E  # noqa: E402
-from paper_2312_01476_gb300 import learned as L  # noqa: E402
+import sketch_reference as L  # noqa: E402
 
 
 def _tiny(seed=0, n=300, d=48, hid=32):
     rng = np.random.default_rng(seed)
     X = rng.standard_normal((n, d)).astype(np.float32) * 3.0
-    flat = L.init_params(d, hid, 64, seed)
+    flat = inputs.sketch_init_params(d, hid, 64, seed)
     flat[hid * d:hid * d + hid] = rng.standard_normal(hid).astype(np.float32) * 0.1
     return X, flat
 
@@ -85,14 +88,22 @@ def test_training_lowers_the_loss():
     with pkg.Ctx(device=0, prec="bf16") as ctx:
         Xd = torch.from_numpy(X).cuda()
         sk = E.Sketch(ctx, d, 64, 64)
-        sk.set_params(L.init_params(d, 64, 64, 3))
+        sk.set_params(inputs.sketch_init_params(d, 64, 64, 3))
         p, q, t, w = L.labelled_pairs(ctx, Xd, 0.8, 40000, seed=1)
         inv = E.ejoin_row_inv_norm(ctx, Xd)
         _, l0 = sk.grad(Xd, inv, p, q, t, w)
         L.train(sk, Xd, p, q, t, w, epochs=4, batch=8192, lr=3e-3)
         _, l1 = sk.grad(Xd, inv, p, q, t, w)
+        # the library's own training from its seeded initialisation, on the same rows
+        eps_sk, rep = E.ejoin_sketch_train(sk, Xd, Xd, 0.8, n_pairs=40000, epochs=4, batch=8192, lr=3e-3, seed=1,
+                                           init=True)
+        _, l2 = sk.grad(Xd, inv, p, q, t, w)
         sk.close()
     assert l1 < 0.5 * l0, (l0, l1)
+    assert rep["loss_last"] < 0.5 * rep["loss_first"], rep
+    assert l2 < 0.5 * l0, (l0, l2)
+    assert rep["labelled_join"] + rep["labelled_random"] == 40000
+    assert -1.0 <= eps_sk <= 1.0
 
 
 def test_pruning_disabled_equals_plain_join():
@@ -102,7 +113,7 @@ def test_pruning_disabled_equals_plain_join():
     eps = 0.3
     with pkg.Ctx(device=0, prec="bf16") as ctx:
         sk = E.Sketch(ctx, 96, 64, 64)
-        sk.set_params(L.init_params(96, 64, 64, 4))
+        sk.set_params(inputs.sketch_init_params(96, 64, 64, 4))
         Xd, Sd = torch.from_numpy(X).cuda(), torch.from_numpy(S).cuda()
         res, st = E.ejoin_threshold_pruned(ctx, sk, Xd, Sd, eps, -2.0)
         got = set(zip(res.i.cpu().numpy().tolist(), res.j.cpu().numpy().tolist()))
@@ -126,7 +137,7 @@ def test_pruned_self_join_equals_plain_join():
     eps = 0.3
     with pkg.Ctx(device=0, prec="bf16") as ctx:
         sk = E.Sketch(ctx, 96, 64, 64)
-        sk.set_params(L.init_params(96, 64, 64, 5))
+        sk.set_params(inputs.sketch_init_params(96, 64, 64, 5))
         Xd = torch.from_numpy(X).cuda()
         res, st = E.ejoin_threshold_pruned(ctx, sk, Xd, Xd, eps, -2.0)
         got = dict(zip(zip(res.i.cpu().numpy().tolist(), res.j.cpu().numpy().tolist()), res.sim.cpu().numpy().tolist()))
@@ -152,27 +163,39 @@ def test_trained_sketch_prunes_with_recall():
         Xd, Xtrd, Xcald = (torch.from_numpy(a).cuda() for a in (X, Xtr, Xcal))
         plain = pkg.ejoin_threshold(ctx, Xd, Xd, eps)
         exact = set(zip(plain.i.cpu().numpy().tolist(), plain.j.cpu().numpy().tolist()))
-        kept = {}
-        for name, train in (("trained", True), ("untrained", False)):
+        kept, recalls = {}, {}
+        # "library": trained and calibrated by ejoin_sketch_train through the C ABI alone; "python": the
+        # same recipe orchestrated over the primitive calls (sketch_reference); "untrained": calibration only
+        for name in ("library", "python", "untrained"):
             sk = E.Sketch(ctx, d, 128, 64)
-            sk.set_params(L.init_params(d, 128, 64, 11))
-            if train:
-                p, q, t, w = L.labelled_pairs(ctx, Xtrd, eps, 200000, seed=2)
-                L.train(sk, Xtrd, p, q, t, w, epochs=6, batch=16384, lr=3e-3)
-            eps_sk = L.calibrate(sk, ctx, Xcald, eps, recall=0.999)
-            res, st = E.ejoin_threshold_pruned(ctx, sk, Xd, Xd, eps, eps_sk)
+            sk.set_params(inputs.sketch_init_params(d, 128, 64, 11))
+            if name == "library":
+                eps_sk, rep = E.ejoin_sketch_train(sk, Xtrd, Xcald, eps, n_pairs=200000, epochs=6, batch=16384,
+                                                   lr=3e-3, recall=0.999, seed=2, init=False)
+                assert rep["labelled_join"] > 1000 and rep["loss_last"] < rep["loss_first"], rep
+                assert rep["calibration_matches"] > 1000
+            else:
+                if name == "python":
+                    p, q, t, w = L.labelled_pairs(ctx, Xtrd, eps, 200000, seed=2)
+                    L.train(sk, Xtrd, p, q, t, w, epochs=6, batch=16384, lr=3e-3)
+                eps_sk = L.calibrate(sk, ctx, Xcald, eps, recall=0.999)
+            res, st = E.ejoin_threshold_pruned(ctx, sk, Xd, Xd, eps, eps_sk, recall_est=True)
             got = set(zip(res.i.cpu().numpy().tolist(), res.j.cpu().numpy().tolist()))
             assert got <= exact
-            recall = len(got) / len(exact)
+            recalls[name] = len(got) / len(exact)
             kept[name] = st["tiles_kept"] / st["tiles_total"]
-            print(name, "eps_sketch", eps_sk, "recall", recall, "kept", kept[name])
-            if train:
-                assert recall >= 0.995, recall
+            # the library's estimate from 2048 sampled rows against the recall over all rows
+            assert abs(st["recall_est"] - recalls[name]) <= 0.02, (name, st["recall_est"], recalls[name])
+            assert st["recall_sample_rows"] == 2048 and st["recall_sample_matches"] > 0
+            print(name, "eps_sketch", eps_sk, "recall", recalls[name], "estimate", st["recall_est"],
+                  "kept", kept[name])
             sk.close()
+    assert recalls["library"] >= 0.995 and recalls["python"] >= 0.995, recalls
+    assert abs(recalls["library"] - recalls["python"]) <= 0.005, recalls
     # 120 clusters of ~200 rows: a tile pair can hold matches only when both tiles share a
     # cluster, a few percent of all pairs; the untrained network cannot separate them
-    assert kept["trained"] < 0.08, kept
-    assert kept["trained"] < 0.25 * kept["untrained"], kept
+    assert kept["library"] < 0.08 and kept["python"] < 0.08, kept
+    assert kept["library"] < 0.25 * kept["untrained"], kept
 
 
 def test_pair_sims_beyond_one_grid_of_rows():
@@ -184,7 +207,7 @@ def test_pair_sims_beyond_one_grid_of_rows():
     q = rng.integers(0, 5000, n).astype(np.int32)
     with pkg.Ctx(device=0, prec="bf16") as ctx:
         sk = E.Sketch(ctx, 32, 16, 64)
-        flat = L.init_params(32, 16, 64, 5)
+        flat = inputs.sketch_init_params(32, 16, 64, 5)
         sk.set_params(flat)
         Xd = torch.from_numpy(X).cuda()
         inv = E.ejoin_row_inv_norm(ctx, Xd)

@@ -367,3 +367,26 @@ def test_accurate_tier_matches_fp64(prec, d):
     assert st["fp64_rescored"] == st["candidates"] > 0
     oi, oj, os_ = oracle.join(R, S, eps)
     compare(R, S, eps, gi, gj, gs, oi, oj, os_, band=1e-7, tol=1.2e-7)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "f32"])
+def test_library_allocated_result_self_join(prec):
+    # out->d_pairs == NULL: the library sizes the buffer itself; a symmetric self-join writes every
+    # off-diagonal pair twice, so the buffer must hold twice its candidates
+    import ctypes
+    from paper_2312_01476_gb300 import ejoin as E
+    X = gauss(31, 900, 64)
+    X[450:] = X[:450] + np.float32(0.2) * gauss(32, 450, 64)
+    eps = 0.5
+    lib = E.load_library()
+    with pkg.Ctx(device=0, prec=prec) as ctx:
+        Xd = dev(X)
+        out = E.ejoin_pairs(None, 0, None, 0)
+        st = lib.ejoin_threshold(ctx.handle, E._dev_rel(Xd), E._dev_rel(Xd), ctypes.c_float(eps), None, None,
+                                 ctypes.byref(out))
+        assert st == 0, pkg.ejoin_strerror(st)
+        n = int(out.count)
+        assert out.d_pairs and out.capacity >= n
+        assert lib.ejoin_pairs_free(ctx.handle, ctypes.byref(out)) == 0
+        want = pkg.ejoin_threshold(ctx, Xd, Xd, eps)  # the binding's caller-owned buffer (checked elsewhere)
+    assert n == want.count and n > 2 * len(X)
