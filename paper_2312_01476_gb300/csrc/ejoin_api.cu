@@ -155,6 +155,23 @@ using namespace ej::host;
 
 namespace ej {
 namespace host {
+cudaError_t band_norms(ejoin_ctx *c, int64_t nR, int64_t nS, BandNorms *bn)
+{
+    nR = std::max<int64_t>(nR, 1);
+    nS = std::max<int64_t>(nS, 1);
+    const size_t bytes = (size_t)(nR + nS) * 8 + (size_t)(nR + nS);
+    cudaError_t e = ensure(c->band_rows, bytes);
+    if (e != cudaSuccess) return e;
+    char *p = (char *)c->band_rows.p;
+    bn->nrmR = (double *)p;
+    bn->nrmS = bn->nrmR + nR;
+    bn->flagR = (unsigned char *)(bn->nrmS + nS);
+    bn->flagS = bn->flagR + nR;
+    bn->nR = nR;
+    bn->nS = nS;
+    return cudaSuccess;
+}
+
 ejoin_status sort_result(ejoin_ctx *c, ejoin_pair *pairs, uint64_t n, uint64_t n_i, uint64_t n_j)
 {
     if (n <= 1) return EJOIN_OK;
@@ -282,6 +299,7 @@ void ejoin_destroy(ejoin_ctx *c)
         release(c->pbuf);
         release(c->sort_tmp);
         release(c->sort_scratch);
+        release(c->band_rows);
         release(c->top);
         release(c->topseg);
         for (auto &b : c->host_in) release(b);
@@ -569,6 +587,9 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
     auto rescore = [&]() -> cudaError_t {
         cudaError_t ee = ensure(c->band, c->cand_cap * sizeof(uint2));
         if (ee != cudaSuccess) return ee;
+        BandNorms bn;
+        if (c->fp64_band > 0.f && (ee = band_norms(c, R.n, S.n, &bn)) != cudaSuccess) return ee;
+        const BandNorms *bnp = c->fp64_band > 0.f ? &bn : nullptr;
         const uint32_t *idsA = selR ? (const uint32_t *)sa.ids.p : nullptr;
         const uint32_t *idsB = selS ? (const uint32_t *)sb.ids.p : nullptr;
         if (panels) {
@@ -579,16 +600,16 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
                                        (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
                                        count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count,
                                        count_only ? 1 : 0, c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap,
-                                       sym ? 1 : 0);
+                                       sym ? 1 : 0, bnp);
             if (ee != cudaSuccess) return ee;
-            c->stats.launches += c->fp64_band > 0.f ? 7 : 6;
+            c->stats.launches += c->fp64_band > 0.f ? 10 : 6;
         } else {
             ee = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, xR, ldR, xS, ldS, R.d, idsA,
                                 idsB, (const float *)sa.inv.p, (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
                                 count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count, count_only ? 1 : 0,
-                                c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0);
+                                c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap, sym ? 1 : 0, bnp);
             if (ee != cudaSuccess) return ee;
-            c->stats.launches += c->fp64_band > 0.f ? 2 : 1;
+            c->stats.launches += c->fp64_band > 0.f ? 5 : 1;
         }
         if (timing) cudaEventRecord(c->ev[3], c->stream);
         if (d_count_user)

@@ -264,6 +264,16 @@ cudaError_t launch_topk_scatter(const uint2 *cand, const unsigned long long *can
 cudaError_t launch_topk_select(const unsigned long long *seg, const unsigned *row_off, const unsigned *row_cnt,
                                const long long *nA_dev, int64_t nA_max, int kk, const uint32_t *idsR, ejoin_pair *out,
                                uint64_t out_cap, unsigned long long *missing, int num_sms, cudaStream_t st);
+// Workspace of the accurate tier's squared row norms (compensated dot products finished in FP64): per
+// row of R (nR rows) and of S (nS rows) a flag and a norm.  When a launcher gets one, the rows listed in
+// the band list have their norms computed once, and each listed candidate only its cross product; the
+// similarities are the same bit for bit.
+struct BandNorms {
+    unsigned char *flagR = nullptr, *flagS = nullptr;
+    double *nrmR = nullptr, *nrmS = nullptr;
+    int64_t nR = 0, nS = 0;
+};
+
 // Candidates: cand[0 .. min(*cand_count, cand_cap)).  Candidates whose FP32 similarity
 // lies within fp64_band of eps are listed in band_list (capacity band_cap >= cand_cap,
 // counted in *band_count) and decided by a second kernel, the accurate tier.  mirror: the
@@ -274,7 +284,8 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
                            const uint32_t *idsR, const uint32_t *idsS, const float *invR, const float *invS,
                            float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                            unsigned long long *out_count, unsigned long long *band_count, int count_only,
-                           int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror = 0);
+                           int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror = 0,
+                           const BandNorms *bn = nullptr);
 
 // Panel-ordered re-score (same decisions and similarities as launch_rescore, bit for bit): the candidates
 // are bucketed into `sorted` (cand_cap entries) by (block of S rows sized for L2, panel of
@@ -291,7 +302,8 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
                                   int d, const uint32_t *idsR, const uint32_t *idsS, const float *invR,
                                   const float *invS, float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                                   unsigned long long *out_count, unsigned long long *band_count, int count_only,
-                                  int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror);
+                                  int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror,
+                                  const BandNorms *bn = nullptr);
 
 // Sort of n result records by (i, j) ascending (sort.cu), i < n_i and j < n_j: LSD radix sort over the
 // significant bits of j, then of i, ping-ponging between data and tmp (n records); the result ends in
@@ -578,6 +590,43 @@ static __device__ __noinline__ double accurate_cosine4(const float *__restrict__
     const double dd = dot2_warp_total(xy[0]), nr = dot2_warp_total(xx[0]), ns = dot2_warp_total(yy[0]);
     double c = (nr > 0.0 && ns > 0.0) ? dd / (sqrt(nr) * sqrt(ns)) : 0.0;
     return fmin(1.0, fmax(-1.0, c));
+}
+
+// One compensated dot product x.y of two raw FP32 rows (one warp), finished in FP64, with the lane
+// partition and the order of accurate_cosine (plain) or accurate_cosine4 (VEC: 16-byte aligned rows,
+// d % 4 == 0).  accurate_dot(r, r) is bit for bit the x.x of accurate_cosine, so squared norms computed
+// once per row give that function's value: dd / (sqrt(nr) sqrt(ns)).
+template <bool VEC>
+static __device__ __noinline__ double accurate_dot(const float *__restrict__ r, const float *__restrict__ s, int d,
+                                                   int lane)
+{
+    if constexpr (!VEC) {
+        Dot2Acc xy{0.f, 0.f};
+        for (int k = lane; k < d; k += 32) dot2_add(xy, __ldg(r + k), __ldg(s + k));
+        return dot2_warp_total(xy);
+    } else {
+        Dot2Acc xy[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        const float4 *r4 = reinterpret_cast<const float4 *>(r), *s4 = reinterpret_cast<const float4 *>(s);
+        const int d4 = d >> 2;
+        int g = lane;
+        for (; g + 32 < d4; g += 64) {
+            const float4 a0 = __ldg(r4 + g), b0 = __ldg(s4 + g), a1 = __ldg(r4 + g + 32), b1 = __ldg(s4 + g + 32);
+            dot2_add(xy[0], a0.x, b0.x), dot2_add(xy[1], a1.x, b1.x);
+            dot2_add(xy[0], a0.y, b0.y), dot2_add(xy[1], a1.y, b1.y);
+            dot2_add(xy[0], a0.z, b0.z), dot2_add(xy[1], a1.z, b1.z);
+            dot2_add(xy[0], a0.w, b0.w), dot2_add(xy[1], a1.w, b1.w);
+        }
+        if (g < d4) {
+            const float4 a0 = __ldg(r4 + g), b0 = __ldg(s4 + g);
+            dot2_add(xy[0], a0.x, b0.x), dot2_add(xy[0], a0.y, b0.y), dot2_add(xy[0], a0.z, b0.z),
+                dot2_add(xy[0], a0.w, b0.w);
+        }
+        float t, e;
+        two_sum(xy[0].s, xy[1].s, t, e);
+        xy[0].s = t;
+        xy[0].c = __fadd_rn(xy[0].c, __fadd_rn(xy[1].c, e));
+        return dot2_warp_total(xy[0]);
+    }
 }
 
 #endif  // __CUDACC__

@@ -61,6 +61,8 @@ namespace host {
 // EJOIN_FLAG_SORT: sort the n records at `pairs` (device-accessible) by (i, j), i < n_i, j < n_j, on the
 // context's stream, and synchronise.
 ejoin_status sort_result(ejoin_ctx *c, ejoin_pair *pairs, uint64_t n, uint64_t n_i, uint64_t n_j);
+// The accurate tier's per-row workspace for R.n and S.n rows (grown in the context).
+cudaError_t band_norms(ejoin_ctx *c, int64_t nR, int64_t nS, BandNorms *bn);
 }  // namespace host
 }  // namespace ej
 
@@ -84,6 +86,7 @@ struct ejoin_ctx {
     ej::host::Buf psorted;  // panel-ordered re-score: the candidates bucketed by panel of R rows
     ej::host::Buf pbuf;     // panel-ordered re-score: per-panel counts, offsets and chunk offsets
     ej::host::Buf sort_tmp, sort_scratch;  // EJOIN_FLAG_SORT: second record buffer and digit counts
+    ej::host::Buf band_rows;               // accurate tier: per-row flags and squared norms of R and S
     ej::host::Buf top;     // top-k: per operand row scratch (maxima, thresholds, counts, offsets)
     ej::host::Buf topseg;  // top-k, k > 1: the candidates' keys bucketed by row
     ej::host::Buf host_in[6];

@@ -353,6 +353,92 @@ __global__ void __launch_bounds__(256) rescore_band_kernel(const uint2 *__restri
     }
 }
 
+// Accurate tier with per-row norms (BandNorms): flag the rows of the listed candidates, compute their
+// squared norms once (a warp per flagged row), then each entry's cross product only.
+__global__ void band_flag_kernel(const uint2 *__restrict__ band_list, const unsigned long long *__restrict__ band_count,
+                                 uint64_t band_cap, unsigned char *flagR, unsigned char *flagS)
+{
+    uint64_t n = *band_count;
+    if (n > band_cap) n = band_cap;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint2 e = band_list[k];
+        flagR[e.x] = 1;
+        flagS[e.y] = 1;
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) band_norm_kernel(const float *__restrict__ X, int64_t ld, int d, int64_t n,
+                                                        const unsigned char *__restrict__ flag, double *nrm)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw) {
+        if (!flag[r]) continue;  // warp-uniform
+        const float *x = X + r * ld;
+        const double v = accurate_dot<VEC>(x, x, d, lane);
+        if (lane == 0) nrm[r] = v;
+    }
+}
+
+template <bool MIRROR, bool VEC>
+__global__ void __launch_bounds__(256) rescore_band_norms_kernel(
+    const uint2 *__restrict__ band_list, const unsigned long long *__restrict__ band_count, uint64_t band_cap,
+    const float *__restrict__ R, int64_t ldR, const float *__restrict__ S, int64_t ldS, int d,
+    const double *__restrict__ nrmR, const double *__restrict__ nrmS, float eps, ejoin_pair *__restrict__ out,
+    uint64_t out_cap, unsigned long long *out_count, int count_only)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t n = *band_count;
+    if (n > band_cap) n = band_cap;
+    const double eps_d = (double)eps;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t base = w0 * 32; base < n; base += nw * 32) {
+        const int len = (int)(n - base < 32 ? n - base : 32);
+        const uint2 mine_e = lane < len ? band_list[base + lane] : make_uint2(0u, 0u);
+        const double my_nr = lane < len ? nrmR[mine_e.x] : 0.0, my_ns = lane < len ? nrmS[mine_e.y] : 0.0;
+        bool my_emit = false;
+        float my_sim = 0.f;
+        for (int q = 0; q < len; ++q) {
+            const uint32_t i = __shfl_sync(0xffffffffu, mine_e.x, q), j = __shfl_sync(0xffffffffu, mine_e.y, q);
+            const double dd = accurate_dot<VEC>(R + (int64_t)i * ldR, S + (int64_t)j * ldS, d, lane);
+            if (lane == q) {
+                // the expression of accurate_cosine, with the norms computed once per row
+                double c = (my_nr > 0.0 && my_ns > 0.0) ? dd / (sqrt(my_nr) * sqrt(my_ns)) : 0.0;
+                c = fmin(1.0, fmax(-1.0, c));
+                my_emit = c >= eps_d;
+                my_sim = (float)c;
+            }
+        }
+        const int mine = my_emit ? ((MIRROR && mine_e.x != mine_e.y) ? 2 : 1) : 0;
+        int incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        unsigned long long pos0 = 0;
+        if (lane == 0 && tot) pos0 = atomicAdd(out_count, (unsigned long long)tot);
+        pos0 = __shfl_sync(0xffffffffu, pos0, 0);
+        if (mine && !count_only) {
+            const unsigned long long pos = pos0 + (unsigned long long)(incl - mine);
+            ejoin_pair p;
+            p.i = mine_e.x;
+            p.j = mine_e.y;
+            p.sim = my_sim;
+            if (pos < out_cap) out[pos] = p;
+            if (mine == 2 && pos + 1 < out_cap) {
+                p.i = mine_e.y;
+                p.j = mine_e.x;
+                out[pos + 1] = p;
+            }
+        }
+    }
+}
+
 // Batched re-score: candidate (a, b) holds rows of the concatenated operands;
 // job j owns a in [a_off[j], a_off[j+1]) and b in [b_off[j], b_off[j+1]).  The
 // FP32 rows are read from the job's own input (row a - a_off[j] of R_j, row
@@ -555,10 +641,38 @@ cudaError_t launch_score_pairs(const float *R, int64_t ldR, const float *S, int6
 static cudaError_t launch_band_tier(const uint2 *band_list, const unsigned long long *band_count, uint64_t band_cap,
                                     const float *R, int64_t ldR, const float *S, int64_t ldS, int d, float eps,
                                     ejoin_pair *out, uint64_t out_cap, unsigned long long *out_count, int count_only,
-                                    bool aligned, bool mirror, int num_sms, cudaStream_t st)
+                                    bool aligned, bool mirror, int num_sms, cudaStream_t st,
+                                    const BandNorms *bn = nullptr)
 {
     const unsigned gb = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((band_cap + 255) / 256, (uint64_t)num_sms * 8));
+    if (bn) {
+        cudaError_t e = cudaMemsetAsync(bn->flagR, 0, (size_t)bn->nR, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(bn->flagS, 0, (size_t)bn->nS, st);
+        if (e != cudaSuccess) return e;
+        band_flag_kernel<<<gb, 256, 0, st>>>(band_list, band_count, band_cap, bn->flagR, bn->flagS);
+        const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((bn->nR + 7) / 8, (int64_t)num_sms * 16));
+        const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((bn->nS + 7) / 8, (int64_t)num_sms * 16));
+        if (aligned) {
+            band_norm_kernel<true><<<gr, 256, 0, st>>>(R, ldR, d, bn->nR, bn->flagR, bn->nrmR);
+            band_norm_kernel<true><<<gs, 256, 0, st>>>(S, ldS, d, bn->nS, bn->flagS, bn->nrmS);
+        } else {
+            band_norm_kernel<false><<<gr, 256, 0, st>>>(R, ldR, d, bn->nR, bn->flagR, bn->nrmR);
+            band_norm_kernel<false><<<gs, 256, 0, st>>>(S, ldS, d, bn->nS, bn->flagS, bn->nrmS);
+        }
+#define EJ_BANDN(M, V)                                                                                            \
+    rescore_band_norms_kernel<M, V><<<gb, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d,        \
+                                                       bn->nrmR, bn->nrmS, eps, out, out_cap, out_count, count_only)
+        if (mirror) {
+            if (aligned) EJ_BANDN(true, true);
+            else EJ_BANDN(true, false);
+        } else {
+            if (aligned) EJ_BANDN(false, true);
+            else EJ_BANDN(false, false);
+        }
+#undef EJ_BANDN
+        return cudaGetLastError();
+    }
 #define EJ_BAND(M, V)                                                                                               \
     rescore_band_kernel<M, V><<<gb, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, \
                                                   out_count, count_only)
@@ -578,7 +692,7 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
                            const uint32_t *idsS, const float *invR, const float *invS, float eps, float fp64_band,
                            ejoin_pair *out, uint64_t out_cap, unsigned long long *out_count,
                            unsigned long long *band_count, int count_only, int num_sms, cudaStream_t st,
-                           uint2 *band_list, uint64_t band_cap, int mirror)
+                           uint2 *band_list, uint64_t band_cap, int mirror, const BandNorms *bn)
 {
     if (cand_cap == 0) return cudaSuccess;
     // every candidate may fall in the band: the list must hold them all
@@ -612,7 +726,7 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
 #undef EJ_RESCORE_ARGS
     if (e != cudaSuccess || fp64_band <= 0.f) return e;
     return launch_band_tier(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, out_count,
-                            count_only, aligned, mirror != 0, num_sms, st);
+                            count_only, aligned, mirror != 0, num_sms, st, bn);
 }
 
 // ---------------------------------------------------------------------------
@@ -1164,7 +1278,8 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
                                   int d, const uint32_t *idsR, const uint32_t *idsS, const float *invR,
                                   const float *invS, float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                                   unsigned long long *out_count, unsigned long long *band_count, int count_only,
-                                  int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror)
+                                  int num_sms, cudaStream_t st, uint2 *band_list, uint64_t band_cap, int mirror,
+                                  const BandNorms *bn)
 {
     if (cand_cap == 0) return cudaSuccess;
     if (fp64_band > 0.f && (!band_list || band_cap < cand_cap)) return cudaErrorInvalidValue;
@@ -1213,7 +1328,7 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
 #undef EJ_PANEL_ARGS
     if (e != cudaSuccess || fp64_band <= 0.f) return e;
     return launch_band_tier(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, out_count,
-                            count_only, true, mirror != 0, num_sms, st);
+                            count_only, true, mirror != 0, num_sms, st, bn);
 }
 
 }  // namespace ej

@@ -9,15 +9,15 @@
 // partition offsets m0, n0).  D never leaves the chip (Sec. V-B: the
 // "buffer" of a partition pair is a TMEM accumulator here).
 //
-// Structure (one persistent CTA per SM, 320 threads; 576 for e4m3):
+// Structure (one persistent CTA per SM, 320 threads; 576 for e4m3 at short K):
 //   warp 0      TMA producer: 128-byte-swizzled K-slices of the R tile
 //               (128 rows) and S tile (256 rows) into a 4-stage smem ring.
 //   warp 1      TMEM owner and MMA issuer: 4 x tcgen05.mma per stage into one
 //               of two 128 x 256 FP32 accumulators (512 TMEM columns).
-//   warps 2..    epilogue, two (e4m3: four) warps per TMEM lane quarter, each
-//               on 128 (64) of the 256 accumulator columns: software-pipelined
-//               tcgen05.ld of 32
-//               columns, tree max-reduce for a fast reject, per-lane match
+//   warps 2..    epilogue, two (e4m3 at short K: four) warps per TMEM lane
+//               quarter, each on 128 (64) of the 256 accumulator columns:
+//               software-pipelined tcgen05.ld of 32 columns, tree
+//               max-reduce for a fast reject, per-lane match
 //               masks, warp prefix sums, staging in shared memory, one global
 //               atomic per flush of up to 512 candidates.
 // Every wait is bounded by `timeout` SM cycles; on expiry the CTA raises an
@@ -35,13 +35,15 @@ constexpr int ROW_BYTES = 128;  // K bytes of one stage row = one 128-byte swizz
 constexpr int A_STAGE = BM * ROW_BYTES;
 constexpr int B_STAGE = BN * ROW_BYTES;
 constexpr int FLUSH_TILES = 16;  // tiles between candidate flushes of an epilogue warp (or when staging is full)
-// Epilogue warps: the same number per TMEM lane quarter, each on a slice of the accumulator columns.  e4m3
-// tiles take half the MMA time of BF16 tiles, so their epilogue is split over 16 warps (64 columns each);
-// BF16 and TF32 use 8 (128 columns each), which leaves the MMA warp's scheduler less crowded.
-constexpr int epi_warps(int kind) { return kind == 1 ? 16 : 8; }
+// Epilogue warps: the same number per TMEM lane quarter, each on a slice of the accumulator columns.  An
+// e4m3 tile of short K (at most 512 values, 4 K-slices) takes too little MMA time for 8 warps to scan its
+// accumulator, so its epilogue is split over 16 warps (64 columns each); longer K and BF16 / TF32 use 8
+// (128 columns each), which leaves the MMA warp's scheduler less crowded.
+constexpr int EPI_WIDE_MAX_KP = 512;
+constexpr int epi_warps(int kind, bool wide) { return kind == 1 && wide ? 16 : 8; }
 constexpr int EPI_WARPS_MAX = 16;
 constexpr int STAGING_BYTES = 32768;  // candidate staging of all epilogue warps
-// fused re-score: warps 2 + epi_warps(kind) .. consume candidates from a shared-memory ring that
+// fused re-score: the warps after the epilogue warps consume candidates from a shared-memory ring that
 // replaces the epilogue staging: QN cells of 8 data bytes, QN 32-bit cell sequence numbers,
 // then RS_STG staged result records per re-score warp
 constexpr int RS_WARPS_F = 4;
@@ -214,10 +216,7 @@ __device__ __forceinline__ void sym_coords(long long t, const SymRaster &sr, lon
     diag = x == y;
 }
 
-constexpr int threads_for(int kind, int mode)
-{
-    return (2 + epi_warps(kind) + (mode == MODE_FUSED ? RS_WARPS_F : 0)) * 32;
-}
+constexpr int threads_for(int ew, int mode) { return (2 + ew + (mode == MODE_FUSED ? RS_WARPS_F : 0)) * 32; }
 
 // Re-score role of the fused kernel: take 8 queue slots at a time, gather the
 // FP32 rows of up to 8 candidates at once, FP32 dot (FP64 tier inside the
@@ -431,8 +430,8 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
 
 }  // namespace
 
-template <int KIND, int MODE>
-__global__ void __launch_bounds__(threads_for(KIND, MODE), 1)
+template <int KIND, int MODE, int EW>
+__global__ void __launch_bounds__(threads_for(EW, MODE), 1)
     sim_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int kp,
                   const long long *__restrict__ nA_ptr, const long long *__restrict__ nB_ptr, float thr,
                   const float *__restrict__ scaleA, const float *__restrict__ scaleB, uint2 *__restrict__ cand,
@@ -451,7 +450,7 @@ __global__ void __launch_bounds__(threads_for(KIND, MODE), 1)
     uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(smem + OFF_MISC);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + OFF_MISC + 4);
 
-    constexpr int EPI_WARPS = epi_warps(KIND);
+    constexpr int EPI_WARPS = EW;
     constexpr int SLICE_COLS = BN / (EPI_WARPS / 4);  // accumulator columns per epilogue warp
     constexpr int EPI_CHUNKS = SLICE_COLS / 32;       // 32-column chunks per epilogue warp
     constexpr int STAGING = STAGING_BYTES / 8 / EPI_WARPS;  // candidate slots per epilogue warp
@@ -900,12 +899,12 @@ __global__ void __launch_bounds__(threads_for(KIND, MODE), 1)
 
 size_t sim_tc_smem_bytes() { return (size_t)SMEM_BYTES; }
 
-template <int KIND, int MODE>
-static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
-                              const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
-                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
-                              int count_only, int grid, int group_m, const BatchTables &bt, cudaStream_t st,
-                              const FuseArgs &fa = FuseArgs{})
+template <int KIND, int MODE, int EW>
+static cudaError_t launch_ew(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                             const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
+                             uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                             int count_only, int grid, int group_m, const BatchTables &bt, cudaStream_t st,
+                             const FuseArgs &fa)
 {
     // the shared-memory opt-in is set once per device (and therefore never inside a stream capture
     // that follows a first eager launch)
@@ -915,14 +914,33 @@ static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, in
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!((configured >> dev) & 1ull)) {
-        e = cudaFuncSetAttribute(sim_tc_kernel<KIND, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        e = cudaFuncSetAttribute(sim_tc_kernel<KIND, MODE, EW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 SMEM_BYTES);
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
-    sim_tc_kernel<KIND, MODE><<<grid, threads_for(KIND, MODE), SMEM_BYTES, st>>>(
+    sim_tc_kernel<KIND, MODE, EW><<<grid, threads_for(EW, MODE), SMEM_BYTES, st>>>(
         *tmA, *tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap, cand_count, status, timeout, count_only,
         group_m < 1 ? 1 : group_m, bt, fa);
     return cudaGetLastError();
+}
+
+template <int KIND, int MODE>
+static cudaError_t launch_one(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                              const long long *nB, float thr, const float *scaleA, const float *scaleB, uint2 *cand,
+                              uint64_t cap, unsigned long long *cand_count, unsigned *status, uint64_t timeout,
+                              int count_only, int grid, int group_m, const BatchTables &bt, cudaStream_t st,
+                              const FuseArgs &fa = FuseArgs{})
+{
+    if constexpr (KIND == 1) {
+        if (kp <= EPI_WIDE_MAX_KP)
+            return launch_ew<KIND, MODE, epi_warps(KIND, true)>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap,
+                                                                cand_count, status, timeout, count_only, grid,
+                                                                group_m, bt, st, fa);
+    }
+    return launch_ew<KIND, MODE, epi_warps(KIND, false)>(tmA, tmB, kp, nA, nB, thr, scaleA, scaleB, cand, cap,
+                                                         cand_count, status, timeout, count_only, grid, group_m, bt,
+                                                         st, fa);
 }
 
 cudaError_t launch_sim_tc(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,

@@ -783,6 +783,9 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
         // so its R rows are staged once in shared memory
         const bool aligned = R.d % 4 == 0 && R.d <= 1024 && R.ld % 4 == 0 && S.ld % 4 == 0 &&
                              (reinterpret_cast<uintptr_t>(R.x) & 15) == 0 && (reinterpret_cast<uintptr_t>(S.x) & 15) == 0;
+        BandNorms bn;
+        if (c->fp64_band > 0.f && (e = band_norms(c, R.n, S.n, &bn)) != cudaSuccess) return from_cuda(e);
+        const BandNorms *bnp = c->fp64_band > 0.f ? &bn : nullptr;
         if (aligned && !(c->flags & EJOIN_FLAG_GATHER_RESCORE)) {
             if ((e = ensure(c->psorted, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
             if ((e = ensure(c->pbuf, rescore_panel_buf_bytes(R.n, S.n, R.d))) != cudaSuccess) return from_cuda(e);
@@ -791,13 +794,13 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
                                       (const uint32_t *)pa.perm.p, (const uint32_t *)pb.perm.p, (const float *)pa.inv.p,
                                       (const float *)pb.inv.p, eps, c->fp64_band, out->d_pairs, out->capacity,
                                       &dm->pair_count, &dm->band_count, 0, c->num_sms, st, (uint2 *)c->band.p,
-                                      c->cand_cap, self ? 1 : 0);
+                                      c->cand_cap, self ? 1 : 0, bnp);
         } else {
             e = launch_rescore((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, R.x, R.ld, S.x, S.ld, R.d,
                                (const uint32_t *)pa.perm.p, (const uint32_t *)pb.perm.p, (const float *)pa.inv.p,
                                (const float *)pb.inv.p, eps, c->fp64_band, out->d_pairs, out->capacity,
                                &dm->pair_count, &dm->band_count, 0, c->num_sms, st, (uint2 *)c->band.p, c->cand_cap,
-                               self ? 1 : 0);
+                               self ? 1 : 0, bnp);
         }
         if (e != cudaSuccess) return from_cuda(e);
     }
