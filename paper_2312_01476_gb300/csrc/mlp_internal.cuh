@@ -110,6 +110,20 @@ cudaError_t launch_anchor_argmax(const uint2 *cand, const unsigned long long *ca
                                  const float *anchors, unsigned long long *best, int num_sms, cudaStream_t st);
 cudaError_t launch_anchor_keys(const unsigned long long *best, int64_t n, int n_anchor, uint32_t *key, int num_sms,
                                cudaStream_t st);
+// Tile-pair bounds on the tensor cores: rows of ball_k() FP32 columns whose dot product is >= 0 exactly when
+// the ball pair's bound reaches eps_sketch (side 0: the A balls, with alpha = acos(eps_sketch) folded in;
+// side 1: the B balls); rows n_balls .. rows_pad - 1 are zero padding.
+int ball_k();
+cudaError_t launch_ball_rows(const float *cent, const float *rad, int64_t n_balls, int64_t rows_pad,
+                             float eps_sketch, int side, float *out, int num_sms, cudaStream_t st);
+// The kept ball pairs (candidates of the threshold contraction of the two ball matrices) as the list of kept
+// (A tile, B tile) pairs, ordered by A tile then B tile (bits: tA * tB bits, row_cnt: tA entries); sym: only
+// block pairs on or above the diagonal.  *list_count = the number of kept tile pairs (the list holds the
+// first list_cap).
+cudaError_t launch_ball_pairs_to_list(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                      int64_t tA, int64_t tB, int sym, uint32_t *bits, uint32_t *row_cnt,
+                                      uint2 *list, uint64_t list_cap, unsigned long long *list_count, int num_sms,
+                                      cudaStream_t st);
 // Balls per tile in the pruning bound.
 constexpr int PRUNE_BALLS = 4;
 // Per tile of `tile_rows` (<= 256) consecutive sketch rows: up to PRUNE_BALLS balls formed greedily

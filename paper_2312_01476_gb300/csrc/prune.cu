@@ -541,6 +541,189 @@ cudaError_t launch_tile_pairs(const float *cA, const float *rA, int64_t tA, cons
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------------------
+// Tile-pair bounds on the tensor cores.  The bound of a ball pair (unit centroids c_a, c_b, angular radii
+// r_a, r_b) keeps it when angle(c_a, c_b) <= r_a + alpha + r_b, alpha = acos(eps_sketch).  With
+// u = r_a + alpha < pi/2 and r_b < pi/2 that is cos(angle) >= cos(u + r_b) = cos u cos r_b - sin u sin r_b,
+// i.e. the dot product of the augmented rows  a = [c_a, -cos u, sin u, 0, 1, 0, 1]  and
+// b = [c_b, cos r_b, sin r_b, 1, 0, 1, 0]  is >= 0.  The last four columns make the other cases exact:
+// a "wide" ball (u >= pi/2, resp. r_b >= pi/2) has a zero centroid part and a 1 that meets a 1 of every
+// used ball of the other side (kept with all of them, a superset of the angle test), and an unused ball
+// carries -4 against a 1 of every ball of the other side (never kept).  Rows have BALL_K = 96 FP32 columns
+// (70 used, zero padding): the TF32 threshold contraction of the two ball matrices at -margin then lists
+// every kept ball pair.
+constexpr int BALL_K = 96;
+
+__global__ void ball_rows_kernel(const float *__restrict__ cent, const float *__restrict__ rad, int64_t n_balls,
+                                 int64_t rows_pad, float alpha, int side, float *__restrict__ out)
+{
+    // one warp per ball row (rows beyond n_balls are zero padding)
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = w0; k < rows_pad; k += nw) {
+        float *o = out + k * BALL_K;
+        const float r = k < n_balls ? rad[k] : -1.f;
+        const bool used = r >= 0.f;
+        const float u = side == 0 ? r + alpha : r;
+        const bool wide = used && u >= 0.5f * PI_F;
+        const bool normal = used && !wide;
+        for (int q = lane; q < BALL_K; q += 32) {
+            float v = 0.f;
+            if (q < SK) {
+                v = normal ? cent[k * SK + q] : 0.f;
+            } else if (side == 0) {
+                switch (q) {
+                case SK: v = normal ? -cosf(u) : 0.f; break;
+                case SK + 1: v = normal ? sinf(u) : 0.f; break;
+                case SK + 2: v = wide ? 1.f : 0.f; break;
+                case SK + 3: v = used ? 1.f : 0.f; break;
+                case SK + 4: v = used ? 0.f : -4.f; break;
+                case SK + 5: v = 1.f; break;
+                default: break;
+                }
+            } else {
+                switch (q) {
+                case SK: v = normal ? cosf(u) : 0.f; break;
+                case SK + 1: v = normal ? sinf(u) : 0.f; break;
+                case SK + 2: v = used ? 1.f : 0.f; break;
+                case SK + 3: v = wide ? 1.f : 0.f; break;
+                case SK + 4: v = 1.f; break;
+                case SK + 5: v = used ? 0.f : -4.f; break;
+                default: break;
+                }
+            }
+            o[q] = v;
+        }
+    }
+}
+
+// bit (ta * tB + tb) for each kept ball pair (ball rows a, b: tiles a / NB, b / NB); sym: only block pairs on
+// or above the diagonal (ta / 2 <= tb)
+__global__ void ball_pairs_bitmap_kernel(const uint2 *__restrict__ cand, const unsigned long long *__restrict__ count,
+                                         uint64_t cap, int64_t tA, int64_t tB, int sym, uint32_t *bits)
+{
+    uint64_t n = *count;
+    if (n > cap) n = cap;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+        const int64_t ta = cand[k].x / NB, tb = cand[k].y / NB;
+        if (ta >= tA || tb >= tB || (sym && (ta >> 1) > tb)) continue;
+        const uint64_t b = (uint64_t)ta * (uint64_t)tB + (uint64_t)tb;
+        atomicOr(bits + (b >> 5), 1u << (b & 31));
+    }
+}
+
+// row_cnt[ta] = kept tile pairs of A tile ta (one warp per row of the bitmap)
+__global__ void bitmap_row_count_kernel(const uint32_t *__restrict__ bits, int64_t tA, int64_t tB, uint32_t *row_cnt)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ta = w0; ta < tA; ta += nw) {
+        uint32_t c = 0;
+        const uint64_t b0 = (uint64_t)ta * (uint64_t)tB;
+        for (int64_t tb = lane; tb < tB; tb += 32) {
+            const uint64_t b = b0 + (uint64_t)tb;
+            c += (bits[b >> 5] >> (b & 31)) & 1u;
+        }
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) row_cnt[ta] = c;
+    }
+}
+
+// one block: exclusive scan of the row counts in place; *count = total
+__global__ void __launch_bounds__(1024) bitmap_row_scan_kernel(uint32_t *row_cnt, int64_t tA,
+                                                              unsigned long long *count)
+{
+    __shared__ uint32_t w[32];
+    __shared__ unsigned long long carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b0 = 0; b0 < tA; b0 += 1024) {
+        const int64_t i = b0 + threadIdx.x;
+        const uint32_t v = i < tA ? row_cnt[i] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t a = w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, a, o);
+                if (lane >= o) a += y;
+            }
+            w[lane] = a;
+        }
+        __syncthreads();
+        if (i < tA) row_cnt[i] = (uint32_t)carry + (warp ? w[warp - 1] : 0u) + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += w[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = carry;
+}
+
+// list[row_off[ta] + rank] = (ta, tb) for the set bits of row ta, in ascending tb (one warp per row)
+__global__ void bitmap_row_write_kernel(const uint32_t *__restrict__ bits, int64_t tA, int64_t tB,
+                                        const uint32_t *__restrict__ row_off, uint2 *__restrict__ list, uint64_t cap)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t ta = w0; ta < tA; ta += nw) {
+        uint64_t pos = row_off[ta];
+        const uint64_t b0 = (uint64_t)ta * (uint64_t)tB;
+        for (int64_t t0 = 0; t0 < tB; t0 += 32) {
+            const int64_t tb = t0 + lane;
+            bool set = false;
+            if (tb < tB) {
+                const uint64_t b = b0 + (uint64_t)tb;
+                set = (bits[b >> 5] >> (b & 31)) & 1u;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, set);
+            if (set) {
+                const uint64_t p = pos + __popc(m & ((1u << lane) - 1u));
+                if (p < cap) list[p] = make_uint2((uint32_t)ta, (uint32_t)tb);
+            }
+            pos += __popc(m);
+        }
+    }
+}
+
+int ball_k() { return BALL_K; }
+
+cudaError_t launch_ball_rows(const float *cent, const float *rad, int64_t n_balls, int64_t rows_pad,
+                             float eps_sketch, int side, float *out, int num_sms, cudaStream_t st)
+{
+    const float alpha = eps_sketch >= 1.f ? 0.f : (eps_sketch <= -1.f ? PI_F : acosf(eps_sketch));
+    const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((rows_pad + 7) / 8, (int64_t)num_sms * 16));
+    ball_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(cent, rad, n_balls, rows_pad, alpha, side, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ball_pairs_to_list(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                      int64_t tA, int64_t tB, int sym, uint32_t *bits, uint32_t *row_cnt,
+                                      uint2 *list, uint64_t list_cap, unsigned long long *list_count, int num_sms,
+                                      cudaStream_t st)
+{
+    const uint64_t words = ((uint64_t)tA * (uint64_t)tB + 31) / 32;
+    cudaError_t e = cudaMemsetAsync(bits, 0, words * 4, st);
+    if (e != cudaSuccess) return e;
+    const unsigned gc = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((cand_cap + 255) / 256, (uint64_t)num_sms * 8));
+    ball_pairs_bitmap_kernel<<<gc, 256, 0, st>>>(cand, cand_count, cand_cap, tA, tB, sym, bits);
+    const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((tA + 7) / 8, (int64_t)num_sms * 16));
+    bitmap_row_count_kernel<<<gr, 256, 0, st>>>(bits, tA, tB, row_cnt);
+    bitmap_row_scan_kernel<<<1, 1024, 0, st>>>(row_cnt, tA, list_count);
+    bitmap_row_write_kernel<<<gr, 256, 0, st>>>(bits, tA, tB, row_cnt, list, list_cap);
+    return cudaGetLastError();
+}
+
 }  // namespace ej
 
 namespace ej {

@@ -48,6 +48,9 @@ struct ejoin_sketch {
     } pw[2];
     Buf list, list_count;
     uint64_t list_cap = 0;
+    // tile-pair bounds on the tensor cores: augmented ball rows of both sides, kept ball pairs, bitmap
+    Buf ballA, ballB, bcand, bmisc, bits, rowcnt;
+    uint64_t bcand_cap = 0;
 };
 
 namespace {
@@ -281,7 +284,7 @@ void ejoin_sketch_destroy(ejoin_sketch *sk)
         cudaDeviceSynchronize();
         for (Buf *b : {&sk->params, &sk->grads, &sk->m, &sk->v, &sk->idx, &sk->A1, &sk->H, &sk->Z, &sk->S, &sk->nz,
                        &sk->dS, &sk->dZ, &sk->dH, &sk->scal, &sk->fH, &sk->fZ, &sk->finv, &sk->list,
-                       &sk->list_count})
+                       &sk->list_count, &sk->ballA, &sk->ballB, &sk->bcand, &sk->bmisc, &sk->bits, &sk->rowcnt})
             release(*b);
         for (auto &w : sk->pw)
             for (Buf *b : {&w.S, &w.key1, &w.perm1, &w.perm, &w.hist, &w.a_idx, &w.anchors2, &w.norm, &w.inv,
@@ -451,6 +454,61 @@ namespace {
 
 constexpr int SKW = 64;
 constexpr int64_t PRUNE_RECALL_ROWS = 2048;  // sampled rows of R for the recall estimate
+// Threshold of the ball-row contraction: below 0 by more than its TF32 error (at most 2 * 2 * 2^-10 with the
+// augmented rows' dot products bounded by 2), so that no ball pair the exact test keeps is lost.
+constexpr float BALL_MARGIN = 0.006f;
+
+// The kept tile pairs of the pruned join (sk->list, *n_list) from the balls of both sides on the tensor cores.
+// cudaErrorNotSupported: the ball matrices exceed the index range of the contraction (the caller then uses the
+// CUDA-core bound kernel).
+cudaError_t tile_list_tc(ejoin_sketch *sk, ejoin_ctx *c, Buf &centA, Buf &radA, int64_t tA, const float *cB,
+                         const float *rB, int64_t tB, float eps_sketch, bool self, unsigned long long *n_list)
+{
+    cudaStream_t st = c->stream;
+    const int K = ball_k();
+    const int64_t nbA = tA * PRUNE_BALLS, nbB = tB * PRUNE_BALLS;
+    const int64_t padA = round_up(nbA, 256), padB = round_up(nbB, 256);
+    if (padA >= (1ll << 31) || padB >= (1ll << 31)) return cudaErrorNotSupported;
+    const uint64_t words = ((uint64_t)tA * (uint64_t)tB + 31) / 32;
+    cudaError_t e;
+    if ((e = ensure(sk->ballA, (size_t)padA * K * 4)) || (e = ensure(sk->ballB, (size_t)padB * K * 4)) ||
+        (e = ensure(sk->bmisc, 64)) || (e = ensure(sk->bits, words * 4)) || (e = ensure(sk->rowcnt, (size_t)tA * 4)))
+        return e;
+    if (sk->bcand_cap == 0) sk->bcand_cap = 1ull << 22;
+    long long *ncnt = (long long *)sk->bmisc.p;  // [0] ball rows of A, [1] of B
+    unsigned long long *bcount = (unsigned long long *)(ncnt + 2);
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    if ((e = launch_ball_rows(P(centA), P(radA), nbA, padA, eps_sketch, 0, P(sk->ballA), c->num_sms, st)) ||
+        (e = launch_ball_rows(cB, rB, nbB, padB, eps_sketch, 1, P(sk->ballB), c->num_sms, st)) ||
+        (e = launch_set_count(ncnt, nbA, st)) || (e = launch_set_count(ncnt + 1, nbB, st)))
+        return e;
+    CUtensorMap tmA, tmB;
+    if (!make_tmap(&tmA, sk->ballA.p, FMT_F32, K, padA, 128) || !make_tmap(&tmB, sk->ballB.p, FMT_F32, K, padB, 256))
+        return cudaErrorNotSupported;
+    unsigned long long nb = 0;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if ((e = ensure(sk->bcand, sk->bcand_cap * sizeof(uint2))) || (e = cudaMemsetAsync(bcount, 0, 8, st)) ||
+            (e = launch_sim_tc(2, &tmA, &tmB, K, ncnt, ncnt + 1, -BALL_MARGIN, nullptr, nullptr, (uint2 *)sk->bcand.p,
+                               sk->bcand_cap, bcount, &dm->status, c->timeout, 0, c->num_sms, default_group_m(K), st)) ||
+            (e = cudaMemcpyAsync(&nb, bcount, 8, cudaMemcpyDeviceToHost, st)) || (e = cudaStreamSynchronize(st)))
+            return e;
+        if (nb <= sk->bcand_cap) break;
+        sk->bcand_cap = nb + nb / 4 + 1024;
+    }
+    if (nb > sk->bcand_cap) return cudaErrorNotSupported;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        if ((e = ensure(sk->list, sk->list_cap * sizeof(uint2))) || (e = ensure(sk->list_count, 8)) ||
+            (e = launch_ball_pairs_to_list((const uint2 *)sk->bcand.p, bcount, sk->bcand_cap, tA, tB, self ? 1 : 0,
+                                           (uint32_t *)sk->bits.p, (uint32_t *)sk->rowcnt.p, (uint2 *)sk->list.p,
+                                           sk->list_cap, (unsigned long long *)sk->list_count.p, c->num_sms, st)) ||
+            (e = cudaMemcpyAsync(n_list, sk->list_count.p, 8, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            return e;
+        if (*n_list <= sk->list_cap) return cudaSuccess;
+        sk->list_cap = *n_list;
+    }
+    return cudaErrorNotSupported;
+}
 // covering anchors (see prune.cu): sample size, candidates per round, anchor limit, coverage cosine
 constexpr int64_t COVER_SAMPLE = 262144;
 constexpr int COVER_ROUND = 4096;
@@ -692,7 +750,17 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     }
     if (sk->list_cap == 0) sk->list_cap = std::min<uint64_t>((uint64_t)tA * tB, 1ull << 22);
     unsigned long long n_list = 0;
-    for (int attempt = 0; attempt < 3; ++attempt) {
+    // tile-pair bounds as a TF32 threshold contraction of augmented ball rows (prune.cu), the kept ball
+    // pairs turned into the ordered tile list; the CUDA-core kernel below when that path cannot run
+    bool listed = false;
+    if ((e = tile_list_tc(sk, c, pa.cent, pa.rad, tA, cB, rB, tB, eps_sketch, self, &n_list)) == cudaSuccess)
+        listed = true;
+    else if (e != cudaErrorNotSupported) {
+        release(centB);
+        release(radB);
+        return from_cuda(e);
+    }
+    for (int attempt = 0; attempt < 3 && !listed; ++attempt) {
         if ((e = ensure(sk->list, sk->list_cap * sizeof(uint2))) || (e = ensure(sk->list_count, 8)) ||
             (e = cudaMemsetAsync(sk->list_count.p, 0, 8, st)) ||
             (e = launch_tile_pairs((const float *)pa.cent.p, (const float *)pa.rad.p, tA, cB, rB, tB, SKW, eps_sketch,
