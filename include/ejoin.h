@@ -358,6 +358,11 @@ ejoin_status ejoin_sketch_set_params(ejoin_sketch *sk, const float *h_params);
 ejoin_status ejoin_sketch_get_params(const ejoin_sketch *sk, float *h_params);
 /* Sketches of the rows of X (device, raw rows; normalised internally) into d_S [X.n x 64]. */
 ejoin_status ejoin_sketch_forward(ejoin_sketch *sk, ejoin_rel X, float *d_S);
+/* The same on the tensor cores, as the pruned join computes its sketches: both layers are TF32 products
+ * of the FP32 operands with FP32 accumulation (bias, GELU and the row scale in the epilogue), so each
+ * sketch carries a relative error of about 1e-3 against ejoin_sketch_forward.  Needs X.ld, d and hidden
+ * multiples of 4 and a 16-byte aligned X.x (else EJOIN_EUNSUPPORTED). */
+ejoin_status ejoin_sketch_forward_tc(ejoin_sketch *sk, ejoin_rel X, float *d_S);
 /* Pairs k = (rows d_p[k], d_q[k] of X), d_inv = 1/|row| of X's rows (device, see
  * ejoin_row_inv_norm).  grad: loss and its gradient (flat parameter layout,
  * device, optional) without changing the parameters; train_step: the same

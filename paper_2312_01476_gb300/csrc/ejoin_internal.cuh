@@ -69,6 +69,13 @@ struct BatchTables {
     // pass 0 may sample every top_stride-th column tile while that leaves at least top_min_tiles
     int top_stride, top_min_tiles;
     float top_margin;
+    // GEMM mode (a dense layer): out[r * out_ld + c] = act(rowscale[r] * acc(r, c) + bias[c]) for the valid
+    // rows and columns; rowscale and bias optional, act: 0 none, 1 exact GELU
+    const float *g_rowscale;
+    const float *g_bias;
+    float *g_out;
+    long long g_ld;
+    int g_act;
 };
 
 // Order-preserving map of floats to unsigned integers (and back): a < b iff f2ord(a) < f2ord(b)
@@ -193,6 +200,12 @@ cudaError_t launch_sim_tc_fused(int kind, const CUtensorMap *tmA, const CUtensor
                                 const long long *nA, const long long *nB, float thr, const float *scaleA,
                                 const float *scaleB, const FuseArgs &fa, unsigned long long *cand_count,
                                 unsigned *status, uint64_t timeout, int grid, int group_m, cudaStream_t st);
+// Dense layer on the tensor cores (TF32 from FP32 operands, FP32 accumulation): out = act(rowscale * A B^T + bias)
+// for A [nA x kp] and B [nB x kp] (tensor maps as for the contraction, kind TF32), out [nA x nB] with row
+// stride out_ld; act 0 none, 1 exact GELU.
+cudaError_t launch_gemm_tc(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                           const long long *nB, const float *rowscale, const float *bias, int act, float *out,
+                           long long out_ld, unsigned *status, uint64_t timeout, int grid, cudaStream_t st);
 // Contraction over an explicit list of (row tile, column tile) pairs (pruned joins); sym: see
 // BatchTables::sym.
 cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,

@@ -26,6 +26,9 @@ size_t fmt_bytes(int fmt);
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 // 2-D K-major operand [rows x kp] with a (128-byte x box_rows) box and 128-byte swizzle.
 bool make_tmap(CUtensorMap *m, const void *base, int fmt, int64_t kp, int64_t rows, uint32_t box_rows);
+// 2-D tensor map over raw FP32 rows (d columns, ld floats apart, columns past d read as zeros), a
+// (32-float x box_rows) box, 128-byte swizzle; needs a 16-byte aligned base and ld % 4 == 0.
+bool make_tmap_rows_f32(CUtensorMap *m, const float *base, int64_t d, int64_t ld, int64_t rows, uint32_t box_rows);
 // Rigorous default guard band of a precision at padded dimension kp.
 float default_band(int prec, int64_t kp);
 // Default half-width around eps inside which the accurate tier (compensated dot products finished in

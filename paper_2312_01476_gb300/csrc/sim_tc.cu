@@ -147,7 +147,9 @@ struct TileInfo {
 };
 
 enum : int { MODE_SINGLE = 0, MODE_BATCH = 1, MODE_LIST = 2, MODE_FUSED = 3, MODE_SYM = 4, MODE_TOPMAX = 5,
-             MODE_TOPCAND = 6, MODE_TOP1 = 7 };
+             MODE_TOPCAND = 6, MODE_TOP1 = 7, MODE_GEMM = 8 };
+// MODE_GEMM: the accumulator tile is written out as a dense layer (row scale, bias, activation) instead
+// of being compared with a threshold: the sketch network's layers on the tensor cores.
 // MODE_TOPMAX / MODE_TOPCAND: the two contraction passes of the top-k join condition (Sec. VI-E),
 // tiled like MODE_SINGLE.  TOPMAX keeps, per row of A and column group, the largest bulk similarity
 // over the valid columns (no candidates); TOPCAND emits the candidates within a margin of a per-row
@@ -691,6 +693,34 @@ __global__ void __launch_bounds__(threads_for(EW, MODE), 1)
             auto process = [&](uint32_t (&v)[32], int c) {
                 const long long col0 = colbase + c * 32;
                 const int left = ti.limB - (colbase_local + c * 32);  // valid columns in this chunk
+                if constexpr (MODE == MODE_GEMM) {
+                    // dense layer: each lane writes its row's 32 columns of this chunk (float4 stores)
+                    if (row_ok && left > 0) {
+                        const float rsc = bt.g_rowscale ? __ldg(bt.g_rowscale + row) : 1.f;
+                        float *o = bt.g_out + row * bt.g_ld + col0;
+#pragma unroll
+                        for (int k4 = 0; k4 < 8; ++k4) {
+                            float y[4];
+#pragma unroll
+                            for (int t = 0; t < 4; ++t) {
+                                const int k = 4 * k4 + t;
+                                float x = __uint_as_float(v[k]) * rsc;
+                                if (bt.g_bias && k < left) x += __ldg(bt.g_bias + col0 + k);
+                                if (bt.g_act == 1) x = 0.5f * x * (1.f + erff(x * 0.70710678118654752f));
+                                y[t] = x;
+                            }
+                            if (4 * k4 + 3 < left) {
+                                *reinterpret_cast<float4 *>(o + 4 * k4) = make_float4(y[0], y[1], y[2], y[3]);
+                            } else {
+#pragma unroll
+                                for (int t = 0; t < 4; ++t)
+                                    if (4 * k4 + t < left) o[4 * k4 + t] = y[t];
+                            }
+                        }
+                    }
+                    __syncwarp();  // reconverge before the caller's .sync.aligned tcgen05 instructions
+                    return;
+                }
                 float f[32];
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
@@ -1061,6 +1091,21 @@ cudaError_t launch_sim_tc_fused(int kind, const CUtensorMap *tmA, const CUtensor
                                          timeout, fa.count_only, grid, group_m, none, st, fa);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_gemm_tc(const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,
+                           const long long *nB, const float *rowscale, const float *bias, int act, float *out,
+                           long long out_ld, unsigned *status, uint64_t timeout, int grid, cudaStream_t st)
+{
+    if (out_ld % 4 != 0 || (reinterpret_cast<uintptr_t>(out) & 15) != 0) return cudaErrorInvalidValue;
+    BatchTables bt{};
+    bt.g_rowscale = rowscale;
+    bt.g_bias = bias;
+    bt.g_out = out;
+    bt.g_ld = out_ld;
+    bt.g_act = act;
+    return launch_one<2, MODE_GEMM>(tmA, tmB, kp, nA, nB, 0.f, nullptr, nullptr, nullptr, 0, nullptr, status, timeout,
+                                    0, grid, default_group_m(kp), bt, st);
 }
 
 cudaError_t launch_sim_tc_list(int kind, const CUtensorMap *tmA, const CUtensorMap *tmB, int kp, const long long *nA,

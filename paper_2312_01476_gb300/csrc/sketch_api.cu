@@ -38,7 +38,7 @@ struct ejoin_sketch {
     // training workspace (grown on demand)
     Buf idx, A1, H, Z, S, nz, dS, dZ, dH, scal;  // scal: [loss, wsum]
     // forward workspace
-    Buf fH, fZ, finv;
+    Buf fH, fZ, finv, fcnt;
     // pruned-join workspace, per side
     struct Side {
         Buf S, key1, perm1, perm, hist, a_idx, anchors2, norm, inv, scale, sS, maxdot, cent, rad;
@@ -60,6 +60,48 @@ constexpr int64_t FWD_CHUNK = 1 << 20;
 cudaError_t grow(Buf &b, size_t bytes) { return ensure(b, bytes); }
 
 float *P(Buf &b) { return (float *)b.p; }
+
+// The same forward with both layers on the tensor cores (TF32 from the FP32 operands, FP32 accumulation):
+// H = GELU(inv * X W1^T + b1), Z = H W2^T + b2, rows of Z normalised.  The products carry TF32 rounding
+// (relative 2^-10 per operand element) instead of FP32's, a sketch-cosine error of about 1e-3, well inside
+// the calibration margin; the pruned join uses it for its sketches.  cudaErrorNotSupported when the
+// layout does not allow tensor maps (the caller then uses sketch_forward).
+cudaError_t sketch_forward_tc(ejoin_sketch *sk, const float *x, int64_t n, int64_t ld, const float *inv, float *S_out,
+                              cudaStream_t st)
+{
+    ejoin_ctx *c = sk->ctx;
+    const float *W = P(sk->params);
+    const int d = sk->d, hid = sk->hid, out = sk->out;
+    if (ld % 4 || d % 4 || hid % 4 || (reinterpret_cast<uintptr_t>(x) & 15) || (sk->oW2 % 4) || (sk->ob1 % 4))
+        return cudaErrorNotSupported;
+    cudaError_t e;
+    const int64_t chunk = std::min<int64_t>(n, FWD_CHUNK);
+    if ((e = grow(sk->fH, (size_t)std::max<int64_t>(chunk, 1) * hid * 4)) ||
+        (e = grow(sk->fZ, (size_t)std::max<int64_t>(chunk, 1) * out * 4)) || (e = grow(sk->fcnt, 64)))
+        return e;
+    long long *cnt = (long long *)sk->fcnt.p;  // [0] rows of the chunk, [1] hid, [2] out
+    if ((e = launch_set_count(cnt + 1, hid, st)) || (e = launch_set_count(cnt + 2, out, st))) return e;
+    CUtensorMap tW1, tW2, tH;
+    if (!make_tmap_rows_f32(&tW1, W + sk->oW1, d, d, hid, 256) ||
+        !make_tmap_rows_f32(&tW2, W + sk->oW2, hid, hid, out, 256) ||
+        !make_tmap_rows_f32(&tH, P(sk->fH), hid, hid, std::max<int64_t>(chunk, 1), 128))
+        return cudaErrorNotSupported;
+    DevMisc *dm = (DevMisc *)c->misc.p;
+    const int kp1 = (int)round_up(d, 32), kp2 = (int)round_up(hid, 32);
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t m = std::min<int64_t>(chunk, n - r0);
+        CUtensorMap tX;
+        if (!make_tmap_rows_f32(&tX, x + r0 * ld, d, ld, m, 128)) return cudaErrorNotSupported;
+        if ((e = launch_set_count(cnt, m, st)) ||
+            (e = launch_gemm_tc(&tX, &tW1, kp1, cnt, cnt + 1, inv + r0, W + sk->ob1, ACT_GELU, P(sk->fH), hid,
+                                &dm->status, c->timeout, c->num_sms, st)) ||
+            (e = launch_gemm_tc(&tH, &tW2, kp2, cnt, cnt + 2, nullptr, W + sk->ob2, ACT_NONE, P(sk->fZ), out,
+                                &dm->status, c->timeout, c->num_sms, st)) ||
+            (e = launch_rownorm(P(sk->fZ), m, out, S_out + r0 * out, nullptr, c->num_sms, st)))
+            return e;
+    }
+    return cudaSuccess;
+}
 
 // Forward of rows [0, n) of x (raw rows; inv = their inverse norms) into S_out (n x out).
 cudaError_t sketch_forward(ejoin_sketch *sk, const float *x, int64_t n, int64_t ld, const float *inv, float *S_out,
@@ -283,7 +325,7 @@ void ejoin_sketch_destroy(ejoin_sketch *sk)
         DeviceGuard g(sk->device);
         cudaDeviceSynchronize();
         for (Buf *b : {&sk->params, &sk->grads, &sk->m, &sk->v, &sk->idx, &sk->A1, &sk->H, &sk->Z, &sk->S, &sk->nz,
-                       &sk->dS, &sk->dZ, &sk->dH, &sk->scal, &sk->fH, &sk->fZ, &sk->finv, &sk->list,
+                       &sk->dS, &sk->dZ, &sk->dH, &sk->scal, &sk->fH, &sk->fZ, &sk->finv, &sk->fcnt, &sk->list,
                        &sk->list_count, &sk->ballA, &sk->ballB, &sk->bcand, &sk->bmisc, &sk->bits, &sk->rowcnt})
             release(*b);
         for (auto &w : sk->pw)
@@ -326,6 +368,18 @@ ejoin_status ejoin_sketch_forward(ejoin_sketch *sk, ejoin_rel X, float *d_S)
     cudaError_t e = ensure(sk->finv, (size_t)X.n * 4);
     if (e == cudaSuccess) e = launch_row_inv_norm(X.x, X.n, X.d, X.ld, P(sk->finv), sk->ctx->num_sms, sk->ctx->stream);
     if (e == cudaSuccess) e = sketch_forward(sk, X.x, X.n, X.ld, P(sk->finv), d_S, sk->ctx->stream);
+    return from_cuda(e);
+}
+
+ejoin_status ejoin_sketch_forward_tc(ejoin_sketch *sk, ejoin_rel X, float *d_S)
+{
+    if (!sk || !d_S || X.d != sk->d || X.ld < X.d || X.n < 0 || (X.n && !X.x)) return EJOIN_EINVAL;
+    if (X.n == 0) return EJOIN_OK;
+    DeviceGuard g(sk->ctx->device);
+    cudaError_t e = ensure(sk->finv, (size_t)X.n * 4);
+    if (e == cudaSuccess) e = launch_row_inv_norm(X.x, X.n, X.d, X.ld, P(sk->finv), sk->ctx->num_sms, sk->ctx->stream);
+    if (e == cudaSuccess) e = sketch_forward_tc(sk, X.x, X.n, X.ld, P(sk->finv), d_S, sk->ctx->stream);
+    if (e == cudaErrorNotSupported) return EJOIN_EUNSUPPORTED;
     return from_cuda(e);
 }
 
@@ -543,8 +597,9 @@ ejoin_status prune_side(ejoin_sketch *sk, int w, const ejoin_rel &r, int fmt, in
     if ((e = launch_normalize(fmt, r.x, r.ld, r.d, nullptr, n_dev, n, sd.norm.p, kp, (int)kp, (float *)sd.inv.p,
                               (float *)sd.scale.p, &dm->status, c->num_sms, st)) != cudaSuccess)
         return from_cuda(e);
-    if ((e = sketch_forward(sk, r.x, n, r.ld, (const float *)sd.inv.p, (float *)pw.S.p, st)) != cudaSuccess)
-        return from_cuda(e);
+    e = sketch_forward_tc(sk, r.x, n, r.ld, (const float *)sd.inv.p, (float *)pw.S.p, st);
+    if (e == cudaErrorNotSupported) e = sketch_forward(sk, r.x, n, r.ld, (const float *)sd.inv.p, (float *)pw.S.p, st);
+    if (e != cudaSuccess) return from_cuda(e);
     if (w == 0) cudaEventRecord(c->ev[5], st);
 
     // covering anchors over a strided sample of m rows, candidates taken in a fixed pseudo-random order

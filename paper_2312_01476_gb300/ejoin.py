@@ -192,6 +192,8 @@ def load_library(path: str = LIB_PATH):
     lib.ejoin_threshold_pruned.restype = ctypes.c_int
     lib.ejoin_threshold_pruned.argtypes = [vp, vp, ejoin_rel, ejoin_rel, ctypes.c_float, ctypes.c_float,
                                            P(ejoin_pairs), P(ejoin_prune_stats), P(ctypes.c_float)]
+    lib.ejoin_sketch_forward_tc.restype = ctypes.c_int
+    lib.ejoin_sketch_forward_tc.argtypes = [vp, ejoin_rel, vp]
     lib.ejoin_sketch_train.restype = ctypes.c_int
     lib.ejoin_sketch_train.argtypes = [vp, ejoin_rel, ejoin_rel, P(ejoin_sketch_train_cfg), P(ctypes.c_float),
                                        P(ejoin_sketch_train_report)]
@@ -629,6 +631,13 @@ class Sketch:
         import torch
         S = torch.empty((max(X.shape[0], 1), self.out), dtype=torch.float32, device=X.device)
         _check(load_library().ejoin_sketch_forward(self.handle, _dev_rel(X), _ptr(S)), "ejoin_sketch_forward")
+        return S[: X.shape[0]]
+
+    def forward_tc(self, X):
+        """Sketches on the tensor cores (TF32 layers), as the pruned join computes them."""
+        import torch
+        S = torch.empty((max(X.shape[0], 1), self.out), dtype=torch.float32, device=X.device)
+        _check(load_library().ejoin_sketch_forward_tc(self.handle, _dev_rel(X), _ptr(S)), "ejoin_sketch_forward_tc")
         return S[: X.shape[0]]
 
     def grad(self, X, inv, p, q, t, w):

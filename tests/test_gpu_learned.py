@@ -53,6 +53,32 @@ def test_forward_matches_fp64_reference():
     assert np.abs(S - ref).max() < 2e-5
 
 
+@pytest.mark.parametrize("n,d,hid", [(300, 48, 32), (5000, 768, 256), (1300, 100, 64)])
+def test_tensor_core_forward_matches_fp64_reference(n, d, hid):
+    # the TF32 forward the pruned join uses: sketches and sketch cosines within a few 1e-3 of FP64
+    rng = np.random.default_rng(n)
+    X = (rng.standard_normal((n, d)) * 2.0).astype(np.float32)
+    flat = inputs.sketch_init_params(d, hid, 64, 7)
+    flat[hid * d:hid * d + hid] = rng.standard_normal(hid).astype(np.float32) * 0.1
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        sk = E.Sketch(ctx, d, hid, 64)
+        sk.set_params(flat)
+        Xd = torch.from_numpy(X).cuda()
+        St = sk.forward_tc(Xd).cpu().numpy()
+        params = sk.unflatten(flat.astype(np.float64))
+        sk.close()
+    Xu = X.astype(np.float64) / np.linalg.norm(X.astype(np.float64), axis=1, keepdims=True)
+    ref = mlp_ref.forward(params, Xu)["s"]
+    err = np.abs(St - ref)
+    # TF32 products: about 1e-3 relative on z; a row of small |z| magnifies it in the normalised sketch
+    assert np.median(err) < 1e-3 and np.quantile(err, 0.999) < 5e-3 and err.max() < 3e-2, (np.median(err),
+                                                                                          err.max())
+    p = rng.integers(0, n, 2000)
+    q = rng.integers(0, n, 2000)
+    cerr = np.abs(np.sum(St[p] * St[q], 1) - np.sum(ref[p] * ref[q], 1))
+    assert np.quantile(cerr, 0.999) < 3e-3 and cerr.max() < 3e-2, cerr.max()
+
+
 def test_gradients_match_fp64_reference():
     X, flat = _tiny(2)
     rng = np.random.default_rng(5)
