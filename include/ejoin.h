@@ -448,6 +448,8 @@ typedef struct ejoin_prune_stats {
        rows that the pruned join returns, the rows sampled and their exact matches */
     float recall_est;
     uint64_t recall_sample_rows, recall_sample_matches;
+    float ms_tile_stats;   /* the part of ms_bound spent on the balls of the tiles (the rest: tile-pair bounds) */
+    int32_t reserved;
 } ejoin_prune_stats;
 
 /* Threshold join of R and S (device, no selection) that contracts only the

@@ -159,14 +159,14 @@ cudaError_t band_norms(ejoin_ctx *c, int64_t nR, int64_t nS, BandNorms *bn)
 {
     nR = std::max<int64_t>(nR, 1);
     nS = std::max<int64_t>(nS, 1);
-    const size_t bytes = (size_t)(nR + nS) * 8 + (size_t)(nR + nS);
+    const size_t bytes = (size_t)(nR + nS) * 12;
     cudaError_t e = ensure(c->band_rows, bytes);
     if (e != cudaSuccess) return e;
     char *p = (char *)c->band_rows.p;
     bn->nrmR = (double *)p;
     bn->nrmS = bn->nrmR + nR;
-    bn->flagR = (unsigned char *)(bn->nrmS + nS);
-    bn->flagS = bn->flagR + nR;
+    bn->claimR = (unsigned *)(bn->nrmS + nS);
+    bn->claimS = bn->claimR + nR;
     bn->nR = nR;
     bn->nS = nS;
     return cudaSuccess;
@@ -593,10 +593,16 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         const uint32_t *idsA = selR ? (const uint32_t *)sa.ids.p : nullptr;
         const uint32_t *idsB = selS ? (const uint32_t *)sb.ids.p : nullptr;
         if (panels) {
+            // the kept rows and the candidates are known here (read back before the re-score): they size the
+            // panels and decide how far S blocks may split them
+            const int64_t rows_a = std::max<long long>(hm.n_sel[0], 1);
+            const int64_t rows_b = std::max<long long>(self ? hm.n_sel[0] : hm.n_sel[1], 1);
+            const uint64_t hint = std::max<unsigned long long>(hm.cand_count, 1);
             if ((ee = ensure(c->psorted, c->cand_cap * sizeof(uint2))) != cudaSuccess) return ee;
-            if ((ee = ensure(c->pbuf, rescore_panel_buf_bytes(R.n, S.n, R.d))) != cudaSuccess) return ee;
+            if ((ee = ensure(c->pbuf, rescore_panel_buf_bytes(rows_a, rows_b, R.d, hint))) != cudaSuccess) return ee;
             ee = launch_rescore_panels((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, (uint2 *)c->psorted.p,
-                                       c->pbuf.p, R.n, S.n, nA, xR, ldR, xS, ldS, R.d, idsA, idsB, (const float *)sa.inv.p,
+                                       c->pbuf.p, rows_a, rows_b, hint, nA, xR, ldR, xS, ldS, R.d, idsA, idsB,
+                                       (const float *)sa.inv.p,
                                        (const float *)sb.inv.p, eps, c->fp64_band, *pairs_io,
                                        count_only ? 0 : *cap_io, &dm->pair_count, &dm->band_count,
                                        count_only ? 1 : 0, c->num_sms, c->stream, (uint2 *)c->band.p, c->cand_cap,
@@ -617,11 +623,12 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
                                  c->stream);
         return ee;
     };
-    // With the result buffer known, the re-score is launched before the candidate count is read back:
-    // one host synchronisation per call.  If the candidates overflowed their buffer, its pairs are
-    // discarded and the call continues as below.
+    // With the result buffer known, the emission-order re-score is launched before the candidate count is
+    // read back: one host synchronisation per call.  If the candidates overflowed their buffer, its pairs
+    // are discarded and the call continues as below.  The panel-ordered re-score is sized by the counts,
+    // so it follows their read-back.
     bool done = false;
-    if (*pairs_io != nullptr || count_only) {
+    if ((*pairs_io != nullptr || count_only) && !panels) {
         if ((e = rescore()) != cudaSuccess) return from_cuda(e);
         if ((e = read_misc()) != cudaSuccess) return from_cuda(e);
         if (hm.status) return status_of(hm.status);

@@ -278,11 +278,11 @@ cudaError_t launch_topk_select(const unsigned long long *seg, const unsigned *ro
                                const long long *nA_dev, int64_t nA_max, int kk, const uint32_t *idsR, ejoin_pair *out,
                                uint64_t out_cap, unsigned long long *missing, int num_sms, cudaStream_t st);
 // Workspace of the accurate tier's squared row norms (compensated dot products finished in FP64): per
-// row of R (nR rows) and of S (nS rows) a flag and a norm.  When a launcher gets one, the rows listed in
+// row of R (nR rows) and of S (nS rows) a claim word and a norm.  When a launcher gets one, the rows listed in
 // the band list have their norms computed once, and each listed candidate only its cross product; the
 // similarities are the same bit for bit.
 struct BandNorms {
-    unsigned char *flagR = nullptr, *flagS = nullptr;
+    unsigned *claimR = nullptr, *claimS = nullptr;  // contiguous: claimS = claimR + nR
     double *nrmR = nullptr, *nrmS = nullptr;
     int64_t nR = 0, nS = 0;
 };
@@ -305,13 +305,14 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
 // rescore_panel_rows(d) consecutive operand rows of R), and each panel's FP32 R rows are staged in shared
 // memory once, so only the S rows are gathered per candidate.  Needs d % 4 == 0, d <= 1024,
 // ldR % 4 == 0, ldS % 4 == 0 and 16-byte aligned R and S (cudaErrorInvalidValue otherwise); panel_buf
-// holds rescore_panel_buf_bytes(n_rows, n_rows_s, d) bytes, n_rows and n_rows_s upper bounds of the
-// operand rows of R (*nA_dev at run time) and of S.
+// holds rescore_panel_buf_bytes(n_rows, n_rows_s, d, cand_hint) bytes, n_rows and n_rows_s upper bounds of
+// the operand rows of R (*nA_dev at run time) and of S, cand_hint the number of candidates (0: unknown;
+// S blocks then split the panels by the L2 size only).
 int rescore_panel_rows(int d);
-size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d);
+size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d, uint64_t cand_hint);
 cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                                   uint2 *sorted, void *panel_buf, int64_t n_rows, int64_t n_rows_s,
-                                  const long long *nA_dev, const float *R, int64_t ldR, const float *S, int64_t ldS,
+                                  uint64_t cand_hint, const long long *nA_dev, const float *R, int64_t ldR, const float *S, int64_t ldS,
                                   int d, const uint32_t *idsR, const uint32_t *idsS, const float *invR,
                                   const float *invS, float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                                   unsigned long long *out_count, unsigned long long *band_count, int count_only,

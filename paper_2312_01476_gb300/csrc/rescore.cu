@@ -353,32 +353,34 @@ __global__ void __launch_bounds__(256) rescore_band_kernel(const uint2 *__restri
     }
 }
 
-// Accurate tier with per-row norms (BandNorms): flag the rows of the listed candidates, compute their
-// squared norms once (a warp per flagged row), then each entry's cross product only.
-__global__ void band_flag_kernel(const uint2 *__restrict__ band_list, const unsigned long long *__restrict__ band_count,
-                                 uint64_t band_cap, unsigned char *flagR, unsigned char *flagS)
-{
-    uint64_t n = *band_count;
-    if (n > band_cap) n = band_cap;
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
-        const uint2 e = band_list[k];
-        flagR[e.x] = 1;
-        flagS[e.y] = 1;
-    }
-}
-
+// Accurate tier with per-row norms (BandNorms): the squared norms of the listed candidates' rows once, then
+// each entry's cross product only.
+// The squared norms of the rows the band list names, one warp per entry and side: the first warp to reach
+// a row claims it (flag 0 -> 1, the flags cleared before the list is written) and computes its norm, so the
+// work follows the list, not the relations' sizes.
 template <bool VEC>
-__global__ void __launch_bounds__(256) band_norm_kernel(const float *__restrict__ X, int64_t ld, int d, int64_t n,
-                                                        const unsigned char *__restrict__ flag, double *nrm)
+__global__ void __launch_bounds__(256) band_norm_kernel(const uint2 *__restrict__ band_list,
+                                                        const unsigned long long *__restrict__ band_count,
+                                                        uint64_t band_cap, const float *__restrict__ R, int64_t ldR,
+                                                        const float *__restrict__ S, int64_t ldS, int d,
+                                                        unsigned *claimR, unsigned *claimS, double *nrmR, double *nrmS)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w0; r < n; r += nw) {
-        if (!flag[r]) continue;  // warp-uniform
-        const float *x = X + r * ld;
+    uint64_t n = *band_count;
+    if (n > band_cap) n = band_cap;
+    const uint64_t w0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t k = w0; k < 2 * n; k += nw) {
+        const bool side_s = k >= n;
+        const uint2 e = band_list[side_s ? k - n : k];
+        const uint32_t row = side_s ? e.y : e.x;
+        unsigned won = 0;
+        if (lane == 0) won = atomicExch(side_s ? claimS + row : claimR + row, 1u) == 0u;
+        won = __shfl_sync(0xffffffffu, won, 0);
+        if (!won) continue;  // warp-uniform
+        const float *x = side_s ? S + (int64_t)row * ldS : R + (int64_t)row * ldR;
         const double v = accurate_dot<VEC>(x, x, d, lane);
-        if (lane == 0) nrm[r] = v;
+        if (lane == 0) (side_s ? nrmS : nrmR)[row] = v;
     }
 }
 
@@ -647,19 +649,16 @@ static cudaError_t launch_band_tier(const uint2 *band_list, const unsigned long 
     const unsigned gb = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((band_cap + 255) / 256, (uint64_t)num_sms * 8));
     if (bn) {
-        cudaError_t e = cudaMemsetAsync(bn->flagR, 0, (size_t)bn->nR, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(bn->flagS, 0, (size_t)bn->nS, st);
+        cudaError_t e = cudaMemsetAsync(bn->claimR, 0, (size_t)(bn->nR + bn->nS) * 4, st);
         if (e != cudaSuccess) return e;
-        band_flag_kernel<<<gb, 256, 0, st>>>(band_list, band_count, band_cap, bn->flagR, bn->flagS);
-        const unsigned gr = (unsigned)std::max<int64_t>(1, std::min<int64_t>((bn->nR + 7) / 8, (int64_t)num_sms * 16));
-        const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((bn->nS + 7) / 8, (int64_t)num_sms * 16));
-        if (aligned) {
-            band_norm_kernel<true><<<gr, 256, 0, st>>>(R, ldR, d, bn->nR, bn->flagR, bn->nrmR);
-            band_norm_kernel<true><<<gs, 256, 0, st>>>(S, ldS, d, bn->nS, bn->flagS, bn->nrmS);
-        } else {
-            band_norm_kernel<false><<<gr, 256, 0, st>>>(R, ldR, d, bn->nR, bn->flagR, bn->nrmR);
-            band_norm_kernel<false><<<gs, 256, 0, st>>>(S, ldS, d, bn->nS, bn->flagS, bn->nrmS);
-        }
+        const unsigned gn = (unsigned)std::max<uint64_t>(
+            1, std::min<uint64_t>((2 * band_cap + 7) / 8, (uint64_t)num_sms * 16));
+        if (aligned)
+            band_norm_kernel<true><<<gn, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d, bn->claimR,
+                                                       bn->claimS, bn->nrmR, bn->nrmS);
+        else
+            band_norm_kernel<false><<<gn, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d,
+                                                        bn->claimR, bn->claimS, bn->nrmR, bn->nrmS);
 #define EJ_BANDN(M, V)                                                                                            \
     rescore_band_norms_kernel<M, V><<<gb, 256, 0, st>>>(band_list, band_count, band_cap, R, ldR, S, ldS, d,        \
                                                        bn->nrmR, bn->nrmS, eps, out, out_cap, out_count, count_only)
@@ -749,11 +748,15 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
 // dense bucket does not serialise on one CTA.
 namespace {
 constexpr int PANEL_CHUNK = 2048;
-constexpr int PANEL_SMEM_MAX = 49152;  // staged R rows per CTA (three CTAs per SM with the sorted chunk and staging)
 constexpr int PANEL_MAX_ROWS = 128;
-constexpr int PANEL_CTAS = 3;
+constexpr int PANEL_CTAS = 3;    // CTAs per SM for rows of up to 512 values, 2 above
+constexpr int SMAJ_BINS = 1024;  // a chunk whose S rows span fewer positions is processed S row by S row
+// Shared memory for the staged R rows of a CTA: three CTAs per SM with the sorted chunk and the staging
+// area for rows of up to 512 values, two above.
+constexpr int panel_smem(int d) { return d > 512 ? 81920 : 40960; }
 constexpr int64_t PANEL_SBLOCK_BYTES = 32ll << 20;
 constexpr int64_t PANEL_MAX_BUCKETS = 1ll << 22;
+constexpr int64_t PANEL_MIN_BUCKET = 1024;
 constexpr int SCAN_THREADS = 1024;
 
 // Bucket geometry: bucket(c) = (c.y / sb) * np + (c.x >> shift), nb = nsb * np buckets.
@@ -770,11 +773,14 @@ int rescore_panel_rows(int d)
 {
     const int row_bytes = ((d + 3) / 4) * 16;
     int p = PANEL_MAX_ROWS;
-    while (p > 8 && p * row_bytes > PANEL_SMEM_MAX) p >>= 1;
-    return p * row_bytes <= PANEL_SMEM_MAX ? p : 0;
+    while (p > 8 && p * row_bytes > panel_smem(d)) p >>= 1;
+    return p * row_bytes <= panel_smem(d) ? p : 0;
 }
 
-static PanelGeom panel_geom(int64_t n_rows, int64_t n_rows_s, int d)
+// cand_hint (0: unknown): the number of candidates.  S blocks split a panel's candidates only while a bucket
+// keeps about PANEL_MIN_BUCKET of them: a sparse join is not fragmented into chunks of a few candidates, whose
+// fixed cost (staging, sorting, barriers) would exceed the L2 locality gained.
+static PanelGeom panel_geom(int64_t n_rows, int64_t n_rows_s, int d, uint64_t cand_hint)
 {
     PanelGeom g{};
     const int P = rescore_panel_rows(d);
@@ -784,6 +790,7 @@ static PanelGeom panel_geom(int64_t n_rows, int64_t n_rows_s, int d)
     const int64_t ns = std::max<int64_t>(1, n_rows_s);
     int64_t nsb = std::max<int64_t>(1, (ns * row_bytes + PANEL_SBLOCK_BYTES - 1) / PANEL_SBLOCK_BYTES);
     nsb = std::min<int64_t>(nsb, std::max<int64_t>(1, PANEL_MAX_BUCKETS / g.np));
+    if (cand_hint) nsb = std::min<int64_t>(nsb, std::max<int64_t>(1, (int64_t)(cand_hint / (uint64_t)(g.np * PANEL_MIN_BUCKET))));
     g.sb = (ns + nsb - 1) / nsb;
     g.nsb = (ns + g.sb - 1) / g.sb;
     g.nb = g.nsb * g.np;
@@ -1060,6 +1067,97 @@ __device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, flo
     __syncwarp();
 }
 
+// A chunk sorted by S row (rescore_panel_kernel, clustered candidates): each warp takes 16 consecutive
+// candidates at a time; the S row, gathered from global memory once per run of equal S rows, stays in
+// registers, and the R rows are read from the staged panel.  Lane partials, their order and the reduction
+// tree are those of rescore_mlp_kernel (fmaf(R element, S element, acc) over v, then the butterfly pairs),
+// so the similarities are bit-identical to the R-major path.
+template <int V, bool MIRROR>
+__device__ __forceinline__ void rescore_smajor_chunk(
+    const uint2 *cs, int len, long long row0, const float4 *panel, int d4, const float *__restrict__ S, int64_t ldS,
+    const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
+    const float *__restrict__ invS, float eps, float fp64_band, unsigned long long *band_count,
+    uint2 *__restrict__ band_list, uint64_t band_cap, ejoin_pair *stg, int &stg_n, unsigned long long *out_count,
+    ejoin_pair *__restrict__ out, uint64_t out_cap, int count_only, int lane, int warp)
+{
+    constexpr int C = V <= 2 ? 8 : 4;  // candidates reduced together
+    static_assert(RS_PER_WARP % C == 0, "candidates per warp step");
+    for (int gbase = warp * RS_PER_WARP; gbase < len; gbase += RS_PER_BLOCK) {
+        bool my_emit = false;
+        uint32_t my_i = 0, my_j = 0;
+        float my_sim = 0.f;
+        uint32_t gi = 0, gj = 0, lr = 0, sr = 0;
+        float sc = 0.f;
+        bool valid = false;
+        if (lane < RS_PER_WARP && gbase + lane < len) {
+            const uint2 c = cs[gbase + lane];
+            gi = idsR ? idsR[c.x] : c.x;
+            gj = idsS ? idsS[c.y] : c.y;
+            lr = (uint32_t)((long long)c.x - row0);
+            sr = c.y;
+            sc = invR[c.x] * invS[c.y];
+            valid = true;
+        }
+        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+        if (vmask) {  // warp-uniform
+            float4 b[V];
+            uint32_t cur = 0xffffffffu;  // S operand row held in b[]
+#pragma unroll
+            for (int v = 0; v < V; ++v) b[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+            for (int q0 = 0; q0 < RS_PER_WARP; q0 += C) {
+                if (!((vmask >> q0) & 1u)) break;  // warp-uniform
+                float part[C];
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const bool ok = (vmask >> (q0 + c)) & 1u;
+                    const uint32_t srow = __shfl_sync(0xffffffffu, sr, q0 + c);
+                    const uint32_t jj = __shfl_sync(0xffffffffu, gj, q0 + c);
+                    const uint32_t r = __shfl_sync(0xffffffffu, lr, q0 + c);
+                    if (ok && srow != cur) {  // warp-uniform; once per run of the sorted chunk
+                        cur = srow;
+                        const float4 *g = reinterpret_cast<const float4 *>(S + (int64_t)jj * ldS);
+#pragma unroll
+                        for (int v = 0; v < V; ++v) {
+                            const int x = lane + 32 * v;
+                            b[v] = x < d4 ? __ldg(g + x) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    }
+                    float acc = 0.f;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int x = lane + 32 * v;
+                        const float4 a = ok && x < d4 ? panel[r * (uint32_t)d4 + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+                        acc = fmaf(a.x, b[v].x, acc);
+                        acc = fmaf(a.y, b[v].y, acc);
+                        acc = fmaf(a.z, b[v].z, acc);
+                        acc = fmaf(a.w, b[v].w, acc);
+                    }
+                    part[c] = acc;
+                }
+                const float tot = transpose_sum<C>(part, lane);
+                const float mine = __shfl_sync(0xffffffffu, tot, ((lane - q0) & (C - 1)) * (32 / C));
+                if (lane >= q0 && lane < q0 + C && ((vmask >> lane) & 1u)) {
+                    float sim = mine * sc;
+                    sim = fminf(1.f, fmaxf(-1.f, sim));
+                    bool emit = sim >= eps;
+                    if (fabsf(sim - eps) < fp64_band) {
+                        // near eps: decided by the accurate tier
+                        const unsigned long long p = atomicAdd(band_count, 1ull);
+                        if (p < band_cap) band_list[p] = make_uint2(gi, gj);
+                        emit = false;
+                    }
+                    my_emit = emit;
+                    my_i = gi;
+                    my_j = gj;
+                    my_sim = sim;
+                }
+            }
+        }
+        warp_emit<MIRROR>(my_emit, my_i, my_j, my_sim, stg, stg_n, out_count, out, out_cap, count_only, lane, false);
+    }
+}
+
 // Re-score of bucket-sorted candidates (d % 4 == 0, 16-byte aligned rows, d <= 128 V).  Per chunk (at
 // most PANEL_CHUNK candidates of one bucket): the panel's R rows are staged in shared memory (cp.async)
 // while the chunk's candidates are counting-sorted by R row in shared memory.  Each warp then takes 16
@@ -1079,7 +1177,10 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
 {
     static_assert(RS_PER_WARP % C == 0 && (C & (C - 1)) == 0, "candidates per warp step");
     extern __shared__ float4 dyn[];
-    __shared__ int rcnt[PANEL_MAX_ROWS];
+    // counts of the chunk's counting sort: R rows, or (rows of more than 512 values) S positions
+    __shared__ int rcnt[V >= 6 ? SMAJ_BINS : PANEL_MAX_ROWS];
+    __shared__ unsigned char rused[PANEL_MAX_ROWS];  // the panel rows the chunk uses (only those are staged)
+    __shared__ unsigned s_range[2];  // the chunk's smallest and largest S operand row
     __shared__ ejoin_pair stg_all[RS_WARPS][PANEL_STG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ejoin_pair *stg = stg_all[warp];
@@ -1104,18 +1205,94 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
         const long long row0 = (long long)(lo % pg.np) << shift;  // the bucket's R panel
         const int rows = (int)min((long long)P, nA - row0);
         __syncthreads();  // the previous chunk is done with the panel, the sorted chunk and the counts
+        // the span of the chunk's S rows: within SMAJ_BINS positions (clustered rows in sketch order), the
+        // chunk is sorted by S row and each S row is gathered once for all its candidates; otherwise by R row
+        // the chunk's candidates, read once into registers (PANEL_CHUNK / blockDim.x per thread)
+        constexpr int ITEMS = PANEL_CHUNK / (RS_WARPS * 32);
+        uint2 mine[ITEMS];
+#pragma unroll
+        for (int t = 0; t < ITEMS; ++t) {
+            const int k = threadIdx.x + t * (RS_WARPS * 32);
+            mine[t] = k < len ? sorted[k0 + k] : make_uint2(0u, 0u);
+        }
+        bool smajor = false;
+        unsigned s_lo = 0;
+        if constexpr (V >= 6) {
+            // rows of more than 512 values: when the chunk's S rows span fewer than SMAJ_BINS positions
+            // (clustered rows in sketch order) it is sorted by S row and each S row is gathered once for all
+            // its candidates (rows of up to 512 values keep their registers for the R-major path)
+            if (threadIdx.x == 0) {
+                s_range[0] = 0xffffffffu;
+                s_range[1] = 0u;
+            }
+            __syncthreads();
+            unsigned lo = 0xffffffffu, hi = 0u;
+#pragma unroll
+            for (int t = 0; t < ITEMS; ++t) {
+                if (threadIdx.x + t * (RS_WARPS * 32) < len) {
+                    lo = min(lo, mine[t].y);
+                    hi = max(hi, mine[t].y);
+                }
+            }
+            lo = __reduce_min_sync(0xffffffffu, lo);
+            hi = __reduce_max_sync(0xffffffffu, hi);
+            if (lane == 0) {
+                atomicMin(&s_range[0], lo);
+                atomicMax(&s_range[1], hi);
+            }
+            __syncthreads();
+            s_lo = s_range[0];
+            smajor = s_range[1] - s_lo < (unsigned)SMAJ_BINS;
+        }
+        // counting sort of the chunk; the R rows it uses are flagged and only those are staged (the copies
+        // are in flight during the scan and the scatter)
+        const int nbins = smajor ? (int)(s_range[1] - s_lo) + 1 : P;
+        for (int r = threadIdx.x; r < nbins; r += blockDim.x) rcnt[r] = 0;
+        for (int r = threadIdx.x; r < P; r += blockDim.x) rused[r] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int t = 0; t < ITEMS; ++t) {
+            if (threadIdx.x + t * (RS_WARPS * 32) < len) {
+                atomicAdd(&rcnt[smajor ? (int)(mine[t].y - s_lo) : (int)(mine[t].x - row0)], 1);
+                rused[mine[t].x - row0] = 1;
+            }
+        }
+        __syncthreads();
         for (int r = warp; r < rows; r += RS_WARPS) {
+            if (!rused[r]) continue;  // warp-uniform
             const long long o = row0 + r;
             const uint32_t src = idsR ? idsR[o] : (uint32_t)o;
             const float4 *g = reinterpret_cast<const float4 *>(R + (int64_t)src * ldR);
             for (int x = lane; x < d4; x += 32) cp_async16(panel + r * d4 + x, g + x);
         }
-        // counting sort of the chunk by R row (while the panel copies are in flight)
-        for (int r = threadIdx.x; r < P; r += blockDim.x) rcnt[r] = 0;
-        __syncthreads();
-        for (int k = threadIdx.x; k < len; k += blockDim.x) atomicAdd(&rcnt[sorted[k0 + k].x - row0], 1);
-        __syncthreads();
-        if (warp == 0) {
+        if (V >= 6 && smajor) {
+            // exclusive scan of up to SMAJ_BINS counts, SMAJ_BINS / blockDim.x per thread
+            constexpr int PER = V >= 6 ? SMAJ_BINS / (RS_WARPS * 32) : 1;
+            int v[PER], sum = 0;
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                const int r = threadIdx.x * PER + t;
+                v[t] = r < nbins ? rcnt[r] : 0;
+                sum += v[t];
+            }
+            int incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            __shared__ int wsum[RS_WARPS];
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            int run = incl - sum;
+            for (int w = 0; w < warp; ++w) run += wsum[w];
+#pragma unroll
+            for (int t = 0; t < PER; ++t) {
+                const int r = threadIdx.x * PER + t;
+                if (r < nbins) rcnt[r] = run;
+                run += v[t];
+            }
+        } else if (warp == 0) {
             // exclusive scan of the P <= 128 counts, 4 per lane
             int v[PANEL_MAX_ROWS / 32], s = 0;
 #pragma unroll
@@ -1139,12 +1316,20 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
             }
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < len; k += blockDim.x) {
-            const uint2 c = sorted[k0 + k];
-            cs[atomicAdd(&rcnt[c.x - row0], 1)] = c;
-        }
+#pragma unroll
+        for (int t = 0; t < ITEMS; ++t)
+            if (threadIdx.x + t * (RS_WARPS * 32) < len)
+                cs[atomicAdd(&rcnt[smajor ? (int)(mine[t].y - s_lo) : (int)(mine[t].x - row0)], 1)] = mine[t];
         cp_async_wait_all();
         __syncthreads();
+        if constexpr (V >= 6) {
+            if (smajor) {
+                rescore_smajor_chunk<V, MIRROR>(cs, len, row0, panel, d4, S, ldS, idsR, idsS, invR, invS, eps,
+                                                fp64_band, band_count, band_list, band_cap, stg, stg_n, out_count, out,
+                                                out_cap, count_only, lane, warp);
+                continue;
+            }
+        }
         // warps take the chunk's candidates 16 at a time, with no block-wide step
         for (int gbase = warp * RS_PER_WARP; gbase < len; gbase += RS_PER_BLOCK) {
             bool my_emit = false;
@@ -1236,10 +1421,10 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
     warp_emit<MIRROR>(false, 0u, 0u, 0.f, stg, stg_n, out_count, out, out_cap, count_only, lane, true);
 }
 
-size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d)
+size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d, uint64_t cand_hint)
 {
     if (rescore_panel_rows(d) == 0) return 0;
-    const PanelGeom g = panel_geom(n_rows, n_rows_s, d);
+    const PanelGeom g = panel_geom(n_rows, n_rows_s, d, cand_hint);
     const int64_t scan_blocks = (g.nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
     return (size_t)(4 * g.nb + 2 + 2 * scan_blocks + 2) * sizeof(unsigned long long);
 }
@@ -1262,7 +1447,7 @@ static cudaError_t launch_panel_kernel(unsigned grid, size_t smem, cudaStream_t 
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!((configured >> dev) & 1ull)) {
         e = cudaFuncSetAttribute(rescore_panel_kernel<V, C, M, CTAS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 PANEL_SMEM_MAX + PANEL_CHUNK * (int)sizeof(uint2));
+                                 panel_smem(CTAS == PANEL_CTAS ? 512 : 1024) + PANEL_CHUNK * (int)sizeof(uint2));
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
@@ -1274,7 +1459,7 @@ static cudaError_t launch_panel_kernel(unsigned grid, size_t smem, cudaStream_t 
 
 cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
                                   uint2 *sorted, void *panel_buf, int64_t n_rows, int64_t n_rows_s,
-                                  const long long *nA_dev, const float *R, int64_t ldR, const float *S, int64_t ldS,
+                                  uint64_t cand_hint, const long long *nA_dev, const float *R, int64_t ldR, const float *S, int64_t ldS,
                                   int d, const uint32_t *idsR, const uint32_t *idsS, const float *invR,
                                   const float *invS, float eps, float fp64_band, ejoin_pair *out, uint64_t out_cap,
                                   unsigned long long *out_count, unsigned long long *band_count, int count_only,
@@ -1287,7 +1472,7 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
                          (reinterpret_cast<uintptr_t>(R) % 16 == 0) && (reinterpret_cast<uintptr_t>(S) % 16 == 0);
     const int P = rescore_panel_rows(d);
     if (!aligned || d > 1024 || P == 0 || !sorted || !panel_buf) return cudaErrorInvalidValue;
-    const PanelGeom g = panel_geom(n_rows, n_rows_s, d);
+    const PanelGeom g = panel_geom(n_rows, n_rows_s, d, cand_hint);
     if (g.nb >= (int64_t)0xffffffffll) return cudaErrorInvalidValue;
     unsigned long long *cnt = static_cast<unsigned long long *>(panel_buf);
     unsigned long long *off = cnt + g.nb;        // nb + 1

@@ -803,6 +803,14 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
         release(radB);
         return from_cuda(e);
     }
+    struct EventGuard {
+        cudaEvent_t e = nullptr;
+        ~EventGuard()
+        {
+            if (e) cudaEventDestroy(e);
+        }
+    } ev_stats;
+    if (cudaEventCreate(&ev_stats.e) == cudaSuccess) cudaEventRecord(ev_stats.e, st);  // tile statistics done
     if (sk->list_cap == 0) sk->list_cap = std::min<uint64_t>((uint64_t)tA * tB, 1ull << 22);
     unsigned long long n_list = 0;
     // tile-pair bounds as a TF32 threshold contraction of augmented ball rows (prune.cu), the kept ball
@@ -911,9 +919,10 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
         const BandNorms *bnp = c->fp64_band > 0.f ? &bn : nullptr;
         if (aligned && !(c->flags & EJOIN_FLAG_GATHER_RESCORE)) {
             if ((e = ensure(c->psorted, c->cand_cap * sizeof(uint2))) != cudaSuccess) return from_cuda(e);
-            if ((e = ensure(c->pbuf, rescore_panel_buf_bytes(R.n, S.n, R.d))) != cudaSuccess) return from_cuda(e);
+            if ((e = ensure(c->pbuf, rescore_panel_buf_bytes(R.n, S.n, R.d, hm.cand_count))) != cudaSuccess)
+                return from_cuda(e);
             e = launch_rescore_panels((const uint2 *)c->cand.p, &dm->cand_count, c->cand_cap, (uint2 *)c->psorted.p,
-                                      c->pbuf.p, R.n, S.n, &dm->n_sel[0], R.x, R.ld, S.x, S.ld, R.d,
+                                      c->pbuf.p, R.n, S.n, hm.cand_count, &dm->n_sel[0], R.x, R.ld, S.x, S.ld, R.d,
                                       (const uint32_t *)pa.perm.p, (const uint32_t *)pb.perm.p, (const float *)pa.inv.p,
                                       (const float *)pb.inv.p, eps, c->fp64_band, out->d_pairs, out->capacity,
                                       &dm->pair_count, &dm->band_count, 0, c->num_sms, st, (uint2 *)c->band.p,
@@ -943,6 +952,11 @@ ejoin_status ejoin_threshold_pruned(ejoin_ctx *c, ejoin_sketch *sk, ejoin_rel R,
     P_.pairs = hm.pair_count;
     P_.ms_prepare = ms(0, 1);
     P_.ms_bound = ms(1, 2);
+    if (ev_stats.e) {
+        float x = 0.f;
+        cudaEventElapsedTime(&x, ev[1], ev_stats.e);
+        P_.ms_tile_stats = x;
+    }
     P_.ms_contract = ms(2, 3);
     P_.ms_rescore = ms(3, 4);
     P_.ms_total = ms(0, 4);

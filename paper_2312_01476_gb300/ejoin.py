@@ -85,7 +85,8 @@ class ejoin_prune_stats(ctypes.Structure):
                 ("anchors_a", ctypes.c_uint64), ("max_group_rows_a", ctypes.c_uint64),
                 ("ms_sketch_a", ctypes.c_float), ("ms_cover_a", ctypes.c_float), ("ms_assign_a", ctypes.c_float),
                 ("recall_est", ctypes.c_float), ("recall_sample_rows", ctypes.c_uint64),
-                ("recall_sample_matches", ctypes.c_uint64)]
+                ("recall_sample_matches", ctypes.c_uint64), ("ms_tile_stats", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
 
 
 class ejoin_sketch_train_cfg(ctypes.Structure):
