@@ -307,6 +307,7 @@ typedef struct ejoin_batch_stats {
     int32_t graph;        /* 1 if runs replay a CUDA graph */
     uint64_t candidate_capacity, pair_capacity;
     float band;
+    float ms_normalize, ms_contract, ms_rescore;  /* stages of one eager run timed when the plan was made */
 } ejoin_batch_stats;
 
 /* Plan a batch over the jobs' device inputs (the pointers are captured: the

@@ -36,6 +36,7 @@ struct ejoin_batch {
     int kind = 0;
     float band = 0.f;
     int group_m = 16;
+    float ms_normalize = 0.f, ms_contract = 0.f, ms_rescore = 0.f;  // stage split of one eager run at plan time
     uint32_t flags = 0;
     // device tables
     Buf tile_off, a_off, b_off, nA, nB, thr, eps, xR, ldR, xS, ldS, rowoffA, rowoffB;
@@ -62,11 +63,15 @@ cudaError_t upload(Buf &b, const std::vector<T> &v)
 }
 
 // Enqueue one run of the batch pipeline on stream st (eager or under capture).
-cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_only = false)
+// evs (optional, eager runs only): four events recorded before the normalisations, before the
+// contraction, before the re-score and after it.
+cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_only = false,
+                    cudaEvent_t *evs = nullptr)
 {
     ejoin_ctx *c = b->ctx;
     DevMisc *dm = (DevMisc *)b->misc.p;
     cudaError_t e;
+    if (evs) cudaEventRecord(evs[0], st);
     if (!contract_only) {
         if ((e = cudaMemsetAsync(dm, 0, sizeof(DevMisc), st)) != cudaSuccess) return e;
         if ((e = launch_normalize_batch(b->fmt, (const float *const *)b->xR.p, (const long long *)b->ldR.p,
@@ -82,6 +87,7 @@ cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_
     } else {
         if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     }
+    if (evs) cudaEventRecord(evs[1], st);
     BatchTables bt{(const long long *)b->tile_off.p, (const long long *)b->a_off.p, (const long long *)b->b_off.p,
                    (const int *)b->nA.p, (const int *)b->nB.p, (const float *)b->thr.p, b->n_jobs};
     if ((e = launch_sim_tc_batch(b->kind, &b->tmA, &b->tmB, (int)b->kp, bt, (const float *)b->scaleA.p,
@@ -89,13 +95,15 @@ cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_
                                  &dm->status, c->timeout, c->num_sms, group_m, st)) != cudaSuccess)
         return e;
     if (contract_only) return cudaSuccess;
+    if (evs) cudaEventRecord(evs[2], st);
     BatchRows br{(const float *const *)b->xR.p, (const long long *)b->ldR.p, (const float *const *)b->xS.p,
                  (const long long *)b->ldS.p, (const long long *)b->a_off.p, (const long long *)b->b_off.p,
                  (const float *)b->eps.p, b->n_jobs};
-    return launch_rescore_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, br, b->d,
-                                (const float *)b->invA.p, (const float *)b->invB.p, c->fp64_band,
-                                (BatchPair *)b->pairs.p, b->pair_cap, &dm->pair_count, &dm->band_count, b->aligned,
-                                c->num_sms, st);
+    e = launch_rescore_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, br, b->d,
+                             (const float *)b->invA.p, (const float *)b->invB.p, c->fp64_band, (BatchPair *)b->pairs.p,
+                             b->pair_cap, &dm->pair_count, &dm->band_count, b->aligned, c->num_sms, st);
+    if (evs) cudaEventRecord(evs[3], st);
+    return e;
 }
 
 ejoin_status read_misc(ejoin_batch *b, DevMisc &hm, cudaStream_t st)
@@ -327,6 +335,14 @@ ejoin_status ejoin_batch_create(ejoin_ctx *c, const ejoin_job *jobs, int32_t n_j
     if (flags & EJOIN_BATCH_AUTOTUNE) {
         if ((st = autotune(b)) != EJOIN_OK) return fail(st);
     }
+    // one eager run with events between the stages: the stage split reported by ejoin_batch_info
+    if (c->events) {
+        if ((e = enqueue(b, c->stream, b->group_m, false, c->ev)) != cudaSuccess) return fail(from_cuda(e));
+        if ((st = read_misc(b, hm, c->stream)) != EJOIN_OK) return fail(st);
+        cudaEventElapsedTime(&b->ms_normalize, c->ev[0], c->ev[1]);
+        cudaEventElapsedTime(&b->ms_contract, c->ev[1], c->ev[2]);
+        cudaEventElapsedTime(&b->ms_rescore, c->ev[2], c->ev[3]);
+    }
     if (flags & EJOIN_BATCH_GRAPH) {
         if ((e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return fail(from_cuda(e));
@@ -384,6 +400,9 @@ ejoin_status ejoin_batch_info(const ejoin_batch *b, ejoin_batch_stats *out)
     out->rows_r = b->rowsA;
     out->rows_s = b->rowsB;
     out->group_m = b->group_m;
+    out->ms_normalize = b->ms_normalize;
+    out->ms_contract = b->ms_contract;
+    out->ms_rescore = b->ms_rescore;
     out->graph = b->exec != nullptr;
     out->candidate_capacity = b->cand_cap;
     out->pair_capacity = b->pair_cap;

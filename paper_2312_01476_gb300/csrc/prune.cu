@@ -205,65 +205,85 @@ __global__ void cover_mark_kernel(const uint2 *__restrict__ cand, const unsigned
 // the balls small when the tile holds up to NB well-separated groups.  Ball = unit centroid + angular radius (largest
 // angle between the centroid and a member, plus a rounding margin); unused
 // balls get radius -1.
+// Balls of one tile (a block per tile of tile_rows <= 256 sketch rows): NB seeds by farthest-point sampling
+// (the first row, then the row least similar to the seeds so far, ties to the smaller row), every row joins
+// its most similar seed (ties to the earlier seed), and each ball is the unit centroid of its rows with the
+// angular radius that covers them (RADIUS_MARGIN added; -1: unused ball).  The tile's rows are staged in
+// shared memory (rows padded to SK + 1 floats, so that the lanes' rows fall in distinct banks) and every
+// warp takes part; the dot products are the per-row FMA chains over q in order.
+constexpr int TS_LD = SK + 1;
+
+__device__ __forceinline__ float row_dot(const float *x, const float *y)
+{
+    float dot = 0.f;
+#pragma unroll 16
+    for (int q = 0; q < SK; ++q) dot = fmaf(x[q], y[q], dot);
+    return dot;
+}
+
 __global__ void __launch_bounds__(256) tile_stats_kernel(const float *__restrict__ S, int64_t n, int tile_rows,
                                                          float *__restrict__ centroid, float *__restrict__ radius)
 {
+    extern __shared__ float xs[];  // [tile_rows][TS_LD]
     __shared__ float c[NB][SK];
     __shared__ int run_of[256];
     __shared__ float maxd[256];
     __shared__ int seeds[NB];
     __shared__ int cnt[NB];
+    __shared__ float wv[8];
+    __shared__ int wi[8];
     const int64_t r0 = (int64_t)blockIdx.x * tile_rows;
     int64_t r1 = r0 + tile_rows;
     if (r1 > n) r1 = n;
     const int rows = (int)(r1 - r0);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < rows * SK; e += blockDim.x) xs[(e / SK) * TS_LD + e % SK] = S[r0 * SK + e];
     for (int e = tid; e < NB * SK; e += blockDim.x) c[e / SK][e % SK] = 0.f;
     if (tid < NB) cnt[tid] = 0;
-    // balls: NB seeds by farthest-point sampling inside the tile (first row,
-    // then the row least similar to the seeds so far), each row joins its most
-    // similar seed
-    if (warp == 0) {
-        int seed = 0;
-        for (int j = 0; j < NB; ++j) {
-            if (lane == 0) seeds[j] = seed;
-            const float *y = S + (r0 + seed) * SK;
-            float bv = 3.f;
-            int bi = 0;
-            for (int r = lane; r < rows; r += 32) {
-                const float *x = S + (r0 + r) * SK;
-                float dot = 0.f;
-#pragma unroll 16
-                for (int q = 0; q < SK; ++q) dot = fmaf(x[q], y[q], dot);
-                const float m = j == 0 ? dot : fmaxf(maxd[r], dot);
-                maxd[r] = m;
-                if (m < bv) {
-                    bv = m;
-                    bi = r;
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-                if (ov < bv || (ov == bv && oi < bi)) {
-                    bv = ov;
-                    bi = oi;
-                }
-            }
-            seed = bi;
-        }
-    }
     __syncthreads();
+    // farthest-point seeds
+    int seed = 0;
+    for (int j = 0; j < NB; ++j) {
+        if (tid == 0) seeds[j] = seed;
+        float bv = 3.f;
+        int bi = 0x7fffffff;
+        if (tid < rows) {
+            const float dot = row_dot(xs + tid * TS_LD, xs + seed * TS_LD);
+            const float m = j == 0 ? dot : fmaxf(maxd[tid], dot);
+            maxd[tid] = m;
+            bv = m;
+            bi = tid;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov < bv || (ov == bv && oi < bi)) {
+                bv = ov;
+                bi = oi;
+            }
+        }
+        if (lane == 0) {
+            wv[warp] = bv;
+            wi[warp] = bi;
+        }
+        __syncthreads();
+        bv = wv[0];
+        bi = wi[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (wv[w] < bv || (wv[w] == bv && wi[w] < bi)) {
+                bv = wv[w];
+                bi = wi[w];
+            }
+        seed = bi;
+        __syncthreads();
+    }
     if (tid < rows) {
-        const float *x = S + (r0 + tid) * SK;
+        const float *x = xs + tid * TS_LD;
         float best = -3.f;
         int bb = 0;
         for (int j = 0; j < NB; ++j) {
-            const float *y = S + (r0 + seeds[j]) * SK;
-            float dot = 0.f;
-#pragma unroll 16
-            for (int q = 0; q < SK; ++q) dot = fmaf(x[q], y[q], dot);
+            const float dot = row_dot(x, xs + seeds[j] * TS_LD);
             if (dot > best) {
                 best = dot;
                 bb = j;
@@ -279,7 +299,7 @@ __global__ void __launch_bounds__(256) tile_stats_kernel(const float *__restrict
         int k = 0;
         for (int r = 0; r < rows; ++r)
             if (run_of[r] == bl) {
-                acc += S[(r0 + r) * SK + q];
+                acc += xs[r * TS_LD + q];
                 ++k;
             }
         c[bl][q] = acc;
@@ -302,7 +322,7 @@ __global__ void __launch_bounds__(256) tile_stats_kernel(const float *__restrict
             if (run_of[r] != warp) continue;
             float dot = 0.f;
 #pragma unroll 16
-            for (int q = 0; q < SK; ++q) dot = fmaf(c[warp][q], S[(r0 + r) * SK + q], dot);
+            for (int q = 0; q < SK; ++q) dot = fmaf(c[warp][q], xs[r * TS_LD + q], dot);
             mn = fminf(mn, dot);
         }
 #pragma unroll
@@ -523,7 +543,10 @@ cudaError_t launch_tile_stats(const float *S, int64_t n, int k, int tile_rows, f
     if (k != SK || tile_rows > 256) return cudaErrorInvalidValue;
     const int64_t tiles = (n + tile_rows - 1) / tile_rows;
     if (tiles <= 0) return cudaSuccess;
-    tile_stats_kernel<<<(unsigned)tiles, 256, 0, st>>>(S, n, tile_rows, centroid, radius);
+    const int smem = tile_rows * TS_LD * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(tile_stats_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 256 * TS_LD * 4);
+    if (e != cudaSuccess) return e;
+    tile_stats_kernel<<<(unsigned)tiles, 256, smem, st>>>(S, n, tile_rows, centroid, radius);
     return cudaGetLastError();
 }
 

@@ -381,7 +381,7 @@ __device__ __forceinline__ float fmax3(float a, float b, float c)
 template <int MODE>
 __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &bt, long long tiles_m,
                                                 long long tiles_n, long long nA, long long nB, float thr, int group_m,
-                                                long long col_stride = 1)
+                                                long long col_stride, int &job)
 {
     TileInfo ti;
     ti.diag = false;
@@ -405,12 +405,11 @@ __device__ __forceinline__ TileInfo decode_tile(long long t, const BatchTables &
         ti.limB = (int)min((long long)BN, nB - n * BN);
         ti.thr = thr;
     } else if constexpr (MODE == MODE_BATCH) {
-        int lo = 0, hi = bt.n_jobs;  // tile_off[lo] <= t < tile_off[hi]
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (__ldg(bt.tile_off + mid) <= t) lo = mid;
-            else hi = mid;
-        }
+        // the job holding tile t: a CTA visits its tiles in increasing order, so `job` (the previous tile's
+        // job, 0 at the start) only moves forward, one job table entry at a time
+        int lo = job;
+        while (lo + 1 < bt.n_jobs && __ldg(bt.tile_off + lo + 1) <= t) ++lo;
+        job = lo;
         const long long na = __ldg(bt.nA + lo), nb = __ldg(bt.nB + lo);
         tile_coords(t - __ldg(bt.tile_off + lo), (na + BM - 1) / BM, (nb + BN - 1) / BN, group_m, m, n);
         ti.rowA = __ldg(bt.a_off + lo) + m * BM;
@@ -514,9 +513,11 @@ __global__ void __launch_bounds__(threads_for(EW, MODE), 1)
             int stage = 0;
             uint32_t phase = 0;
             uint64_t issued = 0;
+            int job_p = 0;  // MODE_BATCH: job of the last decoded tile
             bool ok = true;
             for (long long t = blockIdx.x; t < total && ok; t += gridDim.x) {
-                const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m, col_stride);
+                const TileInfo ti =
+                    decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m, col_stride, job_p);
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!mbar_wait_bounded(empty_bar(stage), phase ^ 1u, timeout, abort_flag, status)) {
                         ok = false;
@@ -602,6 +603,7 @@ __global__ void __launch_bounds__(threads_for(EW, MODE), 1)
         if (MODE != MODE_FUSED && lane == 0) *stg_ctr = 0;
         __syncwarp();
         int stg_cnt = 0;
+        int job_e = 0;  // MODE_BATCH: job of the last decoded tile
         int tiles_since_flush = 0;
         unsigned long long counted = 0;
         int acc = 0;
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(threads_for(EW, MODE), 1)
         };
 
         for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-            const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m, col_stride);
+            const TileInfo ti = decode_tile<MODE>(t, bt, tiles_m, tiles_n, nA, nB, thr, group_m, col_stride, job_e);
             const float thr_t = ti.thr;
             // top-k modes: the row's threshold / running maximum, loaded before the accumulator wait so
             // that its latency hides behind the MMAs

@@ -70,7 +70,8 @@ class ejoin_batch_stats(ctypes.Structure):
     _fields_ = [("n_jobs", ctypes.c_int32), ("total_tiles", ctypes.c_int64), ("rows_r", ctypes.c_int64),
                 ("rows_s", ctypes.c_int64), ("group_m", ctypes.c_int32), ("graph", ctypes.c_int32),
                 ("candidate_capacity", ctypes.c_uint64), ("pair_capacity", ctypes.c_uint64),
-                ("band", ctypes.c_float)]
+                ("band", ctypes.c_float), ("ms_normalize", ctypes.c_float), ("ms_contract", ctypes.c_float),
+                ("ms_rescore", ctypes.c_float)]
 
 
 EJOIN_BATCH_GRAPH, EJOIN_BATCH_AUTOTUNE = 0x1, 0x2
