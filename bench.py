@@ -748,6 +748,7 @@ def run_batch(args):
         lat.append(a.elapsed_time(z))
     n_pairs = b.wait()
     clocks = sampler.stop()
+    launches_per_run = int(pkg.ejoin_last_stats(ctx)["launches"])
     logical = int((sizes[:, 0] * sizes[:, 1]).sum())
 
     # baselines: the same joins one ejoin_threshold call at a time (BF16), and the plain FP32
@@ -788,7 +789,7 @@ def run_batch(args):
                         "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
                         "frac": round(flop / float(np.mean(lat_s)) / 1e12 / pk["bf16_tflops"], 4),
                         "note": "whole batch (normalise + contraction + re-score) per replay"},
-           "gpu_launches": 4 * args.steps, "clocks": clocks, "baselines": baselines}
+           "gpu_launches": launches_per_run * args.steps, "clocks": clocks, "baselines": baselines}
     print(json.dumps(out), flush=True)
     b.close()
     ctx.close()

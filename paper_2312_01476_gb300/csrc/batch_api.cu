@@ -42,6 +42,9 @@ struct ejoin_batch {
     Buf tile_off, a_off, b_off, nA, nB, thr, eps, xR, ldR, xS, ldS, rowoffA, rowoffB;
     // operands and results
     Buf A, B, invA, invB, scaleA, scaleB, misc, cand, pairs;
+    // streaming re-score: the candidates sorted by A row, and its bucket tables
+    Buf sorted, sbuf;
+    bool stream = false;
     uint64_t cand_cap = 0, pair_cap = 0;
     int64_t rowsA = 0, rowsB = 0, total_tiles = 0;
     bool aligned = false;
@@ -99,9 +102,16 @@ cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_
     BatchRows br{(const float *const *)b->xR.p, (const long long *)b->ldR.p, (const float *const *)b->xS.p,
                  (const long long *)b->ldS.p, (const long long *)b->a_off.p, (const long long *)b->b_off.p,
                  (const float *)b->eps.p, b->n_jobs};
-    e = launch_rescore_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, br, b->d,
-                             (const float *)b->invA.p, (const float *)b->invB.p, c->fp64_band, (BatchPair *)b->pairs.p,
-                             b->pair_cap, &dm->pair_count, &dm->band_count, b->aligned, c->num_sms, st);
+    if (b->stream)
+        e = launch_rescore_stream_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, (uint2 *)b->sorted.p,
+                                        b->sbuf.p, b->rowsA, br, b->d, (const float *)b->invA.p,
+                                        (const float *)b->invB.p, c->fp64_band, (BatchPair *)b->pairs.p, b->pair_cap,
+                                        &dm->pair_count, &dm->band_count, c->num_sms, st);
+    else
+        e = launch_rescore_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, br, b->d,
+                                 (const float *)b->invA.p, (const float *)b->invB.p, c->fp64_band,
+                                 (BatchPair *)b->pairs.p, b->pair_cap, &dm->pair_count, &dm->band_count, b->aligned,
+                                 c->num_sms, st);
     if (evs) cudaEventRecord(evs[3], st);
     return e;
 }
@@ -217,7 +227,7 @@ void destroy_batch(ejoin_batch *b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (Buf *x : {&b->tile_off, &b->a_off, &b->b_off, &b->nA, &b->nB, &b->thr, &b->eps, &b->xR, &b->ldR, &b->xS,
                    &b->ldS, &b->rowoffA, &b->rowoffB, &b->A, &b->B, &b->invA, &b->invB, &b->scaleA, &b->scaleB,
-                   &b->misc, &b->cand, &b->pairs})
+                   &b->misc, &b->cand, &b->pairs, &b->sorted, &b->sbuf})
         release(*x);
     delete b;
 }
@@ -331,6 +341,14 @@ ejoin_status ejoin_batch_create(ejoin_ctx *c, const ejoin_job *jobs, int32_t n_j
     if (hm.cand_count > b->cand_cap) return fail(EJOIN_EOVERFLOW);
     b->pair_cap = std::max<uint64_t>(hm.cand_count, 1);
     if ((e = ensure(b->pairs, b->pair_cap * sizeof(BatchPair))) != cudaSuccess) return fail(from_cuda(e));
+    // the re-score streams the candidates in A-row order where the rows allow it (the sizing runs above
+    // gathered them in emission order)
+    if (aligned && d <= 1024 && sumA > 0 && !(c->flags & EJOIN_FLAG_GATHER_RESCORE)) {
+        if ((e = ensure(b->sorted, b->cand_cap * sizeof(uint2))) ||
+            (e = ensure(b->sbuf, rescore_stream_batch_buf_bytes(sumA))))
+            return fail(from_cuda(e));
+        b->stream = true;
+    }
 
     if (flags & EJOIN_BATCH_AUTOTUNE) {
         if ((st = autotune(b)) != EJOIN_OK) return fail(st);
@@ -353,7 +371,9 @@ ejoin_status ejoin_batch_create(ejoin_ctx *c, const ejoin_job *jobs, int32_t n_j
         if (e2 != cudaSuccess || e3 != cudaSuccess) return fail(from_cuda(e2 != cudaSuccess ? e2 : e3));
         if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return fail(from_cuda(e));
     }
-    b->launches_per_run = 4;  // two normalisations, contraction, re-score
+    // two normalisations, the contraction and the re-score (streaming path: row-to-job table, histogram,
+    // three scan phases, scatter and the re-score)
+    b->launches_per_run = b->stream ? 10 : 4;
     *out = b;
     return EJOIN_OK;
 }

@@ -1025,12 +1025,14 @@ __device__ __forceinline__ float transpose_sum(float (&p)[C], int lane)
 // staging area of PANEL_STG records and claims global space with one atomic per flush, so no block-wide
 // barrier is needed per step.  mirror: a pair (i, j), i != j, is written as (i, j) and (j, i).
 constexpr int PANEL_STG = 96;
-template <bool MIRROR>
-__device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, float sim, ejoin_pair *stg, int &stg_n,
-                                          unsigned long long *out_count, ejoin_pair *__restrict__ out,
-                                          uint64_t out_cap, int count_only, int lane, bool final_flush)
+__device__ __forceinline__ ejoin_pair swapped(const ejoin_pair &r) { return ejoin_pair{r.j, r.i, r.sim}; }
+__device__ __forceinline__ BatchPair swapped(const BatchPair &r) { return BatchPair{r.job, r.j, r.i, r.sim}; }
+template <bool MIRROR, typename Rec>
+__device__ __forceinline__ void warp_emit_rec(bool emit, const Rec &rec, Rec *stg, int &stg_n,
+                                              unsigned long long *out_count, Rec *__restrict__ out, uint64_t out_cap,
+                                              int count_only, int lane, bool final_flush)
 {
-    const int mine = emit ? ((MIRROR && i != j) ? 2 : 1) : 0;
+    const int mine = emit ? ((MIRROR && rec.i != rec.j) ? 2 : 1) : 0;
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -1050,8 +1052,8 @@ __device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, flo
                 if (base + (unsigned long long)x < out_cap) out[base + x] = stg[x];
             if (mine) {
                 const unsigned long long pos = base + (unsigned long long)(stg_n + incl - mine);
-                if (pos < out_cap) out[pos] = ejoin_pair{i, j, sim};
-                if (mine == 2 && pos + 1 < out_cap) out[pos + 1] = ejoin_pair{j, i, sim};
+                if (pos < out_cap) out[pos] = rec;
+                if (mine == 2 && pos + 1 < out_cap) out[pos + 1] = swapped(rec);
             }
         }
         stg_n = 0;
@@ -1060,11 +1062,20 @@ __device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, flo
     }
     if (mine && !count_only) {
         const int pos = stg_n + incl - mine;
-        stg[pos] = ejoin_pair{i, j, sim};
-        if (mine == 2) stg[pos + 1] = ejoin_pair{j, i, sim};
+        stg[pos] = rec;
+        if (mine == 2) stg[pos + 1] = swapped(rec);
     }
     stg_n += tot;
     __syncwarp();
+}
+
+template <bool MIRROR>
+__device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, float sim, ejoin_pair *stg, int &stg_n,
+                                          unsigned long long *out_count, ejoin_pair *__restrict__ out,
+                                          uint64_t out_cap, int count_only, int lane, bool final_flush)
+{
+    warp_emit_rec<MIRROR>(emit, ejoin_pair{i, j, sim}, stg, stg_n, out_count, out, out_cap, count_only, lane,
+                          final_flush);
 }
 
 // A chunk sorted by S row (rescore_panel_kernel, clustered candidates): each warp takes 16 consecutive
@@ -1430,7 +1441,7 @@ size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d, uint64_t
 }
 
 template <int V, int C, bool M, int CTAS = PANEL_CTAS>
-static cudaError_t launch_panel_kernel(unsigned grid, size_t smem, cudaStream_t st, const uint2 *sorted,
+static cudaError_t launch_panel_kernel(unsigned grid, int num_sms, size_t smem, cudaStream_t st, const uint2 *sorted,
                                        const unsigned long long *off, const unsigned long long *choff,
                                        const PanelGeom &pg, const long long *nA_dev, const float *R, int64_t ldR,
                                        const float *S, int64_t ldS, int d, const uint32_t *idsR,
@@ -1451,6 +1462,8 @@ static cudaError_t launch_panel_kernel(unsigned grid, size_t smem, cudaStream_t 
         if (e != cudaSuccess) return e;
         configured |= 1ull << dev;
     }
+    // persistent CTAs: no more than are resident at once (a later wave would start after the first finished)
+    grid = std::min<unsigned>(grid, (unsigned)(num_sms * CTAS));
     rescore_panel_kernel<V, C, M, CTAS><<<grid, RS_WARPS * 32, smem, st>>>(
         sorted, off, choff, pg, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap,
         out_count, band_count, count_only, band_list, band_cap);
@@ -1495,7 +1508,7 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
         (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(max_chunks, (uint64_t)num_sms * PANEL_CTAS));
     const size_t smem = (size_t)P * (size_t)(d / 4) * 16 + PANEL_CHUNK * sizeof(uint2);
 #define EJ_PANEL_ARGS                                                                                            \
-    grid, smem, st, sorted, off, choff, g, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, \
+    grid, num_sms, smem, st, sorted, off, choff, g, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, \
         out_cap, out_count, band_count, count_only, band_list, band_cap
 #define EJ_PANEL(M)                                                                            \
     if (d <= 128) e = launch_panel_kernel<1, 8, M>(EJ_PANEL_ARGS);                             \
@@ -1514,6 +1527,320 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
     if (e != cudaSuccess || fp64_band <= 0.f) return e;
     return launch_band_tier(band_list, band_count, band_cap, R, ldR, S, ldS, d, eps, out, out_cap, out_count,
                             count_only, true, mirror != 0, num_sms, st, bn);
+}
+
+// job of the first row of every panel of 2^shift rows: the last j with a_off[j] <= p 2^shift
+__global__ void __launch_bounds__(256) panel_job_kernel(const long long *__restrict__ a_off, int n_jobs, int shift,
+                                                        int64_t np, int *__restrict__ panel_job)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    const long long r = (long long)p << shift;
+    int lo = 0, hi = n_jobs;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(a_off + mid) <= r) lo = mid;
+        else hi = mid;
+    }
+    panel_job[p] = lo;
+}
+
+// Streaming batched re-score.  The candidates are counting-sorted by A row (one bucket per concatenated A
+// row), so each A row's candidates are contiguous; the A row then stays in registers for its whole run.
+// Every warp walks its own units of 32 consecutive sorted candidates with no block-wide barrier: the S row
+// of each candidate is copied into a per-warp shared-memory ring of NS slots (cp.async, NS - 1 rows in
+// flight while one is consumed), and the next unit's candidate, job and scale lookups are issued in
+// stages across the current unit's steps.  A slot holds 32 V float4; lanes past the row's end copy a
+// zero float4, and lanes with no candidate (the stream's tail) repeat a valid one, so the per-candidate
+// path has no predicate.  Lane partials, their order, the reduction tree, the clamp and the decision are
+// those of rescore_batch_kernel, so the records are identical.
+__device__ __align__(16) float4 g_zero4;  // zero-initialised: the source of the copies past a row's end
+
+template <int V, int C, int NS, bool RAGGED, int CTAS>
+__global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kernel(
+    const uint2 *__restrict__ sorted, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
+    const int *__restrict__ row_job, const BatchRows br, int d, const float *__restrict__ invA,
+    const float *__restrict__ invB, float fp64_band, BatchPair *__restrict__ out, uint64_t out_cap,
+    unsigned long long *out_count, unsigned long long *band_count)
+{
+    static_assert((C & (C - 1)) == 0 && 32 % C == 0 && NS >= 2 && NS <= 8, "step shape");
+    constexpr int STEPS = 32 / C;
+    // the first step that issues a copy for the next unit, and the stages of its lookups before it
+    constexpr int FIN = (33 - NS) / C;
+    constexpr int R2 = FIN / 3, R3 = (2 * FIN) / 3;
+    static_assert(FIN >= 2 && R2 >= 1 && R3 > R2 && FIN > R3, "lookup stages");
+    constexpr int SLOT = 32 * V;  // float4 per ring slot
+    extern __shared__ float4 dyn[];
+    __shared__ BatchPair stg_all[RS_WARPS][PANEL_STG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d4 = d >> 2;
+    float4 *ring = dyn + (size_t)warp * NS * SLOT;
+    BatchPair *stg = stg_all[warp];
+    int stg_n = 0;
+    uint64_t n = *cand_count;
+    if (n > cand_cap) n = cand_cap;
+    const uint64_t units = (n + 31) / 32;
+    const uint64_t W = (uint64_t)gridDim.x * RS_WARPS;
+    uint64_t u = (uint64_t)blockIdx.x * RS_WARPS + warp;
+    if (u >= units) return;  // warp-uniform; the kernel has no block-wide barrier
+
+    // this lane's candidate of the current unit (lanes past the end repeat the unit's first)
+    uint32_t x, job, gi, gj;
+    const float *sp;
+    float sc, ej;
+    bool ok;
+    {
+        const uint64_t k = u * 32 + lane;
+        ok = k < n;
+        const uint2 c = sorted[ok ? k : u * 32];
+        job = (uint32_t)__ldg(row_job + c.x);
+        const long long ao = __ldg(br.a_off + job), bo = __ldg(br.b_off + job);
+        x = c.x;
+        gi = (uint32_t)((long long)c.x - ao);
+        gj = (uint32_t)((long long)c.y - bo);
+        sp = br.S[job] + (int64_t)gj * br.ldS[job];
+        sc = invA[c.x] * invB[c.y];
+        ej = __ldg(br.eps + job);
+    }
+    const uint32_t ring_s = smem_u32(ring) + (uint32_t)lane * 16u;
+    auto issue = [&](const float *row, int slot) {
+        const float4 *g = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int e = lane + 32 * v;
+            const float4 *src = (!RAGGED || e < d4) ? g + e : &g_zero4;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ring_s + (uint32_t)((slot * SLOT + 32 * v) * 16)),
+                         "l"(src)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll
+    for (int q = 0; q < NS - 1; ++q)
+        issue(reinterpret_cast<const float *>(
+                  __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(sp), q)),
+              q);
+    int slot = 0;  // ring slot of the candidate being computed
+    uint32_t cur_row = 0xffffffffu;
+    float4 a[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) a[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (;;) {
+        const uint64_t un = u + W;
+        const bool has_next = un < units;
+        // the next unit's lookups (stages 0, R2, R3, FIN); with no next unit they resolve candidate 0
+        uint2 nc = make_uint2(0u, 0u);
+        bool nok = false;
+        uint32_t njob = 0;
+        float nia = 0.f, nib = 0.f, nej = 0.f;
+        long long nao = 0, nbo = 0, nld = 0;
+        const float *nS = nullptr;
+        uint32_t nx = 0, ngi = 0, ngj = 0;
+        const float *nsp = nullptr;
+        float nsc = 0.f;
+        bool my_emit = false;
+        BatchPair my{};
+#pragma unroll 1
+        for (int j = 0; j < STEPS; ++j) {
+            if (j == 0) {
+                const uint64_t k = un * 32 + lane;
+                nok = has_next && k < n;
+                nc = sorted[nok ? k : (has_next ? un * 32 : 0ull)];
+            } else if (j == R2) {
+                njob = (uint32_t)__ldg(row_job + nc.x);
+                nia = invA[nc.x];
+                nib = invB[nc.y];
+            } else if (j == R3) {
+                nao = __ldg(br.a_off + njob);
+                nbo = __ldg(br.b_off + njob);
+                nS = br.S[njob];
+                nld = br.ldS[njob];
+                nej = __ldg(br.eps + njob);
+            } else if (j == FIN) {
+                nx = nc.x;
+                ngi = (uint32_t)((long long)nc.x - nao);
+                ngj = (uint32_t)((long long)nc.y - nbo);
+                nsp = nS + (int64_t)ngj * nld;
+                nsc = nia * nib;
+            }
+            float part[C];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const int q = j * C + c;
+                // copy the S row of candidate q + NS - 1 into the slot freed by candidate q - 1
+                const int qi = q + NS - 1;
+                const uintptr_t rp = qi < 32 ? reinterpret_cast<uintptr_t>(sp) : reinterpret_cast<uintptr_t>(nsp);
+                issue(reinterpret_cast<const float *>(__shfl_sync(0xffffffffu, (unsigned long long)rp, qi & 31)),
+                      slot == 0 ? NS - 1 : slot - 1);
+                asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+                __syncwarp();
+                const uint32_t xq = __shfl_sync(0xffffffffu, x, q);
+                if (xq != cur_row) {  // warp-uniform: the next A row's run starts
+                    cur_row = xq;
+                    const uint32_t jq = __shfl_sync(0xffffffffu, job, q);
+                    const uint32_t iq = __shfl_sync(0xffffffffu, gi, q);
+                    const float4 *ra = reinterpret_cast<const float4 *>(br.R[jq] + (int64_t)iq * br.ldR[jq]);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) {
+                        const int e = lane + 32 * v;
+                        a[v] = (!RAGGED || e < d4) ? __ldg(ra + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+                const float4 *b = ring + slot * SLOT + lane;
+                float acc = 0.f;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float4 bv = b[32 * v];
+                    acc = fmaf(a[v].x, bv.x, acc);
+                    acc = fmaf(a[v].y, bv.y, acc);
+                    acc = fmaf(a[v].z, bv.z, acc);
+                    acc = fmaf(a[v].w, bv.w, acc);
+                }
+                part[c] = acc;
+                __syncwarp();  // every lane is done with the slot before it is refilled
+                slot = slot + 1 == NS ? 0 : slot + 1;
+            }
+            const float tot = transpose_sum<C>(part, lane);
+            const int q0 = j * C;
+            const float dotv = __shfl_sync(0xffffffffu, tot, ((lane - q0) & (C - 1)) * (32 / C));
+            const bool decide = lane >= q0 && lane < q0 + C && ok;
+            float sim = fminf(1.f, fmaxf(-1.f, dotv * sc));
+            const bool near = decide && fabsf(sim - ej) < fp64_band;
+            bool emit = sim >= ej;
+            unsigned nm = __ballot_sync(0xffffffffu, near);
+            while (nm) {
+                const int q = __ffs(nm) - 1;
+                nm &= nm - 1u;
+                const uint32_t qj = __shfl_sync(0xffffffffu, job, q);
+                const uint32_t qi2 = __shfl_sync(0xffffffffu, gi, q);
+                const float *qs = reinterpret_cast<const float *>(
+                    __shfl_sync(0xffffffffu, (unsigned long long)reinterpret_cast<uintptr_t>(sp), q));
+                const double s64 = accurate_cosine(br.R[qj] + (int64_t)qi2 * br.ldR[qj], qs, d, lane);
+                if (lane == q) {
+                    emit = s64 >= (double)ej;
+                    sim = (float)s64;
+                }
+            }
+            if (near) atomicAdd(band_count, 1ull);
+            if (decide) {
+                my_emit = emit;
+                my = BatchPair{job, gi, gj, sim};
+            }
+        }
+        warp_emit_rec<false>(my_emit, my, stg, stg_n, out_count, out, out_cap, 0, lane, false);
+        if (!has_next) break;
+        u = un;
+        x = nx;
+        job = njob;
+        gi = ngi;
+        gj = ngj;
+        sp = nsp;
+        sc = nsc;
+        ej = nej;
+        ok = nok;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    warp_emit_rec<false>(false, BatchPair{}, stg, stg_n, out_count, out, out_cap, 0, lane, true);
+}
+
+static int64_t stream_scan_blocks(int64_t rows_a) { return (rows_a + SCAN_ITEMS - 1) / SCAN_ITEMS; }
+
+size_t rescore_stream_batch_buf_bytes(int64_t rows_a)
+{
+    const int64_t nb = std::max<int64_t>(1, rows_a);
+    return (size_t)(4 * nb + 2 + 2 * stream_scan_blocks(nb) + 2) * sizeof(unsigned long long) +
+           (size_t)nb * sizeof(int);
+}
+
+template <int V, int C, int NS, bool RAGGED, int CTAS>
+static cudaError_t launch_stream_kernel_r(int num_sms, cudaStream_t st, const uint2 *sorted,
+                                        const unsigned long long *cand_count, uint64_t cand_cap, const int *row_job,
+                                        const BatchRows &br, int d, const float *invA, const float *invB,
+                                        float fp64_band, BatchPair *out, uint64_t out_cap,
+                                        unsigned long long *out_count, unsigned long long *band_count)
+{
+    constexpr int MAX_SMEM = 98304;  // eight warps' rings at the widest rows of the instantiation
+    static unsigned long long configured = 0ull;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!((configured >> dev) & 1ull)) {
+        e = cudaFuncSetAttribute(rescore_stream_batch_kernel<V, C, NS, RAGGED, CTAS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, MAX_SMEM);
+        if (e != cudaSuccess) return e;
+        configured |= 1ull << dev;
+    }
+    const size_t smem = (size_t)RS_WARPS * NS * 32 * V * 16;
+    if (smem > (size_t)MAX_SMEM) return cudaErrorInvalidValue;
+    const uint64_t units = (cand_cap + 31) / 32;
+    const uint64_t blocks = (units + RS_WARPS - 1) / RS_WARPS;
+    const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)num_sms * CTAS));
+    rescore_stream_batch_kernel<V, C, NS, RAGGED, CTAS><<<grid, RS_WARPS * 32, smem, st>>>(
+        sorted, cand_count, cand_cap, row_job, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count);
+    return cudaGetLastError();
+}
+
+template <int V, int C, int NS, int CTAS = 2>
+static cudaError_t launch_stream_kernel(int num_sms, cudaStream_t st, const uint2 *sorted,
+                                        const unsigned long long *cand_count, uint64_t cand_cap, const int *row_job,
+                                        const BatchRows &br, int d, const float *invA, const float *invB,
+                                        float fp64_band, BatchPair *out, uint64_t out_cap,
+                                        unsigned long long *out_count, unsigned long long *band_count)
+{
+    // rows of exactly 32 V float4 need no zero fill
+    if (d == 128 * V)
+        return launch_stream_kernel_r<V, C, NS, false, CTAS>(num_sms, st, sorted, cand_count, cand_cap, row_job, br,
+                                                             d, invA, invB, fp64_band, out, out_cap, out_count,
+                                                             band_count);
+    return launch_stream_kernel_r<V, C, NS, true, CTAS>(num_sms, st, sorted, cand_count, cand_cap, row_job, br, d, invA,
+                                                        invB, fp64_band, out, out_cap, out_count, band_count);
+}
+
+cudaError_t launch_rescore_stream_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
+                                        uint2 *sorted, void *buf, int64_t rows_a, const BatchRows &br, int d,
+                                        const float *invA, const float *invB, float fp64_band, BatchPair *out,
+                                        uint64_t out_cap, unsigned long long *out_count,
+                                        unsigned long long *band_count, int num_sms, cudaStream_t st)
+{
+    if (cand_cap == 0) return cudaSuccess;
+    if (d % 4 != 0 || d > 1024 || !sorted || !buf || rows_a < 1) return cudaErrorInvalidValue;
+    // one bucket per concatenated A row
+    PanelGeom g{};
+    g.shift = 0;
+    g.np = rows_a;
+    g.sb = 1ll << 32;
+    g.nsb = 1;
+    g.nb = rows_a;
+    if (g.nb >= (int64_t)0xffffffffll) return cudaErrorInvalidValue;
+    const int64_t scan_blocks = stream_scan_blocks(g.nb);
+    unsigned long long *cnt = static_cast<unsigned long long *>(buf);
+    unsigned long long *off = cnt + g.nb;        // nb + 1
+    unsigned long long *cursor = off + g.nb + 1;  // nb
+    unsigned long long *choff = cursor + g.nb;    // nb + 1
+    unsigned long long *tot = choff + g.nb + 1;    // 2 * scan_blocks + 2
+    int *row_job = reinterpret_cast<int *>(tot + 2 * scan_blocks + 2);  // rows_a
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)g.nb * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    panel_job_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, st>>>(br.a_off, br.n_jobs, 0, g.np, row_job);
+    const unsigned gs = (unsigned)std::max<uint64_t>(
+        1, std::min<uint64_t>((cand_cap + 255) / 256, (uint64_t)num_sms * 8));
+    panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cnt);
+    panel_scan_reduce_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot);
+    panel_scan_top_kernel<<<1, SCAN_THREADS, 0, st>>>(tot, (int)scan_blocks);
+    panel_scan_down_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot, off, cursor, choff);
+    panel_scatter_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cursor, sorted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+#define EJ_SB_ARGS \
+    num_sms, st, sorted, cand_count, cand_cap, row_job, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count
+    if (d <= 128) return launch_stream_kernel<1, 8, 8>(EJ_SB_ARGS);
+    if (d <= 256) return launch_stream_kernel<2, 4, 8>(EJ_SB_ARGS);
+    if (d <= 384) return launch_stream_kernel<3, 4, 8>(EJ_SB_ARGS);
+    if (d <= 512) return launch_stream_kernel<4, 2, 6>(EJ_SB_ARGS);
+    if (d <= 768) return launch_stream_kernel<6, 2, 4>(EJ_SB_ARGS);
+    return launch_stream_kernel<8, 1, 3>(EJ_SB_ARGS);
+#undef EJ_SB_ARGS
 }
 
 }  // namespace ej

@@ -106,3 +106,44 @@ def test_batch_clustered_lognormal_small():
         job, gi, gj, gs = pkg.ejoin_batch(ctx, to_dev(jobs_np), graph=True)
     assert len(job) > 1000
     check_batch(jobs_np, job, gi.view(np.uint32), gj.view(np.uint32), gs)
+
+
+def records(ctx_kw, jobs_dev, flags=0):
+    with pkg.Ctx(device=0, flags=flags, **ctx_kw) as ctx:
+        job, gi, gj, gs = pkg.ejoin_batch(ctx, jobs_dev, graph=True)
+        st = pkg.ejoin_last_stats(ctx)
+    key = (job.astype(np.int64) << 42) | (gi.view(np.uint32).astype(np.int64) << 21) | gj.view(np.uint32)
+    o = np.argsort(key)
+    return key[o], gs[o].view(np.uint32), st
+
+
+# row widths of every streaming instantiation (V = 1, 2, 3, 4, 6, 8 float4 per lane), with rows that fill
+# the lanes exactly (128, 256, 384, 512, 768, 1024) and ragged ones (96, 200, 500)
+@pytest.mark.parametrize("d", [96, 128, 200, 256, 384, 500, 512, 768, 1024])
+def test_batch_stream_rescore_equals_gather(d):
+    # tiny and empty jobs between larger ones, a job with long runs of candidates per A row, units of 32
+    # candidates that cross job boundaries, planted near pairs
+    sizes = [(3, 50), (0, 40), (1, 1), (0, 0), (70, 90), (2, 300), (0, 5), (1500, 1200), (5, 0), (130, 260), (7, 7)]
+    jobs_np = make_jobs(11, sizes, d, 0.5 / np.sqrt(d), 1.5 / np.sqrt(d))  # 7 % to 31 % of the pairs
+    jobs_dev = to_dev(jobs_np)
+    kp, sp, st_p = records({"prec": "bf16"}, jobs_dev)
+    kg, sg, st_g = records({"prec": "bf16"}, jobs_dev, pkg.EJOIN_FLAG_GATHER_RESCORE)
+    assert len(kp) > 20000
+    assert np.array_equal(kp, kg)
+    assert np.array_equal(sp, sg)
+    assert st_p["launches"] > st_g["launches"]  # the streaming path ran (its sort kernels)
+    job = (kp >> 42).astype(np.int64)
+    gi = ((kp >> 21) & ((1 << 21) - 1)).astype(np.uint32)
+    gj = (kp & ((1 << 21) - 1)).astype(np.uint32)
+    check_batch(jobs_np, job, gi, gj, sp.view(np.float32))
+
+
+def test_batch_stream_rescore_accurate_tier():
+    # a wide FP64 band sends many candidates through the accurate tier of both paths
+    jobs_np = make_jobs(12, [(400, 500), (90, 30), (1000, 700)], 128, 0.05, 0.12)
+    jobs_dev = to_dev(jobs_np)
+    kw = {"prec": "bf16", "fp64_band": 0.05}
+    kp, sp, st_p = records(kw, jobs_dev)
+    kg, sg, st_g = records(kw, jobs_dev, pkg.EJOIN_FLAG_GATHER_RESCORE)
+    assert st_p["fp64_rescored"] > 1000 and st_p["fp64_rescored"] == st_g["fp64_rescored"]
+    assert np.array_equal(kp, kg) and np.array_equal(sp, sg)
