@@ -42,9 +42,11 @@ struct ejoin_batch {
     Buf tile_off, a_off, b_off, nA, nB, thr, eps, xR, ldR, xS, ldS, rowoffA, rowoffB;
     // operands and results
     Buf A, B, invA, invB, scaleA, scaleB, misc, cand, pairs;
-    // streaming re-score: the candidates sorted by A row, and its bucket tables
-    Buf sorted, sbuf;
+    // streaming re-score: the candidates sorted by (job, S block, A row), its bucket tables, the first bucket
+    // of every job and the S block height
+    Buf sorted, sbuf, bbase;
     bool stream = false;
+    int64_t n_buckets = 0, sblock_rows = 0;
     uint64_t cand_cap = 0, pair_cap = 0;
     int64_t rowsA = 0, rowsB = 0, total_tiles = 0;
     bool aligned = false;
@@ -56,6 +58,8 @@ struct ejoin_batch {
 };
 
 namespace {
+
+constexpr int64_t STREAM_SBLOCK_BYTES = 32ll << 20;
 
 template <typename T>
 cudaError_t upload(Buf &b, const std::vector<T> &v)
@@ -104,7 +108,8 @@ cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_
                  (const float *)b->eps.p, b->n_jobs};
     if (b->stream)
         e = launch_rescore_stream_batch((const uint2 *)b->cand.p, &dm->cand_count, b->cand_cap, (uint2 *)b->sorted.p,
-                                        b->sbuf.p, b->rowsA, br, b->d, (const float *)b->invA.p,
+                                        b->sbuf.p, b->rowsA, br, (const long long *)b->bbase.p, (const int *)b->nA.p,
+                                        b->n_buckets, b->sblock_rows, b->d, (const float *)b->invA.p,
                                         (const float *)b->invB.p, c->fp64_band, (BatchPair *)b->pairs.p, b->pair_cap,
                                         &dm->pair_count, &dm->band_count, c->num_sms, st);
     else
@@ -227,7 +232,7 @@ void destroy_batch(ejoin_batch *b)
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     for (Buf *x : {&b->tile_off, &b->a_off, &b->b_off, &b->nA, &b->nB, &b->thr, &b->eps, &b->xR, &b->ldR, &b->xS,
                    &b->ldS, &b->rowoffA, &b->rowoffB, &b->A, &b->B, &b->invA, &b->invB, &b->scaleA, &b->scaleB,
-                   &b->misc, &b->cand, &b->pairs, &b->sorted, &b->sbuf})
+                   &b->misc, &b->cand, &b->pairs, &b->sorted, &b->sbuf, &b->bbase})
         release(*x);
     delete b;
 }
@@ -344,10 +349,24 @@ ejoin_status ejoin_batch_create(ejoin_ctx *c, const ejoin_job *jobs, int32_t n_j
     // the re-score streams the candidates in A-row order where the rows allow it (the sizing runs above
     // gathered them in emission order)
     if (aligned && d <= 1024 && sumA > 0 && !(c->flags & EJOIN_FLAG_GATHER_RESCORE)) {
-        if ((e = ensure(b->sorted, b->cand_cap * sizeof(uint2))) ||
-            (e = ensure(b->sbuf, rescore_stream_batch_buf_bytes(sumA))))
-            return fail(from_cuda(e));
-        b->stream = true;
+        // S blocks of about STREAM_SBLOCK_BYTES: the S rows a wave of warps reads stay in L2 while the job's
+        // A rows stream past them (a job's A rows are read once per S block)
+        b->sblock_rows = std::max<int64_t>(1, STREAM_SBLOCK_BYTES / ((int64_t)((d + 3) / 4) * 16));
+        std::vector<long long> bbase(n_jobs + 1);
+        long long nbk = 0;
+        for (int j = 0; j < n_jobs; ++j) {
+            bbase[j] = nbk;
+            const long long nsb = std::max<long long>(1, (nB[j] + b->sblock_rows - 1) / b->sblock_rows);
+            nbk += (long long)nA[j] * nsb;
+        }
+        bbase[n_jobs] = nbk;
+        b->n_buckets = nbk;
+        if (nbk > 0 && nbk < 0xffffffffll) {
+            if ((e = upload(b->bbase, bbase)) || (e = ensure(b->sorted, b->cand_cap * sizeof(uint2))) ||
+                (e = ensure(b->sbuf, rescore_stream_batch_buf_bytes(nbk, sumA))))
+                return fail(from_cuda(e));
+            b->stream = true;
+        }
     }
 
     if (flags & EJOIN_BATCH_AUTOTUNE) {

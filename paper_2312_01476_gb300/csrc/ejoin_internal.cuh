@@ -221,14 +221,16 @@ cudaError_t launch_sim_tc_batch(int kind, const CUtensorMap *tmA, const CUtensor
 cudaError_t launch_score_pairs(const float *R, int64_t ldR, const float *S, int64_t ldS, int d, const uint32_t *pi,
                                const uint32_t *pj, const float *invR, const float *invS, int64_t n, float *out,
                                int num_sms, cudaStream_t st);
-// Streaming batched re-score (16-byte aligned rows, d % 4 == 0, d <= 1024): candidates counting-sorted by A
-// row into `sorted` (cand_cap entries), then re-scored by warps that keep the A row in registers and the S
-// rows in flight through a shared-memory ring; records and counts identical to launch_rescore_batch.
-// buf: rescore_stream_batch_buf_bytes(rows_a) bytes.
-size_t rescore_stream_batch_buf_bytes(int64_t rows_a);
+// Streaming batched re-score (16-byte aligned rows, d % 4 == 0, d <= 1024): candidates counting-sorted into
+// `sorted` (cand_cap entries) by job, S block of sblock_rows rows within the job and A row, then re-scored by
+// warps that keep the A row in registers and the S rows in flight through a shared-memory ring; records and
+// counts identical to launch_rescore_batch.  bbase[j]: first bucket of job j (n_jobs + 1 entries, the last
+// n_buckets), nA[j]: its A rows.  buf: rescore_stream_batch_buf_bytes(n_buckets, rows_a) bytes.
+size_t rescore_stream_batch_buf_bytes(int64_t n_buckets, int64_t rows_a);
 cudaError_t launch_rescore_stream_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
-                                        uint2 *sorted, void *buf, int64_t rows_a, const BatchRows &br, int d,
-                                        const float *invA, const float *invB, float fp64_band, BatchPair *out,
+                                        uint2 *sorted, void *buf, int64_t rows_a, const BatchRows &br,
+                                        const long long *bbase, const int *nA, int64_t n_buckets, int64_t sblock_rows,
+                                        int d, const float *invA, const float *invB, float fp64_band, BatchPair *out,
                                         uint64_t out_cap, unsigned long long *out_count,
                                         unsigned long long *band_count, int num_sms, cudaStream_t st);
 cudaError_t launch_rescore_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,

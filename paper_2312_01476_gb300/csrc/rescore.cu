@@ -802,10 +802,33 @@ __device__ __forceinline__ unsigned panel_bucket(uint2 c, int shift, int64_t np,
     return (unsigned)((int64_t)(c.y / (uint64_t)sb) * np + (int64_t)(c.x >> shift));
 }
 
+// Bucket of a candidate in a panel geometry (single join)
+struct GridBucket {
+    PanelGeom g;
+    __device__ __forceinline__ unsigned operator()(uint2 c) const { return panel_bucket(c, g.shift, g.np, g.sb); }
+};
+
+// Bucket of a batched candidate (a, b): its job j (the job of A row a), then the S block of b within the
+// job (sb rows each), then the A row: bbase[j] + ((b - b_off[j]) / sb) nA[j] + (a - a_off[j]).  Buckets
+// are ordered job by job, S block by S block, A row by A row.
+struct JobBlockBucket {
+    const int *row_job;
+    const long long *bbase, *a_off, *b_off;
+    const int *nA;
+    unsigned sb;
+    __device__ __forceinline__ unsigned operator()(uint2 c) const
+    {
+        const int j = __ldg(row_job + c.x);
+        const unsigned blk = (unsigned)((long long)c.y - __ldg(b_off + j)) / sb;
+        return (unsigned)(__ldg(bbase + j) + (long long)blk * __ldg(nA + j) + ((long long)c.x - __ldg(a_off + j)));
+    }
+};
+
 // cnt[bucket(c)] += 1 for every candidate (one atomic per group of lanes sharing a bucket)
+template <class Bucket>
 __global__ void __launch_bounds__(256) panel_hist_kernel(const uint2 *__restrict__ cand,
                                                          const unsigned long long *__restrict__ cand_count,
-                                                         uint64_t cand_cap, PanelGeom g, unsigned long long *cnt)
+                                                         uint64_t cand_cap, Bucket bucket, unsigned long long *cnt)
 {
     const int lane = threadIdx.x & 31;
     uint64_t n = *cand_count;
@@ -815,7 +838,7 @@ __global__ void __launch_bounds__(256) panel_hist_kernel(const uint2 *__restrict
     for (uint64_t base = w0 * 32; base < n; base += nw * 32) {
         const uint64_t k = base + lane;
         const bool ok = k < n;
-        const unsigned p = ok ? panel_bucket(cand[k], g.shift, g.np, g.sb) : 0xffffffffu;
+        const unsigned p = ok ? bucket(cand[k]) : 0xffffffffu;
         const unsigned peers = __match_any_sync(0xffffffffu, p);
         if (ok && lane == __ffs(peers) - 1) atomicAdd(cnt + p, (unsigned long long)__popc(peers));
     }
@@ -956,10 +979,11 @@ __global__ void __launch_bounds__(SCAN_THREADS) panel_scan_down_kernel(const uns
 }
 
 // sorted[cursor[b]++] = candidate, b its bucket (one atomic per group of lanes sharing a bucket)
+template <class Bucket>
 __global__ void __launch_bounds__(256) panel_scatter_kernel(const uint2 *__restrict__ cand,
                                                             const unsigned long long *__restrict__ cand_count,
-                                                            uint64_t cand_cap, PanelGeom g, unsigned long long *cursor,
-                                                            uint2 *__restrict__ sorted)
+                                                            uint64_t cand_cap, Bucket bucket,
+                                                            unsigned long long *cursor, uint2 *__restrict__ sorted)
 {
     const int lane = threadIdx.x & 31;
     uint64_t n = *cand_count;
@@ -970,7 +994,7 @@ __global__ void __launch_bounds__(256) panel_scatter_kernel(const uint2 *__restr
         const uint64_t k = base + lane;
         const bool ok = k < n;
         const uint2 c = ok ? cand[k] : make_uint2(0u, 0u);
-        const unsigned p = ok ? panel_bucket(c, g.shift, g.np, g.sb) : 0xffffffffu;
+        const unsigned p = ok ? bucket(c) : 0xffffffffu;
         const unsigned peers = __match_any_sync(0xffffffffu, p);
         const int leader = __ffs(peers) - 1;
         unsigned long long pos = 0;
@@ -1497,11 +1521,11 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
     if (e != cudaSuccess) return e;
     const unsigned gs = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((cand_cap + 255) / 256, (uint64_t)num_sms * 8));
-    panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cnt);
+    panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, GridBucket{g}, cnt);
     panel_scan_reduce_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot);
     panel_scan_top_kernel<<<1, SCAN_THREADS, 0, st>>>(tot, (int)scan_blocks);
     panel_scan_down_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot, off, cursor, choff);
-    panel_scatter_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cursor, sorted);
+    panel_scatter_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, GridBucket{g}, cursor, sorted);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const uint64_t max_chunks = (uint64_t)g.nb + cand_cap / PANEL_CHUNK + 1;
     const unsigned grid =
@@ -1561,7 +1585,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
     const uint2 *__restrict__ sorted, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
     const int *__restrict__ row_job, const BatchRows br, int d, const float *__restrict__ invA,
     const float *__restrict__ invB, float fp64_band, BatchPair *__restrict__ out, uint64_t out_cap,
-    unsigned long long *out_count, unsigned long long *band_count)
+    unsigned long long *out_count, unsigned long long *band_count, unsigned long long *unit_ticket)
 {
     static_assert((C & (C - 1)) == 0 && 32 % C == 0 && NS >= 2 && NS <= 8, "step shape");
     constexpr int STEPS = 32 / C;
@@ -1580,9 +1604,16 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
     uint64_t n = *cand_count;
     if (n > cand_cap) n = cand_cap;
     const uint64_t units = (n + 31) / 32;
-    const uint64_t W = (uint64_t)gridDim.x * RS_WARPS;
-    uint64_t u = (uint64_t)blockIdx.x * RS_WARPS + warp;
+    // units are handed out in order from one ticket counter, so the units in progress at any moment are
+    // consecutive (the S rows they read stay in L2); each warp holds the ticket of its next unit
+    auto ticket = [&]() {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(unit_ticket, 1ull);
+        return (uint64_t)__shfl_sync(0xffffffffu, t, 0);
+    };
+    uint64_t u = ticket();
     if (u >= units) return;  // warp-uniform; the kernel has no block-wide barrier
+    uint64_t un = ticket();
 
     // this lane's candidate of the current unit (lanes past the end repeat the unit's first)
     uint32_t x, job, gi, gj;
@@ -1627,8 +1658,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
     for (int v = 0; v < V; ++v) a[v] = make_float4(0.f, 0.f, 0.f, 0.f);
 
     for (;;) {
-        const uint64_t un = u + W;
         const bool has_next = un < units;
+        uint64_t unn = units;  // the ticket after the next unit (taken only while units remain)
         // the next unit's lookups (stages 0, R2, R3, FIN); with no next unit they resolve candidate 0
         uint2 nc = make_uint2(0u, 0u);
         bool nok = false;
@@ -1651,6 +1682,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
                 njob = (uint32_t)__ldg(row_job + nc.x);
                 nia = invA[nc.x];
                 nib = invB[nc.y];
+                if (has_next) unn = ticket();
             } else if (j == R3) {
                 nao = __ldg(br.a_off + njob);
                 nbo = __ldg(br.b_off + njob);
@@ -1731,6 +1763,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
         warp_emit_rec<false>(my_emit, my, stg, stg_n, out_count, out, out_cap, 0, lane, false);
         if (!has_next) break;
         u = un;
+        un = unn;
         x = nx;
         job = njob;
         gi = ngi;
@@ -1744,13 +1777,12 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
     warp_emit_rec<false>(false, BatchPair{}, stg, stg_n, out_count, out, out_cap, 0, lane, true);
 }
 
-static int64_t stream_scan_blocks(int64_t rows_a) { return (rows_a + SCAN_ITEMS - 1) / SCAN_ITEMS; }
-
-size_t rescore_stream_batch_buf_bytes(int64_t rows_a)
+size_t rescore_stream_batch_buf_bytes(int64_t n_buckets, int64_t rows_a)
 {
-    const int64_t nb = std::max<int64_t>(1, rows_a);
-    return (size_t)(4 * nb + 2 + 2 * stream_scan_blocks(nb) + 2) * sizeof(unsigned long long) +
-           (size_t)nb * sizeof(int);
+    const int64_t nb = std::max<int64_t>(1, n_buckets);
+    const int64_t scan_blocks = (nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    return (size_t)(4 * nb + 2 + 2 * scan_blocks + 2 + 2) * sizeof(unsigned long long) +
+           (size_t)std::max<int64_t>(1, rows_a) * sizeof(int);
 }
 
 template <int V, int C, int NS, bool RAGGED, int CTAS>
@@ -1758,7 +1790,8 @@ static cudaError_t launch_stream_kernel_r(int num_sms, cudaStream_t st, const ui
                                         const unsigned long long *cand_count, uint64_t cand_cap, const int *row_job,
                                         const BatchRows &br, int d, const float *invA, const float *invB,
                                         float fp64_band, BatchPair *out, uint64_t out_cap,
-                                        unsigned long long *out_count, unsigned long long *band_count)
+                                        unsigned long long *out_count, unsigned long long *band_count,
+                                        unsigned long long *unit_ticket)
 {
     constexpr int MAX_SMEM = 98304;  // eight warps' rings at the widest rows of the instantiation
     static unsigned long long configured = 0ull;
@@ -1778,7 +1811,8 @@ static cudaError_t launch_stream_kernel_r(int num_sms, cudaStream_t st, const ui
     const uint64_t blocks = (units + RS_WARPS - 1) / RS_WARPS;
     const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(blocks, (uint64_t)num_sms * CTAS));
     rescore_stream_batch_kernel<V, C, NS, RAGGED, CTAS><<<grid, RS_WARPS * 32, smem, st>>>(
-        sorted, cand_count, cand_cap, row_job, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count);
+        sorted, cand_count, cand_cap, row_job, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count,
+        unit_ticket);
     return cudaGetLastError();
 }
 
@@ -1787,53 +1821,56 @@ static cudaError_t launch_stream_kernel(int num_sms, cudaStream_t st, const uint
                                         const unsigned long long *cand_count, uint64_t cand_cap, const int *row_job,
                                         const BatchRows &br, int d, const float *invA, const float *invB,
                                         float fp64_band, BatchPair *out, uint64_t out_cap,
-                                        unsigned long long *out_count, unsigned long long *band_count)
+                                        unsigned long long *out_count, unsigned long long *band_count,
+                                        unsigned long long *unit_ticket)
 {
     // rows of exactly 32 V float4 need no zero fill
     if (d == 128 * V)
         return launch_stream_kernel_r<V, C, NS, false, CTAS>(num_sms, st, sorted, cand_count, cand_cap, row_job, br,
                                                              d, invA, invB, fp64_band, out, out_cap, out_count,
-                                                             band_count);
+                                                             band_count, unit_ticket);
     return launch_stream_kernel_r<V, C, NS, true, CTAS>(num_sms, st, sorted, cand_count, cand_cap, row_job, br, d, invA,
-                                                        invB, fp64_band, out, out_cap, out_count, band_count);
+                                                        invB, fp64_band, out, out_cap, out_count, band_count,
+                                                        unit_ticket);
 }
 
 cudaError_t launch_rescore_stream_batch(const uint2 *cand, const unsigned long long *cand_count, uint64_t cand_cap,
-                                        uint2 *sorted, void *buf, int64_t rows_a, const BatchRows &br, int d,
-                                        const float *invA, const float *invB, float fp64_band, BatchPair *out,
+                                        uint2 *sorted, void *buf, int64_t rows_a, const BatchRows &br,
+                                        const long long *bbase, const int *nA, int64_t n_buckets, int64_t sblock_rows,
+                                        int d, const float *invA, const float *invB, float fp64_band, BatchPair *out,
                                         uint64_t out_cap, unsigned long long *out_count,
                                         unsigned long long *band_count, int num_sms, cudaStream_t st)
 {
     if (cand_cap == 0) return cudaSuccess;
-    if (d % 4 != 0 || d > 1024 || !sorted || !buf || rows_a < 1) return cudaErrorInvalidValue;
-    // one bucket per concatenated A row
-    PanelGeom g{};
-    g.shift = 0;
-    g.np = rows_a;
-    g.sb = 1ll << 32;
-    g.nsb = 1;
-    g.nb = rows_a;
-    if (g.nb >= (int64_t)0xffffffffll) return cudaErrorInvalidValue;
-    const int64_t scan_blocks = stream_scan_blocks(g.nb);
+    if (d % 4 != 0 || d > 1024 || !sorted || !buf || rows_a < 1 || n_buckets < 1 || n_buckets >= 0xffffffffll ||
+        sblock_rows < 1 || sblock_rows > 0x7fffffffll)
+        return cudaErrorInvalidValue;
+    const int64_t nb = n_buckets;
+    const int64_t scan_blocks = (nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
     unsigned long long *cnt = static_cast<unsigned long long *>(buf);
-    unsigned long long *off = cnt + g.nb;        // nb + 1
-    unsigned long long *cursor = off + g.nb + 1;  // nb
-    unsigned long long *choff = cursor + g.nb;    // nb + 1
-    unsigned long long *tot = choff + g.nb + 1;    // 2 * scan_blocks + 2
-    int *row_job = reinterpret_cast<int *>(tot + 2 * scan_blocks + 2);  // rows_a
-    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)g.nb * sizeof(unsigned long long), st);
+    unsigned long long *off = cnt + nb;        // nb + 1
+    unsigned long long *cursor = off + nb + 1;  // nb
+    unsigned long long *choff = cursor + nb;    // nb + 1
+    unsigned long long *tot = choff + nb + 1;    // 2 * scan_blocks + 2
+    unsigned long long *unit_ticket = tot + 2 * scan_blocks + 2;           // 2 (one used)
+    int *row_job = reinterpret_cast<int *>(unit_ticket + 2);              // rows_a
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)nb * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
-    panel_job_kernel<<<(unsigned)((g.np + 255) / 256), 256, 0, st>>>(br.a_off, br.n_jobs, 0, g.np, row_job);
+    e = cudaMemsetAsync(unit_ticket, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    panel_job_kernel<<<(unsigned)((rows_a + 255) / 256), 256, 0, st>>>(br.a_off, br.n_jobs, 0, rows_a, row_job);
+    const JobBlockBucket bucket{row_job, bbase, br.a_off, br.b_off, nA, (unsigned)sblock_rows};
     const unsigned gs = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((cand_cap + 255) / 256, (uint64_t)num_sms * 8));
-    panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cnt);
-    panel_scan_reduce_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot);
+    panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, bucket, cnt);
+    panel_scan_reduce_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, nb, tot);
     panel_scan_top_kernel<<<1, SCAN_THREADS, 0, st>>>(tot, (int)scan_blocks);
-    panel_scan_down_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, g.nb, tot, off, cursor, choff);
-    panel_scatter_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, g, cursor, sorted);
+    panel_scan_down_kernel<<<(unsigned)scan_blocks, SCAN_THREADS, 0, st>>>(cnt, nb, tot, off, cursor, choff);
+    panel_scatter_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, bucket, cursor, sorted);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 #define EJ_SB_ARGS \
-    num_sms, st, sorted, cand_count, cand_cap, row_job, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count
+    num_sms, st, sorted, cand_count, cand_cap, row_job, br, d, invA, invB, fp64_band, out, out_cap, out_count, band_count, \
+        unit_ticket
     if (d <= 128) return launch_stream_kernel<1, 8, 8>(EJ_SB_ARGS);
     if (d <= 256) return launch_stream_kernel<2, 4, 8>(EJ_SB_ARGS);
     if (d <= 384) return launch_stream_kernel<3, 4, 8>(EJ_SB_ARGS);
