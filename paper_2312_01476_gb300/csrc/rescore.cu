@@ -1208,10 +1208,11 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
     const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
     const float *__restrict__ invS, float eps, float fp64_band, ejoin_pair *__restrict__ out, uint64_t out_cap,
     unsigned long long *out_count, unsigned long long *band_count, int count_only, uint2 *__restrict__ band_list,
-    uint64_t band_cap)
+    uint64_t band_cap, unsigned long long *chunk_ticket)
 {
     static_assert(RS_PER_WARP % C == 0 && (C & (C - 1)) == 0, "candidates per warp step");
     extern __shared__ float4 dyn[];
+    __shared__ unsigned long long s_tk[2];  // chunk tickets: this chunk's successor, double-buffered
     // counts of the chunk's counting sort: R rows, or (rows of more than 512 values) S positions
     __shared__ int rcnt[V >= 6 ? SMAJ_BINS : PANEL_MAX_ROWS];
     __shared__ unsigned char rused[PANEL_MAX_ROWS];  // the panel rows the chunk uses (only those are staged)
@@ -1227,7 +1228,13 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
     uint2 *cs = reinterpret_cast<uint2 *>(dyn + (size_t)P * (size_t)d4);  // the chunk, sorted by row
     const long long nA = *nA_dev;
     const unsigned long long n_chunks = choff[pg.nb];
-    for (unsigned long long ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+    // chunks are handed out in order from one ticket counter, so the chunks in progress at any moment are
+    // neighbours in bucket order (their S rows stay in L2); the successor's ticket is taken one chunk ahead
+    if (threadIdx.x == 0) s_tk[1] = atomicAdd(chunk_ticket, 1ull);
+    __syncthreads();
+    int par = 0;
+    for (unsigned long long ch = s_tk[1]; ch < n_chunks; ch = s_tk[par], par ^= 1) {
+        if (threadIdx.x == 0) s_tk[par] = atomicAdd(chunk_ticket, 1ull);  // read after this chunk's barriers
         // the chunk's bucket: the last b with choff[b] <= ch (it holds at least one chunk)
         int64_t lo = 0, hi = pg.nb;
         while (hi - lo > 1) {
@@ -1461,7 +1468,7 @@ size_t rescore_panel_buf_bytes(int64_t n_rows, int64_t n_rows_s, int d, uint64_t
     if (rescore_panel_rows(d) == 0) return 0;
     const PanelGeom g = panel_geom(n_rows, n_rows_s, d, cand_hint);
     const int64_t scan_blocks = (g.nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
-    return (size_t)(4 * g.nb + 2 + 2 * scan_blocks + 2) * sizeof(unsigned long long);
+    return (size_t)(4 * g.nb + 2 + 2 * scan_blocks + 2 + 2) * sizeof(unsigned long long);
 }
 
 template <int V, int C, bool M, int CTAS = PANEL_CTAS>
@@ -1472,7 +1479,7 @@ static cudaError_t launch_panel_kernel(unsigned grid, int num_sms, size_t smem, 
                                        const uint32_t *idsS, const float *invR, const float *invS, float eps,
                                        float fp64_band, ejoin_pair *out, uint64_t out_cap,
                                        unsigned long long *out_count, unsigned long long *band_count, int count_only,
-                                       uint2 *band_list, uint64_t band_cap)
+                                       uint2 *band_list, uint64_t band_cap, unsigned long long *chunk_ticket)
 {
     // the shared-memory opt-in, once per device and instantiation
     static unsigned long long configured = 0ull;
@@ -1490,7 +1497,7 @@ static cudaError_t launch_panel_kernel(unsigned grid, int num_sms, size_t smem, 
     grid = std::min<unsigned>(grid, (unsigned)(num_sms * CTAS));
     rescore_panel_kernel<V, C, M, CTAS><<<grid, RS_WARPS * 32, smem, st>>>(
         sorted, off, choff, pg, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, out_cap,
-        out_count, band_count, count_only, band_list, band_cap);
+        out_count, band_count, count_only, band_list, band_cap, chunk_ticket);
     return cudaGetLastError();
 }
 
@@ -1517,8 +1524,10 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
     unsigned long long *choff = cursor + g.nb;    // nb + 1
     unsigned long long *tot = choff + g.nb + 1;    // 2 * scan_blocks + 2
     const int64_t scan_blocks = (g.nb + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    unsigned long long *chunk_ticket = tot + 2 * scan_blocks + 2;  // 2 (one used)
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)g.nb * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(chunk_ticket, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     const unsigned gs = (unsigned)std::max<uint64_t>(
         1, std::min<uint64_t>((cand_cap + 255) / 256, (uint64_t)num_sms * 8));
     panel_hist_kernel<<<gs, 256, 0, st>>>(cand, cand_count, cand_cap, GridBucket{g}, cnt);
@@ -1533,7 +1542,7 @@ cudaError_t launch_rescore_panels(const uint2 *cand, const unsigned long long *c
     const size_t smem = (size_t)P * (size_t)(d / 4) * 16 + PANEL_CHUNK * sizeof(uint2);
 #define EJ_PANEL_ARGS                                                                                            \
     grid, num_sms, smem, st, sorted, off, choff, g, nA_dev, R, ldR, S, ldS, d, idsR, idsS, invR, invS, eps, fp64_band, out, \
-        out_cap, out_count, band_count, count_only, band_list, band_cap
+        out_cap, out_count, band_count, count_only, band_list, band_cap, chunk_ticket
 #define EJ_PANEL(M)                                                                            \
     if (d <= 128) e = launch_panel_kernel<1, 8, M>(EJ_PANEL_ARGS);                             \
     else if (d <= 256) e = launch_panel_kernel<2, 4, M>(EJ_PANEL_ARGS);                        \
