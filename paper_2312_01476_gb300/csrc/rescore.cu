@@ -1583,12 +1583,10 @@ __global__ void __launch_bounds__(256) panel_job_kernel(const long long *__restr
 // Every warp walks its own units of 32 consecutive sorted candidates with no block-wide barrier: the S row
 // of each candidate is copied into a per-warp shared-memory ring of NS slots (cp.async, NS - 1 rows in
 // flight while one is consumed), and the next unit's candidate, job and scale lookups are issued in
-// stages across the current unit's steps.  A slot holds 32 V float4; lanes past the row's end copy a
-// zero float4, and lanes with no candidate (the stream's tail) repeat a valid one, so the per-candidate
-// path has no predicate.  Lane partials, their order, the reduction tree, the clamp and the decision are
+// stages across the current unit's steps.  A slot holds 32 V float4 (positions past the row's end stay
+// zero), and lanes with no candidate (the stream's tail) repeat a valid one, so the per-candidate path
+// has no branch.  Lane partials, their order, the reduction tree, the clamp and the decision are
 // those of rescore_batch_kernel, so the records are identical.
-__device__ __align__(16) float4 g_zero4;  // zero-initialised: the source of the copies past a row's end
-
 template <int V, int C, int NS, bool RAGGED, int CTAS>
 __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kernel(
     const uint2 *__restrict__ sorted, const unsigned long long *__restrict__ cand_count, uint64_t cand_cap,
@@ -1643,15 +1641,22 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
         ej = __ldg(br.eps + job);
     }
     const uint32_t ring_s = smem_u32(ring) + (uint32_t)lane * 16u;
+    // ragged rows: the slot positions past the row's end are zeroed once and never copied to
+    if (RAGGED) {
+        for (int t = lane; t < NS * SLOT; t += 32)
+            if (t % SLOT >= d4) ring[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncwarp();
+    }
     auto issue = [&](const float *row, int slot) {
         const float4 *g = reinterpret_cast<const float4 *>(row);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const int e = lane + 32 * v;
-            const float4 *src = (!RAGGED || e < d4) ? g + e : &g_zero4;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ring_s + (uint32_t)((slot * SLOT + 32 * v) * 16)),
-                         "l"(src)
-                         : "memory");
+            if (!RAGGED || e < d4)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                 ring_s + (uint32_t)((slot * SLOT + 32 * v) * 16)),
+                             "l"(g + e)
+                             : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
