@@ -84,12 +84,12 @@ cudaError_t enqueue(ejoin_batch *b, cudaStream_t st, int group_m, bool contract_
         if ((e = launch_normalize_batch(b->fmt, (const float *const *)b->xR.p, (const long long *)b->ldR.p,
                                         (const long long *)b->rowoffA.p, b->n_jobs, b->rowsA, b->d, b->A.p,
                                         (int)b->kp, (float *)b->invA.p, (float *)b->scaleA.p, &dm->status,
-                                        c->num_sms, st)) != cudaSuccess)
+                                        c->num_sms, st, b->aligned)) != cudaSuccess)
             return e;
         if ((e = launch_normalize_batch(b->fmt, (const float *const *)b->xS.p, (const long long *)b->ldS.p,
                                         (const long long *)b->rowoffB.p, b->n_jobs, b->rowsB, b->d, b->B.p,
                                         (int)b->kp, (float *)b->invB.p, (float *)b->scaleB.p, &dm->status,
-                                        c->num_sms, st)) != cudaSuccess)
+                                        c->num_sms, st, b->aligned)) != cudaSuccess)
             return e;
     } else {
         if ((e = cudaMemsetAsync(&dm->cand_count, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;

@@ -164,7 +164,8 @@ cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, cons
                                          int64_t raw_ld = 0);
 cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
                                    int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
-                                   float *scale, unsigned *status, int num_sms, cudaStream_t st);
+                                   float *scale, unsigned *status, int num_sms, cudaStream_t st,
+                                   bool aligned = false);
 cudaError_t launch_sim_simt(const float *A, const float *B, int kp, const long long *nA, const long long *nB,
                             float thr, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
                             int count_only, int num_sms, cudaStream_t st);

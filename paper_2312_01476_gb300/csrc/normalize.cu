@@ -298,6 +298,123 @@ __global__ void __launch_bounds__(256) normalize_batch_kernel(const float *const
     }
 }
 
+// Batched form for 16-byte aligned rows with d % 4 == 0 and d <= 128 V: each warp takes RW consecutive rows
+// at a time and issues all their loads before reducing, so RW rows are in flight per warp; the job of a
+// row is found by one search per warp, then by moving forward (a warp's rows only increase).  Sums,
+// maxima, their order and the butterfly are those of normalize_row, so the outputs are bit-identical; a
+// row whose plain sum of squares over- or underflows is handed to normalize_row.
+template <int FMT, int V, int RW>
+__global__ void __launch_bounds__(256) normalize_batch_rows_kernel(const float *const *__restrict__ xs,
+                                                                   const long long *__restrict__ lds,
+                                                                   const long long *__restrict__ row_off, int n_rel,
+                                                                   int d, void *__restrict__ out, int kp,
+                                                                   float *__restrict__ inv_norm,
+                                                                   float *__restrict__ scale, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = row_off[n_rel];
+    const int d4 = d >> 2, groups = kp >> 2;
+    int job = -1;
+    for (int64_t g0 = warp_global * RW; g0 < total; g0 += n_warps * RW) {
+        if (job < 0) {
+            int lo = 0, hi = n_rel;  // row_off[lo] <= g0 < row_off[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(row_off + mid) <= g0) lo = mid;
+                else hi = mid;
+            }
+            job = lo;
+        }
+        float4 v[RW][V];
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int64_t g = g0 + r;
+            const float *src = nullptr;
+            if (g < total) {  // warp-uniform
+                while (__ldg(row_off + job + 1) <= g) ++job;
+                src = xs[job] + (g - __ldg(row_off + job)) * lds[job];
+            }
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int e = lane + 32 * q;
+                v[r][q] = (src && e < d4) ? __ldg(reinterpret_cast<const float4 *>(src) + e)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int64_t g = g0 + r;
+            if (g >= total) break;  // warp-uniform
+            float ss = 0.f, mx = 0.f;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                if (lane + 32 * q < d4) {
+                    ss = fmaf(v[r][q].x, v[r][q].x, ss);
+                    ss = fmaf(v[r][q].y, v[r][q].y, ss);
+                    ss = fmaf(v[r][q].z, v[r][q].z, ss);
+                    ss = fmaf(v[r][q].w, v[r][q].w, ss);
+                    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[r][q].x), fabsf(v[r][q].y)),
+                                         fmaxf(fabsf(v[r][q].z), fabsf(v[r][q].w))));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ss += __shfl_xor_sync(0xffffffffu, ss, o);
+                mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            const bool bad = isnan(ss) || !isfinite(mx);
+            if (!bad && !(isfinite(ss) && (ss >= 0x1p-100f || mx == 0.f))) {
+                // over- or underflow of the plain sum: the rescaled path
+                int jb = job;
+                while (__ldg(row_off + jb) > g) --jb;
+                normalize_row<FMT>(xs[jb] + (g - __ldg(row_off + jb)) * lds[jb], d, true, out, g, kp, kp, inv_norm,
+                                   scale, status, lane);
+                continue;
+            }
+            const float inv = bad ? 0.f : (ss > 0.f ? 1.0f / sqrtf(ss) : 0.f);
+            if (bad && lane == 0) atomicOr(status, ERR_NONFINITE);
+            float rsc = 1.f;
+            if (FMT == FMT_FP8) {
+                const float ymax = mx * inv;
+                const float sc = ymax > 0.f ? ymax / 448.f : 1.f;
+                rsc = 1.0f / sc;
+                if (lane == 0) scale[g] = sc;
+            }
+            if (lane == 0 && inv_norm) inv_norm[g] = inv;
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int e = lane + 32 * q;
+                if (e >= groups) break;
+                float4 y = e < d4 ? v[r][q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                y.x *= inv;
+                y.y *= inv;
+                y.z *= inv;
+                y.w *= inv;
+                const int k = 4 * e;
+                if (FMT == FMT_F32) {
+                    *reinterpret_cast<float4 *>(reinterpret_cast<float *>(out) + g * kp + k) = y;
+                } else if (FMT == FMT_BF16) {
+                    __nv_bfloat162 lo = __floats2bfloat162_rn(y.x, y.y);
+                    __nv_bfloat162 hi = __floats2bfloat162_rn(y.z, y.w);
+                    uint2 u;
+                    u.x = *reinterpret_cast<uint32_t *>(&lo);
+                    u.y = *reinterpret_cast<uint32_t *>(&hi);
+                    *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(out) + g * kp + k) = u;
+                } else {
+                    const __nv_fp8x2_storage_t lo =
+                        __nv_cvt_float2_to_fp8x2(make_float2(y.x * rsc, y.y * rsc), __NV_SATFINITE, __NV_E4M3);
+                    const __nv_fp8x2_storage_t hi =
+                        __nv_cvt_float2_to_fp8x2(make_float2(y.z * rsc, y.w * rsc), __NV_SATFINITE, __NV_E4M3);
+                    *reinterpret_cast<uint32_t *>(reinterpret_cast<__nv_fp8_storage_t *>(out) + g * kp + k) =
+                        (uint32_t)lo | ((uint32_t)hi << 16);
+                }
+            }
+        }
+    }
+}
+
 // e4m3 with a scale shared by each group of G consecutive output rows (the
 // rows of one column tile of the contraction): scale[c] = the largest per-row
 // scale max|y|/448 of c's group, so the epilogue can fold one column scale per
@@ -441,11 +558,62 @@ cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const u
     return cudaGetLastError();
 }
 
+template <int FMT, int V>
+static void launch_batch_rows(int64_t total_rows, const float *const *xs, const long long *lds,
+                              const long long *row_off, int n_rel, int d, void *out, int kp, float *inv_norm,
+                              float *scale, unsigned *status, int num_sms, cudaStream_t st)
+{
+    constexpr int RW = V <= 4 ? 4 : 2;
+    // one wave of resident blocks walks the rows (a second wave would start only after the first ended)
+    static int per_sm = 0;
+    if (per_sm == 0 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, normalize_batch_rows_kernel<FMT, V, RW>, 256, 0) !=
+            cudaSuccess)
+        per_sm = 1;
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (total_rows + 8 * RW - 1) / (8 * RW);
+    const int64_t cap = (int64_t)num_sms * per_sm;
+    if (blocks > cap) blocks = cap;
+    normalize_batch_rows_kernel<FMT, V, RW><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
+                                                                              inv_norm, scale, status);
+}
+
+template <int FMT>
+static cudaError_t launch_batch_rows_d(int64_t total_rows, const float *const *xs, const long long *lds,
+                                       const long long *row_off, int n_rel, int d, void *out, int kp,
+                                       float *inv_norm, float *scale, unsigned *status, int num_sms, cudaStream_t st)
+{
+#define EJ_NB_ARGS total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale, status, num_sms, st
+    if (d <= 128) launch_batch_rows<FMT, 1>(EJ_NB_ARGS);
+    else if (d <= 256) launch_batch_rows<FMT, 2>(EJ_NB_ARGS);
+    else if (d <= 384) launch_batch_rows<FMT, 3>(EJ_NB_ARGS);
+    else if (d <= 512) launch_batch_rows<FMT, 4>(EJ_NB_ARGS);
+    else if (d <= 768) launch_batch_rows<FMT, 6>(EJ_NB_ARGS);
+    else launch_batch_rows<FMT, 8>(EJ_NB_ARGS);
+#undef EJ_NB_ARGS
+    return cudaGetLastError();
+}
+
 cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
                                    int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
-                                   float *scale, unsigned *status, int num_sms, cudaStream_t st)
+                                   float *scale, unsigned *status, int num_sms, cudaStream_t st, bool aligned)
 {
     if (total_rows <= 0) return cudaSuccess;
+    if (aligned && d % 4 == 0 && d <= 1024 && kp <= 4 * 32 * ((d + 127) / 128)) {
+        // every relation's rows start on 16 bytes (checked by the host)
+        switch (fmt) {
+        case FMT_F32:
+            return launch_batch_rows_d<FMT_F32>(total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale,
+                                                status, num_sms, st);
+        case FMT_BF16:
+            return launch_batch_rows_d<FMT_BF16>(total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale,
+                                                 status, num_sms, st);
+        case FMT_FP8:
+            return launch_batch_rows_d<FMT_FP8>(total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale,
+                                                status, num_sms, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     int64_t blocks = (total_rows + 7) / 8;
     const int64_t cap = (int64_t)num_sms * 16;
     if (blocks > cap) blocks = cap;
