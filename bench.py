@@ -720,7 +720,7 @@ def run_batch(args):
     import ejoin_inputs as inputs
     import paper_2312_01476_gb300 as pkg
     d = 384
-    sizes, eps = inputs.c4_batch_sizes()
+    sizes, eps = inputs.c4_batch_sizes(n_jobs=args.batch_jobs)
     centres = torch.from_numpy(inputs.sphere_centres(1000, d, inputs.seed_for(4))).cuda()
     jobs = []
     for k, ((nr, ns), e) in enumerate(zip(sizes.tolist(), eps.tolist())):
@@ -779,7 +779,7 @@ def run_batch(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(float(np.mean(lat)), 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
            "data": "synthetic",
-           "config": {"workload": "batched joins: 512 jobs, lognormal sizes (median 20,000, sigma 1, clipped "
+           "config": {"workload": f"batched joins: {args.batch_jobs} jobs, lognormal sizes (median 20,000, sigma 1, clipped "
                                   "[1,000, 200,000]), d=384, clustered (1000 centres, 0.3 rad), eps ~ U[0.8, 0.95]",
                       "pairs_per_batch": logical, "result_pairs": int(n_pairs), "plan_seconds": round(plan_s, 2),
                       **{k: v for k, v in info.items()}},
@@ -924,6 +924,8 @@ def main():
                     choices=["c2", "c2-capture", "c1", "c3", "c3-capture", "c4", "c5", "top1", "top1-capture",
                              "top32", "top32-capture", "esel"])
     ap.add_argument("--esel-rows", type=int, default=10_000_000, help="rows of R for --workload esel")
+    ap.add_argument("--batch-jobs", type=int, default=512,
+                    help="jobs of --workload c4 (512: the configuration; fewer: a small case of the same shape)")
     ap.add_argument("--peaks", action="store_true", help="print cuBLAS BF16 / TF32 / FP8 throughput and exit")
     ap.add_argument("--sel-pct", type=int, default=100,
                     help="top-k workloads: percent of S kept by the predicate attr < sel-pct")
