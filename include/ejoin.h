@@ -84,10 +84,14 @@ typedef enum ejoin_prec {
 #define EJOIN_FLAG_HOST_COPY  0x10u /* ejoin_threshold_host: copy the inputs to the device whole even when
                                        the kernels could read them in place (see there) */
 #define EJOIN_FLAG_GATHER_RESCORE 0x20u /* re-score the candidates in emission order, gathering both FP32 rows of
-                                           each from global memory.  By default, for d % 4 == 0, d <= 1024 and
-                                           16-byte aligned rows, the candidates are first bucketed by panels of
+                                           each from global memory.  By default, for d % 4 == 0, d <= 1024,
+                                           16-byte aligned rows and joins of at least 2^27 pairs (before
+                                           selection), the candidates are first bucketed by panels of
                                            consecutive R rows and each panel's rows are staged in shared memory
                                            once; both give the same pairs and similarities */
+#define EJOIN_FLAG_PANEL_RESCORE 0x80u /* the panel-ordered re-score at any join size (where the rows allow
+                                          it); without it smaller joins gather in emission order, which
+                                          needs one synchronisation less per call */
 #define EJOIN_FLAG_SORT       0x40u /* ejoin_threshold, ejoin_threshold_host, ejoin_eselect and
                                        ejoin_threshold_pruned return their records sorted by (i, j)
                                        ascending (a device radix sort after the join; the call
@@ -276,13 +280,21 @@ ejoin_status ejoin_pairs_free(ejoin_ctx *ctx, ejoin_pairs *pairs);
  * (job, row tile, column tile), so tiles of every job share one persistent
  * grid (the tiles of different jobs are independent blocks of the
  * decomposition of Sec. IV-C, Eq. (Block Matrix Dot Product Decomposition)).
- * No selection predicates (apply ejoin_normalize-style compaction upstream).
+ * Selection predicates per job: ejoin_batch_create_sel.
  * ------------------------------------------------------------------------- */
 typedef struct ejoin_job {
     ejoin_rel R;  /* device rows of this job's R (all jobs of a batch share d) */
     ejoin_rel S;  /* device rows of this job's S */
     float eps;    /* this job's similarity threshold */
 } ejoin_job;
+
+/* The selections of one job of a batch (Sec. III-C, Eq. (E-Selection); the pre-filter of Sec. VI-E): the R
+ * and S predicates of ejoin_threshold (device attr / bits arrays of that job's rows).  A side whose attr and
+ * bits are both NULL keeps every row. */
+typedef struct ejoin_job_sel {
+    ejoin_sel R;
+    ejoin_sel S;
+} ejoin_job_sel;
 
 /* One result record of a batched join: job index, original row ids, similarity. */
 typedef struct ejoin_batch_pair {
@@ -318,6 +330,16 @@ typedef struct ejoin_batch_stats {
  * EJOIN_EOVERFLOW from ejoin_batch_wait (re-create the plan). */
 ejoin_status ejoin_batch_create(ejoin_ctx *ctx, const ejoin_job *jobs, int32_t n_jobs, uint32_t flags,
                                 ejoin_batch **out);
+
+/* ejoin_batch_create with per-job selections: sels[j] holds job j's predicates (sels == NULL: none).  Every
+ * run evaluates them on the device before the normalisation: each job's kept rows are compacted in order,
+ * and the job table, the tile counts and the re-score's sort buckets are rebuilt from the kept counts, so
+ * only kept rows are normalised and contracted, and a replayed graph follows whatever the attribute arrays
+ * hold when it runs (their pointers are captured like the rows').  Records carry original row ids.  The
+ * buffers are sized from the rows kept when the plan is made; a later run that finds more candidates or
+ * pairs than fit reports EJOIN_EOVERFLOW from ejoin_batch_wait.  EJOIN_EINVAL for an unknown op. */
+ejoin_status ejoin_batch_create_sel(ejoin_ctx *ctx, const ejoin_job *jobs, const ejoin_job_sel *sels, int32_t n_jobs,
+                                    uint32_t flags, ejoin_batch **out);
 
 /* Enqueue one run on the context's stream (a graph launch when captured); no host synchronisation. */
 ejoin_status ejoin_batch_run(ejoin_batch *batch);

@@ -8,7 +8,7 @@ The C ABI is declared in include/ejoin.h; ``ejoin`` is its Python binding.
 """
 from .ejoin import (  # noqa: F401
     EJOIN_BF16, EJOIN_F32, EJOIN_FP8_E4M3, EJOIN_TF32, EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED,
-    EJOIN_FLAG_NO_SYMMETRY, EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE, EJOIN_FLAG_SORT, PAIR_DTYPE,
+    EJOIN_FLAG_NO_SYMMETRY, EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE, EJOIN_FLAG_SORT, EJOIN_FLAG_PANEL_RESCORE, PAIR_DTYPE,
     Ctx, EJoinError, Result, Sel, ejoin_create, ejoin_destroy, ejoin_last_stats, ejoin_normalize, ejoin_set_timeout,
     ejoin_padded_dim, ejoin_strerror, ejoin_threshold, ejoin_threshold_host, ejoin_top1, ejoin_topk, ejoin_eselect, ejoin_version, load_library,
     Batch, ejoin_batch,

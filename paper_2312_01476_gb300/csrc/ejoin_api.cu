@@ -582,8 +582,12 @@ ejoin_status run_threshold(ejoin_ctx *c, const ejoin_rel &R, const ejoin_rel &S,
         return ee == cudaSuccess ? cudaStreamSynchronize(c->stream) : ee;
     };
     // exact re-score of the candidates (it reads their count on the device): panel-ordered where the rows
-    // allow it (R rows staged in shared memory per panel), else plain gathers in emission order
-    const bool panels = aligned_rows && R.d <= 1024 && !(c->flags & EJOIN_FLAG_GATHER_RESCORE);
+    // allow it (R rows staged in shared memory per panel), else plain gathers in emission order.  Joins of
+    // fewer than PANEL_MIN_PAIRS pairs (before selection) keep the gathers: their few candidates do not repay
+    // the bucket sort, and the call then needs a single synchronisation.
+    constexpr double PANEL_MIN_PAIRS = 134217728.0;  // 2^27
+    const bool panels = aligned_rows && R.d <= 1024 && !(c->flags & EJOIN_FLAG_GATHER_RESCORE) &&
+                        ((c->flags & EJOIN_FLAG_PANEL_RESCORE) || (double)R.n * (double)S.n >= PANEL_MIN_PAIRS);
     auto rescore = [&]() -> cudaError_t {
         cudaError_t ee = ensure(c->band, c->cand_cap * sizeof(uint2));
         if (ee != cudaSuccess) return ee;

@@ -39,6 +39,26 @@ struct SelArgs {
     const uint32_t *bits;
 };
 
+// Row r passes `attr[r] op c` (when attr is set) and bit r of bits (when bits is set).
+__device__ __forceinline__ bool sel_keep(const SelArgs &s, int64_t r)
+{
+    bool k = true;
+    if (s.attr) {
+        const int a = s.attr[r];
+        switch (s.op) {
+        case EJOIN_LT: k = a < s.c; break;
+        case EJOIN_LE: k = a <= s.c; break;
+        case EJOIN_GT: k = a > s.c; break;
+        case EJOIN_GE: k = a >= s.c; break;
+        case EJOIN_EQ: k = a == s.c; break;
+        case EJOIN_NE: k = a != s.c; break;
+        default: k = false;
+        }
+    }
+    if (k && s.bits) k = (s.bits[r >> 5] >> (r & 31)) & 1u;
+    return k;
+}
+
 // Job table of a batched contraction (device arrays).  Job j owns the tiles
 // [tile_off[j], tile_off[j+1]) of the global tile space, the operand rows
 // [a_off[j], a_off[j] + nA[j]) of the concatenated R operand and
@@ -103,7 +123,9 @@ __host__ __device__ __forceinline__ float ord2f(unsigned o)
 #endif
 }
 
-// Per-job row sources of a batched re-score (device arrays).
+// Per-job row sources of a batched re-score (device arrays).  Operand row a of job j is row
+// idsA[a] - srcA_off[j] of R_j when the batch has selections (idsA: the kept rows' indices among all of
+// the jobs' concatenated rows, srcA_off: the jobs' offsets there), else row a - a_off[j]; likewise for S.
 struct BatchRows {
     const float *const *R;
     const long long *ldR;
@@ -113,7 +135,21 @@ struct BatchRows {
     const long long *b_off;
     const float *eps;
     int n_jobs;
+    const uint32_t *idsA = nullptr, *idsB = nullptr;
+    const long long *srcA_off = nullptr, *srcB_off = nullptr;
 };
+
+// Original row of operand row a of job j (see BatchRows).
+__device__ __forceinline__ uint32_t batch_row_a(const BatchRows &br, uint32_t a, uint32_t j)
+{
+    return br.idsA ? (uint32_t)((long long)__ldg(br.idsA + a) - __ldg(br.srcA_off + j))
+                   : (uint32_t)((long long)a - __ldg(br.a_off + j));
+}
+__device__ __forceinline__ uint32_t batch_row_b(const BatchRows &br, uint32_t b, uint32_t j)
+{
+    return br.idsB ? (uint32_t)((long long)__ldg(br.idsB + b) - __ldg(br.srcB_off + j))
+                   : (uint32_t)((long long)b - __ldg(br.b_off + j));
+}
 
 // Arguments of the re-score fused into the contraction (single join).
 struct FuseArgs {
@@ -165,7 +201,8 @@ cudaError_t launch_normalize_fp8_grouped(const float *x, int64_t ld, int d, cons
 cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
                                    int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
                                    float *scale, unsigned *status, int num_sms, cudaStream_t st,
-                                   bool aligned = false);
+                                   bool aligned = false,
+                                   const uint32_t *ids = nullptr, const long long *src_off = nullptr);
 cudaError_t launch_sim_simt(const float *A, const float *B, int kp, const long long *nA, const long long *nB,
                             float thr, uint2 *cand, uint64_t cap, unsigned long long *cand_count,
                             int count_only, int num_sms, cudaStream_t st);

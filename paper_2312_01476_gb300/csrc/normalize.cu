@@ -15,25 +15,6 @@
 
 namespace ej {
 
-__device__ __forceinline__ bool sel_keep(const SelArgs &s, int64_t r)
-{
-    bool k = true;
-    if (s.attr) {
-        const int a = s.attr[r];
-        switch (s.op) {
-        case EJOIN_LT: k = a < s.c; break;
-        case EJOIN_LE: k = a <= s.c; break;
-        case EJOIN_GT: k = a > s.c; break;
-        case EJOIN_GE: k = a >= s.c; break;
-        case EJOIN_EQ: k = a == s.c; break;
-        case EJOIN_NE: k = a != s.c; break;
-        default: k = false;
-        }
-    }
-    if (k && s.bits) k = (s.bits[r >> 5] >> (r & 31)) & 1u;
-    return k;
-}
-
 __device__ __forceinline__ int block_sum(int v, int *red)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -278,7 +259,9 @@ __global__ void __launch_bounds__(256) normalize_batch_kernel(const float *const
                                                               const long long *__restrict__ row_off, int n_rel,
                                                               int d, void *__restrict__ out, int kp,
                                                               float *__restrict__ inv_norm,
-                                                              float *__restrict__ scale, unsigned *status)
+                                                              float *__restrict__ scale, unsigned *status,
+                                                              const uint32_t *__restrict__ ids,
+                                                              const long long *__restrict__ src_off)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -294,7 +277,8 @@ __global__ void __launch_bounds__(256) normalize_batch_kernel(const float *const
         const float *x = xs[lo];
         const int64_t ld = lds[lo];
         const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(x) & 15) == 0);
-        normalize_row<FMT>(x + (g - row_off[lo]) * ld, d, vec, out, g, kp, kp, inv_norm, scale, status, lane);
+        const int64_t r = ids ? (int64_t)ids[g] - src_off[lo] : g - row_off[lo];
+        normalize_row<FMT>(x + r * ld, d, vec, out, g, kp, kp, inv_norm, scale, status, lane);
     }
 }
 
@@ -309,13 +293,19 @@ __global__ void __launch_bounds__(256) normalize_batch_rows_kernel(const float *
                                                                    const long long *__restrict__ row_off, int n_rel,
                                                                    int d, void *__restrict__ out, int kp,
                                                                    float *__restrict__ inv_norm,
-                                                                   float *__restrict__ scale, unsigned *status)
+                                                                   float *__restrict__ scale, unsigned *status,
+                                                                   const uint32_t *__restrict__ ids,
+                                                                   const long long *__restrict__ src_off)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const int64_t total = row_off[n_rel];
     const int d4 = d >> 2, groups = kp >> 2;
+    // source row of operand row g of relation j
+    auto src_row = [&](int64_t g, int j) -> int64_t {
+        return ids ? (int64_t)__ldg(ids + g) - __ldg(src_off + j) : g - __ldg(row_off + j);
+    };
     int job = -1;
     for (int64_t g0 = warp_global * RW; g0 < total; g0 += n_warps * RW) {
         if (job < 0) {
@@ -334,7 +324,7 @@ __global__ void __launch_bounds__(256) normalize_batch_rows_kernel(const float *
             const float *src = nullptr;
             if (g < total) {  // warp-uniform
                 while (__ldg(row_off + job + 1) <= g) ++job;
-                src = xs[job] + (g - __ldg(row_off + job)) * lds[job];
+                src = xs[job] + src_row(g, job) * lds[job];
             }
 #pragma unroll
             for (int q = 0; q < V; ++q) {
@@ -369,8 +359,8 @@ __global__ void __launch_bounds__(256) normalize_batch_rows_kernel(const float *
                 // over- or underflow of the plain sum: the rescaled path
                 int jb = job;
                 while (__ldg(row_off + jb) > g) --jb;
-                normalize_row<FMT>(xs[jb] + (g - __ldg(row_off + jb)) * lds[jb], d, true, out, g, kp, kp, inv_norm,
-                                   scale, status, lane);
+                normalize_row<FMT>(xs[jb] + src_row(g, jb) * lds[jb], d, true, out, g, kp, kp, inv_norm, scale,
+                                   status, lane);
                 continue;
             }
             const float inv = bad ? 0.f : (ss > 0.f ? 1.0f / sqrtf(ss) : 0.f);
@@ -561,7 +551,8 @@ cudaError_t launch_normalize(int fmt, const float *x, int64_t ld, int d, const u
 template <int FMT, int V>
 static void launch_batch_rows(int64_t total_rows, const float *const *xs, const long long *lds,
                               const long long *row_off, int n_rel, int d, void *out, int kp, float *inv_norm,
-                              float *scale, unsigned *status, int num_sms, cudaStream_t st)
+                              float *scale, unsigned *status, int num_sms, cudaStream_t st, const uint32_t *ids,
+                              const long long *src_off)
 {
     constexpr int RW = V <= 4 ? 4 : 2;
     // one wave of resident blocks walks the rows (a second wave would start only after the first ended)
@@ -575,15 +566,16 @@ static void launch_batch_rows(int64_t total_rows, const float *const *xs, const 
     const int64_t cap = (int64_t)num_sms * per_sm;
     if (blocks > cap) blocks = cap;
     normalize_batch_rows_kernel<FMT, V, RW><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
-                                                                              inv_norm, scale, status);
+                                                                              inv_norm, scale, status, ids, src_off);
 }
 
 template <int FMT>
 static cudaError_t launch_batch_rows_d(int64_t total_rows, const float *const *xs, const long long *lds,
                                        const long long *row_off, int n_rel, int d, void *out, int kp,
-                                       float *inv_norm, float *scale, unsigned *status, int num_sms, cudaStream_t st)
+                                       float *inv_norm, float *scale, unsigned *status, int num_sms, cudaStream_t st,
+                                       const uint32_t *ids, const long long *src_off)
 {
-#define EJ_NB_ARGS total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale, status, num_sms, st
+#define EJ_NB_ARGS total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale, status, num_sms, st, ids, src_off
     if (d <= 128) launch_batch_rows<FMT, 1>(EJ_NB_ARGS);
     else if (d <= 256) launch_batch_rows<FMT, 2>(EJ_NB_ARGS);
     else if (d <= 384) launch_batch_rows<FMT, 3>(EJ_NB_ARGS);
@@ -596,7 +588,8 @@ static cudaError_t launch_batch_rows_d(int64_t total_rows, const float *const *x
 
 cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long long *lds, const long long *row_off,
                                    int n_rel, int64_t total_rows, int d, void *out, int kp, float *inv_norm,
-                                   float *scale, unsigned *status, int num_sms, cudaStream_t st, bool aligned)
+                                   float *scale, unsigned *status, int num_sms, cudaStream_t st, bool aligned,
+                                   const uint32_t *ids, const long long *src_off)
 {
     if (total_rows <= 0) return cudaSuccess;
     if (aligned && d % 4 == 0 && d <= 1024 && kp <= 4 * 32 * ((d + 127) / 128)) {
@@ -604,13 +597,13 @@ cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long l
         switch (fmt) {
         case FMT_F32:
             return launch_batch_rows_d<FMT_F32>(total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale,
-                                                status, num_sms, st);
+                                                status, num_sms, st, ids, src_off);
         case FMT_BF16:
             return launch_batch_rows_d<FMT_BF16>(total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale,
-                                                 status, num_sms, st);
+                                                 status, num_sms, st, ids, src_off);
         case FMT_FP8:
             return launch_batch_rows_d<FMT_FP8>(total_rows, xs, lds, row_off, n_rel, d, out, kp, inv_norm, scale,
-                                                status, num_sms, st);
+                                                status, num_sms, st, ids, src_off);
         default: return cudaErrorInvalidValue;
         }
     }
@@ -620,15 +613,15 @@ cudaError_t launch_normalize_batch(int fmt, const float *const *xs, const long l
     switch (fmt) {
     case FMT_F32:
         normalize_batch_kernel<FMT_F32><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
-                                                                          inv_norm, scale, status);
+                                                                          inv_norm, scale, status, ids, src_off);
         break;
     case FMT_BF16:
         normalize_batch_kernel<FMT_BF16><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
-                                                                           inv_norm, scale, status);
+                                                                           inv_norm, scale, status, ids, src_off);
         break;
     case FMT_FP8:
         normalize_batch_kernel<FMT_FP8><<<(unsigned)blocks, 256, 0, st>>>(xs, lds, row_off, n_rel, d, out, kp,
-                                                                          inv_norm, scale, status);
+                                                                          inv_norm, scale, status, ids, src_off);
         break;
     default: return cudaErrorInvalidValue;
     }

@@ -478,8 +478,8 @@ __global__ void __launch_bounds__(RS_WARPS * 32, 2) rescore_batch_kernel(
                 else hi = mid;
             }
             job = (uint32_t)lo;
-            gi = (uint32_t)(c.x - __ldg(br.a_off + lo));
-            gj = (uint32_t)(c.y - __ldg(br.b_off + lo));
+            gi = batch_row_a(br, c.x, job);
+            gj = batch_row_b(br, c.y, job);
             sc = invA[c.x] * invB[c.y];
             ej = __ldg(br.eps + lo);
             valid = true;
@@ -1632,10 +1632,9 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
         ok = k < n;
         const uint2 c = sorted[ok ? k : u * 32];
         job = (uint32_t)__ldg(row_job + c.x);
-        const long long ao = __ldg(br.a_off + job), bo = __ldg(br.b_off + job);
         x = c.x;
-        gi = (uint32_t)((long long)c.x - ao);
-        gj = (uint32_t)((long long)c.y - bo);
+        gi = batch_row_a(br, c.x, job);
+        gj = batch_row_b(br, c.y, job);
         sp = br.S[job] + (int64_t)gj * br.ldS[job];
         sc = invA[c.x] * invB[c.y];
         ej = __ldg(br.eps + job);
@@ -1679,7 +1678,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
         bool nok = false;
         uint32_t njob = 0;
         float nia = 0.f, nib = 0.f, nej = 0.f;
-        long long nao = 0, nbo = 0, nld = 0;
+        long long nld = 0;
         const float *nS = nullptr;
         uint32_t nx = 0, ngi = 0, ngj = 0;
         const float *nsp = nullptr;
@@ -1698,15 +1697,13 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_stream_batch_kern
                 nib = invB[nc.y];
                 if (has_next) unn = ticket();
             } else if (j == R3) {
-                nao = __ldg(br.a_off + njob);
-                nbo = __ldg(br.b_off + njob);
+                ngi = batch_row_a(br, nc.x, njob);
+                ngj = batch_row_b(br, nc.y, njob);
                 nS = br.S[njob];
                 nld = br.ldS[njob];
                 nej = __ldg(br.eps + njob);
             } else if (j == FIN) {
                 nx = nc.x;
-                ngi = (uint32_t)((long long)nc.x - nao);
-                ngj = (uint32_t)((long long)nc.y - nbo);
                 nsp = nS + (int64_t)ngj * nld;
                 nsc = nia * nib;
             }

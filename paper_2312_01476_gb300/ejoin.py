@@ -23,7 +23,7 @@ EJOIN_OK, EJOIN_EINVAL, EJOIN_ENOMEM, EJOIN_EOVERFLOW = 0, 1, 2, 3
 EJOIN_ENONFINITE, EJOIN_ECUDA, EJOIN_ETIMEOUT, EJOIN_EUNSUPPORTED = 4, 5, 6, 7
 EJOIN_F32, EJOIN_BF16, EJOIN_FP8_E4M3, EJOIN_TF32 = 0, 1, 2, 3
 EJOIN_FLAG_COUNT_ONLY, EJOIN_FLAG_TIMING, EJOIN_FLAG_FUSED, EJOIN_FLAG_NO_SYMMETRY = 0x1, 0x2, 0x4, 0x8
-EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE, EJOIN_FLAG_SORT = 0x10, 0x20, 0x40
+EJOIN_FLAG_HOST_COPY, EJOIN_FLAG_GATHER_RESCORE, EJOIN_FLAG_SORT, EJOIN_FLAG_PANEL_RESCORE = 0x10, 0x20, 0x40, 0x80
 OPS = {"<": 0, "<=": 1, ">": 2, ">=": 3, "==": 4, "!=": 5}
 PRECS = {"f32": EJOIN_F32, "bf16": EJOIN_BF16, "fp8": EJOIN_FP8_E4M3, "tf32": EJOIN_TF32}
 
@@ -64,6 +64,10 @@ class ejoin_stats(ctypes.Structure):
 
 class ejoin_job(ctypes.Structure):
     _fields_ = [("R", ejoin_rel), ("S", ejoin_rel), ("eps", ctypes.c_float)]
+
+
+class ejoin_job_sel(ctypes.Structure):
+    _fields_ = [("R", ejoin_sel), ("S", ejoin_sel)]
 
 
 class ejoin_batch_stats(ctypes.Structure):
@@ -154,6 +158,9 @@ def load_library(path: str = LIB_PATH):
     lib.ejoin_strerror.argtypes = [ctypes.c_int]
     lib.ejoin_version.restype = ctypes.c_char_p
     lib.ejoin_version.argtypes = []
+    lib.ejoin_batch_create_sel.restype = ctypes.c_int
+    lib.ejoin_batch_create_sel.argtypes = [ctypes.c_void_p, P(ejoin_job), P(ejoin_job_sel), ctypes.c_int32,
+                                           ctypes.c_uint32, P(ctypes.c_void_p)]
     lib.ejoin_batch_create.restype = ctypes.c_int
     lib.ejoin_batch_create.argtypes = [ctypes.c_void_p, P(ejoin_job), ctypes.c_int32, ctypes.c_uint32,
                                        P(ctypes.c_void_p)]
@@ -499,7 +506,8 @@ class Batch:
     """A planned batch of independent E-joins (ejoin_batch_create); runs replay a CUDA graph
     when ``graph`` is set.  ``jobs``: list of (R, S, eps) with R, S float32 CUDA tensors."""
 
-    def __init__(self, ctx: Ctx, jobs, graph: bool = True, autotune: bool = False):
+    def __init__(self, ctx: Ctx, jobs, graph: bool = True, autotune: bool = False, sels=None):
+        """sels (optional): per job a pair (Sel or None for R, Sel or None for S)."""
         lib = load_library()
         self.ctx = ctx
         self._keep = [(R, S) for R, S, _ in jobs]
@@ -510,7 +518,19 @@ class Batch:
             arr[k].eps = float(eps)
         flags = (EJOIN_BATCH_GRAPH if graph else 0) | (EJOIN_BATCH_AUTOTUNE if autotune else 0)
         h = ctypes.c_void_p()
-        _check(lib.ejoin_batch_create(ctx.handle, arr, len(jobs), flags, ctypes.byref(h)), "ejoin_batch_create")
+        if sels is None:
+            _check(lib.ejoin_batch_create(ctx.handle, arr, len(jobs), flags, ctypes.byref(h)), "ejoin_batch_create")
+        else:
+            if len(sels) != len(jobs):
+                raise ValueError("one (selR, selS) pair per job")
+            sarr = (ejoin_job_sel * len(jobs))()
+            none = ejoin_sel(None, 0, 0, None)
+            for k, (sR, sS) in enumerate(sels):
+                sarr[k].R = _dev_sel(sR) or none
+                sarr[k].S = _dev_sel(sS) or none
+                self._keep.append((sR, sS))
+            _check(lib.ejoin_batch_create_sel(ctx.handle, arr, sarr, len(jobs), flags, ctypes.byref(h)),
+                   "ejoin_batch_create_sel")
         self.handle = h
         _live_dependents.add(self)
 
@@ -564,9 +584,9 @@ class _DevBuf:
                                          "version": 3, "strides": None}
 
 
-def ejoin_batch(ctx: Ctx, jobs, graph: bool = True, autotune: bool = False):
+def ejoin_batch(ctx: Ctx, jobs, graph: bool = True, autotune: bool = False, sels=None):
     """One-shot batched join: plan, run, wait; returns (job, i, j, sim) host numpy arrays."""
-    b = Batch(ctx, jobs, graph=graph, autotune=autotune)
+    b = Batch(ctx, jobs, graph=graph, autotune=autotune, sels=sels)
     b.run()
     n = b.wait()
     job, i, j, sim = (x.cpu().numpy() for x in b.result(n))

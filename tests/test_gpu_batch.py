@@ -147,3 +147,120 @@ def test_batch_stream_rescore_accurate_tier():
     kg, sg, st_g = records(kw, jobs_dev, pkg.EJOIN_FLAG_GATHER_RESCORE)
     assert st_p["fp64_rescored"] > 1000 and st_p["fp64_rescored"] == st_g["fp64_rescored"]
     assert np.array_equal(kp, kg) and np.array_equal(sp, sg)
+
+
+OPS_NP = {"<": np.less, "<=": np.less_equal, ">": np.greater, ">=": np.greater_equal, "==": np.equal,
+          "!=": np.not_equal}
+
+
+def job_selection(rng, n, kind):
+    """(device Sel or None, host keep mask) for one side of one job."""
+    if kind is None or n == 0:
+        return None, np.ones(n, dtype=bool)
+    attr = rng.integers(0, 100, n).astype(np.int32)
+    bits = None
+    keep = np.ones(n, dtype=bool)
+    op, c = "<", 0
+    if kind in OPS_NP:
+        op, c = kind, int(rng.integers(20, 80))
+        keep = OPS_NP[op](attr, c)
+    elif kind == "none":
+        op, c = "<", 0  # attr >= 0: keeps nothing
+        keep = np.zeros(n, dtype=bool)
+    if kind in ("bits", "attr+bits"):
+        b = rng.integers(0, 2, n).astype(bool)
+        words = np.zeros((n + 31) // 32, dtype=np.uint32)
+        for r in np.nonzero(b)[0]:
+            words[r >> 5] |= np.uint32(1) << np.uint32(r & 31)
+        bits = torch.from_numpy(words.view(np.int32)).cuda()
+        if kind == "attr+bits":
+            op, c = ">=", 30
+            keep = (attr >= 30) & b
+        else:
+            keep = b
+    a_dev = torch.from_numpy(attr).cuda() if kind != "bits" else None
+    return pkg.Sel(a_dev, op, c, bits), keep
+
+
+def as_oracle_sel(keep):
+    # the kept rows as a predicate the oracle evaluates: attr' = 0 for kept rows, 1 otherwise, attr' < 1
+    return oracle.Selection(np.where(keep, 0, 1).astype(np.int32), "<", 1)
+
+
+SEL_KINDS = [("<", None), (None, ">="), ("<=", "=="), ("!=", "bits"), ("attr+bits", ">"), (None, None),
+             ("none", "<"), (">", "attr+bits"), ("bits", None), ("==", "!="), ("<", "<")]
+
+
+def selected_batch(seed, d):
+    rng = np.random.default_rng(seed)
+    sizes = [(300, 700), (0, 50), (40, 0), (129, 257), (1000, 513), (37, 2000), (256, 256), (5, 900), (777, 31),
+             (2000, 1500), (64, 64)]
+    jobs_np = make_jobs(seed, sizes, d, 0.5 / np.sqrt(d), 1.5 / np.sqrt(d))
+    sels, keeps = [], []
+    for (R, S, _), (kr, ks) in zip(jobs_np, SEL_KINDS):
+        sr, mr = job_selection(rng, R.shape[0], kr)
+        ss, ms = job_selection(rng, S.shape[0], ks)
+        sels.append((sr, ss))
+        keeps.append((mr, ms))
+    return jobs_np, sels, keeps
+
+
+@pytest.mark.parametrize("prec,d", [("bf16", 96), ("fp8", 128), ("tf32", 64), ("bf16", 384)])
+def test_batch_per_job_selections_match_oracle(prec, d):
+    jobs_np, sels, keeps = selected_batch(31, d)
+    with pkg.Ctx(device=0, prec=prec) as ctx:
+        job, gi, gj, gs = pkg.ejoin_batch(ctx, to_dev(jobs_np), graph=True, sels=sels)
+    assert len(job) > 1000
+    gi, gj = gi.view(np.uint32), gj.view(np.uint32)
+    for k, ((R, S, eps), (mr, ms)) in enumerate(zip(jobs_np, keeps)):
+        sel = job == k
+        oi, oj, os_ = oracle.join(R, S, eps, as_oracle_sel(mr) if len(mr) else None,
+                                  as_oracle_sel(ms) if len(ms) else None)
+        compare(R, S, eps, gi[sel], gj[sel], gs[sel], oi, oj, os_)
+        if sel.any():
+            assert mr[gi[sel]].all() and ms[gj[sel]].all()
+
+
+def test_batch_selections_stream_equals_gather_and_follow_new_attributes():
+    jobs_np, sels, keeps = selected_batch(32, 384)
+    jobs_dev = to_dev(jobs_np)
+    got = {}
+    for flags in (0, pkg.EJOIN_FLAG_GATHER_RESCORE):
+        with pkg.Ctx(device=0, prec="bf16", flags=flags) as ctx:
+            job, gi, gj, gs = pkg.ejoin_batch(ctx, jobs_dev, graph=True, sels=sels)
+        key = (job.astype(np.int64) << 42) | (gi.view(np.uint32).astype(np.int64) << 21) | gj.view(np.uint32)
+        o = np.argsort(key)
+        got[flags] = (key[o], gs[o].view(np.uint32))
+    assert np.array_equal(got[0][0], got[pkg.EJOIN_FLAG_GATHER_RESCORE][0])
+    assert np.array_equal(got[0][1], got[pkg.EJOIN_FLAG_GATHER_RESCORE][1])
+    # a replayed plan evaluates the predicates on the attribute values of each run: the odd rows are given
+    # a failing value, so each side keeps the even rows of its former kept set (the sized buffers still fit)
+    fail = {"<": 99, "<=": 99, ">": 0, ">=": 0}
+    with pkg.Ctx(device=0, prec="bf16") as ctx:
+        b = pkg.Batch(ctx, jobs_dev, graph=True, sels=sels)
+        b.run()
+        n0 = b.wait()
+        new_keeps = []
+        for (sr, ss), (mr, ms) in zip(sels, keeps):
+            nk = []
+            for s, m in ((sr, mr), (ss, ms)):
+                if s is not None and s.attr is not None:
+                    a2 = s.attr.cpu().numpy().copy()
+                    a2[1::2] = fail.get(s.op, s.c + 1 if s.op == "==" else s.c)
+                    s.attr.copy_(torch.from_numpy(a2))
+                    m = m.copy()
+                    m[1::2] = False
+                nk.append(m)
+            new_keeps.append(tuple(nk))
+        torch.cuda.synchronize()
+        b.run()
+        n1 = b.wait()
+        job, gi, gj, gs = (x.cpu().numpy() for x in b.result(n1))
+        b.close()
+    assert n0 > n1 > 0
+    gi, gj = gi.view(np.uint32), gj.view(np.uint32)
+    for k, ((R, S, eps), (mr, ms)) in enumerate(zip(jobs_np, new_keeps)):
+        sel = job == k
+        oi, oj, os_ = oracle.join(R, S, eps, as_oracle_sel(mr) if len(mr) else None,
+                                  as_oracle_sel(ms) if len(ms) else None)
+        compare(R, S, eps, gi[sel], gj[sel], gs[sel], oi, oj, os_)

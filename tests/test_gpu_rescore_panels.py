@@ -40,6 +40,9 @@ def clustered(seed, n, d, centres, spread):
 
 
 def joined(prec, R, S, eps, flags=0, selR=None, selS=None, **kw):
+    # these joins are below the size where the panel order is the default: ask for it unless gathering
+    if not flags & pkg.EJOIN_FLAG_GATHER_RESCORE:
+        flags |= pkg.EJOIN_FLAG_PANEL_RESCORE
     with pkg.Ctx(device=0, prec=prec, flags=flags, **kw) as ctx:
         Rd = dev(R)
         Sd = Rd if S is R else dev(S)
