@@ -436,6 +436,11 @@ def run_ejoin(args):
         del R, S
         torch.cuda.empty_cache()
         large = measure_large_join(args, local)
+    forms = None
+    if args.workload == "c2" and args.prec == "bf16" and not args.no_forms and world == 1:
+        # the batched and the learned form on their own workloads, each beside the plain FP32 path on the
+        # same GPU (summaries of the lines `--workload c4` and `--workload c5` print)
+        forms = measure_forms(args)
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -451,11 +456,42 @@ def run_ejoin(args):
                "stages_ms": {"normalize": round(statistics.mean(stage["normalize"]), 4),
                              "contract": round(c_ms, 4), "rescore": round(statistics.mean(stage["rescore"]), 4)},
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clocks, "large_join": large}
+               "clocks": clocks, "large_join": large, "forms": forms}
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def measure_forms(args):
+    """Summaries of the batched form (c4: 512 joins, graph replay, 5 timed steps) and of the learned form
+    (c5: the 4M-row self-join with learned tile pruning, 2 timed steps), each with the plain FP32 CUDA-core
+    path measured on the same GPU."""
+    import argparse
+    ba = argparse.Namespace(**{**vars(args), "workload": "c4", "steps": 5, "warmup": 3, "prec": "bf16"})
+    b = run_batch(ba, emit=False)
+    la = argparse.Namespace(**{**vars(args), "workload": "c5", "steps": 2, "warmup": 3, "prec": "bf16"})
+    lr = run_learned(la, emit=False)
+    bl = b["baselines"]
+    return {
+        "batched": {"workload": b["config"]["workload"], "value": b["value"], "unit": b["unit"],
+                    "ms_per_step": b["ms_per_step"], "steps": b["steps"], "warmup": b["warmup"],
+                    "latency_ms": b["latency_ms"], "roofline": b["roofline"], "clocks": b["clocks"],
+                    "stages_ms": {"normalize": b["config"]["ms_normalize"], "contract": b["config"]["ms_contract"],
+                                  "rescore": b["config"]["ms_rescore"]},
+                    "sequential_calls_pairs_per_s": bl["sequential_calls_pairs_per_s"],
+                    "fp32_cuda_cores_pairs_per_s": bl["fp32_cuda_cores_pairs_per_s"], "fp32_sample": bl["fp32_sample"],
+                    "speedup_vs_fp32_cuda_cores": b["value"] / bl["fp32_cuda_cores_pairs_per_s"]},
+        "learned": {"workload": lr["config"]["workload"], "value": lr["value"], "unit": lr["unit"],
+                    "ms_per_step": lr["ms_per_step"], "steps": lr["steps"], "warmup": lr["warmup"],
+                    "recall": lr["recall"], "recall_est": lr["pruned"]["recall_est"],
+                    "plain_bf16_ms_per_step": lr["plain_bf16"]["ms_per_step"],
+                    "speedup_vs_plain_bf16": lr["speedup_vs_plain_bf16"],
+                    "fp32_cuda_cores_pairs_per_s": lr["plain_fp32_cuda_cores"]["pairs_per_s"],
+                    "fp32_sample": lr["plain_fp32_cuda_cores"]["sample"],
+                    "speedup_vs_fp32_cuda_cores": lr["speedup_vs_plain_fp32"],
+                    "stages_ms": {k: lr["pruned"][k] for k in ("ms_prepare", "ms_bound", "ms_contract", "ms_rescore")}},
+    }
 
 
 def measure_large_join(args, local):
@@ -713,7 +749,7 @@ def run_eselect(args):
     ctx.close()
 
 
-def run_batch(args):
+def run_batch(args, emit=True):
     """512 independent joins (lognormal sizes, per-job eps) in one persistent launch, replayed from a
     CUDA graph; reports the batch latency p50/p99 and pairs/s."""
     import torch
@@ -790,12 +826,16 @@ def run_batch(args):
                         "frac": round(flop / float(np.mean(lat_s)) / 1e12 / pk["bf16_tflops"], 4),
                         "note": "whole batch (normalise + contraction + re-score) per replay"},
            "gpu_launches": launches_per_run * args.steps, "clocks": clocks, "baselines": baselines}
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
     b.close()
     ctx.close()
+    del jobs, b
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_learned(args):
+def run_learned(args, emit=True):
     """4M-row self-join with learned tile pruning against the plain BF16 join, which checks its result."""
     import torch
     import ejoin_inputs as inputs
@@ -872,9 +912,13 @@ def run_learned(args):
            "plain_fp32_cuda_cores": {"pairs_per_s": f32_pps, "sample": "first 65,536 rows x all rows"},
            "speedup_vs_plain_fp32": (logical / (ms_pruned * 1e-3)) / f32_pps,
            "gpu_launches": None, "sampled_rows": sample}
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
     sk.close()
     ctx.close()
+    del X, Xtr, Xcal
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_library_peaks():
@@ -938,6 +982,8 @@ def main():
     ap.add_argument("--no-large-join", action="store_true",
                     help="skip the 2M-row self-join (large_join) the default line adds after the c2 workload")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched (c4) and learned (c5) summaries the default line adds after the c2 workload")
     ap.add_argument("--no-parity", action="store_true", help="accepted for compatibility; parity lives in tests/")
     args = ap.parse_args()
     if args.peaks:
