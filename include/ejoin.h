@@ -31,7 +31,8 @@
  *   - Result: every pair whose FP64 similarity differs from eps by at least
  *     1e-5 is in the result iff sim >= eps; each emitted similarity is within
  *     1e-5 of the FP64 value (it is re-scored in FP32 from the input rows,
- *     in FP64 when it lies within fp64_band of eps).  Order is unspecified.
+ *     in FP64 when it lies within fp64_band of eps).  Order is unspecified
+ *     unless EJOIN_FLAG_SORT asks for ascending (i, j).
  *   - A context holds the workspace and statistics of its calls, so calls on
  *     one context must not overlap (from several host threads at once).
  *     Separate contexts may be used from separate threads; each calls
