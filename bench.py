@@ -841,7 +841,10 @@ def run_learned(args, emit=True):
     import ejoin_inputs as inputs
     import paper_2312_01476_gb300 as pkg
     from paper_2312_01476_gb300 import ejoin as E
-    w = inputs.c5_learned(threads=os.cpu_count() or 8)
+    if args.c5_rows == 4_000_000:
+        w = inputs.c5_learned(threads=os.cpu_count() or 8)
+    else:  # a smaller case of the same shape: groups of ~200 rows
+        w = inputs.c5_learned(n=args.c5_rows, n_clusters=max(1, args.c5_rows // 200), threads=os.cpu_count() or 8)
     d = int(w.R.shape[1])
     X = torch.from_numpy(w.R).cuda()
     Xtr = torch.from_numpy(w.extra["train"]).cuda()
@@ -968,6 +971,8 @@ def main():
                     choices=["c2", "c2-capture", "c1", "c3", "c3-capture", "c4", "c5", "top1", "top1-capture",
                              "top32", "top32-capture", "esel"])
     ap.add_argument("--esel-rows", type=int, default=10_000_000, help="rows of R for --workload esel")
+    ap.add_argument("--c5-rows", type=int, default=4_000_000,
+                    help="rows of --workload c5 (4,000,000: the configuration; fewer: a small case of the same shape)")
     ap.add_argument("--batch-jobs", type=int, default=512,
                     help="jobs of --workload c4 (512: the configuration; fewer: a small case of the same shape)")
     ap.add_argument("--peaks", action="store_true", help="print cuBLAS BF16 / TF32 / FP8 throughput and exit")

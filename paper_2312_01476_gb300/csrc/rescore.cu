@@ -1102,104 +1102,114 @@ __device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, flo
                           final_flush);
 }
 
-// A chunk sorted by S row (rescore_panel_kernel, clustered candidates): each warp takes 16 consecutive
-// candidates at a time; the S row, gathered from global memory once per run of equal S rows, stays in
-// registers, and the R rows are read from the staged panel.  Lane partials, their order and the reduction
-// tree are those of rescore_mlp_kernel (fmaf(R element, S element, acc) over v, then the butterfly pairs),
-// so the similarities are bit-identical to the R-major path.
+// A chunk whose S rows span few positions (rescore_panel_kernel, clustered rows in sketch order), given as
+// one mask per S position of the panel rows it pairs with (P <= 32).  Each warp takes two S positions at a
+// time and holds both S rows in registers; every panel row either of them pairs with is read from shared
+// memory once and serves both, so a dense block of candidates reads half an R row per candidate.  Lane
+// partials, their order and the reduction tree are those of rescore_mlp_kernel (fmaf(R element, S element,
+// acc) over v, then the butterfly pairs), so the similarities are bit-identical to the R-major path.
 template <int V, bool MIRROR>
-__device__ __forceinline__ void rescore_smajor_chunk(
-    const uint2 *cs, int len, long long row0, const float4 *panel, int d4, const float *__restrict__ S, int64_t ldS,
-    const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS, const float *__restrict__ invR,
-    const float *__restrict__ invS, float eps, float fp64_band, unsigned long long *band_count,
-    uint2 *__restrict__ band_list, uint64_t band_cap, ejoin_pair *stg, int &stg_n, unsigned long long *out_count,
-    ejoin_pair *__restrict__ out, uint64_t out_cap, int count_only, int lane, int warp)
+__device__ __forceinline__ void rescore_smajor_masked(
+    const unsigned *masks, int nbins, unsigned s_lo, long long row0, const float4 *panel, int d4,
+    const float *__restrict__ S, int64_t ldS, const uint32_t *__restrict__ idsR, const uint32_t *__restrict__ idsS,
+    const float *__restrict__ invR, const float *__restrict__ invS, float eps, float fp64_band,
+    unsigned long long *band_count, uint2 *__restrict__ band_list, uint64_t band_cap, ejoin_pair *stg, int &stg_n,
+    unsigned long long *out_count, ejoin_pair *__restrict__ out, uint64_t out_cap, int count_only, int lane, int warp)
 {
-    constexpr int C = V <= 2 ? 8 : 4;  // candidates reduced together
-    static_assert(RS_PER_WARP % C == 0, "candidates per warp step");
-    for (int gbase = warp * RS_PER_WARP; gbase < len; gbase += RS_PER_BLOCK) {
+    // candidate k of the current batch of up to 32 is kept by lane k (its dot product, panel row and S
+    // position); the batch is decided and emitted by all lanes at once
+    int nb = 0;  // warp-uniform
+    float my_dot = 0.f;
+    uint32_t my_r = 0, my_p = 0;
+    auto flush = [&]() {
         bool my_emit = false;
-        uint32_t my_i = 0, my_j = 0;
-        float my_sim = 0.f;
-        uint32_t gi = 0, gj = 0, lr = 0, sr = 0;
-        float sc = 0.f;
-        bool valid = false;
-        if (lane < RS_PER_WARP && gbase + lane < len) {
-            const uint2 c = cs[gbase + lane];
-            gi = idsR ? idsR[c.x] : c.x;
-            gj = idsS ? idsS[c.y] : c.y;
-            lr = (uint32_t)((long long)c.x - row0);
-            sr = c.y;
-            sc = invR[c.x] * invS[c.y];
-            valid = true;
-        }
-        const unsigned vmask = __ballot_sync(0xffffffffu, valid);
-        if (vmask) {  // warp-uniform
-            float4 b[V];
-            uint32_t cur = 0xffffffffu;  // S operand row held in b[]
-#pragma unroll
-            for (int v = 0; v < V; ++v) b[v] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 1
-            for (int q0 = 0; q0 < RS_PER_WARP; q0 += C) {
-                if (!((vmask >> q0) & 1u)) break;  // warp-uniform
-                float part[C];
-#pragma unroll
-                for (int c = 0; c < C; ++c) {
-                    const bool ok = (vmask >> (q0 + c)) & 1u;
-                    const uint32_t srow = __shfl_sync(0xffffffffu, sr, q0 + c);
-                    const uint32_t jj = __shfl_sync(0xffffffffu, gj, q0 + c);
-                    const uint32_t r = __shfl_sync(0xffffffffu, lr, q0 + c);
-                    if (ok && srow != cur) {  // warp-uniform; once per run of the sorted chunk
-                        cur = srow;
-                        const float4 *g = reinterpret_cast<const float4 *>(S + (int64_t)jj * ldS);
-#pragma unroll
-                        for (int v = 0; v < V; ++v) {
-                            const int x = lane + 32 * v;
-                            b[v] = x < d4 ? __ldg(g + x) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        }
-                    }
-                    float acc = 0.f;
-#pragma unroll
-                    for (int v = 0; v < V; ++v) {
-                        const int x = lane + 32 * v;
-                        const float4 a = ok && x < d4 ? panel[r * (uint32_t)d4 + x] : make_float4(0.f, 0.f, 0.f, 0.f);
-                        acc = fmaf(a.x, b[v].x, acc);
-                        acc = fmaf(a.y, b[v].y, acc);
-                        acc = fmaf(a.z, b[v].z, acc);
-                        acc = fmaf(a.w, b[v].w, acc);
-                    }
-                    part[c] = acc;
-                }
-                const float tot = transpose_sum<C>(part, lane);
-                const float mine = __shfl_sync(0xffffffffu, tot, ((lane - q0) & (C - 1)) * (32 / C));
-                if (lane >= q0 && lane < q0 + C && ((vmask >> lane) & 1u)) {
-                    float sim = mine * sc;
-                    sim = fminf(1.f, fmaxf(-1.f, sim));
-                    bool emit = sim >= eps;
-                    if (fabsf(sim - eps) < fp64_band) {
-                        // near eps: decided by the accurate tier
-                        const unsigned long long p = atomicAdd(band_count, 1ull);
-                        if (p < band_cap) band_list[p] = make_uint2(gi, gj);
-                        emit = false;
-                    }
-                    my_emit = emit;
-                    my_i = gi;
-                    my_j = gj;
-                    my_sim = sim;
-                }
+        uint32_t gi = 0, gj = 0;
+        float sim = 0.f;
+        if (lane < nb) {
+            const long long o = row0 + my_r;
+            const uint32_t sidx = s_lo + my_p;
+            gi = idsR ? idsR[o] : (uint32_t)o;
+            gj = idsS ? idsS[sidx] : sidx;
+            sim = fminf(1.f, fmaxf(-1.f, my_dot * (invR[o] * invS[sidx])));
+            my_emit = sim >= eps;
+            if (fabsf(sim - eps) < fp64_band) {
+                // near eps: decided by the accurate tier
+                const unsigned long long q = atomicAdd(band_count, 1ull);
+                if (q < band_cap) band_list[q] = make_uint2(gi, gj);
+                my_emit = false;
             }
         }
-        warp_emit<MIRROR>(my_emit, my_i, my_j, my_sim, stg, stg_n, out_count, out, out_cap, count_only, lane, false);
+        warp_emit<MIRROR>(my_emit, gi, gj, sim, stg, stg_n, out_count, out, out_cap, count_only, lane, false);
+        nb = 0;
+    };
+    auto keep = [&](float dot, uint32_t r, uint32_t p) {
+        if (lane == nb) {
+            my_dot = dot;
+            my_r = r;
+            my_p = p;
+        }
+        ++nb;
+    };
+    auto load_s = [&](float4 (&b)[V], uint32_t p) {
+        const uint32_t sidx = s_lo + p;
+        const uint32_t j = idsS ? idsS[sidx] : sidx;
+        const float4 *g = reinterpret_cast<const float4 *>(S + (int64_t)j * ldS);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const int x = lane + 32 * v;
+            b[v] = x < d4 ? __ldg(g + x) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto dot_with = [&](const float4 (&a)[V], const float4 (&b)[V]) {
+        float acc = 0.f;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            acc = fmaf(a[v].x, b[v].x, acc);
+            acc = fmaf(a[v].y, b[v].y, acc);
+            acc = fmaf(a[v].z, b[v].z, acc);
+            acc = fmaf(a[v].w, b[v].w, acc);
+        }
+        return acc;
+    };
+    for (int p0 = 2 * warp; p0 < nbins; p0 += 2 * RS_WARPS) {
+        const unsigned m0 = masks[p0];
+        const unsigned m1 = p0 + 1 < nbins ? masks[p0 + 1] : 0u;
+        if ((m0 | m1) == 0u) continue;  // warp-uniform
+        float4 b0[V], b1[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) b0[v] = b1[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m0) load_s(b0, (uint32_t)p0);
+        if (m1) load_s(b1, (uint32_t)p0 + 1u);
+        unsigned m = m0 | m1;
+        while (m) {  // warp-uniform
+            const int r = __ffs(m) - 1;
+            m &= m - 1u;
+            if (nb > 30) flush();
+            float4 a[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const int x = lane + 32 * v;
+                a[v] = x < d4 ? panel[(uint32_t)r * (uint32_t)d4 + x] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            const bool in0 = (m0 >> r) & 1u, in1 = (m1 >> r) & 1u;
+            if (in0 && in1) {
+                // both positions pair with row r: one transposed reduction of the two partials
+                float part[2] = {dot_with(a, b0), dot_with(a, b1)};
+                const float tot = transpose_sum<2>(part, lane);
+                const float t0 = __shfl_sync(0xffffffffu, tot, 0), t1 = __shfl_sync(0xffffffffu, tot, 16);
+                keep(t0, (uint32_t)r, (uint32_t)p0);
+                keep(t1, (uint32_t)r, (uint32_t)p0 + 1u);
+            } else {
+                float acc = in0 ? dot_with(a, b0) : dot_with(a, b1);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                keep(acc, (uint32_t)r, in0 ? (uint32_t)p0 : (uint32_t)p0 + 1u);
+            }
+        }
     }
+    if (nb > 0) flush();
 }
 
-// Re-score of bucket-sorted candidates (d % 4 == 0, 16-byte aligned rows, d <= 128 V).  Per chunk (at
-// most PANEL_CHUNK candidates of one bucket): the panel's R rows are staged in shared memory (cp.async)
-// while the chunk's candidates are counting-sorted by R row in shared memory.  Each warp then takes 16
-// consecutive candidates per block step: the S rows of C of them are gathered at once (fenced, as in
-// rescore_mlp_kernel), the R row is read from shared memory into registers only when it changes (the
-// chunk is sorted by row), and the C per-lane partial sums are reduced together (transpose_sum).
-// Per candidate the lane partials and their reduction tree are those of rescore_mlp_kernel.
 template <int V, int C, bool MIRROR, int CTAS>
 __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
     const uint2 *__restrict__ sorted, const unsigned long long *__restrict__ off,
@@ -1284,10 +1294,10 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
             }
             __syncthreads();
             s_lo = s_range[0];
-            smajor = s_range[1] - s_lo < (unsigned)SMAJ_BINS;
+            smajor = s_range[1] - s_lo < (unsigned)SMAJ_BINS && P <= 32;  // one 32-bit row mask per position
         }
-        // counting sort of the chunk; the R rows it uses are flagged and only those are staged (the copies
-        // are in flight during the scan and the scatter)
+        // counting sort of the chunk (S-major: one mask of panel rows per S position instead); the R rows it
+        // uses are flagged and only those are staged (the copies are in flight during the scan and the scatter)
         const int nbins = smajor ? (int)(s_range[1] - s_lo) + 1 : P;
         for (int r = threadIdx.x; r < nbins; r += blockDim.x) rcnt[r] = 0;
         for (int r = threadIdx.x; r < P; r += blockDim.x) rused[r] = 0;
@@ -1295,7 +1305,10 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
 #pragma unroll
         for (int t = 0; t < ITEMS; ++t) {
             if (threadIdx.x + t * (RS_WARPS * 32) < len) {
-                atomicAdd(&rcnt[smajor ? (int)(mine[t].y - s_lo) : (int)(mine[t].x - row0)], 1);
+                if (smajor)
+                    atomicOr(reinterpret_cast<unsigned *>(&rcnt[(int)(mine[t].y - s_lo)]), 1u << (mine[t].x - row0));
+                else
+                    atomicAdd(&rcnt[(int)(mine[t].x - row0)], 1);
                 rused[mine[t].x - row0] = 1;
             }
         }
@@ -1308,32 +1321,7 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
             for (int x = lane; x < d4; x += 32) cp_async16(panel + r * d4 + x, g + x);
         }
         if (V >= 6 && smajor) {
-            // exclusive scan of up to SMAJ_BINS counts, SMAJ_BINS / blockDim.x per thread
-            constexpr int PER = V >= 6 ? SMAJ_BINS / (RS_WARPS * 32) : 1;
-            int v[PER], sum = 0;
-#pragma unroll
-            for (int t = 0; t < PER; ++t) {
-                const int r = threadIdx.x * PER + t;
-                v[t] = r < nbins ? rcnt[r] : 0;
-                sum += v[t];
-            }
-            int incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            __shared__ int wsum[RS_WARPS];
-            if (lane == 31) wsum[warp] = incl;
-            __syncthreads();
-            int run = incl - sum;
-            for (int w = 0; w < warp; ++w) run += wsum[w];
-#pragma unroll
-            for (int t = 0; t < PER; ++t) {
-                const int r = threadIdx.x * PER + t;
-                if (r < nbins) rcnt[r] = run;
-                run += v[t];
-            }
+            // the masks are the chunk's whole description: no scan and no scatter
         } else if (warp == 0) {
             // exclusive scan of the P <= 128 counts, 4 per lane
             int v[PANEL_MAX_ROWS / 32], s = 0;
@@ -1358,17 +1346,19 @@ __global__ void __launch_bounds__(RS_WARPS * 32, CTAS) rescore_panel_kernel(
             }
         }
         __syncthreads();
+        if (!smajor) {
 #pragma unroll
-        for (int t = 0; t < ITEMS; ++t)
-            if (threadIdx.x + t * (RS_WARPS * 32) < len)
-                cs[atomicAdd(&rcnt[smajor ? (int)(mine[t].y - s_lo) : (int)(mine[t].x - row0)], 1)] = mine[t];
+            for (int t = 0; t < ITEMS; ++t)
+                if (threadIdx.x + t * (RS_WARPS * 32) < len) cs[atomicAdd(&rcnt[(int)(mine[t].x - row0)], 1)] = mine[t];
+        }
         cp_async_wait_all();
         __syncthreads();
         if constexpr (V >= 6) {
             if (smajor) {
-                rescore_smajor_chunk<V, MIRROR>(cs, len, row0, panel, d4, S, ldS, idsR, idsS, invR, invS, eps,
-                                                fp64_band, band_count, band_list, band_cap, stg, stg_n, out_count, out,
-                                                out_cap, count_only, lane, warp);
+                rescore_smajor_masked<V, MIRROR>(reinterpret_cast<const unsigned *>(rcnt), nbins, s_lo, row0, panel,
+                                                 d4, S, ldS, idsR, idsS, invR, invS, eps, fp64_band, band_count,
+                                                 band_list, band_cap, stg, stg_n, out_count, out, out_cap, count_only,
+                                                 lane, warp);
                 continue;
             }
         }
