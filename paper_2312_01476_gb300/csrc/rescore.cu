@@ -1122,7 +1122,7 @@ __device__ __forceinline__ void rescore_smajor_masked(
     float my_dot = 0.f;
     uint32_t my_r = 0, my_p = 0;
     auto flush = [&]() {
-        bool my_emit = false;
+        bool my_emit = false, near = false;
         uint32_t gi = 0, gj = 0;
         float sim = 0.f;
         if (lane < nb) {
@@ -1131,12 +1131,19 @@ __device__ __forceinline__ void rescore_smajor_masked(
             gi = idsR ? idsR[o] : (uint32_t)o;
             gj = idsS ? idsS[sidx] : sidx;
             sim = fminf(1.f, fmaxf(-1.f, my_dot * (invR[o] * invS[sidx])));
-            my_emit = sim >= eps;
-            if (fabsf(sim - eps) < fp64_band) {
-                // near eps: decided by the accurate tier
-                const unsigned long long q = atomicAdd(band_count, 1ull);
+            near = fabsf(sim - eps) < fp64_band;  // near eps: decided by the accurate tier
+            my_emit = sim >= eps && !near;
+        }
+        // the batch's entries of the band list claimed with one atomic
+        const unsigned nmask = __ballot_sync(0xffffffffu, near);
+        if (nmask) {  // warp-uniform
+            const int leader = __ffs(nmask) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(band_count, (unsigned long long)__popc(nmask));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (near) {
+                const unsigned long long q = base + (unsigned long long)__popc(nmask & ((1u << lane) - 1u));
                 if (q < band_cap) band_list[q] = make_uint2(gi, gj);
-                my_emit = false;
             }
         }
         warp_emit<MIRROR>(my_emit, gi, gj, sim, stg, stg_n, out_count, out, out_cap, count_only, lane, false);
