@@ -745,12 +745,14 @@ cudaError_t launch_rescore(const uint2 *cand, const unsigned long long *cand_cou
 // arithmetic, its order and the decision are those of rescore_mlp_kernel, so
 // the similarities are bit-identical; only the order of the records differs.
 // Buckets are cut into chunks of at most PANEL_CHUNK candidates so that one
-// dense bucket does not serialise on one CTA.
+// dense bucket does not serialise on one CTA, and CTAs take the chunks in
+// bucket order from a ticket counter, so the chunks in progress at any moment
+// are neighbours and their S rows stay in L2.
 namespace {
 constexpr int PANEL_CHUNK = 2048;
 constexpr int PANEL_MAX_ROWS = 128;
 constexpr int PANEL_CTAS = 3;    // CTAs per SM for rows of up to 512 values, 2 above
-constexpr int SMAJ_BINS = 1024;  // a chunk whose S rows span fewer positions is processed S row by S row
+constexpr int SMAJ_BINS = 1024;  // a chunk whose S rows span fewer positions is described by masks per S position
 // Shared memory for the staged R rows of a CTA: three CTAs per SM with the sorted chunk and the staging
 // area for rows of up to 512 values, two above.
 constexpr int panel_smem(int d) { return d > 512 ? 81920 : 40960; }
@@ -1105,9 +1107,11 @@ __device__ __forceinline__ void warp_emit(bool emit, uint32_t i, uint32_t j, flo
 // A chunk whose S rows span few positions (rescore_panel_kernel, clustered rows in sketch order), given as
 // one mask per S position of the panel rows it pairs with (P <= 32).  Each warp takes two S positions at a
 // time and holds both S rows in registers; every panel row either of them pairs with is read from shared
-// memory once and serves both, so a dense block of candidates reads half an R row per candidate.  Lane
-// partials, their order and the reduction tree are those of rescore_mlp_kernel (fmaf(R element, S element,
-// acc) over v, then the butterfly pairs), so the similarities are bit-identical to the R-major path.
+// memory once and serves both, so a dense block of candidates reads half an R row per candidate.  Each
+// result is kept by one lane until 32 are decided and emitted together (the band-list entries of the 32
+// claimed with one atomic).  Lane partials, their order and the reduction tree are those of
+// rescore_mlp_kernel (fmaf(R element, S element, acc) over v, then the butterfly pairs), so the similarities
+// are bit-identical to the R-major path.
 template <int V, bool MIRROR>
 __device__ __forceinline__ void rescore_smajor_masked(
     const unsigned *masks, int nbins, unsigned s_lo, long long row0, const float4 *panel, int d4,
